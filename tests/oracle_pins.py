@@ -1,0 +1,436 @@
+"""Pins of the oracle to things other than itself.
+
+Each pin takes a bound oracle library (the real one, or a copy with a planted
+mistake) and raises AssertionError when the oracle disagrees with what the
+paper or the mathematics fixes:
+
+  * published known-answer vectors of Philox4x32-10;
+  * closed forms of the fixed-point conventions (thresholds, quantisation);
+  * the exact law implied by every alias table (exact rationals);
+  * exact path laws on tiny graphs, enumerated by brute force from the
+    transition rules of Section 2.2 (first order, Node2Vec Eq. 1 over
+    (prev, cur) pairs, MetaPath's label filter), tested by chi-square;
+  * the PPR end-vertex law by a linear solve of the absorbing chain, and the
+    geometric length law (mean 5 vertices at stop 0.2, Section 6.2);
+  * the O-REJ expected number of trials d * p* / sum(p) (Section 2.3);
+  * special cases that must reduce exactly to NAIVE sampling.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+from collections import Counter
+from fractions import Fraction
+
+import numpy as np
+from scipy import stats as sst
+
+import oracle
+import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TWO32 = 1 << 32
+
+# --------------------------------------------------------------- tiny graphs
+
+# A directed graph with a dead end (5) and asymmetric adjacency, so that
+# IsNeighbor's direction matters.
+DIR_EDGES = [(0, 1), (0, 2), (0, 3), (1, 0), (1, 2), (1, 4), (2, 0), (2, 3), (2, 5),
+             (3, 1), (3, 4), (3, 5), (3, 6), (4, 0), (4, 3), (6, 0), (6, 2)]
+DIR_NV = 7
+# Distinct positive weights for the weighted walk, by edge.
+DIR_WEIGHTS = {e: float(w) for e, w in zip(DIR_EDGES, [1, 2, 7, 3, 1.5, 4, 2.25, 9, 1, 5, 1, 2, 3.5, 6, 1, 1, 8])}
+# Labels in {0,1,2} for MetaPath.
+DIR_LABELS = {e: l for e, l in zip(DIR_EDGES, [0, 1, 0, 1, 1, 0, 2, 0, 1, 0, 1, 1, 0, 1, 0, 0, 1])}
+
+N_LAW = 200_000
+
+
+def dir_graph():
+    g = synth.from_edges(DIR_NV, DIR_EDGES, symmetric=False)
+    w = np.array([DIR_WEIGHTS[(v, int(c))] for v in range(DIR_NV)
+                  for c in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]], dtype=np.float32)
+    lab = np.array([DIR_LABELS[(v, int(c))] for v in range(DIR_NV)
+                    for c in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]], dtype=np.uint8)
+    g.weights, g.labels = w, lab
+    return g
+
+
+def nbrs(g, v):
+    return [int(c) for c in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]]
+
+
+# ------------------------------------------------------------------ helpers
+
+def chi2_pvalue(counts: Counter, probs: dict, n: int) -> float:
+    """Chi-square goodness of fit; cells with expected count < 5 are pooled.
+    An outcome of probability zero that was observed gives p = 0."""
+    for k, c in counts.items():
+        if c > 0 and probs.get(k, 0.0) == 0.0:
+            return 0.0
+    obs, exp, pool_o, pool_e = [], [], 0.0, 0.0
+    for k, p in probs.items():
+        e = p * n
+        if e < 5:
+            pool_o += counts.get(k, 0)
+            pool_e += e
+        else:
+            obs.append(counts.get(k, 0))
+            exp.append(e)
+    if pool_e > 0:
+        obs.append(pool_o)
+        exp.append(pool_e)
+    obs = np.array(obs, dtype=np.float64)
+    exp = np.array(exp, dtype=np.float64)
+    exp *= obs.sum() / exp.sum()
+    if len(obs) < 2:
+        return 1.0
+    return float(sst.chisquare(obs, exp).pvalue)
+
+
+def path_counts(res) -> Counter:
+    c = Counter()
+    for row, ln in zip(res.paths, res.lengths):
+        c[tuple(int(x) for x in row[:ln])] += 1
+    return c
+
+
+def enumerate_paths(src: int, max_len: int, step_law) -> dict:
+    """Exact law over whole paths: step_law(path) -> {next: prob} ({} = stop)."""
+    out = {}
+
+    def rec(path, p):
+        if len(path) - 1 == max_len:
+            out[tuple(path)] = out.get(tuple(path), 0.0) + p
+            return
+        law = step_law(path)
+        if not law:
+            out[tuple(path)] = out.get(tuple(path), 0.0) + p
+            return
+        for nxt, q in law.items():
+            if q > 0:
+                rec(path + [nxt], p * q)
+
+    rec([src], 1.0)
+    return out
+
+
+# ------------------------------------------------------------------- pins
+
+def pin_philox_kat(lib=None):
+    path = os.path.join(HERE, "golden", "philox4x32_10_kat.txt")
+    n = 0
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        w = [int(x, 16) for x in line.split()]
+        got = oracle.philox4x32_10(w[0:4], w[4:6], lib=lib)
+        assert list(map(int, got)) == w[6:10], f"Philox KAT mismatch for {line}"
+        n += 1
+    assert n == 3
+
+
+def pin_fixed_point(lib=None):
+    # floor(t * 2^32) as an exact rational of the double t.
+    for t in [0.2, 0.5, 0.25, 1 / 3, 0.7, 1e-9, 0.999999999]:
+        want = (Fraction(t) * TWO32).numerator // (Fraction(t) * TWO32).denominator
+        assert oracle.threshold(t, lib=lib) == want, t
+    assert oracle.threshold(0.2, lib=lib) == 858993459
+    assert oracle.threshold(0.0, lib=lib) == 0
+    assert oracle.threshold(1.0, lib=lib) == TWO32
+    # round-half-even(w * 2^16): ties of exactly representable fp32 values
+    assert oracle.quantize_weight(1.0, lib=lib) == 65536
+    assert oracle.quantize_weight(1.5 / 65536, lib=lib) == 2
+    assert oracle.quantize_weight(2.5 / 65536, lib=lib) == 2
+    assert oracle.quantize_weight(3.5 / 65536, lib=lib) == 4
+    assert oracle.quantize_weight(0.75 / 65536, lib=lib) == 1
+    assert oracle.quantize_weight(0.25 / 65536, lib=lib) == 0
+    assert oracle.quantize_weight(99.99999, lib=lib) == round(float(np.float32(99.99999)) * 65536)
+    assert oracle.quantize_weight(1e30, lib=lib) == TWO32 - 1
+    assert oracle.quantize_weight(-1.0, lib=lib) == -1
+    assert oracle.quantize_weight(float("nan"), lib=lib) == -1
+    assert oracle.quantize_weight(float("inf"), lib=lib) == -1
+
+
+def _alias_rows():
+    rng = np.random.default_rng(7)
+    rows = [[5], [1, 1], [3, 3, 3, 3], [1, 2, 3, 4], [0, 7, 0, 1], [0, 0, 5], [2 ** 32 - 1, 1, 1],
+            [65536 * 99, 65536, 65536 * 50, 65537]]
+    rows += [list(rng.integers(65536, 6553600, size=d)) for d in (5, 17, 64, 300)]
+    rows += [list(rng.integers(0, 4, size=50))]
+    return rows
+
+
+def pin_alias_law(lib=None):
+    """The law implied by the tables is W_j / S within 2^-32 per bucket:
+    sum_j |P_j - W_j/S| <= 2 * 2^-32 (each bucket's floor moves < 2^-32 / d
+    of mass between its two elements)."""
+    for W in _alias_rows():
+        d = len(W)
+        H, A1, A2, dead = oracle.alias_build(W, lib=lib)
+        S = sum(int(x) for x in W)
+        assert dead == (1 if S == 0 else 0)
+        if S == 0:
+            continue
+        mass = [Fraction(0)] * d
+        for b in range(d):
+            h = int(H[b])
+            assert 0 <= h <= TWO32
+            assert int(A1[b]) == b, "first element of bucket b is b"
+            if h < TWO32:
+                assert 0 <= int(A2[b]) < d
+                mass[int(A2[b])] += Fraction(TWO32 - h, TWO32 * d)
+            mass[b] += Fraction(h, TWO32 * d)
+        err = sum(abs(mass[j] - Fraction(int(W[j]), S)) for j in range(d))
+        assert err <= Fraction(2, TWO32), (W, float(err))
+        for j in range(d):
+            if int(W[j]) == 0:
+                assert mass[j] == 0, "a zero-weight edge is never picked"
+
+
+def _dir_alias(g, lib):
+    return oracle.prepare_alias(g.row_ptr, g.weights, lib=lib)
+
+
+def pin_law_deepwalk(lib=None):
+    g = dir_graph()
+    res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK, [0], 3, seed=11, walks_per_source=N_LAW, lib=lib)
+    assert res.status == 0
+
+    def law(path):
+        nb = nbrs(g, path[-1])
+        return {c: 1.0 / len(nb) for c in nb}
+
+    p = chi2_pvalue(path_counts(res), enumerate_paths(0, 3, law), N_LAW)
+    assert p > 1e-3, p
+
+
+def pin_law_alias(lib=None):
+    g = dir_graph()
+    al = _dir_alias(g, lib)
+    res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, [0], 3, seed=12, walks_per_source=N_LAW,
+                      alias=al, lib=lib)
+    assert res.status == 0
+
+    def law(path):
+        v = path[-1]
+        nb = nbrs(g, v)
+        ws = [DIR_WEIGHTS[(v, c)] for c in nb]
+        return {c: w / sum(ws) for c, w in zip(nb, ws)}
+
+    p = chi2_pvalue(path_counts(res), enumerate_paths(0, 3, law), N_LAW)
+    assert p > 1e-3, p
+
+
+def node2vec_step_law(g, path, p_ret, q_io):
+    """Eq. 1 with O-REJ's fixed-point acceptance T_k = floor(w_k / p* * 2^32):
+    candidate c is taken with probability proportional to T_class(c)."""
+    v = path[-1]
+    nb = nbrs(g, v)
+    if not nb:
+        return {}
+    if len(path) == 1:
+        return {c: 1.0 / len(nb) for c in nb}
+    u = path[-2]
+    w_ret, w_nb, w_far = 1.0 / p_ret, 1.0, 1.0 / q_io
+    pstar = max(w_ret, w_nb, w_far)
+    T = {k: (Fraction(x / pstar) * TWO32).__floor__() for k, x in (("r", w_ret), ("n", w_nb), ("f", w_far))}
+    nu = set(nbrs(g, u))
+    t = {c: T["r"] if c == u else (T["n"] if c in nu else T["f"]) for c in nb}
+    tot = sum(t.values())
+    return {c: t[c] / tot for c in nb}
+
+
+def pin_law_node2vec(lib=None):
+    g = dir_graph()
+    for (pp, qq, seed) in [(0.5, 2.0, 13), (2.0, 0.5, 14), (0.3, 0.7, 15)]:
+        res = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, [0], 3, seed=seed, walks_per_source=N_LAW,
+                          n2v_p=pp, n2v_q=qq, lib=lib)
+        assert res.status == 0
+        law = enumerate_paths(0, 3, lambda path: node2vec_step_law(g, path, pp, qq))
+        p = chi2_pvalue(path_counts(res), law, N_LAW)
+        assert p > 1e-3, (pp, qq, p)
+
+
+def pin_law_metapath(lib=None):
+    g = dir_graph()
+    schema = [0, 1, 1]
+    res = oracle.walk(g.row_ptr, g.col, oracle.METAPATH, [0, 3], 4, seed=16, walks_per_source=N_LAW // 2,
+                      labels=g.labels, schema=schema, lib=lib)
+    assert res.status == 0
+
+    def law(path):
+        v = path[-1]
+        s = len(path) - 1
+        h = schema[s % len(schema)]
+        ok = [c for c in nbrs(g, v) if DIR_LABELS[(v, c)] == h]
+        return {c: 1.0 / len(ok) for c in ok}
+
+    for src, lo in ((0, 0), (3, N_LAW // 2)):
+        sub = type(res)(res.paths[lo:lo + N_LAW // 2], res.lengths[lo:lo + N_LAW // 2], {}, 0)
+        p = chi2_pvalue(path_counts(sub), enumerate_paths(src, 4, law), N_LAW // 2)
+        assert p > 1e-3, (src, p)
+
+
+def ppr_end_law(g, src, alpha):
+    """End-vertex law of a walk that stops with probability alpha before each
+    move and at dead ends: pi = e_s (I - M)^-1 diag(sigma), M = diag(1-sigma) P."""
+    nv = g.nv
+    P = np.zeros((nv, nv))
+    sigma = np.ones(nv)
+    for v in range(nv):
+        nb = nbrs(g, v)
+        if nb:
+            sigma[v] = alpha
+            for c in nb:
+                P[v, c] = 1.0 / len(nb)
+    M = np.diag(1 - sigma) @ P
+    e = np.zeros(nv)
+    e[src] = 1.0
+    pi = np.linalg.solve((np.eye(nv) - M).T, e) * sigma
+    return {v: float(pi[v]) for v in range(nv)}
+
+
+def pin_ppr(lib=None):
+    g = dir_graph()
+    n = N_LAW
+    res = oracle.walk(g.row_ptr, g.col, oracle.PPR, [1], 1000, seed=17, walks_per_source=n, ppr_stop=0.2,
+                      endpoints_only=True, lib=lib)
+    assert res.status == 0
+    p = chi2_pvalue(Counter(int(x) for x in res.paths), ppr_end_law(g, 1, 0.2), n)
+    assert p > 1e-3, p
+    # Geometric lengths on a graph without dead ends: P(moves = k) = 0.8^k * 0.2,
+    # so E|Q| = 5 vertices (Section 6.2).
+    k4 = synth.from_edges(4, [(a, b) for a in range(4) for b in range(4) if a != b])
+    res = oracle.walk(k4.row_ptr, k4.col, oracle.PPR, [0], 1000, seed=18, walks_per_source=n, ppr_stop=0.2,
+                      lib=lib)
+    assert res.status == 0
+    moves = res.lengths.astype(np.int64) - 1
+    law = {k: 0.8 ** k * 0.2 for k in range(200)}
+    p = chi2_pvalue(Counter(int(m) for m in moves), law, n)
+    assert p > 1e-3, p
+    mean_q = res.lengths.mean()
+    assert abs(mean_q - 5.0) < 6 * np.sqrt(20.0 / n), mean_q  # var of moves = 0.8/0.04 = 20
+
+
+def pin_rejection_trials(lib=None):
+    """Mean O-REJ trials per step equal d * 2^32 / sum_c T_class(c): the
+    fixed-point form of E = d * p* / sum(p) (Section 2.3)."""
+    g = dir_graph()
+    pp, qq = 0.5, 2.0
+    n = N_LAW
+    res = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, [0], 2, seed=19, walks_per_source=n, n2v_p=pp,
+                      n2v_q=qq, lib=lib)
+    assert res.status == 0
+    n0 = nbrs(g, 0)
+    mean = 1.0
+    second = 0.0
+    for v1 in n0:
+        law = node2vec_step_law(g, [0, v1], pp, qq)
+        if not law:
+            continue
+        d = len(nbrs(g, v1))
+        w_ret, w_nb, w_far = 1.0 / pp, 1.0, 1.0 / qq
+        pstar = max(w_ret, w_nb, w_far)
+        T = {"r": (Fraction(w_ret / pstar) * TWO32).__floor__(), "n": (Fraction(w_nb / pstar) * TWO32).__floor__(),
+             "f": (Fraction(w_far / pstar) * TWO32).__floor__()}
+        nu = set(nbrs(g, 0))
+        acc = sum((T["r"] if c == 0 else (T["n"] if c in nu else T["f"])) for c in nbrs(g, v1)) / (d * TWO32)
+        e = 1.0 / acc
+        var = (1 - acc) / acc ** 2
+        mean += e / len(n0)
+        second += (var + e * e) / len(n0)
+    var_tot = second - (mean - 1.0) ** 2
+    got = res.stats["attempts"] / n
+    assert abs(got - mean) < 6 * np.sqrt(var_tot / n), (got, mean)
+
+
+def small_rmat():
+    g = synth.rmat(10, seed=5)
+    g.weights = synth.edge_weights(g, seed=5)
+    g.labels = synth.edge_labels(g, seed=5, nlabels=5)
+    return g
+
+
+def pin_reductions(lib=None):
+    """Cases that must be bit-identical to NAIVE DeepWalk (same draw, same index)."""
+    g = small_rmat()
+    src = synth.vertex_sources(g.nv)
+    L = 20
+    base = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK, src, L, seed=3, lib=lib)
+    assert base.status == 0
+
+    def same(res, what):
+        assert res.status == 0, what
+        assert np.array_equal(res.lengths, base.lengths), what
+        for i in range(g.nv):
+            ln = base.lengths[i]
+            assert np.array_equal(res.paths[i, :ln], base.paths[i, :ln]), (what, i)
+
+    eq = oracle.prepare_alias(g.row_ptr, np.full(g.ne, 3.0, dtype=np.float32), lib=lib)
+    same(oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, L, seed=3, alias=eq, lib=lib),
+         "alias with equal weights")
+    same(oracle.walk(g.row_ptr, g.col, oracle.METAPATH, src, L, seed=3, labels=np.zeros(g.ne, np.uint8),
+                     schema=[0], lib=lib), "metapath on one label")
+    same(oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src, L, seed=3, n2v_p=1.0, n2v_q=1.0, lib=lib),
+         "node2vec p=q=1")
+    same(oracle.walk(g.row_ptr, g.col, oracle.PPR, src, L, seed=3, ppr_stop=0.0, lib=lib), "ppr stop 0")
+
+
+def pin_invariants(lib=None):
+    """Every hop is an edge, lengths are bounded, MetaPath hops carry the
+    schema's label, and walks end early only where the rules say so."""
+    g = small_rmat()
+    al = oracle.prepare_alias(g.row_ptr, g.weights, lib=lib)
+    src = synth.vertex_sources(g.nv)
+    schema = np.array([1, 3, 0, 4, 2], dtype=np.uint8)
+    L = 30
+    adj = [set(nbrs(g, v)) for v in range(g.nv)]
+    lab = {}
+    for v in range(g.nv):
+        for j in range(int(g.row_ptr[v]), int(g.row_ptr[v + 1])):
+            lab[(v, int(g.col[j]))] = int(g.labels[j])
+    for algo, kw in [(oracle.DEEPWALK, {}), (oracle.DEEPWALK_WEIGHTED, {"alias": al}),
+                     (oracle.PPR, {"ppr_stop": 0.2}), (oracle.NODE2VEC, {"n2v_p": 0.5, "n2v_q": 2.0}),
+                     (oracle.METAPATH, {"labels": g.labels, "schema": schema})]:
+        res = oracle.walk(g.row_ptr, g.col, algo, src, L, seed=21, lib=lib, **kw)
+        assert res.status == 0
+        assert res.stats["moves"] == int((res.lengths - 1).sum())
+        for i in range(g.nv):
+            ln = int(res.lengths[i])
+            assert 1 <= ln <= L + 1
+            path = res.paths[i, :ln]
+            assert path[0] == src[i]
+            for s in range(ln - 1):
+                a, b = int(path[s]), int(path[s + 1])
+                assert b in adj[a], (algo, i, s)
+                if algo == oracle.METAPATH:
+                    assert lab[(a, b)] == schema[s % len(schema)]
+            if ln < L + 1 and algo in (oracle.DEEPWALK, oracle.DEEPWALK_WEIGHTED, oracle.NODE2VEC):
+                assert not adj[int(path[-1])], "early stop only at a dead end"
+            if ln < L + 1 and algo == oracle.METAPATH:
+                v = int(path[-1])
+                h = schema[(ln - 1) % len(schema)]
+                assert all(lab[(v, c)] != h for c in adj[v]), "early stop only without a matching label"
+
+
+def pin_sharding(lib=None):
+    """A walk depends only on (seed, walk index): splitting the batch with
+    walk_offset reproduces the whole batch."""
+    g = small_rmat()
+    src = synth.vertex_sources(g.nv)
+    full = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src, 12, seed=9, n2v_p=0.5, n2v_q=2.0, lib=lib)
+    a = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src[:300], 12, seed=9, n2v_p=0.5, n2v_q=2.0, lib=lib)
+    b = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src[300:], 12, seed=9, n2v_p=0.5, n2v_q=2.0,
+                    walk_offset=300, lib=lib)
+    assert np.array_equal(np.concatenate([a.lengths, b.lengths]), full.lengths)
+    for i in range(g.nv):
+        part = a if i < 300 else b
+        j = i if i < 300 else i - 300
+        ln = full.lengths[i]
+        assert np.array_equal(part.paths[j, :ln], full.paths[i, :ln])
+
+
+ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
+            pin_law_metapath, pin_ppr, pin_rejection_trials, pin_reductions, pin_invariants, pin_sharding]
