@@ -1,0 +1,411 @@
+"""Benchmark of the GB300 random-walk engine.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2] [--impl ours|reference]
+
+A step is one trw_walk over the whole batch of the chosen workload (walker
+init, Gather, Move, Update, refill and path staging for every walk), with the
+graph and tables resident in HBM.  The default workload is weighted DeepWalk
+with alias tables on R-MAT scale 22 (4,194,304 walks x 80 moves).  Prints one
+JSON line.  Under torchrun every rank runs its own shard of walk indices
+(walk_offset) on a replicated graph; no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "c1": dict(name="deepwalk-rmat-s14", scale=14, algo="deepwalk", max_len=80, sources="vertices", seed=1),
+    "c2": dict(name="deepwalk-weighted-alias-rmat-s22", scale=22, algo="deepwalk_weighted", max_len=80,
+               sources="vertices", seed=1),
+    "c3": dict(name="node2vec-p0.5-q2-rmat-s24", scale=24, algo="node2vec", max_len=80, sources="vertices", seed=1,
+               n2v_p=0.5, n2v_q=2.0),
+}
+METRIC = "walk steps/sec"
+UNIT = "steps/s"
+
+# Algorithmic bytes per move and per walk of each kernel, at 32-byte sector
+# granularity (the random-access roofline): a move reads the row-offset pair
+# (1.125 sectors on average: an 8-byte pair straddles a sector boundary one
+# time in eight) and the sampled record, and writes one 4-byte path entry.
+SECTOR = 32
+ROW_PAIR = 1.125 * SECTOR
+BYTES_PER_MOVE = {
+    "deepwalk": ROW_PAIR + SECTOR + 4,           # col[off + x]
+    "ppr": ROW_PAIR + SECTOR + 4,
+    "deepwalk_weighted": ROW_PAIR + SECTOR + 4,  # 16-byte alias record {H, first, second}
+}
+BYTES_PER_WALK = 12  # source read, length write, path[0] write
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_graph(wl):
+    t = time.time()
+    g = synth.rmat(wl["scale"], symmetric=wl.get("symmetric", True))
+    if wl["algo"] == "deepwalk_weighted":
+        g.weights = synth.edge_weights(g)
+    if wl["algo"] == "metapath":
+        g.labels = synth.edge_labels(g)
+    log(f"graph {g.name}: nv={g.nv} ne={g.ne} built in {time.time() - t:.1f}s")
+    return g
+
+
+def walk_kwargs(wl):
+    kw = {}
+    for k in ("n2v_p", "n2v_q", "ppr_stop"):
+        if k in wl:
+            kw[k] = wl[k]
+    return kw
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception as e:  # no nvidia-smi: report without clocks
+            log(f"clock sampling unavailable: {e}")
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("walk_kernels.cu", "walk_step.cuh", "trw_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_11983_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or
+    None when absent or captured from a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------ CPU baseline
+
+def cpu_baseline(g, wl, seconds: float = 12.0):
+    """The oracle, as it stands, on a bounded sample of the workload's walks."""
+    import oracle
+
+    algo = {"deepwalk": oracle.DEEPWALK, "deepwalk_weighted": oracle.DEEPWALK_WEIGHTED, "ppr": oracle.PPR,
+            "node2vec": oracle.NODE2VEC, "metapath": oracle.METAPATH}[wl["algo"]]
+    alias = None
+    t = time.time()
+    if algo == oracle.DEEPWALK_WEIGHTED:
+        alias = oracle.prepare_alias(g.row_ptr, g.weights)
+    prep = time.time() - t
+    src = synth.vertex_sources(g.nv)
+    n = 2000
+    done_moves, done_s, walks = 0, 0.0, 0
+    pos = 0
+    while done_s < seconds and pos < src.shape[0]:
+        m = min(n, src.shape[0] - pos)
+        t = time.perf_counter()
+        res = oracle.walk(g.row_ptr, g.col, algo, src[pos:pos + m], wl["max_len"], wl["seed"], alias=alias,
+                          labels=g.labels, walk_offset=pos, **walk_kwargs(wl))
+        dt = time.perf_counter() - t
+        assert res.status == 0
+        done_moves += res.stats["moves"]
+        done_s += dt
+        walks += m
+        pos += m
+        n = min(n * 2, 200000)
+    return {"value": done_moves / done_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {walks} of {src.shape[0]} walks ({done_moves} moves) of the workload, "
+                      f"single-threaded oracle, {done_s:.1f}s walking after {prep:.1f}s of alias preparation"}
+
+
+def run_reference(args, wl):
+    """Reference arm: the oracle on the host cores, a bounded sample per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    g = build_graph(wl)
+    algo = {"deepwalk": oracle.DEEPWALK, "deepwalk_weighted": oracle.DEEPWALK_WEIGHTED,
+            "node2vec": oracle.NODE2VEC}[wl["algo"]]
+    alias = oracle.prepare_alias(g.row_ptr, g.weights) if algo == oracle.DEEPWALK_WEIGHTED else None
+    src = synth.vertex_sources(g.nv)
+    per_step = 20000
+    times, moves = [], []
+    for i in range(args.warmup + args.steps):
+        lo = (i * per_step) % max(1, src.shape[0] - per_step)
+        t = time.perf_counter()
+        res = oracle.walk(g.row_ptr, g.col, algo, src[lo:lo + per_step], wl["max_len"], wl["seed"], alias=alias,
+                          walk_offset=lo, **walk_kwargs(wl))
+        dt = time.perf_counter() - t
+        assert res.status == 0
+        if i >= args.warmup:
+            times.append(dt)
+            moves.append(res.stats["moves"])
+    value = sum(moves) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": wl["name"], "walks_per_step": per_step, "max_len": wl["max_len"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} walks per step of the workload, single-threaded oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2107_11983_gb300 as trw
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = build_graph(wl)
+    t = time.time()
+    G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
+    load_s = time.time() - t
+    algo = trw.ALGOS[wl["algo"]]
+    prep_ms = None
+    if algo == trw.DEEPWALK_WEIGHTED:
+        torch.cuda.synchronize()
+        t = time.time()
+        G.prepare()
+        prep_ms = 1000 * (time.time() - t)
+    kw = walk_kwargs(wl)
+    L = wl["max_len"]
+    src_host = synth.vertex_sources(g.nv)
+    n = src_host.shape[0]
+    walk_offset = rank * n  # each rank its own walks (weak scaling)
+    src = torch.from_numpy(src_host).to(dev)
+    out_paths = torch.empty((n, L + 1), dtype=torch.int32, device=dev)
+    out_len = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def one(kernel):
+        G.walk(algo, src, L, wl["seed"], kernel=kernel, out_paths=out_paths, out_lengths=out_len, stream=sp,
+               sync=False, walk_offset=walk_offset, **kw)
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush.zero_()
+        one(trw.KERNEL_AUTO)
+    G.sync(sp)
+    moves = int((out_len.to(torch.int64) - 1).sum().item())
+
+    # timed region: K steps, L2 flushed between steps outside the events
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        one(trw.KERNEL_AUTO)
+        evs[i][1].record(stream)
+        G.sync(sp)  # collects the device status and the library's kernel-only event time
+        kern_ms.append(G.last_stats()["kernel_ms"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_s = sum(step_ms) / 1000.0
+    if ws > 1:
+        tt = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dev_s = float(tt.item())
+    total_moves = moves * args.steps * ws
+    value = total_moves / dev_s
+
+    # plain one-launch baseline on the same batch (same outputs)
+    plain_ms = []
+    for i in range(max(3, min(args.steps, 5))):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one(trw.KERNEL_PLAIN)
+        b.record(stream)
+        G.sync(sp)
+        plain_ms.append(a.elapsed_time(b))
+    plain_value = moves / (statistics.median(plain_ms) / 1000.0)
+
+    # end to end through the public API: pinned host sources in, pinned host paths out
+    h_src = torch.from_numpy(src_host).pin_memory()
+    h_paths = torch.empty((n, L + 1), dtype=torch.int32).pin_memory()
+    h_len = torch.empty(n, dtype=torch.int32).pin_memory()
+    G.walk(algo, h_src.numpy(), L, wl["seed"], out_paths=h_paths.numpy(), out_lengths=h_len.numpy(),
+           walk_offset=walk_offset, **kw)
+    e2e_t = []
+    for i in range(max(3, min(args.steps, 5))):
+        t = time.perf_counter()
+        G.walk(algo, h_src.numpy(), L, wl["seed"], out_paths=h_paths.numpy(), out_lengths=h_len.numpy(),
+               walk_offset=walk_offset, **kw)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_s = statistics.median(e2e_t)
+    if ws > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = moves * ws / e2e_s
+    assert int((h_len.to(torch.int64) - 1).sum().item()) == moves
+
+    # roofline of the walk kernel
+    peak, peak_kind = measured_peak_hbm()
+    bpm = BYTES_PER_MOVE.get(wl["algo"])
+    kms = statistics.mean(kern_ms)
+    roof = None
+    if bpm is not None:
+        alg_bytes = moves * bpm + n * BYTES_PER_WALK
+        achieved = alg_bytes / (kms / 1000.0) / 1e9
+        key = f"walk_persistent/{wl['name']}"
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(key),
+                "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "walk_persistent",
+                "bytes_per_move": bpm, "algorithmic_bytes_per_launch": int(alg_bytes)}
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline(g, wl) if ws == 1 and not args.no_cpu_baseline else None
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1000 * dev_s / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": wl["name"], "graph": g.name, "nv": g.nv, "ne": g.ne, "walks": n * ws,
+                   "walks_per_gpu": n, "max_len": L, "moves_per_gpu_step": moves,
+                   "parallelism": f"walk shards x{ws}, graph replicated",
+                   "l2": "256 MiB buffer written between timed steps (outside the events)",
+                   "tuning": G.tuning()},
+        "kernel_ms_per_step": round(kms, 4),
+        "wall_s": round(wall, 3),
+        "plain_launch": {"value": round(plain_value, 1), "unit": UNIT, "ms": round(statistics.median(plain_ms), 4),
+                         "speedup_persistent": round(value / ws / plain_value, 3)},
+        "preprocess": {"graph_load_s": round(load_s, 3), "alias_prepare_ms": None if prep_ms is None else round(prep_ms, 2)},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(n * 4),
+                "d2h_bytes_per_step": int(n * (L + 1) * 4 + n * 4), "ms": round(1000 * e2e_s, 3)},
+        "gpu_launches": 2 * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warm-up raised to 3 steps")
+        args.warmup = 3
+    wl = WORKLOADS[args.config]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,287 @@
+/*
+ * trw.h -- C ABI of the GB300 random-walk engine (libtrw.so).
+ *
+ * The engine runs massive numbers of independent random-walk queries under
+ * ThunderRW's step-centric Gather-Move-Update model (Section 4.2,
+ * Algorithm 2): Gather reads (static walks) or builds (dynamic walks) the
+ * transition weights of the current vertex's edges, Move samples the next
+ * edge, Update appends the vertex and decides termination.  Every step runs
+ * in CUDA kernels for sm_103a; the host side only validates, copies and
+ * launches.
+ *
+ * Conventions common to every call:
+ *  - Every call returns a trw_status; no C++ exception crosses this ABI.
+ *    On a non-OK status, trw_last_error() returns a thread-local message.
+ *  - The caller owns every input.  trw_graph_load copies the graph to the
+ *    device, so the caller may free its arrays afterwards.  The library owns
+ *    the device copies and the prepared tables until trw_graph_free.
+ *  - Buffers marked "host or device" may be either; the library detects the
+ *    kind with cudaPointerGetAttributes and copies host data through its own
+ *    device staging buffers.
+ *  - Randomness: walk i of a call draws every random number from
+ *    Philox4x32-10 keyed on the 64-bit seed, with counter
+ *    (walk_offset + i, step, draw, 0).  A walk therefore depends only on
+ *    (graph, algorithm, parameters, seed, walk index): results do not depend
+ *    on batching, kernel choice, launch shape or scheduling.
+ *  - Fixed point replaces real-valued draws: a uniform integer in [0, n) is
+ *    the high 64 bits of r64 * n (r64 = the block's first two words); a
+ *    probability t is the threshold floor(t * 2^32) against a 32-bit word.
+ *  - Graph sizes: nv < 2^31 and ne < 2^31 (int32 device offsets); walk
+ *    indices walk_offset + i < 2^32.
+ */
+#ifndef TRW_H
+#define TRW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct trw_graph trw_graph;
+typedef struct trw_server trw_server;
+
+typedef enum {
+  TRW_OK = 0,
+  TRW_PENDING = 1,              /* serve: request still running */
+  TRW_ERR_INVALID = -1,         /* bad argument; nothing was written */
+  TRW_ERR_OOM = -2,             /* device or host allocation failed */
+  TRW_ERR_NOT_PREPARED = -3,    /* weighted walk before trw_prepare(TRW_PREP_ALIAS) */
+  TRW_ERR_CUDA = -4,            /* a CUDA runtime call failed */
+  TRW_ERR_TIMEOUT = -5,         /* a bounded wait ran out */
+  TRW_ERR_REJECT_CAP = -6,      /* a rejection step exceeded TRW_REJECT_CAP trials */
+  TRW_ERR_BUSY = -7,            /* serve: no capacity to admit the request now */
+  TRW_ERR_NOT_FOUND = -8,       /* serve: unknown request id */
+  TRW_ERR_INTERNAL = -9         /* a device-side consistency check failed */
+} trw_status;
+
+/* Walk algorithms of Section 2.2 and the sampler each uses (Section 4.3's
+ * recommendation: unbiased -> NAIVE, static -> ALIAS, dynamic -> O-REJ when
+ * a bound on the weights is known, else ITS). */
+typedef enum {
+  TRW_DEEPWALK = 0,             /* unbiased, NAIVE sampling */
+  TRW_DEEPWALK_WEIGHTED = 1,    /* static biased by w_e, ALIAS sampling */
+  TRW_PPR = 2,                  /* unbiased with a stop coin per step, NAIVE */
+  TRW_NODE2VEC = 3,             /* dynamic second order (Eq. 1), O-REJ */
+  TRW_METAPATH = 4              /* dynamic label filter, ITS */
+} trw_algo;
+
+/* Kernel choice for trw_walk_ex. */
+typedef enum {
+  TRW_KERNEL_AUTO = 0,          /* the persistent kernel */
+  TRW_KERNEL_PLAIN = 1,         /* baseline: one launch, one thread per walk, no refill */
+  TRW_KERNEL_PERSISTENT = 2     /* persistent kernel, device work queue, refill, staging */
+} trw_kernel;
+
+#define TRW_OUT_PATHS 0u        /* out_paths[i * (max_len + 1) + k] = Q[k] */
+#define TRW_OUT_ENDPOINTS 1u    /* out_paths[i] = the last vertex of walk i */
+
+#define TRW_MAX_SCHEMA 16       /* longest MetaPath schema */
+#define TRW_REJECT_CAP 65536    /* rejection trials per step before TRW_ERR_REJECT_CAP */
+
+/* Per-call walk parameters. */
+typedef struct {
+  double ppr_stop;              /* PPR: termination probability, flipped before every move, in [0, 1] */
+  double n2v_p;                 /* Node2Vec return parameter (the paper's a): weight 1/p on the edge back to prev, > 0 */
+  double n2v_q;                 /* Node2Vec in-out parameter (the paper's b): weight 1/q at distance 2, > 0 */
+  const uint8_t* schema;        /* MetaPath schema H (host memory), step s uses H[s mod schema_len] */
+  int32_t schema_len;           /* 1 .. TRW_MAX_SCHEMA for MetaPath, ignored otherwise */
+  uint32_t out_mode;            /* TRW_OUT_PATHS or TRW_OUT_ENDPOINTS */
+  int32_t walks_per_source;     /* >= 1; walk i starts at sources[i / walks_per_source] */
+  int32_t reserved;
+  int64_t walk_offset;          /* index of walk 0 in the Philox counter (for sharding a batch) */
+} trw_params;
+
+/* Fills *p with defaults: ppr_stop 0.2, p = q = 1, no schema, paths,
+ * one walk per source, offset 0. */
+void trw_params_default(trw_params* p);
+
+#define TRW_LOAD_CHECK 1u        /* validate col ids and strictly increasing rows on the device */
+
+/*
+ * Load a CSR graph (Appendix B "graph storage": vertex array, edge array,
+ * per-edge weight and label arrays; Section 2.1: an undirected edge is two
+ * directed edges).
+ *   nv, ne      vertex and edge counts, 0 <= nv, ne < 2^31.
+ *   row_ptr     host, int64[nv + 1], row_ptr[0] = 0, non-decreasing, row_ptr[nv] = ne.
+ *   col         host, int32[ne], destination of each edge, in [0, nv).
+ *               Node2Vec's IsNeighbor needs every row sorted ascending without
+ *               duplicates (checked under TRW_LOAD_CHECK, else assumed).
+ *   weights     host, fp32[ne] edge weights (finite, >= 0) or NULL.
+ *   labels      host, uint8[ne] edge labels or NULL.
+ *   flags       TRW_LOAD_CHECK or 0.
+ *   out         receives the handle.
+ * Errors: TRW_ERR_INVALID (sizes, offsets, ids, weights), TRW_ERR_OOM, TRW_ERR_CUDA.
+ */
+trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_ptr, const int32_t* col,
+                          const float* weights, const uint8_t* labels, uint32_t flags, trw_graph** out);
+
+/* Release every device buffer of the graph.  NULL is ignored. */
+void trw_graph_free(trw_graph* g);
+
+#define TRW_PREP_ALIAS 1u        /* build the ALIAS tables for TRW_DEEPWALK_WEIGHTED */
+
+/*
+ * Preprocessing for static walks (Algorithm 3): for every vertex v, apply the
+ * weight function to E_v and run the initialisation phase of ALIAS
+ * (Section 2.3), storing C_v on the device.  Weights are quantised to
+ * integers round-half-even(w * 2^16); the tables come from Vose's method on
+ * those integers with first-in first-out work lists, so every table entry is
+ * exact up to one floor of H.  A vertex whose edges all quantise to zero
+ * becomes a dead end for weighted walks.  Runs on the device; synchronous.
+ * Errors: TRW_ERR_INVALID (no weights loaded), TRW_ERR_OOM, TRW_ERR_CUDA.
+ */
+trw_status trw_prepare(trw_graph* g, uint32_t what);
+
+/*
+ * Run n_sources * walks_per_source walks to completion (Algorithm 2 for every
+ * query; one persistent kernel with a device work queue).
+ *   algo, params   algorithm and its parameters (params may be NULL for defaults).
+ *   sources        host or device, int32[n_sources], each in [0, nv).
+ *   max_len        moves per walk, >= 0: a path holds at most max_len + 1 vertices.
+ *   seed           Philox key.
+ *   out_paths      host or device, int32[nwalks * (max_len + 1)] (TRW_OUT_PATHS)
+ *                  or int32[nwalks] (TRW_OUT_ENDPOINTS).  Entries past a walk's
+ *                  length are left unspecified.
+ *   out_lengths    host or device, int32[nwalks]: vertices in walk i (>= 1).
+ * A walk stops after max_len moves, on PPR's stop coin (flipped before each
+ * move), at a vertex without out-edges, or when no edge carries the MetaPath
+ * label of the step.  Synchronous on the graph's stream.
+ * Errors: TRW_ERR_INVALID (a source out of range, max_len < 0, a missing
+ * weight/label array, p or q <= 0, ppr_stop outside [0, 1], bad schema),
+ * TRW_ERR_NOT_PREPARED, TRW_ERR_REJECT_CAP, TRW_ERR_OOM, TRW_ERR_CUDA.
+ */
+trw_status trw_walk(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
+                    int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
+                    int32_t* out_lengths);
+
+/*
+ * trw_walk with an explicit kernel and stream.
+ *   kernel   TRW_KERNEL_AUTO, TRW_KERNEL_PLAIN or TRW_KERNEL_PERSISTENT.
+ *   stream   a cudaStream_t, or NULL for the graph's own stream.
+ *   sync     1: wait and return the device status (as trw_walk);
+ *            0: device buffers only, return after the launch; collect the
+ *               device status later with trw_sync.
+ * Errors as trw_walk; with sync = 0, TRW_ERR_INVALID for host buffers.
+ */
+trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
+                       int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
+                       int32_t* out_lengths, trw_kernel kernel, void* stream, int sync);
+
+/* Wait for the stream (NULL: the graph's) and return, then clear, the status
+ * that kernels launched with sync = 0 left on the device. */
+trw_status trw_sync(trw_graph* g, void* stream);
+
+/*
+ * A mixed batch in ONE persistent launch (the paper's Algorithm 4 admits a new
+ * query whenever one completes; here the device work queue does it across
+ * requests of different algorithms and lengths).  Request r is described by
+ * algos[r], params[r], sources[r] (n_sources[r] entries), max_lens[r],
+ * seeds[r], out_paths[r], out_lengths[r], with the meaning of trw_walk.
+ * Pointers are device pointers.  n_requests in 1 .. TRW_MAX_BATCH.
+ * Synchronous when sync = 1 (see trw_walk_ex).
+ */
+#define TRW_MAX_BATCH 64
+trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw_algo* algos, const trw_params* params,
+                          const int32_t* const* sources, const int64_t* n_sources, const int32_t* max_lens,
+                          const uint64_t* seeds, int32_t* const* out_paths, int32_t* const* out_lengths,
+                          void* stream, int sync);
+
+/* Launch shape and tuning knobs of the persistent kernel (the GPU analogue of
+ * the ring sizes k and k' of Section 5.4). */
+typedef struct {
+  int32_t block_threads;        /* threads per block, multiple of 32, 64..1024 */
+  int32_t blocks_per_sm;        /* resident blocks per SM requested (0: occupancy maximum) */
+  int32_t chunk;                /* walks claimed from the work queue per warp claim, >= 1 */
+  int32_t coop_degree;          /* rows at least this long use warp-cooperative scans/searches */
+} trw_tuning;
+
+/* Read or set the tuning of the graph's persistent kernel.  Setting checks ranges
+ * (TRW_ERR_INVALID).  Results never depend on tuning. */
+trw_status trw_get_tuning(const trw_graph* g, trw_tuning* t);
+trw_status trw_set_tuning(trw_graph* g, const trw_tuning* t);
+
+/*
+ * Autotune (the analogue of Section 5.4's ring-size tuning): time short
+ * pre-walks of the given algorithm from sampled sources over a grid of
+ * tunings and keep the fastest.  Writes the choice to *best when non-NULL.
+ */
+trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params* params, int32_t max_len,
+                        trw_tuning* best);
+
+/* Counters of the last completed call on this graph. */
+typedef struct {
+  int64_t walks;                /* walks run */
+  int64_t moves;                /* total moves (steps) taken */
+  double kernel_ms;             /* device time of the walk kernel (CUDA events) */
+  int32_t grid_blocks;          /* launch shape used */
+  int32_t block_threads;
+} trw_stats;
+trw_status trw_last_stats(const trw_graph* g, trw_stats* s);
+
+/* Graph facts. */
+int64_t trw_graph_nv(const trw_graph* g);
+int64_t trw_graph_ne(const trw_graph* g);
+/* Bytes of device memory the graph holds (CSR, weights, labels, tables). */
+int64_t trw_graph_device_bytes(const trw_graph* g);
+
+/* Copy the device ALIAS tables to host buffers of ne entries each:
+ * H (probability threshold; 0xFFFFFFFF marks a one-element bucket),
+ * first/second destination vertex (-1, -1 for a dead vertex).  For tests. */
+trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int32_t* second);
+
+/* Philox4x32-10 blocks computed on the device: out[4*i..4*i+3] for counter
+ * ctr[4*i..4*i+3] and key (key0, key1).  Host buffers.  For tests. */
+trw_status trw_debug_philox(const uint32_t* ctr, int64_t n, uint32_t key0, uint32_t key1, uint32_t* out);
+
+/* ------------------------------------------------------------- serving */
+
+/* Serving configuration. */
+typedef struct {
+  int64_t max_inflight_walks;   /* admission: walks admitted but not finished */
+  int64_t max_inflight_bytes;   /* admission: output bytes admitted but not collected */
+  int32_t max_requests;         /* request slots, 1 .. 4096 */
+  int32_t idle_timeout_us;      /* the resident kernel exits after this long without work */
+} trw_serve_config;
+
+void trw_serve_config_default(trw_serve_config* c);
+
+/*
+ * Create a server over a loaded (and, for weighted walks, prepared) graph.
+ * Requests that arrive while others run join the running device work queue
+ * (continuous batching): a resident persistent kernel polls a request ring
+ * with bounded waits and exits after idle_timeout_us without work; the next
+ * submit relaunches it.
+ */
+trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg, trw_server** out);
+
+/*
+ * Submit a request (same meaning as trw_walk; out_paths and out_lengths must be
+ * DEVICE buffers that stay valid until poll returns TRW_OK or an error).
+ * sources may be host or device; it is copied at submit.  Returns
+ * TRW_ERR_BUSY when admitting it would exceed the configured walk, byte or
+ * slot limits (nothing is queued), else queues it and writes *req_id.
+ */
+trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* params, const int32_t* sources,
+                            int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
+                            int32_t* out_lengths, uint64_t* req_id);
+
+/* TRW_OK when request req_id has finished (its slot is released), TRW_PENDING
+ * while it runs, TRW_ERR_NOT_FOUND for an unknown or already collected id,
+ * or the request's error status. */
+trw_status trw_serve_poll(trw_server* s, uint64_t req_id);
+
+/* Wait (bounded by timeout_ms) until every submitted request has finished. */
+trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms);
+
+/* Stop the resident kernel, wait for it and free the server. */
+void trw_serve_destroy(trw_server* s);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char* trw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRW_H */

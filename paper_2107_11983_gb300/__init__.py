@@ -1,0 +1,415 @@
+"""GB300-native random-walk engine: Python binding of libtrw.so (include/trw.h).
+
+The binding only marshals arguments: every step of every walk runs in the
+library's CUDA kernels.  Arrays may be numpy (host) or torch tensors (host or
+CUDA).  There is no CPU fallback: importing works without a GPU, but every
+call that needs one raises when the CUDA library or device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["TRWError", "Graph", "Server", "load_library", "build", "DEEPWALK", "DEEPWALK_WEIGHTED", "PPR",
+           "NODE2VEC", "METAPATH", "KERNEL_AUTO", "KERNEL_PLAIN", "KERNEL_PERSISTENT", "OUT_PATHS",
+           "OUT_ENDPOINTS", "philox_device"]
+
+DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT = 0, 1, 2
+OUT_PATHS, OUT_ENDPOINTS = 0, 1
+PREP_ALIAS = 1
+MAX_SCHEMA = 16
+MAX_BATCH = 64
+
+OK, PENDING = 0, 1
+STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "ERR_INVALID", -2: "ERR_OOM", -3: "ERR_NOT_PREPARED", -4: "ERR_CUDA",
+                -5: "ERR_TIMEOUT", -6: "ERR_REJECT_CAP", -7: "ERR_BUSY", -8: "ERR_NOT_FOUND", -9: "ERR_INTERNAL"}
+
+ALGOS = {"deepwalk": DEEPWALK, "deepwalk_weighted": DEEPWALK_WEIGHTED, "ppr": PPR, "node2vec": NODE2VEC,
+         "metapath": METAPATH}
+
+
+class TRWError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("ppr_stop", ctypes.c_double), ("n2v_p", ctypes.c_double), ("n2v_q", ctypes.c_double),
+                ("schema", ctypes.c_void_p), ("schema_len", ctypes.c_int32), ("out_mode", ctypes.c_uint32),
+                ("walks_per_source", ctypes.c_int32), ("reserved", ctypes.c_int32), ("walk_offset", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("coop_degree", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("walks", ctypes.c_int64), ("moves", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
+                ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("max_inflight_walks", ctypes.c_int64), ("max_inflight_bytes", ctypes.c_int64),
+                ("max_requests", ctypes.c_int32), ("idle_timeout_us", ctypes.c_int32)]
+
+
+_lib = None
+
+# Every function the header declares, with its ctypes signature.
+_VP = ctypes.c_void_p
+_SIGS = {
+    "trw_params_default": (None, [_VP]),
+    "trw_graph_load": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_uint32, _VP]),
+    "trw_graph_free": (None, [_VP]),
+    "trw_prepare": (ctypes.c_int, [_VP, ctypes.c_uint32]),
+    "trw_walk": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP,
+                                _VP]),
+    "trw_walk_ex": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP,
+                                   _VP, ctypes.c_int, _VP, ctypes.c_int]),
+    "trw_sync": (ctypes.c_int, [_VP, _VP]),
+    "trw_walk_batch": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                      ctypes.c_int]),
+    "trw_get_tuning": (ctypes.c_int, [_VP, _VP]),
+    "trw_set_tuning": (ctypes.c_int, [_VP, _VP]),
+    "trw_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int32, _VP]),
+    "trw_last_stats": (ctypes.c_int, [_VP, _VP]),
+    "trw_graph_nv": (ctypes.c_int64, [_VP]),
+    "trw_graph_ne": (ctypes.c_int64, [_VP]),
+    "trw_graph_device_bytes": (ctypes.c_int64, [_VP]),
+    "trw_debug_alias": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "trw_debug_philox": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, _VP]),
+    "trw_serve_config_default": (None, [_VP]),
+    "trw_serve_create": (ctypes.c_int, [_VP, _VP, _VP]),
+    "trw_serve_submit": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.c_uint64, _VP, _VP, _VP]),
+    "trw_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "trw_serve_drain": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "trw_serve_destroy": (None, [_VP]),
+    "trw_last_error": (ctypes.c_char_p, []),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile libtrw.so for sm_103a (nvcc) if it is missing or stale."""
+    return _build.build(force=force)
+
+
+def load_library(path: Optional[str] = None):
+    """Load libtrw.so (building it first if missing).  Raises if it cannot be built or loaded."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if path is None and (not os.path.exists(p) or _build.stale()):
+        _build.build()
+    try:
+        lib = ctypes.CDLL(p)
+    except OSError as e:
+        raise RuntimeError(f"cannot load the CUDA walk library {p}: {e}") from e
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int, what: str = ""):
+    if status != OK:
+        msg = load_library().trw_last_error()
+        raise TRWError(status, (what + ": " if what else "") + (msg.decode() if msg else ""))
+
+
+# ------------------------------------------------------------ array helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _as_host(x, dtype):
+    if _is_torch(x):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _is_cuda(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
+def _params(algo: int, ppr_stop: float, n2v_p: float, n2v_q: float, schema, walks_per_source: int,
+            endpoints: bool, walk_offset: int):
+    p = _Params()
+    p.ppr_stop = ppr_stop
+    p.n2v_p = n2v_p
+    p.n2v_q = n2v_q
+    keep = None
+    if schema is not None:
+        keep = np.ascontiguousarray(_as_host(schema, np.uint8))
+        p.schema = keep.ctypes.data
+        p.schema_len = keep.shape[0]
+    p.out_mode = OUT_ENDPOINTS if endpoints else OUT_PATHS
+    p.walks_per_source = walks_per_source
+    p.walk_offset = walk_offset
+    return p, keep
+
+
+@dataclass
+class WalkOutput:
+    paths: object     # int32 [nwalks, max_len+1] or [nwalks] (numpy or torch, like the sources)
+    lengths: object   # int32 [nwalks]
+
+
+class Graph:
+    """A CSR graph resident on the current CUDA device (trw_graph_load)."""
+
+    def __init__(self, row_ptr, col, weights=None, labels=None, check: bool = True):
+        lib = load_library()
+        rp = _as_host(row_ptr, np.int64)
+        cl = _as_host(col, np.int32)
+        w = None if weights is None else _as_host(weights, np.float32)
+        lab = None if labels is None else _as_host(labels, np.uint8)
+        h = ctypes.c_void_p(0)
+        st = lib.trw_graph_load(rp.shape[0] - 1, cl.shape[0], rp.ctypes.data, cl.ctypes.data,
+                                0 if w is None else w.ctypes.data, 0 if lab is None else lab.ctypes.data,
+                                1 if check else 0, ctypes.byref(h))
+        _check(st, "trw_graph_load")
+        self._h = h
+        self.nv = int(rp.shape[0] - 1)
+        self.ne = int(cl.shape[0])
+
+    @classmethod
+    def from_synth(cls, g):
+        return cls(g.row_ptr, g.col, g.weights, g.labels)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().trw_graph_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def prepare(self, what: int = PREP_ALIAS):
+        _check(load_library().trw_prepare(self._h, what), "trw_prepare")
+
+    def device_bytes(self) -> int:
+        return int(load_library().trw_graph_device_bytes(self._h))
+
+    # -------------------------------------------------------------- walks
+    def walk(self, algo: int, sources, max_len: int, seed: int, *, ppr_stop: float = 0.2, n2v_p: float = 1.0,
+             n2v_q: float = 1.0, schema=None, walks_per_source: int = 1, endpoints: bool = False,
+             walk_offset: int = 0, kernel: int = KERNEL_AUTO, out_paths=None, out_lengths=None, stream=None,
+             sync: bool = True) -> WalkOutput:
+        """trw_walk_ex.  Outputs follow the sources: numpy for host sources, CUDA
+        tensors for CUDA sources, unless out_paths / out_lengths are given."""
+        lib = load_library()
+        algo = ALGOS.get(algo, algo) if isinstance(algo, str) else algo
+        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset)
+        if _is_torch(sources):
+            src = sources if sources.dtype == _torch().int32 else sources.to(_torch().int32)
+            src = src.contiguous()
+        else:
+            src = np.ascontiguousarray(sources, dtype=np.int32)
+        n = int(src.shape[0])
+        nwalks = n * walks_per_source
+        shape = (nwalks,) if endpoints else (nwalks, max_len + 1)
+        if out_paths is None:
+            out_paths = (_torch().empty(shape, dtype=_torch().int32, device=src.device) if _is_cuda(src)
+                         else np.empty(shape, dtype=np.int32))
+        if out_lengths is None:
+            out_lengths = (_torch().empty(nwalks, dtype=_torch().int32, device=src.device) if _is_cuda(src)
+                           else np.empty(nwalks, dtype=np.int32))
+        st = lib.trw_walk_ex(self._h, algo, ctypes.byref(p), _ptr(src), n, max_len, seed & ((1 << 64) - 1),
+                             _ptr(out_paths), _ptr(out_lengths), kernel, stream or 0, 1 if sync else 0)
+        _check(st, "trw_walk")
+        return WalkOutput(out_paths, out_lengths)
+
+    def sync(self, stream=None):
+        _check(load_library().trw_sync(self._h, stream or 0), "trw_sync")
+
+    def walk_batch(self, requests: Sequence[dict], stream=None, sync: bool = True):
+        """One persistent launch over a mixed batch.  Each request is a dict with
+        algo, sources (CUDA tensor), max_len, seed and optional parameters; outputs
+        are allocated as CUDA tensors and returned as a list of WalkOutput."""
+        lib = load_library()
+        torch = _torch()
+        nreq = len(requests)
+        if not 1 <= nreq <= MAX_BATCH:
+            raise ValueError(f"1..{MAX_BATCH} requests")
+        algos = (ctypes.c_int * nreq)()
+        params = (_Params * nreq)()
+        srcs = (ctypes.c_void_p * nreq)()
+        ns = (ctypes.c_int64 * nreq)()
+        lens = (ctypes.c_int32 * nreq)()
+        seeds = (ctypes.c_uint64 * nreq)()
+        outs = (ctypes.c_void_p * nreq)()
+        outl = (ctypes.c_void_p * nreq)()
+        keep, results = [], []
+        for i, r in enumerate(requests):
+            algo = r["algo"]
+            algo = ALGOS.get(algo, algo) if isinstance(algo, str) else algo
+            wps = r.get("walks_per_source", 1)
+            ep = r.get("endpoints", False)
+            p, k = _params(algo, r.get("ppr_stop", 0.2), r.get("n2v_p", 1.0), r.get("n2v_q", 1.0), r.get("schema"),
+                           wps, ep, r.get("walk_offset", 0))
+            keep.append(k)
+            src = r["sources"]
+            if not _is_cuda(src):
+                src = torch.as_tensor(np.ascontiguousarray(src, dtype=np.int32)).cuda()
+            src = src.to(torch.int32).contiguous()
+            keep.append(src)
+            n = int(src.shape[0])
+            L = int(r["max_len"])
+            shape = (n * wps,) if ep else (n * wps, L + 1)
+            op = torch.empty(shape, dtype=torch.int32, device=src.device)
+            ol = torch.empty(n * wps, dtype=torch.int32, device=src.device)
+            algos[i], params[i], srcs[i], ns[i], lens[i] = algo, p, src.data_ptr(), n, L
+            seeds[i] = int(r["seed"]) & ((1 << 64) - 1)
+            outs[i], outl[i] = op.data_ptr(), ol.data_ptr()
+            results.append(WalkOutput(op, ol))
+        st = lib.trw_walk_batch(self._h, nreq, algos, params, srcs, ns, lens, seeds, outs, outl, stream or 0,
+                                1 if sync else 0)
+        _check(st, "trw_walk_batch")
+        return results
+
+    # ------------------------------------------------------------- tuning
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(load_library().trw_get_tuning(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        _check(load_library().trw_get_tuning(self._h, ctypes.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(load_library().trw_set_tuning(self._h, ctypes.byref(t)), "trw_set_tuning")
+
+    def autotune(self, algo: int, max_len: int = 10, **kw) -> dict:
+        p, keep = _params(algo, kw.get("ppr_stop", 0.2), kw.get("n2v_p", 1.0), kw.get("n2v_q", 1.0),
+                          kw.get("schema"), 1, kw.get("endpoints", False), 0)
+        t = Tuning()
+        _check(load_library().trw_autotune(self._h, algo, ctypes.byref(p), max_len, ctypes.byref(t)), "trw_autotune")
+        return t.as_dict()
+
+    def last_stats(self) -> dict:
+        s = Stats()
+        _check(load_library().trw_last_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def debug_alias(self):
+        H = np.empty(self.ne, dtype=np.uint32)
+        a = np.empty(self.ne, dtype=np.int32)
+        b = np.empty(self.ne, dtype=np.int32)
+        _check(load_library().trw_debug_alias(self._h, H.ctypes.data, a.ctypes.data, b.ctypes.data), "trw_debug_alias")
+        return H, a, b
+
+
+def philox_device(ctr, key0: int, key1: int) -> np.ndarray:
+    """Philox4x32-10 blocks computed by the device code (for tests)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(c)
+    _check(load_library().trw_debug_philox(c.ctypes.data, c.shape[0], key0, key1, out.ctypes.data), "philox")
+    return out
+
+
+class Server:
+    """Continuous-batching serving loop over a resident graph (trw_serve_*)."""
+
+    def __init__(self, graph: Graph, max_inflight_walks: int = 0, max_inflight_bytes: int = 0,
+                 max_requests: int = 0, idle_timeout_us: int = 0):
+        lib = load_library()
+        cfg = ServeConfig()
+        lib.trw_serve_config_default(ctypes.byref(cfg))
+        if max_inflight_walks:
+            cfg.max_inflight_walks = max_inflight_walks
+        if max_inflight_bytes:
+            cfg.max_inflight_bytes = max_inflight_bytes
+        if max_requests:
+            cfg.max_requests = max_requests
+        if idle_timeout_us:
+            cfg.idle_timeout_us = idle_timeout_us
+        h = ctypes.c_void_p(0)
+        _check(lib.trw_serve_create(graph.handle, ctypes.byref(cfg), ctypes.byref(h)), "trw_serve_create")
+        self._h = h
+        self.graph = graph
+        self._keep = {}
+
+    def submit(self, algo: int, sources, max_len: int, seed: int, out_paths, out_lengths, *, ppr_stop: float = 0.2,
+               n2v_p: float = 1.0, n2v_q: float = 1.0, schema=None, walks_per_source: int = 1,
+               endpoints: bool = False, walk_offset: int = 0) -> int:
+        """Queue a request; raises TRWError(ERR_BUSY) when it cannot be admitted now."""
+        lib = load_library()
+        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset)
+        src = sources if _is_torch(sources) else np.ascontiguousarray(sources, dtype=np.int32)
+        rid = ctypes.c_uint64(0)
+        st = lib.trw_serve_submit(self._h, algo, ctypes.byref(p), _ptr(src), int(src.shape[0]), max_len,
+                                  seed & ((1 << 64) - 1), _ptr(out_paths), _ptr(out_lengths), ctypes.byref(rid))
+        _check(st, "trw_serve_submit")
+        self._keep[rid.value] = (out_paths, out_lengths)
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        """OK (0) when done, PENDING (1) while running; raises on a request error."""
+        st = load_library().trw_serve_poll(self._h, rid)
+        if st == PENDING:
+            return PENDING
+        self._keep.pop(rid, None)
+        _check(st, f"request {rid}")
+        return OK
+
+    def drain(self, timeout_ms: int = 60000):
+        _check(load_library().trw_serve_drain(self._h, timeout_ms), "trw_serve_drain")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().trw_serve_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,580 @@
+// Host side of the C ABI declared in include/trw.h: argument checks, device
+// residency of the graph, staging of host buffers, launches and status.
+// Every step of a walk runs in the kernels of walk_kernels.cu and
+// prepare_kernels.cu; this file never computes a walk on the host.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/trw.h"
+#include "trw_api_internal.h"
+#include "trw_internal.h"
+
+using namespace trw;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string t_last_error;
+
+trw_status trw_fail(trw_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return st;
+}
+
+trw_status trw_cuda_fail(cudaError_t e, const char* what) {
+  return trw_fail(TRW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char* trw_last_error(void) { return t_last_error.c_str(); }
+
+#define CUDA_TRY(call, what)                      \
+  do {                                            \
+    cudaError_t e__ = (call);                     \
+    if (e__ != cudaSuccess) return trw_cuda_fail(e__, what); \
+  } while (0)
+
+// ------------------------------------------------------------ small helpers
+
+bool trw_is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static uint64_t threshold_of(double t) {
+  if (!(t > 0.0)) return 0;
+  if (t >= 1.0) return 4294967296ull;
+  return (uint64_t)std::floor(t * 4294967296.0);
+}
+
+trw_status trw_grow(void** p, size_t* cap, size_t need) {
+  if (*cap >= need) return TRW_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  size_t n = std::max(need, (size_t)4096);
+  cudaError_t e = cudaMalloc(p, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return trw_fail(TRW_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+  }
+  *cap = n;
+  return TRW_OK;
+}
+
+// --------------------------------------------------------------------- load
+
+extern "C" void trw_params_default(trw_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->ppr_stop = 0.2;
+  p->n2v_p = 1.0;
+  p->n2v_q = 1.0;
+  p->schema = nullptr;
+  p->schema_len = 0;
+  p->out_mode = TRW_OUT_PATHS;
+  p->walks_per_source = 1;
+  p->walk_offset = 0;
+}
+
+static void graph_release(trw_graph* g) {
+  if (!g) return;
+  cudaFree(g->row_ptr);
+  cudaFree(g->col);
+  cudaFree(g->weights);
+  cudaFree(g->labels);
+  cudaFree(g->alias);
+  cudaFree(g->ctrl);
+  cudaFree(g->src_stage);
+  cudaFree(g->out_stage);
+  cudaFree(g->len_stage);
+  cudaFree(g->batch_specs);
+  if (g->batch_host) cudaFreeHost(g->batch_host);
+  cudaFree(g->misc);
+  if (g->ev0) cudaEventDestroy(g->ev0);
+  if (g->ev1) cudaEventDestroy(g->ev1);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+extern "C" void trw_graph_free(trw_graph* g) { graph_release(g); }
+
+static trw_status alloc_dev(void** p, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return trw_fail(TRW_ERR_OOM, "cudaMalloc for %s (%zu bytes) failed: %s", what, bytes, cudaGetErrorString(e));
+  }
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_ptr, const int32_t* col,
+                                     const float* weights, const uint8_t* labels, uint32_t flags, trw_graph** out) {
+  (void)flags;
+  if (!out) return trw_fail(TRW_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (nv < 0 || ne < 0 || nv >= (int64_t)INT32_MAX || ne >= (int64_t)INT32_MAX)
+    return trw_fail(TRW_ERR_INVALID, "nv=%lld ne=%lld outside [0, 2^31-1)", (long long)nv, (long long)ne);
+  if (!row_ptr) return trw_fail(TRW_ERR_INVALID, "row_ptr is NULL");
+  if (ne > 0 && !col) return trw_fail(TRW_ERR_INVALID, "col is NULL");
+  if (row_ptr[0] != 0) return trw_fail(TRW_ERR_INVALID, "row_ptr[0] != 0");
+  std::vector<int32_t> rp32((size_t)nv + 1);
+  for (int64_t v = 0; v <= nv; ++v) {
+    const int64_t x = row_ptr[v];
+    if (v > 0 && x < row_ptr[v - 1])
+      return trw_fail(TRW_ERR_INVALID, "row_ptr decreases at vertex %lld", (long long)v);
+    rp32[(size_t)v] = (int32_t)x;
+  }
+  if (row_ptr[nv] != ne) return trw_fail(TRW_ERR_INVALID, "row_ptr[nv]=%lld != ne=%lld", (long long)row_ptr[nv], (long long)ne);
+
+  trw_graph* g = new trw_graph();
+  g->nv = nv;
+  g->ne = ne;
+  trw_status st;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) {
+    graph_release(g);
+    return trw_cuda_fail(e, "cudaGetDevice");
+  }
+  cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (g->num_sms <= 0) g->num_sms = 1;
+#define LOAD_TRY(x)          \
+  do {                       \
+    st = (x);                \
+    if (st != TRW_OK) {      \
+      graph_release(g);      \
+      return st;             \
+    }                        \
+  } while (0)
+#define LOAD_CUDA(call, what)                       \
+  do {                                              \
+    cudaError_t e2 = (call);                        \
+    if (e2 != cudaSuccess) {                        \
+      graph_release(g);                             \
+      return trw_cuda_fail(e2, what);               \
+    }                                               \
+  } while (0)
+  LOAD_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  LOAD_CUDA(cudaEventCreate(&g->ev0), "cudaEventCreate");
+  LOAD_CUDA(cudaEventCreate(&g->ev1), "cudaEventCreate");
+  LOAD_TRY(alloc_dev((void**)&g->row_ptr, sizeof(int32_t) * ((size_t)nv + 1), "row_ptr"));
+  LOAD_TRY(alloc_dev((void**)&g->col, sizeof(int32_t) * ((size_t)ne + 4), "col"));
+  LOAD_TRY(alloc_dev((void**)&g->ctrl, sizeof(Ctrl), "ctrl"));
+  LOAD_TRY(alloc_dev((void**)&g->misc, 256, "misc"));
+  LOAD_CUDA(cudaMemcpy(g->row_ptr, rp32.data(), sizeof(int32_t) * ((size_t)nv + 1), cudaMemcpyHostToDevice), "copy row_ptr");
+  if (ne > 0) LOAD_CUDA(cudaMemcpy(g->col, col, sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice), "copy col");
+  if (weights) {
+    LOAD_TRY(alloc_dev((void**)&g->weights, sizeof(float) * ((size_t)ne + 4), "weights"));
+    if (ne > 0) LOAD_CUDA(cudaMemcpy(g->weights, weights, sizeof(float) * (size_t)ne, cudaMemcpyHostToDevice), "copy weights");
+  }
+  if (labels) {
+    // padded so that aligned 4- and 16-byte loads of the last row stay inside the allocation
+    LOAD_TRY(alloc_dev((void**)&g->labels, (size_t)ne + 64, "labels"));
+    LOAD_CUDA(cudaMemset(g->labels, 0, (size_t)ne + 64), "memset labels");
+    if (ne > 0) LOAD_CUDA(cudaMemcpy(g->labels, labels, (size_t)ne, cudaMemcpyHostToDevice), "copy labels");
+  }
+  // Device checks: ids in range, rows sorted.
+  LOAD_CUDA(cudaMemset(g->ctrl, 0, sizeof(Ctrl)), "memset ctrl");
+  LOAD_CUDA(cudaMemset(g->misc, 0, 256), "memset misc");
+  LOAD_CUDA(launch_check_graph((int32_t)nv, g->row_ptr, g->col, g->ctrl, (int*)g->misc, g->stream), "check graph");
+  LOAD_CUDA(cudaStreamSynchronize(g->stream), "check graph");
+  Ctrl c;
+  int unsorted = 0;
+  LOAD_CUDA(cudaMemcpy(&c, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost), "read ctrl");
+  LOAD_CUDA(cudaMemcpy(&unsorted, g->misc, sizeof(int), cudaMemcpyDeviceToHost), "read flag");
+  if (c.err != 0) {
+    graph_release(g);
+    return trw_fail(TRW_ERR_INVALID, "a column id is outside [0, nv)");
+  }
+  g->sorted = unsorted == 0;
+  g->tuning.block_threads = 256;
+  g->tuning.blocks_per_sm = 0;
+  g->tuning.chunk = 32;
+  g->tuning.coop_degree = 256;
+  g->device_bytes = (int64_t)(sizeof(int32_t) * ((size_t)nv + 1) + sizeof(int32_t) * (size_t)ne +
+                              (weights ? sizeof(float) * (size_t)ne : 0) + (labels ? (size_t)ne : 0));
+  *out = g;
+  return TRW_OK;
+#undef LOAD_TRY
+#undef LOAD_CUDA
+}
+
+extern "C" int64_t trw_graph_nv(const trw_graph* g) { return g ? g->nv : -1; }
+extern "C" int64_t trw_graph_ne(const trw_graph* g) { return g ? g->ne : -1; }
+extern "C" int64_t trw_graph_device_bytes(const trw_graph* g) { return g ? g->device_bytes : -1; }
+
+DevGraph trw_dev_graph(const trw_graph* g) {
+  DevGraph d;
+  d.row_ptr = g->row_ptr;
+  d.col = g->col;
+  d.alias = g->alias;
+  d.labels = g->labels;
+  d.nv = (int32_t)g->nv;
+  d.ne = (int32_t)g->ne;
+  return d;
+}
+
+// ------------------------------------------------------------------ prepare
+
+extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
+  if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (what & ~TRW_PREP_ALIAS) return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
+  if (!(what & TRW_PREP_ALIAS)) return TRW_OK;
+  std::lock_guard<std::mutex> lk(g->mu);
+  if (!g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
+  const size_t ne = (size_t)g->ne;
+  if (!g->alias) {
+    trw_status st = alloc_dev((void**)&g->alias, sizeof(uint4) * (ne + 1), "alias tables");
+    if (st != TRW_OK) return st;
+    g->device_bytes += (int64_t)(sizeof(uint4) * ne);
+  }
+  unsigned long long* q = nullptr;
+  int32_t *sm = nullptr, *lg = nullptr;
+  trw_status st = alloc_dev((void**)&q, sizeof(unsigned long long) * (ne + 1), "alias scratch");
+  if (st == TRW_OK) st = alloc_dev((void**)&sm, sizeof(int32_t) * (ne + 1), "alias scratch");
+  if (st == TRW_OK) st = alloc_dev((void**)&lg, sizeof(int32_t) * (ne + 1), "alias scratch");
+  cudaError_t e = cudaSuccess;
+  Ctrl c{};
+  if (st == TRW_OK) {
+    e = cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), g->stream);
+    if (e == cudaSuccess)
+      e = launch_prepare_alias((int32_t)g->nv, g->row_ptr, g->col, g->weights, g->alias, q, sm, lg, g->ctrl, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&c, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(q);
+  cudaFree(sm);
+  cudaFree(lg);
+  if (st != TRW_OK) return st;
+  if (e != cudaSuccess) return trw_cuda_fail(e, "prepare alias");
+  if (c.err != 0) {
+    g->prepared_alias = false;
+    return trw_fail(TRW_ERR_INVALID, "an edge weight is negative or not finite");
+  }
+  g->prepared_alias = true;
+  return TRW_OK;
+}
+
+// --------------------------------------------------------------------- walk
+
+trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pin, int64_t n_sources,
+                         int32_t max_len, uint64_t seed, WalkSpec* sp) {
+  trw_params p;
+  if (pin) p = *pin;
+  else trw_params_default(&p);
+  std::memset(sp, 0, sizeof(*sp));
+  if ((int)algo < TRW_DEEPWALK || (int)algo > TRW_METAPATH) return trw_fail(TRW_ERR_INVALID, "unknown algorithm %d", (int)algo);
+  if (max_len < 0) return trw_fail(TRW_ERR_INVALID, "max_len < 0");
+  if (n_sources < 0) return trw_fail(TRW_ERR_INVALID, "n_sources < 0");
+  if (p.walks_per_source < 1) return trw_fail(TRW_ERR_INVALID, "walks_per_source < 1");
+  if (p.out_mode != TRW_OUT_PATHS && p.out_mode != TRW_OUT_ENDPOINTS) return trw_fail(TRW_ERR_INVALID, "bad out_mode");
+  if (p.walk_offset < 0) return trw_fail(TRW_ERR_INVALID, "walk_offset < 0");
+  const int64_t nwalks = n_sources * (int64_t)p.walks_per_source;
+  if (n_sources > 0 && nwalks / n_sources != p.walks_per_source) return trw_fail(TRW_ERR_INVALID, "walk count overflows");
+  if (p.walk_offset + nwalks > 4294967296LL) return trw_fail(TRW_ERR_INVALID, "walk indices exceed 2^32");
+  if (n_sources > 0 && g->nv == 0) return trw_fail(TRW_ERR_INVALID, "sources on an empty graph");
+  sp->algo = (int32_t)algo;
+  sp->max_len = max_len;
+  sp->wps = (uint32_t)p.walks_per_source;
+  sp->endpoints = p.out_mode == TRW_OUT_ENDPOINTS ? 1u : 0u;
+  sp->key0 = (uint32_t)seed;
+  sp->key1 = (uint32_t)(seed >> 32);
+  sp->walk_offset = (uint32_t)p.walk_offset;
+  sp->nwalks = nwalks;
+  if (algo == TRW_PPR) {
+    if (!(p.ppr_stop >= 0.0 && p.ppr_stop <= 1.0)) return trw_fail(TRW_ERR_INVALID, "ppr_stop outside [0, 1]");
+    sp->T_stop = threshold_of(p.ppr_stop);
+  }
+  if (algo == TRW_NODE2VEC) {
+    if (!(p.n2v_p > 0.0) || !(p.n2v_q > 0.0) || !std::isfinite(p.n2v_p) || !std::isfinite(p.n2v_q))
+      return trw_fail(TRW_ERR_INVALID, "node2vec p and q must be finite and > 0");
+    if (!g->sorted) return trw_fail(TRW_ERR_INVALID, "node2vec needs sorted adjacency rows");
+    const double w_ret = 1.0 / p.n2v_p, w_nb = 1.0, w_far = 1.0 / p.n2v_q;
+    double pstar = w_ret > w_nb ? w_ret : w_nb;
+    if (w_far > pstar) pstar = w_far;
+    sp->T_ret = threshold_of(w_ret / pstar);
+    sp->T_nb = threshold_of(w_nb / pstar);
+    sp->T_far = threshold_of(w_far / pstar);
+    sp->T_lo = std::min(sp->T_nb, sp->T_far);
+    sp->T_hi = std::max(sp->T_nb, sp->T_far);
+  }
+  if (algo == TRW_METAPATH) {
+    if (!g->labels) return trw_fail(TRW_ERR_INVALID, "metapath needs edge labels");
+    if (!p.schema || p.schema_len < 1 || p.schema_len > TRW_MAX_SCHEMA)
+      return trw_fail(TRW_ERR_INVALID, "metapath schema length must be in [1, %d]", TRW_MAX_SCHEMA);
+    sp->schema_len = (uint32_t)p.schema_len;
+    for (int i = 0; i < p.schema_len; ++i) {
+      if (i < 8) sp->schema_lo |= (uint64_t)p.schema[i] << (8 * i);
+      else sp->schema_hi |= (uint64_t)p.schema[i] << (8 * (i - 8));
+    }
+  }
+  if (algo == TRW_DEEPWALK_WEIGHTED) {
+    if (!g->weights) return trw_fail(TRW_ERR_INVALID, "weighted walks need edge weights");
+    if (!g->prepared_alias) return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_ALIAS) first");
+  }
+  return TRW_OK;
+}
+
+LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
+  LaunchCfg c;
+  c.block_threads = g->tuning.block_threads;
+  int bps = g->tuning.blocks_per_sm;
+  const int occ = persistent_blocks_per_sm(algo, c.block_threads);
+  if (bps <= 0 || bps > occ) bps = occ;
+  c.grid_blocks = g->num_sms * bps;
+  c.chunk = g->tuning.chunk;
+  c.coop_degree = g->tuning.coop_degree;
+  return c;
+}
+
+static trw_status collect_status(trw_graph* g, cudaStream_t stream) {
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "walk kernel");
+  Ctrl c;
+  e = cudaMemcpy(&c, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "read status");
+  float ms = 0.f;
+  if (g->timed && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) g->last.kernel_ms = ms;
+  cudaGetLastError();
+  g->last.moves = (int64_t)c.moves;
+  if (c.err != 0) {
+    cudaMemsetAsync(&g->ctrl->err, 0, sizeof(int), stream);
+    cudaStreamSynchronize(stream);
+    if (c.err == kErrRejectCap) return trw_fail(TRW_ERR_REJECT_CAP, "a rejection step exceeded %d trials", TRW_REJECT_CAP);
+    if (c.err == kErrInvalid) return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
+    return trw_fail(TRW_ERR_INTERNAL, "device status %d", c.err);
+  }
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
+                                  int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
+                                  int32_t* out_lengths, trw_kernel kernel, void* stream_v, int sync) {
+  if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (kernel != TRW_KERNEL_AUTO && kernel != TRW_KERNEL_PLAIN && kernel != TRW_KERNEL_PERSISTENT)
+    return trw_fail(TRW_ERR_INVALID, "unknown kernel %d", (int)kernel);
+  WalkSpec sp;
+  trw_status st = trw_make_spec(g, algo, params, n_sources, max_len, seed, &sp);
+  if (st != TRW_OK) return st;
+  if (n_sources > 0 && (!sources || !out_paths || !out_lengths)) return trw_fail(TRW_ERR_INVALID, "NULL buffer");
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t stream = stream_v ? (cudaStream_t)stream_v : g->stream;
+  const int64_t nwalks = sp.nwalks;
+  const size_t out_elems = sp.endpoints ? (size_t)nwalks : (size_t)nwalks * ((size_t)max_len + 1);
+  const bool src_dev = trw_is_device_ptr(sources);
+  const bool out_dev = trw_is_device_ptr(out_paths);
+  const bool len_dev = trw_is_device_ptr(out_lengths);
+  if (!sync && (!src_dev || !out_dev || !len_dev))
+    return trw_fail(TRW_ERR_INVALID, "asynchronous walks need device buffers");
+  if (!src_dev) {
+    for (int64_t i = 0; i < n_sources; ++i)
+      if (sources[i] < 0 || sources[i] >= g->nv)
+        return trw_fail(TRW_ERR_INVALID, "source %lld = %d is outside [0, %lld)", (long long)i, sources[i], (long long)g->nv);
+  }
+  g->last.walks = nwalks;
+  g->last.moves = 0;
+  g->last.kernel_ms = 0;
+  g->timed = false;
+  if (nwalks == 0) return TRW_OK;
+
+  const int32_t* d_src = sources;
+  int32_t* d_out = out_paths;
+  int32_t* d_len = out_lengths;
+  if (!src_dev) {
+    st = trw_grow((void**)&g->src_stage, &g->src_cap, sizeof(int32_t) * (size_t)n_sources);
+    if (st != TRW_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(g->src_stage, sources, sizeof(int32_t) * (size_t)n_sources, cudaMemcpyHostToDevice, stream),
+             "copy sources");
+    d_src = g->src_stage;
+  }
+  if (!out_dev) {
+    st = trw_grow((void**)&g->out_stage, &g->out_cap, sizeof(int32_t) * out_elems);
+    if (st != TRW_OK) return st;
+    d_out = g->out_stage;
+  }
+  if (!len_dev) {
+    st = trw_grow((void**)&g->len_stage, &g->len_cap, sizeof(int32_t) * (size_t)nwalks);
+    if (st != TRW_OK) return st;
+    d_len = g->len_stage;
+  }
+  sp.sources = d_src;
+  sp.out_paths = d_out;
+  sp.out_lengths = d_len;
+  const DevGraph dg = trw_dev_graph(g);
+  if (sync) CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), stream), "reset ctrl");
+  else CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, offsetof(Ctrl, err), stream), "reset ctrl");
+  if (src_dev) CUDA_TRY(launch_validate_sources(d_src, n_sources, (int32_t)g->nv, g->ctrl, stream), "validate sources");
+  CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
+  if (kernel == TRW_KERNEL_PLAIN) {
+    CUDA_TRY(launch_walk_plain(dg, sp, g->ctrl, stream, 256), "plain walk launch");
+    g->last.grid_blocks = (int32_t)((nwalks + 255) / 256);
+    g->last.block_threads = 256;
+  } else {
+    const LaunchCfg cfg = trw_launch_cfg(g, sp.algo);
+    CUDA_TRY(launch_walk_persistent(dg, sp, g->ctrl, stream, cfg), "persistent walk launch");
+    g->last.grid_blocks = (int32_t)std::min<int64_t>(cfg.grid_blocks, (nwalks + cfg.block_threads - 1) / cfg.block_threads);
+    g->last.block_threads = cfg.block_threads;
+  }
+  CUDA_TRY(cudaEventRecord(g->ev1, stream), "event");
+  g->timed = true;
+  if (!out_dev)
+    CUDA_TRY(cudaMemcpyAsync(out_paths, d_out, sizeof(int32_t) * out_elems, cudaMemcpyDeviceToHost, stream), "copy paths");
+  if (!len_dev)
+    CUDA_TRY(cudaMemcpyAsync(out_lengths, d_len, sizeof(int32_t) * (size_t)nwalks, cudaMemcpyDeviceToHost, stream),
+             "copy lengths");
+  if (!sync) return TRW_OK;
+  return collect_status(g, stream);
+}
+
+extern "C" trw_status trw_walk(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
+                               int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
+                               int32_t* out_lengths) {
+  return trw_walk_ex(g, algo, params, sources, n_sources, max_len, seed, out_paths, out_lengths, TRW_KERNEL_AUTO,
+                     nullptr, 1);
+}
+
+extern "C" trw_status trw_sync(trw_graph* g, void* stream_v) {
+  if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  std::lock_guard<std::mutex> lk(g->mu);
+  return collect_status(g, stream_v ? (cudaStream_t)stream_v : g->stream);
+}
+
+extern "C" trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw_algo* algos, const trw_params* params,
+                                     const int32_t* const* sources, const int64_t* n_sources, const int32_t* max_lens,
+                                     const uint64_t* seeds, int32_t* const* out_paths, int32_t* const* out_lengths,
+                                     void* stream_v, int sync) {
+  if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (n_requests < 1 || n_requests > TRW_MAX_BATCH)
+    return trw_fail(TRW_ERR_INVALID, "n_requests must be in [1, %d]", TRW_MAX_BATCH);
+  if (!algos || !sources || !n_sources || !max_lens || !seeds || !out_paths || !out_lengths)
+    return trw_fail(TRW_ERR_INVALID, "NULL array");
+  std::vector<WalkSpec> specs((size_t)n_requests);
+  std::vector<int64_t> prefix((size_t)n_requests + 1, 0);
+  for (int r = 0; r < n_requests; ++r) {
+    trw_status st = trw_make_spec(g, algos[r], params ? &params[r] : nullptr, n_sources[r], max_lens[r], seeds[r], &specs[r]);
+    if (st != TRW_OK) return trw_fail(st, "request %d: %s", r, trw_last_error());
+    if (specs[r].nwalks > 0) {
+      if (!trw_is_device_ptr(sources[r]) || !trw_is_device_ptr(out_paths[r]) || !trw_is_device_ptr(out_lengths[r]))
+        return trw_fail(TRW_ERR_INVALID, "request %d: batch buffers must be device memory", r);
+    }
+    specs[r].sources = sources[r];
+    specs[r].out_paths = out_paths[r];
+    specs[r].out_lengths = out_lengths[r];
+    prefix[r + 1] = prefix[r] + specs[r].nwalks;
+  }
+  std::lock_guard<std::mutex> lk(g->mu);
+  cudaStream_t stream = stream_v ? (cudaStream_t)stream_v : g->stream;
+  const size_t spec_bytes = sizeof(WalkSpec) * TRW_MAX_BATCH;
+  const size_t need = spec_bytes + sizeof(int64_t) * (TRW_MAX_BATCH + 1);
+  if (!g->batch_specs) {
+    trw_status st = alloc_dev((void**)&g->batch_specs, need, "batch table");
+    if (st != TRW_OK) return st;
+    CUDA_TRY(cudaMallocHost((void**)&g->batch_host, need), "pinned batch table");
+  }
+  // The pinned staging copy stays untouched until the previous copy finished.
+  CUDA_TRY(cudaStreamSynchronize(stream), "batch table");
+  std::memcpy(g->batch_host, specs.data(), sizeof(WalkSpec) * (size_t)n_requests);
+  std::memcpy(g->batch_host + spec_bytes, prefix.data(), sizeof(int64_t) * ((size_t)n_requests + 1));
+  CUDA_TRY(cudaMemcpyAsync(g->batch_specs, g->batch_host, need, cudaMemcpyHostToDevice, stream), "copy batch table");
+  const int64_t total = prefix[(size_t)n_requests];
+  g->last.walks = total;
+  g->last.moves = 0;
+  g->timed = false;
+  if (sync) CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), stream), "reset ctrl");
+  else CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, offsetof(Ctrl, err), stream), "reset ctrl");
+  for (int r = 0; r < n_requests; ++r)
+    if (specs[r].nwalks > 0)
+      CUDA_TRY(launch_validate_sources(specs[r].sources, n_sources[r], (int32_t)g->nv, g->ctrl, stream), "validate");
+  const LaunchCfg cfg = trw_launch_cfg(g, MIXED);
+  CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
+  CUDA_TRY(launch_walk_batch(trw_dev_graph(g), reinterpret_cast<const WalkSpec*>(g->batch_specs),
+                             reinterpret_cast<const int64_t*>(g->batch_specs + spec_bytes), n_requests, total, g->ctrl,
+                             stream, cfg),
+           "batch walk launch");
+  CUDA_TRY(cudaEventRecord(g->ev1, stream), "event");
+  g->timed = true;
+  g->last.grid_blocks = cfg.grid_blocks;
+  g->last.block_threads = cfg.block_threads;
+  if (!sync) return TRW_OK;
+  return collect_status(g, stream);
+}
+
+// ---------------------------------------------------------------- tuning
+
+extern "C" trw_status trw_get_tuning(const trw_graph* g, trw_tuning* t) {
+  if (!g || !t) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  *t = g->tuning;
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_set_tuning(trw_graph* g, const trw_tuning* t) {
+  if (!g || !t) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (t->block_threads < 64 || t->block_threads > 1024 || (t->block_threads & 31))
+    return trw_fail(TRW_ERR_INVALID, "block_threads must be a multiple of 32 in [64, 1024]");
+  if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32) return trw_fail(TRW_ERR_INVALID, "blocks_per_sm in [0, 32]");
+  if (t->chunk < 1 || t->chunk > (1 << 20)) return trw_fail(TRW_ERR_INVALID, "chunk in [1, 2^20]");
+  if (t->coop_degree < 1) return trw_fail(TRW_ERR_INVALID, "coop_degree >= 1");
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->tuning = *t;
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_last_stats(const trw_graph* g, trw_stats* s) {
+  if (!g || !s) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  *s = g->last;
+  return TRW_OK;
+}
+
+// ------------------------------------------------------------------ debug
+
+extern "C" trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int32_t* second) {
+  if (!g || !H || !first || !second) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (!g->prepared_alias) return trw_fail(TRW_ERR_NOT_PREPARED, "no alias tables");
+  std::vector<uint4> rec((size_t)g->ne);
+  if (g->ne > 0) CUDA_TRY(cudaMemcpy(rec.data(), g->alias, sizeof(uint4) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy alias");
+  for (int64_t i = 0; i < g->ne; ++i) {
+    H[i] = rec[(size_t)i].x;
+    first[i] = (int32_t)rec[(size_t)i].y;
+    second[i] = (int32_t)rec[(size_t)i].z;
+  }
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_debug_philox(const uint32_t* ctr, int64_t n, uint32_t key0, uint32_t key1, uint32_t* out) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return trw_fail(TRW_ERR_INVALID, "bad arguments");
+  if (n == 0) return TRW_OK;
+  uint32_t *dc = nullptr, *dout = nullptr;
+  trw_status st = alloc_dev((void**)&dc, sizeof(uint32_t) * 4 * (size_t)n, "philox");
+  if (st != TRW_OK) return st;
+  st = alloc_dev((void**)&dout, sizeof(uint32_t) * 4 * (size_t)n, "philox");
+  if (st != TRW_OK) {
+    cudaFree(dc);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(dc, ctr, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_debug_philox(dc, n, key0, key1, dout, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(dc);
+  cudaFree(dout);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "philox");
+  return TRW_OK;
+}

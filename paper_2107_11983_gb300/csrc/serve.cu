@@ -1,0 +1,632 @@
+// Serving loop with continuous batching.
+//
+// Requests (any algorithm, any size) arrive while others run.  The host
+// writes a request's descriptor into a device slot table and publishes it by
+// bumping a counter in host-mapped memory.  A resident persistent kernel does
+// the rest:
+//   - warp 0 of block 0 is the dispatcher: it reads the published counter
+//     (the only reader of the host ring), cuts each new request into chunks of
+//     walks and pushes them into a device chunk queue;
+//   - every other warp is a worker: it pops chunks (CAS on the queue head),
+//     caches the request's descriptor in shared memory (loaded past L1, so a
+//     reused slot is never read stale), runs the walks with the same step code
+//     as the batch kernels and refills a lane as soon as its walk ends, so
+//     walks of different requests share warps;
+//   - when the last walk of a request ends, the lane that finished it fences
+//     and writes the request's done flag to host-mapped memory.
+// Every wait is bounded: with no work for idle_timeout_us the kernel exits,
+// and the host relaunches it when work is pending (submit, poll, drain).
+// Queue and dispatcher state live in device memory, so nothing is lost
+// between launches.
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "trw_api_internal.h"
+#include "walk_step.cuh"
+
+using namespace trw;
+
+namespace {
+
+constexpr int kCacheEntries = 4;      // request descriptors cached per warp
+constexpr uint32_t kQueueCap = 1u << 16;
+
+struct Chunk {
+  unsigned long long k;   // request number
+  uint32_t begin, end;    // walk range within the request
+};
+
+struct ServeState {       // device memory, persists across launches
+  unsigned long long q_head;      // next queue entry to pop
+  unsigned long long q_tail;      // entries pushed
+  unsigned long long q_consumed;  // entries popped and read
+  unsigned long long disp_k;      // dispatcher: next request to cut
+  unsigned long long disp_pos;    // dispatcher: next walk of that request
+  unsigned long long moves;       // total moves of finished walks
+  int err;
+  int pad;
+};
+
+struct ServeHost {        // host-mapped pinned memory
+  unsigned long long published;   // requests 0..published-1 are visible to the device
+  unsigned int stop;
+  unsigned int pad;
+};
+
+struct ServeDev {
+  ServeState* state;
+  Chunk* queue;                     // [kQueueCap]
+  const WalkSpec* specs;            // [R]
+  const uint32_t* chunk_walks;      // [R] walks per chunk for the request in each slot
+  unsigned long long* finished;     // [R] finished walks
+  int* err;                         // [R] first error of the request
+  volatile ServeHost* host;         // device pointer to host-mapped control
+  volatile unsigned long long* done;// [R] host-mapped: k + 1 once request k finished
+  volatile int* done_err;           // [R] host-mapped: status of request k
+  int R;
+  long long idle_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const volatile unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+
+// Dispatcher: cut published requests into chunks.  One warp; lane 0 works.
+__device__ void dispatcher(const ServeDev& sv) {
+  const int lane = threadIdx.x & 31;
+  long long idle_since = now_ns();
+  for (;;) {
+    int go = 1;
+    if (lane == 0) {
+      bool progress = false;
+      ServeState* st = sv.state;
+      const unsigned long long P = ld_acquire_sys(&sv.host->published);
+      unsigned long long k = st->disp_k, pos = st->disp_pos, tail = st->q_tail;
+      const unsigned long long consumed = ld_acquire_gpu(&st->q_consumed);
+      int pushed = 0;
+      while (k < P && tail - consumed < kQueueCap && pushed < 4096) {
+        const int slot = (int)(k % (unsigned long long)sv.R);
+        const unsigned long long n = (unsigned long long)__ldcg(&sv.specs[slot].nwalks);
+        if (pos >= n) {
+          ++k;
+          pos = 0;
+          continue;
+        }
+        const unsigned long long cw = __ldcg(&sv.chunk_walks[slot]);
+        const unsigned long long end = pos + cw < n ? pos + cw : n;
+        Chunk c;
+        c.k = k;
+        c.begin = (uint32_t)pos;
+        c.end = (uint32_t)end;
+        __stcg(&sv.queue[tail % kQueueCap].k, c.k);
+        __stcg(reinterpret_cast<uint2*>(&sv.queue[tail % kQueueCap].begin), make_uint2(c.begin, c.end));
+        ++tail;
+        ++pushed;
+        pos = end;
+        progress = true;
+      }
+      st->disp_k = k;
+      st->disp_pos = pos;
+      if (progress) {
+        __threadfence();
+        st_release_gpu(&st->q_tail, tail);
+        idle_since = now_ns();
+      } else {
+        const long long t = now_ns();
+        if (sv.host->stop) go = 0;
+        else if (t - idle_since > sv.idle_ns && ld_acquire_gpu(&st->q_consumed) == tail) go = 0;
+        else __nanosleep(2000);
+      }
+    }
+    go = __shfl_sync(0xffffffffu, go, 0);
+    if (!go) return;
+  }
+}
+
+__global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  WalkSpec* cache = reinterpret_cast<WalkSpec*>(smem_raw) + wid * kCacheEntries;
+  unsigned long long* cache_k =
+      reinterpret_cast<unsigned long long*>(smem_raw + sizeof(WalkSpec) * kCacheEntries * nwarps) + wid * kCacheEntries;
+  int32_t* stage_mem = reinterpret_cast<int32_t*>(smem_raw + (sizeof(WalkSpec) + 8) * kCacheEntries * nwarps);
+
+  if (blockIdx.x == 0 && wid == 0) {
+    dispatcher(sv);
+    return;
+  }
+  if (lane < kCacheEntries) cache_k[lane] = ~0ull;
+  __syncwarp();
+
+  const unsigned lt_mask = (1u << lane) - 1u;
+  step::Stage st;
+  st.buf = stage_mem + threadIdx.x * 8;
+  st.gpos = 0;
+  st.lo = 0;
+  step::Walker W;
+  W.w = 0; W.s = 0; W.cur = 0; W.prev = -1; W.off = W.d = W.poff = W.pd = 0; W.att = 0;
+  bool active = false;
+  int ent = 0;
+  int64_t walk = 0;
+  uint32_t wlo = 0, whi = 0;
+  int went = 0;
+  long long idle_since = now_ns();
+  unsigned long long moves_acc = 0;
+
+  for (;;) {
+    unsigned idle = __ballot_sync(0xffffffffu, !active);
+    while (idle != 0u) {
+      if (wlo >= whi) {
+        // A free cache entry is needed before popping a chunk.
+        int free_ent = -1;
+        for (int e = 0; e < kCacheEntries; ++e) {
+          const unsigned used = __ballot_sync(0xffffffffu, active && ent == e);
+          if (used == 0u && free_ent < 0) free_ent = e;
+        }
+        if (free_ent < 0) break;
+        unsigned long long ck = 0;
+        uint32_t cb = 0, ce = 0;
+        int got = 0;
+        if (lane == 0) {
+          ServeState* s = sv.state;
+          for (int tries = 0; tries < 64; ++tries) {
+            const unsigned long long h = *(volatile unsigned long long*)&s->q_head;
+            const unsigned long long t = ld_acquire_gpu(&s->q_tail);
+            if (h >= t) break;
+            if (atomicCAS(&s->q_head, h, h + 1) == h) {
+              const Chunk* c = &sv.queue[h % kQueueCap];
+              ck = __ldcg(&c->k);
+              const uint2 be = __ldcg(reinterpret_cast<const uint2*>(&c->begin));
+              cb = be.x;
+              ce = be.y;
+              __threadfence();
+              atomicAdd(&s->q_consumed, 1ull);
+              got = 1;
+              break;
+            }
+          }
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) break;
+        ck = __shfl_sync(0xffffffffu, ck, 0);
+        cb = __shfl_sync(0xffffffffu, cb, 0);
+        ce = __shfl_sync(0xffffffffu, ce, 0);
+        // Descriptor of request ck: reuse the cached copy or load it past L1.
+        int e_hit = -1;
+        for (int e = 0; e < kCacheEntries; ++e)
+          if (cache_k[e] == ck) e_hit = e;
+        if (e_hit < 0) {
+          e_hit = free_ent;
+          const int slot = (int)(ck % (unsigned long long)sv.R);
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(&sv.specs[slot]);
+          uint32_t* dst = reinterpret_cast<uint32_t*>(&cache[e_hit]);
+          for (int wd = lane; wd < (int)(sizeof(WalkSpec) / 4); wd += 32) dst[wd] = __ldcg(src + wd);
+          if (lane == 0) cache_k[e_hit] = ck;
+          __syncwarp();
+        }
+        wlo = cb;
+        whi = ce;
+        went = e_hit;
+      }
+      const int take = (int)min((uint32_t)__popc(idle), whi - wlo);
+      const int rank = __popc(idle & lt_mask);
+      if (((idle >> lane) & 1u) && rank < take) {
+        const WalkSpec& sp = cache[went];
+        walk = (int64_t)wlo + rank;
+        ent = went;
+        const int32_t src = __ldcg(sp.sources + walk / sp.wps);
+        W.w = sp.walk_offset + (uint32_t)walk;
+        W.s = 0;
+        W.cur = (src >= 0 && src < g.nv) ? src : 0;
+        W.prev = -1;
+        W.att = 0;
+        if (!sp.endpoints) {
+          st.gpos = walk * ((int64_t)sp.max_len + 1);
+          st.lo = (int)(st.gpos & 7);
+          step::stage_put(st, sp.out_paths, W.cur, (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0);
+        }
+        active = true;
+      }
+      wlo += (uint32_t)take;
+      idle = __ballot_sync(0xffffffffu, !active);
+    }
+
+    if (!__any_sync(0xffffffffu, active)) {
+      int go = 1;
+      if (lane == 0) {
+        const long long t = now_ns();
+        if (sv.host->stop) go = 0;
+        else if (t - idle_since > sv.idle_ns) go = 0;
+        else __nanosleep(1000);
+      }
+      if (!__shfl_sync(0xffffffffu, go, 0)) break;
+      continue;
+    }
+    idle_since = now_ns();
+
+    bool finishing = false;
+    if (active) {
+      const WalkSpec& sp = cache[ent];
+      const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
+      int32_t next = -1;
+      const int r = step::step_dispatch<MIXED>(g, sp, W, next);
+      if (r == step::kMoved) {
+        step::advance(W, next);
+        if (!sp.endpoints) step::stage_put(st, sp.out_paths, next, aligned);
+      } else if (r == step::kRetry) {
+        W.att += 1;
+      } else {
+        const int slot = (int)(cache_k[ent] % (unsigned long long)sv.R);
+        if (r == step::kFail) atomicCAS(&sv.err[slot], 0, kErrRejectCap);
+        if (r == step::kBroken) atomicCAS(&sv.err[slot], 0, kErrInternal);
+        if (sp.endpoints) __stcs(sp.out_paths + walk, W.cur);
+        else step::stage_finish(st, sp.out_paths, aligned);
+        __stcs(sp.out_lengths + walk, W.s + 1);
+        moves_acc += (unsigned long long)W.s;
+        finishing = true;
+        active = false;
+      }
+    }
+    // Completion counting, aggregated over the lanes of one request.
+    const unsigned fin = __ballot_sync(0xffffffffu, finishing);
+    if (finishing) {
+      const unsigned long long k = cache_k[ent];
+      const unsigned peers = __match_any_sync(fin, k);
+      const int leader = __ffs(peers) - 1;
+      __threadfence();  // this lane's outputs before its completion count
+      __syncwarp(peers);
+      if (lane == leader) {
+        const int slot = (int)(k % (unsigned long long)sv.R);
+        const unsigned long long cnt = (unsigned long long)__popc(peers);
+        const unsigned long long old = atomicAdd(&sv.finished[slot], cnt);
+        const unsigned long long n = (unsigned long long)cache[ent].nwalks;
+        if (old + cnt == n) {
+          __threadfence();
+          const int e = atomicAdd(&sv.err[slot], 0);
+          sv.done_err[slot] = e;
+          __threadfence_system();
+          sv.done[slot] = k + 1;
+          __threadfence_system();
+        }
+      }
+    }
+  }
+  const unsigned long long mv = step::warp_sum(moves_acc);
+  if (lane == 0 && mv) atomicAdd(&sv.state->moves, mv);
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------- host
+
+struct trw_server {
+  trw_graph* g = nullptr;
+  trw_serve_config cfg{};
+  int R = 0;
+  cudaStream_t stream = nullptr;       // the resident kernel
+  cudaStream_t copy_stream = nullptr;  // descriptor uploads
+  ServeState* state = nullptr;
+  Chunk* queue = nullptr;
+  WalkSpec* specs = nullptr;
+  uint32_t* chunk_walks = nullptr;
+  unsigned long long* finished = nullptr;
+  int* err = nullptr;
+  int32_t* src_pool = nullptr;         // device copies of request sources (ring allocator)
+  int64_t src_cap = 0;
+  ServeHost* host = nullptr;           // mapped
+  unsigned long long* done = nullptr;  // mapped [R]
+  int* done_err = nullptr;             // mapped [R]
+  ServeHost* host_dev = nullptr;
+  unsigned long long* done_dev = nullptr;
+  int* done_err_dev = nullptr;
+  WalkSpec* spec_stage = nullptr;      // pinned staging [R]
+  uint32_t* cw_stage = nullptr;        // pinned [R]
+  // host bookkeeping, ring order
+  unsigned long long next_k = 0;       // next request number
+  unsigned long long oldest = 0;       // oldest request not yet collected
+  std::vector<int64_t> req_walks, req_bytes, req_src_pos, req_src_n;
+  std::vector<char> collected;
+  int64_t inflight_walks = 0, inflight_bytes = 0;
+  int64_t src_head = 0;                // ring allocator: next free position
+  int block_threads = 256;
+  int grid_blocks = 0;
+  size_t smem = 0;
+  std::mutex mu;
+};
+
+extern "C" void trw_serve_config_default(trw_serve_config* c) {
+  if (!c) return;
+  c->max_inflight_walks = 1ll << 26;
+  c->max_inflight_bytes = 16ll << 30;
+  c->max_requests = 1024;
+  c->idle_timeout_us = 2000;
+}
+
+static void server_release(trw_server* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  cudaFree(s->state);
+  cudaFree(s->queue);
+  cudaFree(s->specs);
+  cudaFree(s->chunk_walks);
+  cudaFree(s->finished);
+  cudaFree(s->err);
+  cudaFree(s->src_pool);
+  if (s->host) cudaFreeHost(s->host);
+  if (s->done) cudaFreeHost(s->done);
+  if (s->done_err) cudaFreeHost(s->done_err);
+  if (s->spec_stage) cudaFreeHost(s->spec_stage);
+  if (s->cw_stage) cudaFreeHost(s->cw_stage);
+  delete s;
+}
+
+#define SV_TRY(call, what)                 \
+  do {                                     \
+    cudaError_t e_ = (call);               \
+    if (e_ != cudaSuccess) {               \
+      server_release(s);                   \
+      return trw_cuda_fail(e_, what);      \
+    }                                      \
+  } while (0)
+
+extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg_in, trw_server** out) {
+  if (!g || !out) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  trw_serve_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else trw_serve_config_default(&cfg);
+  if (cfg.max_requests < 1 || cfg.max_requests > 4096) return trw_fail(TRW_ERR_INVALID, "max_requests in [1, 4096]");
+  if (cfg.max_inflight_walks < 1 || cfg.max_inflight_walks > (1ll << 31))
+    return trw_fail(TRW_ERR_INVALID, "max_inflight_walks in [1, 2^31]");
+  if (cfg.max_inflight_bytes < 1) return trw_fail(TRW_ERR_INVALID, "max_inflight_bytes >= 1");
+  if (cfg.idle_timeout_us < 1 || cfg.idle_timeout_us > 10000000) return trw_fail(TRW_ERR_INVALID, "idle_timeout_us in [1, 1e7]");
+  trw_server* s = new trw_server();
+  s->g = g;
+  s->cfg = cfg;
+  s->R = cfg.max_requests;
+  s->src_cap = cfg.max_inflight_walks;
+  const int R = s->R;
+  SV_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking), "stream");
+  SV_TRY(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "stream");
+  SV_TRY(cudaMalloc(&s->state, sizeof(ServeState)), "serve state");
+  SV_TRY(cudaMemset(s->state, 0, sizeof(ServeState)), "serve state");
+  SV_TRY(cudaMalloc(&s->queue, sizeof(Chunk) * kQueueCap), "chunk queue");
+  SV_TRY(cudaMalloc(&s->specs, sizeof(WalkSpec) * R), "slot table");
+  SV_TRY(cudaMemset(s->specs, 0, sizeof(WalkSpec) * R), "slot table");
+  SV_TRY(cudaMalloc(&s->chunk_walks, sizeof(uint32_t) * R), "slot table");
+  SV_TRY(cudaMalloc(&s->finished, sizeof(unsigned long long) * R), "slot table");
+  SV_TRY(cudaMalloc(&s->err, sizeof(int) * R), "slot table");
+  SV_TRY(cudaMalloc(&s->src_pool, sizeof(int32_t) * (size_t)s->src_cap), "source pool");
+  SV_TRY(cudaHostAlloc(&s->host, sizeof(ServeHost), cudaHostAllocMapped), "mapped control");
+  SV_TRY(cudaHostAlloc(&s->done, sizeof(unsigned long long) * R, cudaHostAllocMapped), "mapped flags");
+  SV_TRY(cudaHostAlloc(&s->done_err, sizeof(int) * R, cudaHostAllocMapped), "mapped flags");
+  SV_TRY(cudaHostAlloc(&s->spec_stage, sizeof(WalkSpec) * R, cudaHostAllocDefault), "pinned staging");
+  SV_TRY(cudaHostAlloc(&s->cw_stage, sizeof(uint32_t) * R, cudaHostAllocDefault), "pinned staging");
+  std::memset((void*)s->host, 0, sizeof(ServeHost));
+  std::memset((void*)s->done, 0, sizeof(unsigned long long) * R);
+  std::memset((void*)s->done_err, 0, sizeof(int) * R);
+  SV_TRY(cudaHostGetDevicePointer((void**)&s->host_dev, (void*)s->host, 0), "mapped pointer");
+  SV_TRY(cudaHostGetDevicePointer((void**)&s->done_dev, (void*)s->done, 0), "mapped pointer");
+  SV_TRY(cudaHostGetDevicePointer((void**)&s->done_err_dev, (void*)s->done_err, 0), "mapped pointer");
+  s->req_walks.assign(R, 0);
+  s->req_bytes.assign(R, 0);
+  s->req_src_pos.assign(R, 0);
+  s->req_src_n.assign(R, 0);
+  s->collected.assign(R, 1);
+  s->block_threads = 256;
+  const int nwarps = s->block_threads / 32;
+  s->smem = (sizeof(WalkSpec) + 8) * kCacheEntries * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t);
+  int bps = 0;
+  SV_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, serve_kernel, s->block_threads, s->smem), "occupancy");
+  if (bps < 1) bps = 1;
+  s->grid_blocks = g->num_sms * bps;
+  *out = s;
+  return TRW_OK;
+}
+
+static cudaError_t launch_if_idle(trw_server* s) {
+  if (s->oldest == s->next_k) return cudaSuccess;  // nothing in flight
+  cudaError_t q = cudaStreamQuery(s->stream);
+  if (q == cudaErrorNotReady) return cudaSuccess;  // running
+  if (q != cudaSuccess) return q;
+  ServeDev sv;
+  sv.state = s->state;
+  sv.queue = s->queue;
+  sv.specs = s->specs;
+  sv.chunk_walks = s->chunk_walks;
+  sv.finished = s->finished;
+  sv.err = s->err;
+  sv.host = s->host_dev;
+  sv.done = s->done_dev;
+  sv.done_err = s->done_err_dev;
+  sv.R = s->R;
+  sv.idle_ns = (long long)s->cfg.idle_timeout_us * 1000;
+  serve_kernel<<<s->grid_blocks, s->block_threads, s->smem, s->stream>>>(trw_dev_graph(s->g), sv);
+  return cudaGetLastError();
+}
+
+// Collect finished requests at the front of the ring (frees their slots and source ranges).
+static void retire_front(trw_server* s) {
+  while (s->oldest < s->next_k && s->collected[s->oldest % s->R]) ++s->oldest;
+}
+
+extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* params, const int32_t* sources,
+                                       int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
+                                       int32_t* out_lengths, uint64_t* req_id) {
+  if (!s || !req_id) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  WalkSpec sp;
+  trw_status stt = trw_make_spec(s->g, algo, params, n_sources, max_len, seed, &sp);
+  if (stt != TRW_OK) return stt;
+  if (sp.nwalks > 0 && (!sources || !out_paths || !out_lengths)) return trw_fail(TRW_ERR_INVALID, "NULL buffer");
+  if (sp.nwalks > 0 && (!trw_is_device_ptr(out_paths) || !trw_is_device_ptr(out_lengths)))
+    return trw_fail(TRW_ERR_INVALID, "serve outputs must be device buffers");
+  const bool src_dev = trw_is_device_ptr(sources);
+  if (!src_dev)
+    for (int64_t i = 0; i < n_sources; ++i)
+      if (sources[i] < 0 || sources[i] >= s->g->nv) return trw_fail(TRW_ERR_INVALID, "source %lld out of range", (long long)i);
+  const int64_t out_bytes =
+      (int64_t)sizeof(int32_t) * (sp.endpoints ? sp.nwalks : sp.nwalks * ((int64_t)max_len + 1)) + 4 * sp.nwalks;
+  std::lock_guard<std::mutex> lk(s->mu);
+  retire_front(s);
+  if (s->next_k - s->oldest >= (unsigned long long)s->R) return trw_fail(TRW_ERR_BUSY, "all %d request slots in use", s->R);
+  if (n_sources > s->src_cap || s->inflight_walks + sp.nwalks > s->cfg.max_inflight_walks)
+    return trw_fail(TRW_ERR_BUSY, "walk admission limit %lld reached", (long long)s->cfg.max_inflight_walks);
+  if (s->inflight_bytes + out_bytes > s->cfg.max_inflight_bytes)
+    return trw_fail(TRW_ERR_BUSY, "output byte admission limit reached");
+  // Ring allocation of the source copy, in request order: live ranges run
+  // circularly from the oldest live request's range up to src_head.
+  int64_t pos = -1;
+  if (s->oldest == s->next_k) {
+    s->src_head = 0;
+    if (n_sources <= s->src_cap) pos = 0;
+  } else {
+    const int64_t lo_live = s->req_src_pos[s->oldest % s->R];
+    if (lo_live < s->src_head) {  // free: [src_head, cap) and [0, lo_live)
+      if (s->src_head + n_sources <= s->src_cap) pos = s->src_head;
+      else if (n_sources <= lo_live) pos = 0;
+    } else if (lo_live > s->src_head) {  // free: [src_head, lo_live)
+      if (s->src_head + n_sources <= lo_live) pos = s->src_head;
+    } else if (n_sources == 0) {
+      pos = s->src_head;
+    }
+  }
+  if (pos < 0) return trw_fail(TRW_ERR_BUSY, "source pool full");
+  const unsigned long long k = s->next_k;
+  const int slot = (int)(k % (unsigned long long)s->R);
+  sp.sources = s->src_pool + pos;
+  sp.out_paths = out_paths;
+  sp.out_lengths = out_lengths;
+  // walks per chunk: about 4096 expected moves
+  double exp_moves = (double)max_len;
+  if (algo == TRW_PPR && params && params->ppr_stop > 0) exp_moves = std::min(exp_moves, 1.0 / params->ppr_stop);
+  if (exp_moves < 1) exp_moves = 1;
+  uint32_t cw = (uint32_t)std::max(16.0, std::min(2048.0, 4096.0 / exp_moves));
+  s->spec_stage[slot] = sp;
+  s->cw_stage[slot] = cw;
+  cudaStream_t cs = s->copy_stream;
+  cudaError_t e = cudaSuccess;
+  if (n_sources > 0)
+    e = cudaMemcpyAsync(s->src_pool + pos, sources, sizeof(int32_t) * (size_t)n_sources,
+                        src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->specs[slot], &s->spec_stage[slot], sizeof(WalkSpec), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->chunk_walks[slot], &s->cw_stage[slot], sizeof(uint32_t), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&s->finished[slot], 0, sizeof(unsigned long long), cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&s->err[slot], 0, sizeof(int), cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit upload");
+  if (src_dev) {
+    // device sources are validated on the host side of the copy: check the pool copy
+    std::vector<int32_t> tmp((size_t)n_sources);
+    if (n_sources > 0) {
+      e = cudaMemcpy(tmp.data(), s->src_pool + pos, sizeof(int32_t) * (size_t)n_sources, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit check");
+      for (int64_t i = 0; i < n_sources; ++i)
+        if (tmp[(size_t)i] < 0 || tmp[(size_t)i] >= s->g->nv) return trw_fail(TRW_ERR_INVALID, "source %lld out of range", (long long)i);
+    }
+  }
+  s->done[slot] = 0;
+  s->done_err[slot] = 0;
+  s->req_walks[slot] = sp.nwalks;
+  s->req_bytes[slot] = out_bytes;
+  s->req_src_pos[slot] = pos;
+  s->req_src_n[slot] = n_sources;
+  s->collected[slot] = 0;
+  s->inflight_walks += sp.nwalks;
+  s->inflight_bytes += out_bytes;
+  s->src_head = pos + n_sources;
+  s->next_k = k + 1;
+  if (sp.nwalks == 0) {
+    s->done[slot] = k + 1;  // nothing to run
+  }
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  reinterpret_cast<volatile unsigned long long*>(&s->host->published)[0] = k + 1;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  e = launch_if_idle(s);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel launch");
+  *req_id = k;
+  return TRW_OK;
+}
+
+static trw_status poll_locked(trw_server* s, uint64_t k) {
+  if (k >= s->next_k || k + (unsigned long long)s->R < s->next_k) return trw_fail(TRW_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)k);
+  const int slot = (int)(k % (unsigned long long)s->R);
+  if (s->collected[slot]) return trw_fail(TRW_ERR_NOT_FOUND, "request %llu already collected", (unsigned long long)k);
+  const unsigned long long d = reinterpret_cast<volatile unsigned long long*>(s->done)[slot];
+  if (d != k + 1) {
+    cudaError_t e = launch_if_idle(s);
+    if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel relaunch");
+    return TRW_PENDING;
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  const int err = reinterpret_cast<volatile int*>(s->done_err)[slot];
+  s->collected[slot] = 1;
+  s->inflight_walks -= s->req_walks[slot];
+  s->inflight_bytes -= s->req_bytes[slot];
+  retire_front(s);
+  if (err == kErrRejectCap) return trw_fail(TRW_ERR_REJECT_CAP, "request %llu: a rejection step hit the cap", (unsigned long long)k);
+  if (err != 0) return trw_fail(TRW_ERR_INTERNAL, "request %llu: device status %d", (unsigned long long)k, err);
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_serve_poll(trw_server* s, uint64_t req_id) {
+  if (!s) return trw_fail(TRW_ERR_INVALID, "NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  return poll_locked(s, req_id);
+}
+
+extern "C" trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms) {
+  if (!s) return trw_fail(TRW_ERR_INVALID, "NULL server");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      bool pending = false;
+      for (unsigned long long k = s->oldest; k < s->next_k; ++k) {
+        const int slot = (int)(k % (unsigned long long)s->R);
+        if (s->collected[slot]) continue;
+        const unsigned long long d = reinterpret_cast<volatile unsigned long long*>(s->done)[slot];
+        if (d != k + 1) pending = true;
+      }
+      if (!pending) return TRW_OK;
+      cudaError_t e = launch_if_idle(s);
+      if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel relaunch");
+    }
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+      return trw_fail(TRW_ERR_TIMEOUT, "requests still running after %d ms", timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+extern "C" void trw_serve_destroy(trw_server* s) {
+  if (!s) return;
+  reinterpret_cast<volatile unsigned int*>(&s->host->stop)[0] = 1u;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  cudaStreamSynchronize(s->stream);
+  server_release(s);
+}

@@ -1,0 +1,50 @@
+// The opaque handles of the C ABI and helpers shared by api.cu, serve.cu and
+// autotune.cu.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "../../include/trw.h"
+#include "trw_internal.h"
+
+struct trw_graph {
+  int64_t nv = 0, ne = 0;
+  int device = 0;
+  int num_sms = 1;
+  bool sorted = false;
+  bool prepared_alias = false;
+  int32_t* row_ptr = nullptr;        // [nv + 1]
+  int32_t* col = nullptr;            // [ne]
+  float* weights = nullptr;          // [ne] or null
+  uint8_t* labels = nullptr;         // [ne + 64] or null
+  uint4* alias = nullptr;            // [ne] after trw_prepare(ALIAS)
+  trw::Ctrl* ctrl = nullptr;         // per-call control block
+  void* misc = nullptr;              // 256 bytes of flags
+  int32_t* src_stage = nullptr;      // staging for host buffers (grow-only)
+  size_t src_cap = 0;
+  int32_t* out_stage = nullptr;
+  size_t out_cap = 0;
+  int32_t* len_stage = nullptr;
+  size_t len_cap = 0;
+  char* batch_specs = nullptr;       // device table of a mixed batch
+  char* batch_host = nullptr;        // pinned staging of that table
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  trw_tuning tuning{};
+  trw_stats last{};
+  int64_t device_bytes = 0;
+  std::mutex mu;
+};
+
+trw_status trw_fail(trw_status st, const char* fmt, ...);
+trw_status trw_cuda_fail(cudaError_t e, const char* what);
+bool trw_is_device_ptr(const void* p);
+trw_status trw_grow(void** p, size_t* cap, size_t need);
+trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* p, int64_t n_sources, int32_t max_len,
+                         uint64_t seed, trw::WalkSpec* sp);
+trw::LaunchCfg trw_launch_cfg(const trw_graph* g, int algo);
+trw::DevGraph trw_dev_graph(const trw_graph* g);

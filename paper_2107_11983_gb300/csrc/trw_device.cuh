@@ -1,0 +1,99 @@
+// Device-side building blocks of the walk kernels: the Philox4x32-10 block
+// function, fixed-point sampling helpers, and the structs that describe a
+// loaded graph and one walk request to a kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace trw {
+
+enum Algo : int { DEEPWALK = 0, DEEPWALK_WEIGHTED = 1, PPR = 2, NODE2VEC = 3, METAPATH = 4, MIXED = 5 };
+
+constexpr int kMaxSchema = 16;
+constexpr uint32_t kRejectCap = 65536;
+
+// Status words a kernel may leave in the control block.
+constexpr int kErrInvalid = -1;
+constexpr int kErrRejectCap = -6;
+constexpr int kErrInternal = -9;
+
+// A CSR graph resident in HBM.  Offsets and ids are int32 (nv, ne < 2^31).
+struct DevGraph {
+  const int32_t* __restrict__ row_ptr;   // [nv + 1]
+  const int32_t* __restrict__ col;       // [ne], rows sorted ascending when sorted != 0
+  const uint4* __restrict__ alias;       // [ne] {H, first dst, second dst, 0}, or null
+  const uint8_t* __restrict__ labels;    // [ne + 16] (padded for word loads), or null
+  int32_t nv;
+  int32_t ne;
+};
+
+// One walk request as a kernel sees it.  Thresholds are fixed-point
+// probabilities in [0, 2^32]: a 32-bit word y succeeds when y < T.
+struct WalkSpec {
+  int32_t algo;
+  int32_t max_len;            // moves
+  uint32_t wps;               // walks per source
+  uint32_t endpoints;         // 1: one output vertex per walk
+  uint32_t key0, key1;        // Philox key (seed)
+  uint32_t walk_offset;       // Philox counter word 0 of walk 0
+  uint32_t schema_len;
+  uint64_t T_stop;            // PPR stop threshold
+  uint64_t T_ret, T_nb, T_far;// Node2Vec O-REJ thresholds (Eq. 1 over p*)
+  uint64_t T_lo, T_hi;        // min / max of T_nb, T_far (skip IsNeighbor outside [T_lo, T_hi))
+  const int32_t* sources;
+  int32_t* out_paths;
+  int32_t* out_lengths;
+  int64_t nwalks;
+  uint64_t schema_lo;         // MetaPath labels H[0..7], byte k = H[k]
+  uint64_t schema_hi;         // H[8..15]
+};
+
+// MetaPath label H[k] of a packed schema (no dynamic indexing into local memory).
+__device__ __forceinline__ uint32_t schema_label(const WalkSpec& sp, uint32_t k) {
+  const uint64_t w = k < 8 ? sp.schema_lo : sp.schema_hi;
+  return (uint32_t)(w >> (8 * (k & 7))) & 0xffu;
+}
+
+// Control block shared by the launches of one call (device memory).
+struct Ctrl {
+  unsigned long long head;    // next unclaimed walk of the work queue
+  unsigned long long moves;   // total moves taken
+  int err;                    // first error status (0 = none)
+  int pad;
+};
+
+// ------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy as 1, 2, 3"
+// (SC 2011): ten rounds of two 32x32->64 multiplies with a word swap and a
+// round key; the key advances by the Weyl constants after every round.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Draw `draw` of step `step` of walk `w`.
+__device__ __forceinline__ uint4 draw_block(const WalkSpec& sp, uint32_t w, uint32_t step, uint32_t draw) {
+  return philox10(make_uint4(w, step, draw, 0u), sp.key0, sp.key1);
+}
+
+// Uniform integer in [0, n): high 64 bits of r64 * n, r64 = (B.y:B.x).
+__device__ __forceinline__ uint32_t below(uint4 B, uint32_t n) {
+  const unsigned long long r64 = ((unsigned long long)B.y << 32) | B.x;
+  return (uint32_t)__umul64hi(r64, (unsigned long long)n);
+}
+
+// Read-only loads through the non-coherent path.
+__device__ __forceinline__ int32_t ldg(const int32_t* p) { return __ldg(p); }
+__device__ __forceinline__ uint4 ldg(const uint4* p) { return __ldg(p); }
+
+}  // namespace trw

@@ -1,0 +1,40 @@
+// Host-side declarations shared by the translation units of libtrw.so.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "trw_device.cuh"
+
+namespace trw {
+
+struct LaunchCfg {
+  int block_threads = 256;
+  int grid_blocks = 0;       // persistent: resident blocks over all SMs
+  int chunk = 32;            // walks per warp claim
+  int coop_degree = 256;     // rows this long or longer use warp-cooperative scans
+};
+
+// Occupancy-derived resident blocks per SM of the persistent kernel for algo.
+int persistent_blocks_per_sm(int algo, int block_threads);
+
+cudaError_t launch_validate_sources(const int32_t* src, int64_t n, int32_t nv, Ctrl* ctrl, cudaStream_t st);
+cudaError_t launch_walk_plain(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl, cudaStream_t st, int block);
+cudaError_t launch_walk_persistent(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl, cudaStream_t st,
+                                   const LaunchCfg& cfg);
+cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const int64_t* d_prefix, int nreq,
+                              int64_t total, Ctrl* ctrl, cudaStream_t st, const LaunchCfg& cfg);
+
+// ALIAS preprocessing (Algorithm 3) on the device.
+cudaError_t launch_prepare_alias(int32_t nv, const int32_t* row_ptr, const int32_t* col, const float* weights,
+                                 uint4* alias, unsigned long long* q_scratch, int32_t* small_scratch,
+                                 int32_t* large_scratch, Ctrl* ctrl, cudaStream_t st);
+
+// Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).
+cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl,
+                               int* d_unsorted, cudaStream_t st);
+
+cudaError_t launch_debug_philox(const uint32_t* d_ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* d_out,
+                                cudaStream_t st);
+
+}  // namespace trw

@@ -1,0 +1,283 @@
+// Walk kernels: one step of Algorithm 2 (Gather, Move, Update) per call of
+// step_once, and the two ways of driving it:
+//   walk_plain       the baseline: one thread per walk for its whole length,
+//                    one launch for the batch, no refill, direct path stores;
+//   walk_persistent  one resident grid; each warp claims chunks of walks from a
+//                    device work queue and refills a lane as soon as its walk
+//                    ends (Algorithm 4's "replace a completed query" done on
+//                    the GPU), stages paths in shared memory and flushes whole
+//                    32-byte sectors, and hands long rows to the whole warp.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "trw_device.cuh"
+#include "trw_internal.h"
+#include "walk_step.cuh"
+
+namespace trw {
+
+namespace {
+
+using namespace step;
+
+// ------------------------------------------------------------ plain baseline
+
+template <int A>
+__global__ void __launch_bounds__(256) walk_plain(DevGraph g, WalkSpec sp, Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->err != 0) return;  // the call was rejected: write nothing
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long moves = 0;
+  if (i < sp.nwalks) {
+    const int32_t src = sp.sources[i / sp.wps];
+    if (src >= 0 && src < g.nv) {
+      Walker W;
+      W.w = sp.walk_offset + (uint32_t)i;
+      W.s = 0;
+      W.cur = src;
+      W.prev = -1;
+      W.off = W.d = W.poff = W.pd = 0;
+      W.att = 0;
+      const int64_t base = sp.endpoints ? i : i * ((int64_t)sp.max_len + 1);
+      if (!sp.endpoints) sp.out_paths[base] = src;
+      for (;;) {
+        int32_t next = -1;
+        const int r = step_dispatch<A>(g, sp, W, next);
+        if (r == kMoved) {
+          advance(W, next);
+          if (!sp.endpoints) sp.out_paths[base + W.s] = next;
+        } else if (r == kRetry) {
+          W.att += 1;
+        } else {
+          if (r == kFail) set_err(ctrl, kErrRejectCap);
+          if (r == kBroken) set_err(ctrl, kErrInternal);
+          break;
+        }
+      }
+      if (sp.endpoints) sp.out_paths[i] = W.cur;
+      sp.out_lengths[i] = W.s + 1;
+      moves = (unsigned long long)W.s;
+    } else {
+      set_err(ctrl, kErrInvalid);
+    }
+  }
+  moves = warp_sum(moves);
+  if ((threadIdx.x & 31) == 0 && moves) atomicAdd(&ctrl->moves, moves);
+}
+
+// -------------------------------------------------------- persistent kernel
+
+template <int A>
+__global__ void __launch_bounds__(1024) walk_persistent(DevGraph g, WalkSpec sp0, const WalkSpec* __restrict__ specs,
+                                                       const int64_t* __restrict__ prefix, int nreq, int64_t total,
+                                                       Ctrl* ctrl, int chunk) {
+  extern __shared__ int32_t stage_mem[];
+  if (*(volatile int*)&ctrl->err != 0) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  Stage st;
+  st.buf = stage_mem + threadIdx.x * 8;
+  st.gpos = 0;
+  st.lo = 0;
+  Walker W;
+  W.w = 0; W.s = 0; W.cur = 0; W.prev = -1; W.off = W.d = W.poff = W.pd = 0; W.att = 0;
+  bool active = false;
+  int req = 0;
+  int64_t walk = 0;  // walk index within its request
+
+  int64_t wlo = 0, whi = 0;
+  bool exhausted = false;
+  unsigned long long moves = 0;
+
+  for (;;) {
+    // ---- refill idle lanes from the work queue (warp-uniform control flow)
+    unsigned idle = __ballot_sync(kFull, !active);
+    while (idle != 0u && !exhausted) {
+      if (wlo >= whi) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctrl->head, (unsigned long long)chunk);
+        base = __shfl_sync(kFull, base, 0);
+        if ((int64_t)base >= total) {
+          exhausted = true;
+          break;
+        }
+        wlo = (int64_t)base;
+        whi = min((int64_t)base + chunk, total);
+      }
+      const int take = (int)min((int64_t)__popc(idle), whi - wlo);
+      const int rank = __popc(idle & lt_mask);
+      if (((idle >> lane) & 1u) && rank < take) {
+        const int64_t gidx = wlo + rank;
+        if (A == MIXED) {
+          req = 0;
+          while (req + 1 < nreq && __ldg(prefix + req + 1) <= gidx) ++req;
+          walk = gidx - __ldg(prefix + req);
+        } else {
+          walk = gidx;
+        }
+        const WalkSpec& sp = (A == MIXED) ? specs[req] : sp0;
+        const int32_t src = sp.sources[walk / sp.wps];
+        if (src >= 0 && src < g.nv) {
+          W.w = sp.walk_offset + (uint32_t)walk;
+          W.s = 0;
+          W.cur = src;
+          W.prev = -1;
+          W.att = 0;
+          if (!sp.endpoints) {
+            st.gpos = walk * ((int64_t)sp.max_len + 1);
+            st.lo = (int)(st.gpos & 7);
+            stage_put(st, sp.out_paths, src, (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0);
+          }
+          active = true;
+        } else {
+          set_err(ctrl, kErrInvalid);
+        }
+      }
+      wlo += take;
+      idle = __ballot_sync(kFull, !active);
+    }
+    if (!__any_sync(kFull, active)) break;
+
+    // ---- one unit of work per active lane
+    if (active) {
+      const WalkSpec& sp = (A == MIXED) ? specs[req] : sp0;
+      const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
+      int32_t next = -1;
+      const int r = step_dispatch<A>(g, sp, W, next);
+      if (r == kMoved) {
+        advance(W, next);
+        if (!sp.endpoints) stage_put(st, sp.out_paths, next, aligned);
+      } else if (r == kRetry) {
+        W.att += 1;
+      } else {
+        if (r == kFail) set_err(ctrl, kErrRejectCap);
+        if (r == kBroken) set_err(ctrl, kErrInternal);
+        if (sp.endpoints) {
+          __stcs(sp.out_paths + walk, W.cur);
+        } else {
+          stage_finish(st, sp.out_paths, aligned);
+        }
+        __stcs(sp.out_lengths + walk, W.s + 1);
+        moves += (unsigned long long)W.s;
+        active = false;
+      }
+    }
+  }
+  moves = warp_sum(moves);
+  if (lane == 0 && moves) atomicAdd(&ctrl->moves, moves);
+}
+
+__global__ void validate_sources(const int32_t* __restrict__ src, int64_t n, int32_t nv, Ctrl* ctrl) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = src[i];
+    if (v < 0 || v >= nv) set_err(ctrl, kErrInvalid);
+  }
+}
+
+__global__ void debug_philox(const uint4* __restrict__ ctr, int64_t n, uint32_t k0, uint32_t k1,
+                             uint4* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox10(ctr[i], k0, k1);
+}
+
+template <typename K>
+int blocks_per_sm_of(K kernel, int threads) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, (size_t)threads * 32) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace
+
+int persistent_blocks_per_sm(int algo, int block_threads) {
+  switch (algo) {
+    case DEEPWALK: return blocks_per_sm_of(walk_persistent<DEEPWALK>, block_threads);
+    case DEEPWALK_WEIGHTED: return blocks_per_sm_of(walk_persistent<DEEPWALK_WEIGHTED>, block_threads);
+    case PPR: return blocks_per_sm_of(walk_persistent<PPR>, block_threads);
+    case NODE2VEC: return blocks_per_sm_of(walk_persistent<NODE2VEC>, block_threads);
+    case METAPATH: return blocks_per_sm_of(walk_persistent<METAPATH>, block_threads);
+    default: return blocks_per_sm_of(walk_persistent<MIXED>, block_threads);
+  }
+}
+
+cudaError_t launch_validate_sources(const int32_t* src, int64_t n, int32_t nv, Ctrl* ctrl, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  validate_sources<<<(unsigned)blocks, 256, 0, st>>>(src, n, nv, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_plain(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl, cudaStream_t st, int block) {
+  (void)block;
+  if (sp.nwalks <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = (sp.nwalks + threads - 1) / threads;
+  switch (sp.algo) {
+    case DEEPWALK: walk_plain<DEEPWALK><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case DEEPWALK_WEIGHTED: walk_plain<DEEPWALK_WEIGHTED><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case PPR: walk_plain<PPR><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case NODE2VEC: walk_plain<NODE2VEC><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case METAPATH: walk_plain<METAPATH><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_persistent(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl, cudaStream_t st,
+                                   const LaunchCfg& cfg) {
+  if (sp.nwalks <= 0) return cudaSuccess;
+  const int threads = cfg.block_threads;
+  const size_t smem = (size_t)threads * 8 * sizeof(int32_t);
+  int64_t blocks = cfg.grid_blocks;
+  const int64_t need = (sp.nwalks + threads - 1) / threads;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  const dim3 grid((unsigned)blocks);
+  switch (sp.algo) {
+    case DEEPWALK:
+      walk_persistent<DEEPWALK><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
+      break;
+    case DEEPWALK_WEIGHTED:
+      walk_persistent<DEEPWALK_WEIGHTED><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl,
+                                                                      cfg.chunk);
+      break;
+    case PPR:
+      walk_persistent<PPR><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
+      break;
+    case NODE2VEC:
+      walk_persistent<NODE2VEC><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
+      break;
+    case METAPATH:
+      walk_persistent<METAPATH><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const int64_t* d_prefix, int nreq,
+                              int64_t total, Ctrl* ctrl, cudaStream_t st, const LaunchCfg& cfg) {
+  if (total <= 0) return cudaSuccess;
+  const int threads = cfg.block_threads;
+  const size_t smem = (size_t)threads * 8 * sizeof(int32_t);
+  int64_t blocks = cfg.grid_blocks;
+  const int64_t need = (total + threads - 1) / threads;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  WalkSpec dummy{};
+  walk_persistent<MIXED><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total, ctrl,
+                                                                   cfg.chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_philox(const uint32_t* d_ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* d_out,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  debug_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const uint4*>(d_ctr), n, k0, k1,
+                                                             reinterpret_cast<uint4*>(d_out));
+  return cudaGetLastError();
+}
+
+}  // namespace trw

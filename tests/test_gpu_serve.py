@@ -1,0 +1,152 @@
+"""Serving loop (GPU only): requests of different algorithms and sizes join a
+running persistent kernel, and every result is bit-identical to the oracle,
+alone or in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+import paper_2107_11983_gb300 as trw
+import synth
+from gpu_common import assert_paths_equal, oracle_alias, oracle_walk, rmat_graph
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SCALE = 12
+SCHEMA = np.array([1, 3, 0, 4, 2], np.uint8)
+
+
+@pytest.fixture(scope="module")
+def served():
+    g = rmat_graph(SCALE)
+    G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
+    G.prepare()
+    return g, G
+
+
+def make_request(g, i, rng):
+    kind = i % 5
+    n = int(rng.integers(1, 3000))
+    src = synth.sources(n, g.nv, seed=100 + i)
+    if kind == 0:
+        return dict(algo=trw.PPR, sources=src[:1], walks_per_source=n, max_len=1000, seed=i, ppr_stop=0.2,
+                    endpoints=True)
+    if kind == 1:
+        return dict(algo=trw.DEEPWALK, sources=src, max_len=80, seed=i)
+    if kind == 2:
+        return dict(algo=trw.DEEPWALK_WEIGHTED, sources=src, max_len=80, seed=i)
+    if kind == 3:
+        return dict(algo=trw.NODE2VEC, sources=src, max_len=80, seed=i, n2v_p=0.5, n2v_q=2.0)
+    return dict(algo=trw.METAPATH, sources=src, max_len=60, seed=i, schema=SCHEMA)
+
+
+def submit(S, r):
+    n = r["sources"].shape[0] * r.get("walks_per_source", 1)
+    shape = (n,) if r.get("endpoints") else (n, r["max_len"] + 1)
+    op = torch.full(shape, -1, dtype=torch.int32, device="cuda")
+    ol = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    kw = {k: r[k] for k in ("ppr_stop", "n2v_p", "n2v_q", "schema", "walks_per_source", "endpoints") if k in r}
+    rid = S.submit(r["algo"], r["sources"], r["max_len"], r["seed"], op, ol, **kw)
+    return rid, op, ol
+
+
+def check(g, r, op, ol):
+    kw = {k: r[k] for k in ("ppr_stop", "n2v_p", "n2v_q", "schema", "walks_per_source") if k in r}
+    want = oracle_walk(g, r["algo"], r["sources"], r["max_len"], r["seed"],
+                       alias=oracle_alias(SCALE) if r["algo"] == trw.DEEPWALK_WEIGHTED else None,
+                       endpoints_only=r.get("endpoints", False), **kw)
+    assert_paths_equal(op.cpu().numpy(), ol.cpu().numpy(), want, endpoints=r.get("endpoints", False))
+
+
+def wait(S, rid, timeout=60.0):
+    t = time.time()
+    while S.poll(rid) == trw.PENDING:
+        assert time.time() - t < timeout, f"request {rid} did not finish"
+        time.sleep(0.0005)
+
+
+def test_serve_mix_matches_oracle(served):
+    g, G = served
+    S = trw.Server(G, max_requests=64)
+    rng = np.random.default_rng(0)
+    reqs = [make_request(g, i, rng) for i in range(40)]
+    live = []
+    for r in reqs:  # submitted back to back: later requests join the running kernel
+        live.append((r,) + submit(S, r))
+    for r, rid, op, ol in live:
+        wait(S, rid)
+        check(g, r, op, ol)
+    S.close()
+
+
+def test_serve_same_alone_and_in_mix(served):
+    g, G = served
+    rng = np.random.default_rng(1)
+    reqs = [make_request(g, i, rng) for i in range(10)]
+    S = trw.Server(G, max_requests=32)
+    alone = []
+    for r in reqs:
+        rid, op, ol = submit(S, r)
+        wait(S, rid)
+        alone.append((op.clone(), ol.clone()))
+    # now the same requests overlapped with a large background request
+    big = dict(algo=trw.NODE2VEC, sources=synth.vertex_sources(g.nv), max_len=80, seed=999, n2v_p=0.5, n2v_q=2.0)
+    brid, bop, bol = submit(S, big)
+    mixed = [submit(S, r) for r in reqs]
+    for (rid, op, ol), (aop, aol) in zip(mixed, alone):
+        wait(S, rid)
+        assert torch.equal(ol, aol)
+        if op.dim() == 1:
+            assert torch.equal(op, aop)
+        else:
+            mask = torch.arange(op.shape[1], device="cuda")[None, :] < ol[:, None]
+            assert torch.equal(op[mask], aop[mask])
+    wait(S, brid)
+    check(g, big, bop, bol)
+    S.close()
+
+
+def test_serve_admission_and_ids(served):
+    g, G = served
+    S = trw.Server(G, max_requests=4, max_inflight_walks=5000)
+    r = dict(algo=trw.DEEPWALK, sources=synth.sources(3000, g.nv, seed=5), max_len=80, seed=1)
+    rid, op, ol = submit(S, r)
+    # too many walks in flight -> busy, nothing queued
+    with pytest.raises(trw.TRWError) as e:
+        submit(S, dict(r, sources=synth.sources(2500, g.nv, seed=6)))
+    assert e.value.status == -7
+    wait(S, rid)
+    check(g, r, op, ol)
+    with pytest.raises(trw.TRWError) as e:
+        S.poll(rid)  # already collected
+    assert e.value.status == -8
+    with pytest.raises(trw.TRWError) as e:
+        S.poll(12345)
+    assert e.value.status == -8
+    # more requests than slots, in sequence: slots and source ranges are reused
+    for i in range(12):
+        rr = dict(algo=trw.PPR, sources=synth.sources(1, g.nv, seed=i), walks_per_source=1000, max_len=1000,
+                  seed=i, ppr_stop=0.2, endpoints=True)
+        rid, op, ol = submit(S, rr)
+        wait(S, rid)
+        check(g, rr, op, ol)
+    # invalid requests are refused at submit
+    with pytest.raises(trw.TRWError) as e:
+        submit(S, dict(r, sources=np.array([g.nv], np.int32)))
+    assert e.value.status == -1
+    S.close()
+
+
+def test_serve_relaunch_after_idle(served):
+    g, G = served
+    S = trw.Server(G, max_requests=8, idle_timeout_us=200)
+    for i in range(3):
+        r = dict(algo=trw.DEEPWALK_WEIGHTED, sources=synth.sources(500, g.nv, seed=40 + i), max_len=30, seed=i)
+        rid, op, ol = submit(S, r)
+        wait(S, rid)
+        check(g, r, op, ol)
+        time.sleep(0.05)  # longer than the idle timeout: the resident kernel exits
+    S.drain(10000)
+    S.close()
