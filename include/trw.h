@@ -257,7 +257,9 @@ trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg, trw_serve
 
 /*
  * Submit a request (same meaning as trw_walk; out_paths and out_lengths must be
- * DEVICE buffers that stay valid until poll returns TRW_OK or an error).
+ * DEVICE buffers that stay valid until poll returns TRW_OK or an error, and
+ * that no other stream still writes when submit is called: the server runs
+ * on its own streams and does not order itself after the caller's).
  * sources may be host or device; it is copied at submit.  Returns
  * TRW_ERR_BUSY when admitting it would exceed the configured walk, byte or
  * slot limits (nothing is queued), else queues it and writes *req_id.

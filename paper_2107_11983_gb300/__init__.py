@@ -384,6 +384,10 @@ class Server:
         lib = load_library()
         p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset)
         src = sources if _is_torch(sources) else np.ascontiguousarray(sources, dtype=np.int32)
+        if any(_is_cuda(x) for x in (src, out_paths, out_lengths)):
+            # the server runs on its own streams: work queued on the caller's
+            # stream for these buffers (allocation, fills) must finish first
+            _torch().cuda.current_stream().synchronize()
         rid = ctypes.c_uint64(0)
         st = lib.trw_serve_submit(self._h, algo, ctypes.byref(p), _ptr(src), int(src.shape[0]), max_len,
                                   seed & ((1 << 64) - 1), _ptr(out_paths), _ptr(out_lengths), ctypes.byref(rid))

@@ -8,10 +8,11 @@
 //     (the only reader of the host ring), cuts each new request into chunks of
 //     walks and pushes them into a device chunk queue;
 //   - every other warp is a worker: it pops chunks (CAS on the queue head),
-//     caches the request's descriptor in shared memory (loaded past L1, so a
-//     reused slot is never read stale), runs the walks with the same step code
-//     as the batch kernels and refills a lane as soon as its walk ends, so
-//     walks of different requests share warps;
+//     copies the request's descriptor into shared memory (field by field,
+//     past L1, so a reused slot is never read stale), runs the walks with the
+//     same step code as the batch kernels and refills a lane as soon as its
+//     walk ends.  A warp holds one request at a time and switches when its
+//     lanes have drained; different warps run different requests at once;
 //   - when the last walk of a request ends, the lane that finished it fences
 //     and writes the request's done flag to host-mapped memory.
 // Every wait is bounded: with no work for idle_timeout_us the kernel exits,
@@ -21,6 +22,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <cstdint>
 #include <thread>
 #include <vector>
 
@@ -33,7 +35,6 @@ using namespace trw;
 
 namespace {
 
-constexpr int kCacheEntries = 4;      // request descriptors cached per warp
 constexpr uint32_t kQueueCap = 1u << 16;
 
 struct Chunk {
@@ -48,8 +49,9 @@ struct ServeState {       // device memory, persists across launches
   unsigned long long disp_k;      // dispatcher: next request to cut
   unsigned long long disp_pos;    // dispatcher: next walk of that request
   unsigned long long moves;       // total moves of finished walks
-  int err;
-  int pad;
+  int live_workers;               // worker warps of the running launch
+  int err;                        // first failed self-check (kernel-wide)
+  unsigned long long bad[4];      // what that check saw
 };
 
 struct ServeHost {        // host-mapped pinned memory
@@ -137,7 +139,9 @@ __device__ void dispatcher(const ServeDev& sv) {
       } else {
         const long long t = now_ns();
         if (sv.host->stop) go = 0;
-        else if (t - idle_since > sv.idle_ns && ld_acquire_gpu(&st->q_consumed) == tail) go = 0;
+        else if (t - idle_since > sv.idle_ns &&
+                 (ld_acquire_gpu(&st->q_consumed) == tail || atomicAdd(&st->live_workers, 0) == 0))
+          go = 0;  // nothing left to hand out, or nobody left to take it (the host relaunches)
         else __nanosleep(2000);
       }
     }
@@ -146,22 +150,87 @@ __device__ void dispatcher(const ServeDev& sv) {
   }
 }
 
+// 4- or 8-byte load past L1 (the slot table is rewritten between requests),
+// returned as T through a byte copy.
+template <typename T>
+__device__ __forceinline__ T ldcg_as(const T* p) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4 or 8 bytes");
+  T r;
+  if constexpr (sizeof(T) == 8) {
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    memcpy(&r, &v, 8);
+  } else {
+    unsigned int v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    memcpy(&r, &v, 4);
+  }
+  return r;
+}
+
+// Field-by-field copy of a slot's descriptor into shared memory.
+__device__ __forceinline__ void load_spec(const WalkSpec* src, WalkSpec* dst) {
+  dst->algo = ldcg_as(&src->algo);
+  dst->max_len = ldcg_as(&src->max_len);
+  dst->wps = ldcg_as(&src->wps);
+  dst->endpoints = ldcg_as(&src->endpoints);
+  dst->key0 = ldcg_as(&src->key0);
+  dst->key1 = ldcg_as(&src->key1);
+  dst->walk_offset = ldcg_as(&src->walk_offset);
+  dst->schema_len = ldcg_as(&src->schema_len);
+  dst->T_stop = ldcg_as(&src->T_stop);
+  dst->T_ret = ldcg_as(&src->T_ret);
+  dst->T_nb = ldcg_as(&src->T_nb);
+  dst->T_far = ldcg_as(&src->T_far);
+  dst->T_lo = ldcg_as(&src->T_lo);
+  dst->T_hi = ldcg_as(&src->T_hi);
+  dst->sources = ldcg_as(&src->sources);
+  dst->out_paths = ldcg_as(&src->out_paths);
+  dst->out_lengths = ldcg_as(&src->out_lengths);
+  dst->nwalks = ldcg_as(&src->nwalks);
+  dst->schema_lo = ldcg_as(&src->schema_lo);
+  dst->schema_hi = ldcg_as(&src->schema_hi);
+}
+
+// Usable descriptor for chunk [cb, ce) of request ck?  0 if so, else the
+// number of the failed check.
+__device__ __forceinline__ int spec_check(const WalkSpec& sp, unsigned long long ck, uint32_t cb, uint32_t ce,
+                                          unsigned long long published) {
+  if (ck >= published) return 1;
+  if (!(cb < ce) || (int64_t)ce > sp.nwalks) return 2;
+  if (sp.algo < 0 || sp.algo > 4 || sp.wps < 1 || sp.max_len < 0 || (sp.algo == METAPATH && sp.schema_len < 1)) return 3;
+  const uintptr_t ptrs = reinterpret_cast<uintptr_t>(sp.sources) | reinterpret_cast<uintptr_t>(sp.out_paths) |
+                         reinterpret_cast<uintptr_t>(sp.out_lengths);
+  if (!sp.sources || !sp.out_paths || !sp.out_lengths || (ptrs & 3)) return 4;
+  return 0;
+}
+
+__device__ __forceinline__ void record_bad(const ServeDev& sv, int bad, unsigned long long a, unsigned long long b,
+                                           unsigned long long c, unsigned long long d) {
+  if (atomicCAS(&sv.state->err, 0, bad) == 0) {
+    sv.state->bad[0] = a;
+    sv.state->bad[1] = b;
+    sv.state->bad[2] = c;
+    sv.state->bad[3] = d;
+  }
+}
+
+// Worker warps run walks of one request at a time: lanes are refilled from
+// chunks of that request; a chunk of another request waits until every lane
+// has finished, then the warp switches its descriptor.
 __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  WalkSpec* cache = reinterpret_cast<WalkSpec*>(smem_raw) + wid * kCacheEntries;
-  unsigned long long* cache_k =
-      reinterpret_cast<unsigned long long*>(smem_raw + sizeof(WalkSpec) * kCacheEntries * nwarps) + wid * kCacheEntries;
-  int32_t* stage_mem = reinterpret_cast<int32_t*>(smem_raw + (sizeof(WalkSpec) + 8) * kCacheEntries * nwarps);
+  WalkSpec* spec = reinterpret_cast<WalkSpec*>(smem_raw) + wid;
+  int32_t* stage_mem = reinterpret_cast<int32_t*>(smem_raw + sizeof(WalkSpec) * nwarps);
 
   if (blockIdx.x == 0 && wid == 0) {
     dispatcher(sv);
     return;
   }
-  if (lane < kCacheEntries) cache_k[lane] = ~0ull;
-  __syncwarp();
+  if (lane == 0) atomicAdd(&sv.state->live_workers, 1);
 
   const unsigned lt_mask = (1u << lane) - 1u;
   step::Stage st;
@@ -171,10 +240,12 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
   step::Walker W;
   W.w = 0; W.s = 0; W.cur = 0; W.prev = -1; W.off = W.d = W.poff = W.pd = 0; W.att = 0;
   bool active = false;
-  int ent = 0;
   int64_t walk = 0;
-  uint32_t wlo = 0, whi = 0;
-  int went = 0;
+  unsigned long long cur_k = ~0ull;   // request whose descriptor is in spec (warp-uniform)
+  uint32_t wlo = 0, whi = 0;          // unassigned walks of cur_k (warp-uniform)
+  bool pend = false;                  // a popped chunk of another request (warp-uniform)
+  unsigned long long pk = 0;
+  uint32_t pb = 0, pe = 0;
   long long idle_since = now_ns();
   unsigned long long moves_acc = 0;
 
@@ -182,73 +253,82 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
     unsigned idle = __ballot_sync(0xffffffffu, !active);
     while (idle != 0u) {
       if (wlo >= whi) {
-        // A free cache entry is needed before popping a chunk.
-        int free_ent = -1;
-        for (int e = 0; e < kCacheEntries; ++e) {
-          const unsigned used = __ballot_sync(0xffffffffu, active && ent == e);
-          if (used == 0u && free_ent < 0) free_ent = e;
-        }
-        if (free_ent < 0) break;
-        unsigned long long ck = 0;
-        uint32_t cb = 0, ce = 0;
-        int got = 0;
-        if (lane == 0) {
-          ServeState* s = sv.state;
-          for (int tries = 0; tries < 64; ++tries) {
-            const unsigned long long h = *(volatile unsigned long long*)&s->q_head;
-            const unsigned long long t = ld_acquire_gpu(&s->q_tail);
-            if (h >= t) break;
-            if (atomicCAS(&s->q_head, h, h + 1) == h) {
-              const Chunk* c = &sv.queue[h % kQueueCap];
-              ck = __ldcg(&c->k);
-              const uint2 be = __ldcg(reinterpret_cast<const uint2*>(&c->begin));
-              cb = be.x;
-              ce = be.y;
-              __threadfence();
-              atomicAdd(&s->q_consumed, 1ull);
-              got = 1;
-              break;
+        if (!pend) {
+          unsigned long long ck = 0;
+          uint32_t cb = 0, ce = 0;
+          int got = 0;
+          if (lane == 0) {
+            ServeState* s = sv.state;
+            for (int tries = 0; tries < 64; ++tries) {
+              const unsigned long long h = *(volatile unsigned long long*)&s->q_head;
+              const unsigned long long t = ld_acquire_gpu(&s->q_tail);
+              if (h >= t) break;
+              if (atomicCAS(&s->q_head, h, h + 1) == h) {
+                const Chunk* c = &sv.queue[h % kQueueCap];
+                ck = ldcg_as(&c->k);
+                cb = ldcg_as(&c->begin);
+                ce = ldcg_as(&c->end);
+                __threadfence();
+                atomicAdd(&s->q_consumed, 1ull);
+                got = 1;
+                break;
+              }
             }
           }
+          got = __shfl_sync(0xffffffffu, got, 0);
+          if (!got) break;
+          ck = __shfl_sync(0xffffffffu, ck, 0);
+          cb = __shfl_sync(0xffffffffu, cb, 0);
+          ce = __shfl_sync(0xffffffffu, ce, 0);
+          if (ck == cur_k) {
+            wlo = cb;
+            whi = ce;
+          } else {
+            pend = true;
+            pk = ck;
+            pb = cb;
+            pe = ce;
+          }
         }
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (!got) break;
-        ck = __shfl_sync(0xffffffffu, ck, 0);
-        cb = __shfl_sync(0xffffffffu, cb, 0);
-        ce = __shfl_sync(0xffffffffu, ce, 0);
-        // Descriptor of request ck: reuse the cached copy or load it past L1.
-        int e_hit = -1;
-        for (int e = 0; e < kCacheEntries; ++e)
-          if (cache_k[e] == ck) e_hit = e;
-        if (e_hit < 0) {
-          e_hit = free_ent;
-          const int slot = (int)(ck % (unsigned long long)sv.R);
-          const uint32_t* src = reinterpret_cast<const uint32_t*>(&sv.specs[slot]);
-          uint32_t* dst = reinterpret_cast<uint32_t*>(&cache[e_hit]);
-          for (int wd = lane; wd < (int)(sizeof(WalkSpec) / 4); wd += 32) dst[wd] = __ldcg(src + wd);
-          if (lane == 0) cache_k[e_hit] = ck;
+        if (pend) {
+          // switch only once the warp has drained the current request
+          if (__any_sync(0xffffffffu, active)) break;
+          int bad = 0;
+          if (lane == 0) {
+            load_spec(&sv.specs[(int)(pk % (unsigned long long)sv.R)], spec);
+            bad = spec_check(*spec, pk, pb, pe, ld_acquire_sys(&sv.host->published));
+            if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec->nwalks,
+                                reinterpret_cast<uintptr_t>(spec->out_paths));
+          }
+          bad = __shfl_sync(0xffffffffu, bad, 0);
           __syncwarp();
+          pend = false;
+          if (bad) {
+            cur_k = ~0ull;
+            wlo = whi = 0;
+            continue;
+          }
+          cur_k = pk;
+          wlo = pb;
+          whi = pe;
         }
-        wlo = cb;
-        whi = ce;
-        went = e_hit;
+        continue;
       }
       const int take = (int)min((uint32_t)__popc(idle), whi - wlo);
       const int rank = __popc(idle & lt_mask);
       if (((idle >> lane) & 1u) && rank < take) {
-        const WalkSpec& sp = cache[went];
+        const WalkSpec& sp = *spec;
         walk = (int64_t)wlo + rank;
-        ent = went;
         const int32_t src = __ldcg(sp.sources + walk / sp.wps);
         W.w = sp.walk_offset + (uint32_t)walk;
         W.s = 0;
-        W.cur = (src >= 0 && src < g.nv) ? src : 0;
+        W.cur = src;
         W.prev = -1;
         W.att = 0;
         if (!sp.endpoints) {
           st.gpos = walk * ((int64_t)sp.max_len + 1);
           st.lo = (int)(st.gpos & 7);
-          step::stage_put(st, sp.out_paths, W.cur, (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0);
+          step::stage_put(st, sp.out_paths, src, (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0);
         }
         active = true;
       }
@@ -270,20 +350,24 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
     idle_since = now_ns();
 
     bool finishing = false;
+    const int slot = (int)(cur_k % (unsigned long long)sv.R);
     if (active) {
-      const WalkSpec& sp = cache[ent];
+      const WalkSpec& sp = *spec;
       const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
       int32_t next = -1;
-      const int r = step::step_dispatch<MIXED>(g, sp, W, next);
+      const int r = step::step_dispatch<MIXED, true>(g, sp, W, next);
       if (r == step::kMoved) {
         step::advance(W, next);
         if (!sp.endpoints) step::stage_put(st, sp.out_paths, next, aligned);
       } else if (r == step::kRetry) {
         W.att += 1;
       } else {
-        const int slot = (int)(cache_k[ent] % (unsigned long long)sv.R);
         if (r == step::kFail) atomicCAS(&sv.err[slot], 0, kErrRejectCap);
-        if (r == step::kBroken) atomicCAS(&sv.err[slot], 0, kErrInternal);
+        if (r == step::kBroken) {
+          atomicCAS(&sv.err[slot], 0, kErrInternal);
+          record_bad(sv, 5, cur_k, (unsigned long long)walk, (unsigned long long)(uint32_t)W.cur,
+                     ((unsigned long long)(uint32_t)W.off << 32) | (uint32_t)W.d);
+        }
         if (sp.endpoints) __stcs(sp.out_paths + walk, W.cur);
         else step::stage_finish(st, sp.out_paths, aligned);
         __stcs(sp.out_lengths + walk, W.s + 1);
@@ -292,32 +376,31 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
         active = false;
       }
     }
-    // Completion counting, aggregated over the lanes of one request.
+    // Completion: every active lane belongs to cur_k.
     const unsigned fin = __ballot_sync(0xffffffffu, finishing);
-    if (finishing) {
-      const unsigned long long k = cache_k[ent];
-      const unsigned peers = __match_any_sync(fin, k);
-      const int leader = __ffs(peers) - 1;
-      __threadfence();  // this lane's outputs before its completion count
-      __syncwarp(peers);
-      if (lane == leader) {
-        const int slot = (int)(k % (unsigned long long)sv.R);
-        const unsigned long long cnt = (unsigned long long)__popc(peers);
+    if (fin) {
+      __threadfence();  // outputs of the finishing lanes before their count
+      __syncwarp();
+      if (lane == 0) {
+        const unsigned long long cnt = (unsigned long long)__popc(fin);
         const unsigned long long old = atomicAdd(&sv.finished[slot], cnt);
-        const unsigned long long n = (unsigned long long)cache[ent].nwalks;
-        if (old + cnt == n) {
+        if (old + cnt == (unsigned long long)spec->nwalks) {
           __threadfence();
           const int e = atomicAdd(&sv.err[slot], 0);
           sv.done_err[slot] = e;
           __threadfence_system();
-          sv.done[slot] = k + 1;
+          sv.done[slot] = cur_k + 1;
           __threadfence_system();
         }
       }
     }
   }
   const unsigned long long mv = step::warp_sum(moves_acc);
-  if (lane == 0 && mv) atomicAdd(&sv.state->moves, mv);
+  if (lane == 0) {
+    if (mv) atomicAdd(&sv.state->moves, mv);
+    __threadfence();
+    atomicSub(&sv.state->live_workers, 1);
+  }
 }
 
 }  // namespace
@@ -356,6 +439,7 @@ struct trw_server {
   int block_threads = 256;
   int grid_blocks = 0;
   size_t smem = 0;
+  uint64_t polls = 0;
   std::mutex mu;
 };
 
@@ -441,7 +525,7 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   s->collected.assign(R, 1);
   s->block_threads = 256;
   const int nwarps = s->block_threads / 32;
-  s->smem = (sizeof(WalkSpec) + 8) * kCacheEntries * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t);
+  s->smem = sizeof(WalkSpec) * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t);
   int bps = 0;
   SV_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, serve_kernel, s->block_threads, s->smem), "occupancy");
   if (bps < 1) bps = 1;
@@ -573,6 +657,18 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   return TRW_OK;
 }
 
+// A failed device self-check, reported as TRW_ERR_INTERNAL with what it saw.
+static trw_status check_state(trw_server* s) {
+  ServeState st;
+  cudaError_t e = cudaMemcpyAsync(&st, s->state, sizeof(ServeState), cudaMemcpyDeviceToHost, s->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "serve state");
+  if (st.err != 0)
+    return trw_fail(TRW_ERR_INTERNAL, "serve self-check %d failed: request %llu range %llx nwalks %llu out %llx", st.err,
+                    st.bad[0], st.bad[1], st.bad[2], st.bad[3]);
+  return TRW_OK;
+}
+
 static trw_status poll_locked(trw_server* s, uint64_t k) {
   if (k >= s->next_k || k + (unsigned long long)s->R < s->next_k) return trw_fail(TRW_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)k);
   const int slot = (int)(k % (unsigned long long)s->R);
@@ -581,6 +677,10 @@ static trw_status poll_locked(trw_server* s, uint64_t k) {
   if (d != k + 1) {
     cudaError_t e = launch_if_idle(s);
     if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel relaunch");
+    if ((++s->polls & 63) == 0) {
+      trw_status cs = check_state(s);
+      if (cs != TRW_OK) return cs;
+    }
     return TRW_PENDING;
   }
   std::atomic_thread_fence(std::memory_order_acquire);
@@ -613,9 +713,11 @@ extern "C" trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms) {
         const unsigned long long d = reinterpret_cast<volatile unsigned long long*>(s->done)[slot];
         if (d != k + 1) pending = true;
       }
-      if (!pending) return TRW_OK;
+      if (!pending) return check_state(s);
       cudaError_t e = launch_if_idle(s);
       if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel relaunch");
+      trw_status cs = check_state(s);
+      if (cs != TRW_OK) return cs;
     }
     if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
       return trw_fail(TRW_ERR_TIMEOUT, "requests still running after %d ms", timeout_ms);

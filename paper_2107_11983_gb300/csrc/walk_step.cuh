@@ -100,14 +100,18 @@ __device__ __forceinline__ bool n2v_accept(const WalkSpec& sp, const Walker& W, 
 
 // One unit of work for one walker, thread-serial: a full step, or one
 // rejection trial of a Node2Vec step.
-template <int A>
+// CHECK adds range checks of the walker's vertex and of the row it loads
+// before any access through them (kBroken instead of an out-of-range read).
+template <int A, bool CHECK = false>
 __device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   if (W.s == sp.max_len) return kStop;                         // Update: target length reached
   const uint4 B = draw_block(sp, W.w, (uint32_t)W.s, W.att);
   if (A == PPR && (uint64_t)B.w < sp.T_stop) return kStop;     // Update: PPR stop coin
   if (W.att == 0) {
+    if (CHECK && (uint32_t)W.cur >= (uint32_t)g.nv) return kBroken;
     W.off = ldg(g.row_ptr + W.cur);
     W.d = ldg(g.row_ptr + W.cur + 1) - W.off;
+    if (CHECK && (W.off < 0 || W.d < 0 || (int64_t)W.off + W.d > (int64_t)g.ne)) return kBroken;
   }
   if (W.d == 0) return kStop;                                  // dead end
   if (A == DEEPWALK || A == PPR) {
@@ -152,17 +156,18 @@ __device__ __forceinline__ void advance(Walker& W, int32_t next) {
   W.att = 0;
 }
 
-template <int A>
+template <int A, bool CHECK = false>
 __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   if constexpr (A != MIXED) {
-    return step_serial<A>(g, sp, W, next);
+    return step_serial<A, CHECK>(g, sp, W, next);
   } else {
     switch (sp.algo) {
-      case DEEPWALK: return step_serial<DEEPWALK>(g, sp, W, next);
-      case DEEPWALK_WEIGHTED: return step_serial<DEEPWALK_WEIGHTED>(g, sp, W, next);
-      case PPR: return step_serial<PPR>(g, sp, W, next);
-      case NODE2VEC: return step_serial<NODE2VEC>(g, sp, W, next);
-      default: return step_serial<METAPATH>(g, sp, W, next);
+      case DEEPWALK: return step_serial<DEEPWALK, CHECK>(g, sp, W, next);
+      case DEEPWALK_WEIGHTED: return step_serial<DEEPWALK_WEIGHTED, CHECK>(g, sp, W, next);
+      case PPR: return step_serial<PPR, CHECK>(g, sp, W, next);
+      case NODE2VEC: return step_serial<NODE2VEC, CHECK>(g, sp, W, next);
+      case METAPATH: return step_serial<METAPATH, CHECK>(g, sp, W, next);
+      default: return kBroken;
     }
   }
 }
@@ -185,7 +190,7 @@ struct Stage {
 
 __device__ __forceinline__ void stage_flush(Stage& st, int32_t* __restrict__ out, int hi_slot, bool aligned) {
   const int64_t sec = (st.gpos - 1) & ~int64_t(7);
-  if (st.lo == 0 && hi_slot == 8 && aligned) {
+  if (st.lo == 0 && hi_slot == 8 && aligned && ((reinterpret_cast<uintptr_t>(out + sec) & 31) == 0)) {
     const int4 a = *reinterpret_cast<const int4*>(st.buf);
     const int4 b = *reinterpret_cast<const int4*>(st.buf + 4);
     __stcs(reinterpret_cast<int4*>(out + sec), a);

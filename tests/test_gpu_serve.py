@@ -18,6 +18,20 @@ SCALE = 12
 SCHEMA = np.array([1, 3, 0, 4, 2], np.uint8)
 
 
+@pytest.fixture
+def server_factory():
+    made = []
+
+    def make(G, **kw):
+        S = trw.Server(G, **kw)
+        made.append(S)
+        return S
+
+    yield make
+    for S in made:
+        S.close()
+
+
 @pytest.fixture(scope="module")
 def served():
     g = rmat_graph(SCALE)
@@ -67,9 +81,9 @@ def wait(S, rid, timeout=60.0):
         time.sleep(0.0005)
 
 
-def test_serve_mix_matches_oracle(served):
+def test_serve_mix_matches_oracle(served, server_factory):
     g, G = served
-    S = trw.Server(G, max_requests=64)
+    S = server_factory(G, max_requests=64)
     rng = np.random.default_rng(0)
     reqs = [make_request(g, i, rng) for i in range(40)]
     live = []
@@ -78,14 +92,13 @@ def test_serve_mix_matches_oracle(served):
     for r, rid, op, ol in live:
         wait(S, rid)
         check(g, r, op, ol)
-    S.close()
 
 
-def test_serve_same_alone_and_in_mix(served):
+def test_serve_same_alone_and_in_mix(served, server_factory):
     g, G = served
     rng = np.random.default_rng(1)
     reqs = [make_request(g, i, rng) for i in range(10)]
-    S = trw.Server(G, max_requests=32)
+    S = server_factory(G, max_requests=32)
     alone = []
     for r in reqs:
         rid, op, ol = submit(S, r)
@@ -105,12 +118,11 @@ def test_serve_same_alone_and_in_mix(served):
             assert torch.equal(op[mask], aop[mask])
     wait(S, brid)
     check(g, big, bop, bol)
-    S.close()
 
 
-def test_serve_admission_and_ids(served):
+def test_serve_admission_and_ids(served, server_factory):
     g, G = served
-    S = trw.Server(G, max_requests=4, max_inflight_walks=5000)
+    S = server_factory(G, max_requests=4, max_inflight_walks=5000)
     r = dict(algo=trw.DEEPWALK, sources=synth.sources(3000, g.nv, seed=5), max_len=80, seed=1)
     rid, op, ol = submit(S, r)
     # too many walks in flight -> busy, nothing queued
@@ -136,12 +148,11 @@ def test_serve_admission_and_ids(served):
     with pytest.raises(trw.TRWError) as e:
         submit(S, dict(r, sources=np.array([g.nv], np.int32)))
     assert e.value.status == -1
-    S.close()
 
 
-def test_serve_relaunch_after_idle(served):
+def test_serve_relaunch_after_idle(served, server_factory):
     g, G = served
-    S = trw.Server(G, max_requests=8, idle_timeout_us=200)
+    S = server_factory(G, max_requests=8, idle_timeout_us=200)
     for i in range(3):
         r = dict(algo=trw.DEEPWALK_WEIGHTED, sources=synth.sources(500, g.nv, seed=40 + i), max_len=30, seed=i)
         rid, op, ol = submit(S, r)
@@ -149,4 +160,3 @@ def test_serve_relaunch_after_idle(served):
         check(g, r, op, ol)
         time.sleep(0.05)  # longer than the idle timeout: the resident kernel exits
     S.drain(10000)
-    S.close()
