@@ -68,8 +68,7 @@ def build_graph(wl):
     g = synth.rmat(wl["scale"], symmetric=wl.get("symmetric", True))
     if wl["algo"] == "deepwalk_weighted":
         g.weights = synth.edge_weights(g)
-    if wl["algo"] == "metapath":
-        g.labels = synth.edge_labels(g)
+    g.labels = synth.edge_labels(g)  # MetaPath line of the per-algorithm table
     log(f"graph {g.name}: nv={g.nv} ne={g.ne} built in {time.time() - t:.1f}s")
     return g
 
@@ -99,7 +98,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception as e:  # no nvidia-smi: report without clocks
             log(f"clock sampling unavailable: {e}")
@@ -235,6 +234,80 @@ def run_reference(args, wl):
 
 # ------------------------------------------------------------------ GPU arm
 
+def time_walk(trw, torch, G, flush, sp, algo, src, L, seed, kernel, reps=3, **kw):
+    """Median device time (CUDA events on the launch stream) and moves of one walk call."""
+    import statistics as st
+
+    n = int(src.shape[0]) * kw.get("walks_per_source", 1)
+    shape = (n,) if kw.get("endpoints") else (n, L + 1)
+    out_p = torch.empty(shape, dtype=torch.int32, device=src.device)
+    out_l = torch.empty(n, dtype=torch.int32, device=src.device)
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps + 1):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.walk(algo, src, L, seed, kernel=kernel, out_paths=out_p, out_lengths=out_l, stream=sp, **kw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        if times[-1] > 3000:
+            break
+    moves = int((out_l.to(torch.int64) - 1).sum().item())
+    ms = st.median(times[1:]) if len(times) > 1 else times[0]
+    return ms, moves
+
+
+def measure_per_algo(trw, torch, G, g, flush, sp):
+    """Steps/s of every algorithm, persistent kernel vs the plain one-launch
+    baseline, on the workload's graph (labels drawn for MetaPath)."""
+    import synth as sy
+
+    dev = flush.device
+    verts = torch.from_numpy(sy.vertex_sources(g.nv)).to(dev)
+    ppr_src = torch.from_numpy(sy.sources(1_000_000, g.nv, seed=1)).to(dev)
+    schema = sy.schema(5, 5, seed=1)
+    cases = {
+        "deepwalk": (trw.DEEPWALK, verts, 80, {}),
+        "ppr": (trw.PPR, ppr_src, 1000, {"ppr_stop": 0.2, "endpoints": True}),
+        "node2vec": (trw.NODE2VEC, verts, 80, {"n2v_p": 0.5, "n2v_q": 2.0}),
+    }
+    if G.has_weights:
+        cases["deepwalk_weighted"] = (trw.DEEPWALK_WEIGHTED, verts, 80, {})
+    if G.has_labels:
+        cases["metapath"] = (trw.METAPATH, verts, 80, {"schema": schema})
+    out = {}
+    for name, (algo, src, L, kw) in cases.items():
+        row = {}
+        for kname, kern in (("persistent", trw.KERNEL_PERSISTENT), ("plain", trw.KERNEL_PLAIN)):
+            ms, moves = time_walk(trw, torch, G, flush, sp, algo, src, L, 1, kern, **kw)
+            row[kname] = {"steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3), "moves": moves}
+        row["speedup"] = round(row["persistent"]["steps_per_s"] / row["plain"]["steps_per_s"], 3)
+        row["walks"] = int(src.shape[0])
+        row["max_len"] = L
+        out[name] = row
+        log(f"{name}: {row}")
+    return out
+
+
+def measure_gather_ceiling(trw, g):
+    """Dependent random 16-byte loads over a table the size of the alias
+    records, at walk-kernel occupancy: the practical random-access ceiling."""
+    try:
+        tb = max(1 << 30, 16 * g.ne)
+        r1 = trw.gather_ceiling(tb, 16, 80, 1)
+        r2 = trw.gather_ceiling(tb, 16, 80, 2)
+        best = r1 if r1["loads_per_s"] >= r2["loads_per_s"] else r2
+        best["chains_1"] = r1["loads_per_s"]
+        best["chains_2"] = r2["loads_per_s"]
+        best["bytes_per_s_32B_sectors"] = best["loads_per_s"] * 32
+        return best
+    except Exception as e:  # report, do not hide
+        log(f"gather ceiling failed: {e}")
+        return None
+
+
 def run_ours(args, wl):
     import torch
     import torch.distributed as dist
@@ -267,7 +340,7 @@ def run_ours(args, wl):
     out_len = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
     stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
+    sp = stream.cuda_stream or 1  # torch's default stream is cudaStreamLegacy for the library
 
     def one(kernel):
         G.walk(algo, src, L, wl["seed"], kernel=kernel, out_paths=out_paths, out_lengths=out_len, stream=sp,
@@ -357,6 +430,15 @@ def run_ours(args, wl):
                 "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "walk_persistent",
                 "bytes_per_move": bpm, "algorithmic_bytes_per_launch": int(alg_bytes)}
 
+    per_algo = None
+    gather = None
+    if rank == 0 and not args.no_extras:
+        per_algo = measure_per_algo(trw, torch, G, g, flush, sp)
+        gather = measure_gather_ceiling(trw, g)
+        if roof is not None and gather is not None:
+            roof["random_gather_ceiling_steps_per_s"] = gather["loads_per_s"]
+            roof["frac_of_gather_ceiling"] = round(value / ws / gather["loads_per_s"], 4)
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -380,6 +462,8 @@ def run_ours(args, wl):
                 "d2h_bytes_per_step": int(n * (L + 1) * 4 + n * 4), "ms": round(1000 * e2e_s, 3)},
         "gpu_launches": 2 * args.steps,
         "roofline": roof,
+        "per_algo": per_algo,
+        "gather_ceiling": gather,
         "cpu_baseline": cpu,
         "clocks": clk,
     }
@@ -391,16 +475,21 @@ def run_ours(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-algorithm lines and the gather ceiling")
+    ap.add_argument("--scale", type=int, default=0, help="override the R-MAT scale (smaller profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3
-    wl = WORKLOADS[args.config]
+    wl = dict(WORKLOADS[args.config])
+    if args.scale:
+        wl["name"] = wl["name"].rsplit("-s", 1)[0] + f"-s{args.scale}"
+        wl["scale"] = args.scale
     if args.impl == "reference":
         run_reference(args, wl)
     else:

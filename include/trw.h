@@ -158,7 +158,8 @@ trw_status trw_walk(trw_graph* g, trw_algo algo, const trw_params* params, const
 /*
  * trw_walk with an explicit kernel and stream.
  *   kernel   TRW_KERNEL_AUTO, TRW_KERNEL_PLAIN or TRW_KERNEL_PERSISTENT.
- *   stream   a cudaStream_t, or NULL for the graph's own stream.
+ *   stream   a cudaStream_t (cudaStreamLegacy, i.e. (void*)1, names the legacy
+ *            default stream), or NULL for the graph's own stream.
  *   sync     1: wait and return the device status (as trw_walk);
  *            0: device buffers only, return after the launch; collect the
  *               device status later with trw_sync.
@@ -171,6 +172,18 @@ trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params* params, co
 /* Wait for the stream (NULL: the graph's) and return, then clear, the status
  * that kernels launched with sync = 0 left on the device. */
 trw_status trw_sync(trw_graph* g, void* stream);
+
+/*
+ * Random-gather ceiling (measurement aid, no counterpart in the paper): the
+ * rate at which this GPU serves dependent random loads of record_bytes-wide
+ * records (4, 8 or 16) from a table of table_bytes, with the same occupancy
+ * and chain length as a walk: every thread follows hops_per_chain dependent
+ * random hops of chains_per_thread independent chains.  Allocates and frees
+ * its own table.  Writes loads per second and the kernel time.
+ * Errors: TRW_ERR_INVALID (sizes), TRW_ERR_OOM, TRW_ERR_CUDA.
+ */
+trw_status trw_gather_ceiling(int64_t table_bytes, int32_t record_bytes, int32_t hops_per_chain,
+                              int32_t chains_per_thread, double* loads_per_s, double* kernel_ms);
 
 /*
  * A mixed batch in ONE persistent launch (the paper's Algorithm 4 admits a new

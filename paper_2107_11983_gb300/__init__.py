@@ -100,6 +100,7 @@ _SIGS = {
     "trw_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "trw_serve_drain": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "trw_serve_destroy": (None, [_VP]),
+    "trw_gather_ceiling": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "trw_last_error": (ctypes.c_char_p, []),
 }
 
@@ -171,6 +172,19 @@ def _is_cuda(x) -> bool:
     return _is_torch(x) and x.is_cuda
 
 
+def _stream_arg(stream, *arrays) -> int:
+    """The cudaStream_t to pass: an explicit handle, else torch's current stream
+    when CUDA tensors are involved (handle 0, torch's default stream, is passed
+    as cudaStreamLegacy), else 0 for the graph's own stream."""
+    if stream is not None:
+        if hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        return int(stream) or 1
+    if any(_is_cuda(a) for a in arrays):
+        return int(_torch().cuda.current_stream().cuda_stream) or 1
+    return 0
+
+
 def _params(algo: int, ppr_stop: float, n2v_p: float, n2v_q: float, schema, walks_per_source: int,
             endpoints: bool, walk_offset: int):
     p = _Params()
@@ -211,6 +225,8 @@ class Graph:
         self._h = h
         self.nv = int(rp.shape[0] - 1)
         self.ne = int(cl.shape[0])
+        self.has_weights = w is not None
+        self.has_labels = lab is not None
 
     @classmethod
     def from_synth(cls, g):
@@ -262,12 +278,15 @@ class Graph:
             out_lengths = (_torch().empty(nwalks, dtype=_torch().int32, device=src.device) if _is_cuda(src)
                            else np.empty(nwalks, dtype=np.int32))
         st = lib.trw_walk_ex(self._h, algo, ctypes.byref(p), _ptr(src), n, max_len, seed & ((1 << 64) - 1),
-                             _ptr(out_paths), _ptr(out_lengths), kernel, stream or 0, 1 if sync else 0)
+                             _ptr(out_paths), _ptr(out_lengths), kernel, _stream_arg(stream, src, out_paths, out_lengths),
+                             1 if sync else 0)
         _check(st, "trw_walk")
         return WalkOutput(out_paths, out_lengths)
 
     def sync(self, stream=None):
-        _check(load_library().trw_sync(self._h, stream or 0), "trw_sync")
+        """Wait for the stream (default: torch's current stream) and collect the device status."""
+        sa = _stream_arg(stream) if stream is not None else (int(_torch().cuda.current_stream().cuda_stream) or 1)
+        _check(load_library().trw_sync(self._h, sa), "trw_sync")
 
     def walk_batch(self, requests: Sequence[dict], stream=None, sync: bool = True):
         """One persistent launch over a mixed batch.  Each request is a dict with
@@ -309,8 +328,8 @@ class Graph:
             seeds[i] = int(r["seed"]) & ((1 << 64) - 1)
             outs[i], outl[i] = op.data_ptr(), ol.data_ptr()
             results.append(WalkOutput(op, ol))
-        st = lib.trw_walk_batch(self._h, nreq, algos, params, srcs, ns, lens, seeds, outs, outl, stream or 0,
-                                1 if sync else 0)
+        st = lib.trw_walk_batch(self._h, nreq, algos, params, srcs, ns, lens, seeds, outs, outl,
+                                _stream_arg(stream, *[k for k in keep if _is_torch(k)]), 1 if sync else 0)
         _check(st, "trw_walk_batch")
         return results
 
@@ -345,6 +364,16 @@ class Graph:
         b = np.empty(self.ne, dtype=np.int32)
         _check(load_library().trw_debug_alias(self._h, H.ctypes.data, a.ctypes.data, b.ctypes.data), "trw_debug_alias")
         return H, a, b
+
+
+def gather_ceiling(table_bytes: int, record_bytes: int = 16, hops: int = 80, chains: int = 1) -> dict:
+    """Random dependent-load rate of this GPU (trw_gather_ceiling)."""
+    lps = ctypes.c_double(0)
+    ms = ctypes.c_double(0)
+    _check(load_library().trw_gather_ceiling(table_bytes, record_bytes, hops, chains, ctypes.byref(lps),
+                                             ctypes.byref(ms)), "trw_gather_ceiling")
+    return {"loads_per_s": lps.value, "kernel_ms": ms.value, "table_bytes": table_bytes,
+            "record_bytes": record_bytes, "hops": hops, "chains": chains}
 
 
 def philox_device(ctr, key0: int, key1: int) -> np.ndarray:
