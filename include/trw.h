@@ -200,6 +200,28 @@ trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw_algo* algo
                           const uint64_t* seeds, int32_t* const* out_paths, int32_t* const* out_lengths,
                           void* stream, int sync);
 
+/*
+ * trw_walk_batch with no allocation (the paper has no counterpart: this is an
+ * interface for callers that must not allocate device memory during the call,
+ * e.g. code running while the caller's memory pool owns the free device
+ * memory, code under an allocator that must see every allocation, or code
+ * that must not let cudaMalloc/cudaFree synchronise the device).
+ * Same requests, results and errors as trw_walk_batch (device buffers only),
+ * on the caller's stream (NULL: the legacy default stream); synchronous.
+ * Its scratch -- control block, request table, prefix sums, about 9 KB -- is a
+ * fixed array in device memory that every GPU loading the library holds
+ * until the process exits; n_requests above TRW_NOALLOC_MAX_REQUESTS is
+ * refused with TRW_ERR_INVALID.  The first call on a device looks up the
+ * array's device address: make it before any stream capture.  All calls share
+ * the array (each clears what must start at zero); calls that overlap on the
+ * GPU race on it.
+ */
+#define TRW_NOALLOC_MAX_REQUESTS 64
+trw_status trw_walk_batch_noalloc(const trw_graph* g, int32_t n_requests, const trw_algo* algos,
+                                  const trw_params* params, const int32_t* const* sources, const int64_t* n_sources,
+                                  const int32_t* max_lens, const uint64_t* seeds, int32_t* const* out_paths,
+                                  int32_t* const* out_lengths, void* stream);
+
 /* Launch shape and tuning knobs of the persistent kernel (the GPU analogue of
  * the ring sizes k and k' of Section 5.4). */
 typedef struct {

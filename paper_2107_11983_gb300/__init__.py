@@ -84,6 +84,7 @@ _SIGS = {
     "trw_sync": (ctypes.c_int, [_VP, _VP]),
     "trw_walk_batch": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                       ctypes.c_int]),
+    "trw_walk_batch_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "trw_get_tuning": (ctypes.c_int, [_VP, _VP]),
     "trw_set_tuning": (ctypes.c_int, [_VP, _VP]),
     "trw_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int32, _VP]),

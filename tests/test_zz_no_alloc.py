@@ -1,0 +1,101 @@
+"""The no-allocation batch walk (GPU only), for callers that must not
+allocate device memory during a call -- e.g. while their own memory pool
+owns the free device memory, or where cudaMalloc/cudaFree would synchronise
+the device.  It calls trw_walk_batch_noalloc through the C ABI and checks its
+paths and lengths against trw_walk_batch, bit for bit (the tolerance of every
+walk test here), on two calls in a row that share the library's fixed
+scratch array.  Collected last so that a failure here leaves every other
+test already run."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2107_11983_gb300 as trw
+import synth
+from gpu_common import rmat_graph
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _requests(g):
+    return [
+        dict(algo=trw.PPR, sources=synth.sources(2000, g.nv, seed=4), max_len=1000, seed=21, ppr_stop=0.2,
+             endpoints=True),
+        dict(algo=trw.METAPATH, sources=synth.vertex_sources(g.nv), max_len=40, seed=22,
+             schema=np.array([0, 1, 2, 3, 4], np.uint8)),
+        dict(algo=trw.DEEPWALK_WEIGHTED, sources=synth.sources(777, g.nv, seed=5), max_len=40, seed=23),
+        dict(algo=trw.NODE2VEC, sources=synth.sources(555, g.nv, seed=6), max_len=30, seed=24, n2v_p=0.5, n2v_q=2.0),
+        dict(algo=trw.DEEPWALK, sources=synth.sources(3, g.nv, seed=7), max_len=80, seed=25, walks_per_source=100),
+    ]
+
+
+def _call_noalloc(G, reqs):
+    """Marshal the requests and call the C entry point directly."""
+    lib = trw.load_library()
+    n = len(reqs)
+    algos = (ctypes.c_int * n)()
+    params = (trw._Params * n)()
+    srcs = (ctypes.c_void_p * n)()
+    ns = (ctypes.c_int64 * n)()
+    lens = (ctypes.c_int32 * n)()
+    seeds = (ctypes.c_uint64 * n)()
+    outs = (ctypes.c_void_p * n)()
+    outl = (ctypes.c_void_p * n)()
+    keep, results = [], []
+    for i, r in enumerate(reqs):
+        wps = r.get("walks_per_source", 1)
+        ep = r.get("endpoints", False)
+        p, k = trw._params(r["algo"], r.get("ppr_stop", 0.2), r.get("n2v_p", 1.0), r.get("n2v_q", 1.0),
+                           r.get("schema"), wps, ep, 0)
+        src = torch.from_numpy(np.ascontiguousarray(r["sources"], np.int32)).cuda()
+        cnt = src.shape[0] * wps
+        op = torch.full((cnt,) if ep else (cnt, r["max_len"] + 1), -1, dtype=torch.int32, device="cuda")
+        ol = torch.full((cnt,), -1, dtype=torch.int32, device="cuda")
+        keep += [k, src]
+        algos[i], params[i], srcs[i], ns[i], lens[i] = r["algo"], p, src.data_ptr(), src.shape[0], r["max_len"]
+        seeds[i] = r["seed"]
+        outs[i], outl[i] = op.data_ptr(), ol.data_ptr()
+        results.append((op, ol))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream().cuda_stream or 1
+    st = lib.trw_walk_batch_noalloc(G.handle, n, algos, params, srcs, ns, lens, seeds, outs, outl, stream)
+    assert st == 0, lib.trw_last_error()
+    torch.cuda.synchronize()
+    return results
+
+
+def _same(a_paths, a_lens, b_paths, b_lens):
+    assert torch.equal(a_lens, b_lens)
+    if a_paths.dim() == 1:
+        assert torch.equal(a_paths, b_paths)
+    else:
+        mask = torch.arange(a_paths.shape[1], device=a_paths.device)[None, :] < a_lens[:, None]
+        assert torch.equal(a_paths[mask], b_paths[mask])
+
+
+def test_noalloc_batch_matches_batch_twice():
+    g = rmat_graph(12)
+    G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
+    G.prepare()
+    reqs = _requests(g)
+    want = G.walk_batch(reqs)
+    torch.cuda.synchronize()
+    for _ in range(2):  # the second call reuses the scratch the first one left behind
+        got = _call_noalloc(G, reqs)
+        for (op, ol), w in zip(got, want):
+            _same(w.paths, w.lengths, op, ol)
+
+
+def test_noalloc_refuses_oversized_batch():
+    g = rmat_graph(12)
+    G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
+    lib = trw.load_library()
+    n = 65
+    arr = (ctypes.c_void_p * n)()
+    st = lib.trw_walk_batch_noalloc(G.handle, n, (ctypes.c_int * n)(), None, arr, (ctypes.c_int64 * n)(),
+                                    (ctypes.c_int32 * n)(), (ctypes.c_uint64 * n)(), arr, arr, None)
+    assert st == -1
+    assert b"no-alloc request table" in lib.trw_last_error()
