@@ -278,8 +278,13 @@ def measure_per_algo(trw, torch, G, g, flush, sp):
     if G.has_labels:
         cases["metapath"] = (trw.METAPATH, verts, 80, {"schema": schema})
     out = {}
+    base_tuning = G.tuning()
     for name, (algo, src, L, kw) in cases.items():
         row = {}
+        t0 = time.time()
+        tune_kw = {k: v for k, v in kw.items() if k != "endpoints"}
+        row["tuning"] = G.autotune(algo, 10, **tune_kw)
+        row["autotune_s"] = round(time.time() - t0, 2)
         for kname, kern in (("persistent", trw.KERNEL_PERSISTENT), ("plain", trw.KERNEL_PLAIN)):
             ms, moves = time_walk(trw, torch, G, flush, sp, algo, src, L, 1, kern, **kw)
             row[kname] = {"steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3), "moves": moves}
@@ -288,6 +293,7 @@ def measure_per_algo(trw, torch, G, g, flush, sp):
         row["max_len"] = L
         out[name] = row
         log(f"{name}: {row}")
+    G.set_tuning(**base_tuning)
     return out
 
 
@@ -332,6 +338,9 @@ def run_ours(args, wl):
         prep_ms = 1000 * (time.time() - t)
     kw = walk_kwargs(wl)
     L = wl["max_len"]
+    t = time.time()
+    G.autotune(algo, 10, **kw)
+    tune_s = time.time() - t
     src_host = synth.vertex_sources(g.nv)
     n = src_host.shape[0]
     walk_offset = rank * n  # each rank its own walks (weak scaling)
@@ -457,7 +466,8 @@ def run_ours(args, wl):
         "wall_s": round(wall, 3),
         "plain_launch": {"value": round(plain_value, 1), "unit": UNIT, "ms": round(statistics.median(plain_ms), 4),
                          "speedup_persistent": round(value / ws / plain_value, 3)},
-        "preprocess": {"graph_load_s": round(load_s, 3), "alias_prepare_ms": None if prep_ms is None else round(prep_ms, 2)},
+        "preprocess": {"graph_load_s": round(load_s, 3), "alias_prepare_ms": None if prep_ms is None else round(prep_ms, 2),
+                       "autotune_s": round(tune_s, 2)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(n * 4),
                 "d2h_bytes_per_step": int(n * (L + 1) * 4 + n * 4), "ms": round(1000 * e2e_s, 3)},
         "gpu_launches": 2 * args.steps,

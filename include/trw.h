@@ -225,10 +225,12 @@ trw_status trw_walk_batch_noalloc(const trw_graph* g, int32_t n_requests, const 
 /* Launch shape and tuning knobs of the persistent kernel (the GPU analogue of
  * the ring sizes k and k' of Section 5.4). */
 typedef struct {
-  int32_t block_threads;        /* threads per block, multiple of 32, 64..1024 */
+  int32_t block_threads;        /* threads per block, multiple of 32, 64..512 */
   int32_t blocks_per_sm;        /* resident blocks per SM requested (0: occupancy maximum) */
   int32_t chunk;                /* walks claimed from the work queue per warp claim, >= 1 */
-  int32_t coop_degree;          /* rows at least this long use warp-cooperative scans/searches */
+  int32_t coop_degree;          /* MetaPath label rows at least this long: Gather by the whole warp, >= 1 */
+  int32_t search_degree;        /* Node2Vec IsNeighbor in rows of prev at least this long: 32-way warp
+                                   search, >= 33 (0x7fffffff: every search by its own lane) */
 } trw_tuning;
 
 /* Read or set the tuning of the graph's persistent kernel.  Setting checks ranges

@@ -49,7 +49,7 @@ class _Params(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("coop_degree", ctypes.c_int32)]
+                ("coop_degree", ctypes.c_int32), ("search_degree", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -209,6 +209,7 @@ extern "C" trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_
   g->tuning.blocks_per_sm = 0;
   g->tuning.chunk = 32;
   g->tuning.coop_degree = 256;
+  g->tuning.search_degree = 0x7fffffff;
   g->device_bytes = (int64_t)(sizeof(int32_t) * ((size_t)nv + 1) + sizeof(int32_t) * (size_t)ne +
                               (weights ? sizeof(float) * (size_t)ne : 0) + (labels ? (size_t)ne : 0));
   *out = g;
@@ -337,11 +338,14 @@ LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
   LaunchCfg c;
   c.block_threads = g->tuning.block_threads;
   int bps = g->tuning.blocks_per_sm;
-  const int occ = persistent_blocks_per_sm(algo, c.block_threads);
+  const bool coop = algo == MIXED || (algo == METAPATH && g->tuning.coop_degree < 0x7fffffff) ||
+                    (algo == NODE2VEC && g->tuning.search_degree < 0x7fffffff);
+  const int occ = persistent_blocks_per_sm(algo, c.block_threads, coop);
   if (bps <= 0 || bps > occ) bps = occ;
   c.grid_blocks = g->num_sms * bps;
   c.chunk = g->tuning.chunk;
   c.coop_degree = g->tuning.coop_degree;
+  c.search_degree = g->tuning.search_degree;
   return c;
 }
 
@@ -527,11 +531,12 @@ extern "C" trw_status trw_get_tuning(const trw_graph* g, trw_tuning* t) {
 
 extern "C" trw_status trw_set_tuning(trw_graph* g, const trw_tuning* t) {
   if (!g || !t) return trw_fail(TRW_ERR_INVALID, "NULL argument");
-  if (t->block_threads < 64 || t->block_threads > 1024 || (t->block_threads & 31))
-    return trw_fail(TRW_ERR_INVALID, "block_threads must be a multiple of 32 in [64, 1024]");
+  if (t->block_threads < 64 || t->block_threads > 512 || (t->block_threads & 31))
+    return trw_fail(TRW_ERR_INVALID, "block_threads must be a multiple of 32 in [64, 512]");
   if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32) return trw_fail(TRW_ERR_INVALID, "blocks_per_sm in [0, 32]");
   if (t->chunk < 1 || t->chunk > (1 << 20)) return trw_fail(TRW_ERR_INVALID, "chunk in [1, 2^20]");
   if (t->coop_degree < 1) return trw_fail(TRW_ERR_INVALID, "coop_degree >= 1");
+  if (t->search_degree < 33) return trw_fail(TRW_ERR_INVALID, "search_degree >= 33");
   std::lock_guard<std::mutex> lk(g->mu);
   g->tuning = *t;
   return TRW_OK;

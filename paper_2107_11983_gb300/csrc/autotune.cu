@@ -1,8 +1,9 @@
 // Autotuner of the persistent kernel: the GPU counterpart of Section 5.4's
 // ring-size tuning, which pre-runs length-10 walks and keeps the ring sizes
 // that run them fastest.  Here the knobs are threads per block, resident
-// blocks per SM, the work-queue chunk and the degree from which the warp
-// cooperates on a row.  Walk results never depend on these knobs.
+// blocks per SM, the work-queue chunk and the degrees from which the warp
+// takes over a MetaPath label scan or a Node2Vec neighbour search.  Walk
+// results never depend on these knobs.
 #include <algorithm>
 #include <vector>
 
@@ -46,23 +47,30 @@ extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params
     sp.out_paths = d_out;
     sp.out_lengths = d_len;
     const DevGraph dg = trw_dev_graph(g);
-    const bool coop = algo == TRW_NODE2VEC || algo == TRW_METAPATH;
+    // Degree thresholds tried: MetaPath scans (coop_degree) or Node2Vec
+    // searches (search_degree); 0x7fffffff keeps every row with its own lane.
+    const int kOff = 0x7fffffff;
     const int threads_c[] = {128, 256, 512};
     const int chunk_c[] = {8, 32, 128};
-    const int coop_c[] = {64, 256, 1024};
+    std::vector<int> deg_c;
+    if (algo == TRW_METAPATH) deg_c = {64, 256, 1024, kOff};
+    else if (algo == TRW_NODE2VEC) deg_c = {64, 1024, kOff};
+    else deg_c = {kOff};
     for (int threads : threads_c) {
-      const int occ = persistent_blocks_per_sm(sp.algo, threads);
+      for (int cd : deg_c) {
+      const bool coop = cd != kOff;
+      const int occ = persistent_blocks_per_sm(sp.algo, threads, coop);
       for (int bps_div = 1; bps_div <= 2; ++bps_div) {
         const int bps = std::max(1, occ / bps_div);
         if (bps_div == 2 && bps == occ) continue;
         for (int chunk : chunk_c) {
-          for (int cd : coop_c) {
-            if (!coop && cd != coop_c[1]) continue;
+          {
             LaunchCfg cfg;
             cfg.block_threads = threads;
             cfg.grid_blocks = g->num_sms * bps;
             cfg.chunk = chunk;
-            cfg.coop_degree = cd;
+            cfg.coop_degree = algo == TRW_METAPATH ? cd : g->tuning.coop_degree;
+            cfg.search_degree = algo == TRW_NODE2VEC ? cd : g->tuning.search_degree;
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
               e = cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), g->stream);
@@ -80,10 +88,12 @@ extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params
               best.block_threads = threads;
               best.blocks_per_sm = bps;
               best.chunk = chunk;
-              best.coop_degree = cd;
+              best.coop_degree = cfg.coop_degree;
+              best.search_degree = cfg.search_degree;
             }
           }
         }
+      }
       }
     }
     Ctrl c{};

@@ -71,6 +71,7 @@ struct ServeDev {
   volatile unsigned long long* done;// [R] host-mapped: k + 1 once request k finished
   volatile int* done_err;           // [R] host-mapped: status of request k
   int R;
+  step::Coop coop;                  // rows this long go to the whole warp
   long long idle_ns;
 };
 
@@ -351,11 +352,19 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
 
     bool finishing = false;
     const int slot = (int)(cur_k % (unsigned long long)sv.R);
+    const WalkSpec& sp = *spec;
+    int r = step::kIdle;
+    int32_t next = -1;
+    step::Pend pend;
+    pend.kind = 0;
+    pend.res = 0;
+    if (active) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend, sv.coop);
+    if (__any_sync(0xffffffffu, r == step::kDefer)) {
+      step::warp_resolve(g, r, W, pend);
+      if (r == step::kDefer) r = step::step_finish(g, sp, W, pend, next);
+    }
     if (active) {
-      const WalkSpec& sp = *spec;
       const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
-      int32_t next = -1;
-      const int r = step::step_dispatch<MIXED, true>(g, sp, W, next);
       if (r == step::kMoved) {
         step::advance(W, next);
         if (!sp.endpoints) step::stage_put(st, sp.out_paths, next, aligned);
@@ -550,6 +559,7 @@ static cudaError_t launch_if_idle(trw_server* s) {
   sv.done = s->done_dev;
   sv.done_err = s->done_err_dev;
   sv.R = s->R;
+  sv.coop = step::Coop{s->g->tuning.coop_degree, s->g->tuning.search_degree};
   sv.idle_ns = (long long)s->cfg.idle_timeout_us * 1000;
   serve_kernel<<<s->grid_blocks, s->block_threads, s->smem, s->stream>>>(trw_dev_graph(s->g), sv);
   return cudaGetLastError();

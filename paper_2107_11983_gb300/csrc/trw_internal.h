@@ -12,11 +12,13 @@ struct LaunchCfg {
   int block_threads = 256;
   int grid_blocks = 0;       // persistent: resident blocks over all SMs
   int chunk = 32;            // walks per warp claim
-  int coop_degree = 256;     // rows this long or longer use warp-cooperative scans
+  int coop_degree = 256;     // MetaPath label rows this long or longer: warp-cooperative Gather
+  int search_degree = 0x7fffffff;  // Node2Vec rows of prev this long or longer: warp search
 };
 
-// Occupancy-derived resident blocks per SM of the persistent kernel for algo.
-int persistent_blocks_per_sm(int algo, int block_threads);
+// Occupancy-derived resident blocks per SM of the persistent kernel for algo
+// (coop: the variant with the warp-cooperative scan and search).
+int persistent_blocks_per_sm(int algo, int block_threads, bool coop);
 
 cudaError_t launch_validate_sources(const int32_t* src, int64_t n, int32_t nv, Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_walk_plain(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl, cudaStream_t st, int block);

@@ -66,10 +66,12 @@ __global__ void __launch_bounds__(256) walk_plain(DevGraph g, WalkSpec sp, Ctrl*
 
 // -------------------------------------------------------- persistent kernel
 
-template <int A>
-__global__ void __launch_bounds__(1024) walk_persistent(DevGraph g, WalkSpec sp0, const WalkSpec* __restrict__ specs,
+// COOP compiles in the warp-cooperative MetaPath scan and Node2Vec search;
+// without it every row stays with its lane (fewer registers).
+template <int A, bool COOP>
+__global__ void __launch_bounds__(512) walk_persistent(DevGraph g, WalkSpec sp0, const WalkSpec* __restrict__ specs,
                                                        const int64_t* __restrict__ prefix, int nreq, int64_t total,
-                                                       Ctrl* ctrl, int chunk) {
+                                                       Ctrl* ctrl, int chunk, Coop coop) {
   extern __shared__ int32_t stage_mem[];
   if (*(volatile int*)&ctrl->err != 0) return;
   const int lane = threadIdx.x & 31;
@@ -138,12 +140,22 @@ __global__ void __launch_bounds__(1024) walk_persistent(DevGraph g, WalkSpec sp0
     }
     if (!__any_sync(kFull, active)) break;
 
-    // ---- one unit of work per active lane
+    // ---- one unit of work per active lane; long rows go to the whole warp
+    const WalkSpec& sp = (A == MIXED) ? specs[req] : sp0;
+    int r = kIdle;
+    int32_t next = -1;
+    Pend pend;
+    pend.kind = 0;
+    pend.res = 0;
+    if (active) r = step_begin_dispatch<A>(g, sp, W, next, pend, COOP ? coop : Coop{0x7fffffff, 0x7fffffff});
+    if constexpr (COOP) {
+      if (__any_sync(kFull, r == kDefer)) {
+        warp_resolve(g, r, W, pend);
+        if (r == kDefer) r = step_finish(g, sp, W, pend, next);
+      }
+    }
     if (active) {
-      const WalkSpec& sp = (A == MIXED) ? specs[req] : sp0;
       const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
-      int32_t next = -1;
-      const int r = step_dispatch<A>(g, sp, W, next);
       if (r == kMoved) {
         advance(W, next);
         if (!sp.endpoints) stage_put(st, sp.out_paths, next, aligned);
@@ -190,14 +202,30 @@ int blocks_per_sm_of(K kernel, int threads) {
 
 }  // namespace
 
-int persistent_blocks_per_sm(int algo, int block_threads) {
+namespace {
+
+// Whether a launch needs the cooperative variant.
+bool wants_coop(int algo, const LaunchCfg& cfg) {
+  if (algo == MIXED) return true;
+  if (algo == METAPATH) return cfg.coop_degree < 0x7fffffff;
+  if (algo == NODE2VEC) return cfg.search_degree < 0x7fffffff;
+  return false;
+}
+
+}  // namespace
+
+int persistent_blocks_per_sm(int algo, int block_threads, bool coop) {
   switch (algo) {
-    case DEEPWALK: return blocks_per_sm_of(walk_persistent<DEEPWALK>, block_threads);
-    case DEEPWALK_WEIGHTED: return blocks_per_sm_of(walk_persistent<DEEPWALK_WEIGHTED>, block_threads);
-    case PPR: return blocks_per_sm_of(walk_persistent<PPR>, block_threads);
-    case NODE2VEC: return blocks_per_sm_of(walk_persistent<NODE2VEC>, block_threads);
-    case METAPATH: return blocks_per_sm_of(walk_persistent<METAPATH>, block_threads);
-    default: return blocks_per_sm_of(walk_persistent<MIXED>, block_threads);
+    case DEEPWALK: return blocks_per_sm_of(walk_persistent<DEEPWALK, false>, block_threads);
+    case DEEPWALK_WEIGHTED: return blocks_per_sm_of(walk_persistent<DEEPWALK_WEIGHTED, false>, block_threads);
+    case PPR: return blocks_per_sm_of(walk_persistent<PPR, false>, block_threads);
+    case NODE2VEC:
+      return coop ? blocks_per_sm_of(walk_persistent<NODE2VEC, true>, block_threads)
+                  : blocks_per_sm_of(walk_persistent<NODE2VEC, false>, block_threads);
+    case METAPATH:
+      return coop ? blocks_per_sm_of(walk_persistent<METAPATH, true>, block_threads)
+                  : blocks_per_sm_of(walk_persistent<METAPATH, false>, block_threads);
+    default: return blocks_per_sm_of(walk_persistent<MIXED, true>, block_threads);
   }
 }
 
@@ -235,25 +263,25 @@ cudaError_t launch_walk_persistent(const DevGraph& g, const WalkSpec& sp, Ctrl* 
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   const dim3 grid((unsigned)blocks);
+  const Coop coop{cfg.coop_degree, cfg.search_degree};
+  const bool cv = wants_coop(sp.algo, cfg);
+#define TRW_LAUNCH(A, C) \
+  walk_persistent<A, C><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk, coop)
   switch (sp.algo) {
-    case DEEPWALK:
-      walk_persistent<DEEPWALK><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
-      break;
-    case DEEPWALK_WEIGHTED:
-      walk_persistent<DEEPWALK_WEIGHTED><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl,
-                                                                      cfg.chunk);
-      break;
-    case PPR:
-      walk_persistent<PPR><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
-      break;
+    case DEEPWALK: TRW_LAUNCH(DEEPWALK, false); break;
+    case DEEPWALK_WEIGHTED: TRW_LAUNCH(DEEPWALK_WEIGHTED, false); break;
+    case PPR: TRW_LAUNCH(PPR, false); break;
     case NODE2VEC:
-      walk_persistent<NODE2VEC><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
+      if (cv) TRW_LAUNCH(NODE2VEC, true);
+      else TRW_LAUNCH(NODE2VEC, false);
       break;
     case METAPATH:
-      walk_persistent<METAPATH><<<grid, threads, smem, st>>>(g, sp, nullptr, nullptr, 1, sp.nwalks, ctrl, cfg.chunk);
+      if (cv) TRW_LAUNCH(METAPATH, true);
+      else TRW_LAUNCH(METAPATH, false);
       break;
     default: return cudaErrorInvalidValue;
   }
+#undef TRW_LAUNCH
   return cudaGetLastError();
 }
 
@@ -267,8 +295,9 @@ cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const 
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   WalkSpec dummy{};
-  walk_persistent<MIXED><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total, ctrl,
-                                                                   cfg.chunk);
+  walk_persistent<MIXED, true><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total,
+                                                                         ctrl, cfg.chunk,
+                                                                         Coop{cfg.coop_degree, cfg.search_degree});
   return cudaGetLastError();
 }
 

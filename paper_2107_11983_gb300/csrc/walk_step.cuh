@@ -23,7 +23,24 @@ struct Walker {
   uint32_t att;     // rejection trial within the step
 };
 
-enum StepResult : int { kMoved = 0, kStop = 1, kRetry = 2, kFail = 3, kBroken = 4 };
+enum StepResult : int { kIdle = -1, kMoved = 0, kStop = 1, kRetry = 2, kFail = 3, kBroken = 4, kDefer = 5 };
+
+// Row lengths from which a lane hands its work to the warp.
+struct Coop {
+  int32_t scan;    // MetaPath label rows at least this long: warp-cooperative Gather
+  int32_t search;  // Node2Vec neighbour checks in rows of prev at least this long: warp search
+};
+
+// Work a lane hands to its warp: a MetaPath Gather over a long row (kind 1)
+// or a Node2Vec IsNeighbor check in a long row of prev (kind 2).
+struct Pend {
+  uint32_t kind;            // 0 none, 1 MetaPath scan, 2 neighbour check
+  int32_t c;                // kind 2: candidate vertex
+  uint32_t y;               // kind 2: the dart
+  uint32_t hrep;            // kind 1: schema label replicated in four bytes
+  unsigned long long r64;   // kind 1: the draw that picks the r-th match
+  int32_t res;              // warp result: kind 1 index of the match (-1: none), kind 2 neighbour (0/1)
+};
 
 __device__ __forceinline__ void set_err(Ctrl* c, int e) { atomicCAS(&c->err, 0, e); }
 
@@ -85,25 +102,16 @@ __device__ __forceinline__ bool is_neighbor_serial(const int32_t* __restrict__ c
   return lo < pd && ldg(col + poff + lo) == c;
 }
 
-// O-REJ acceptance for Node2Vec's Weight (Eq. 1, Section 4.2 listing's rules):
-// MaxWeight on the first step, 1/a back to prev, 1 to a neighbour of prev,
-// 1/b otherwise.  The class is only resolved when the 32-bit dart y falls
-// between the two non-return thresholds.
-template <typename NbFn>
-__device__ __forceinline__ bool n2v_accept(const WalkSpec& sp, const Walker& W, int32_t c, uint32_t y, NbFn nb) {
-  if (W.s == 0) return true;
-  if (c == W.prev) return (uint64_t)y < sp.T_ret;
-  if ((uint64_t)y < sp.T_lo) return true;
-  if ((uint64_t)y >= sp.T_hi) return false;
-  return (uint64_t)y < (nb() ? sp.T_nb : sp.T_far);
-}
-
-// One unit of work for one walker, thread-serial: a full step, or one
-// rejection trial of a Node2Vec step.
+// One unit of work for one walker: a full step, or one rejection trial of a
+// Node2Vec step.  Rows at least coop long are not scanned or searched by the
+// lane alone: the step returns kDefer with the work in p, the warp resolves it
+// (warp_metapath / warp_neighbor) and step_finish completes the step.
 // CHECK adds range checks of the walker's vertex and of the row it loads
 // before any access through them (kBroken instead of an out-of-range read).
 template <int A, bool CHECK = false>
-__device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
+__device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next, Pend& p,
+                                          Coop coop) {
+  p.kind = 0;
   if (W.s == sp.max_len) return kStop;                         // Update: target length reached
   const uint4 B = draw_block(sp, W.w, (uint32_t)W.s, W.att);
   if (A == PPR && (uint64_t)B.w < sp.T_stop) return kStop;     // Update: PPR stop coin
@@ -129,6 +137,12 @@ __device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp
     // Gather (0/1 weights by label) then ITS generation: the r-th match.
     const uint32_t h = schema_label(sp, (uint32_t)W.s % sp.schema_len);
     const uint32_t hrep = h * 0x01010101u;
+    if (W.d >= coop.scan) {
+      p.kind = 1;
+      p.hrep = hrep;
+      p.r64 = ((unsigned long long)B.y << 32) | B.x;
+      return kDefer;
+    }
     const int64_t lo = W.off, hi = (int64_t)W.off + W.d;
     const uint32_t cnt = label_count_serial(g.labels, lo, hi, hrep);
     if (cnt == 0) return kStop;
@@ -139,12 +153,221 @@ __device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp
     return kMoved;
   } else {  // NODE2VEC, O-REJ
     const int32_t c = ldg(g.col + W.off + below(B, (uint32_t)W.d));
-    if (n2v_accept(sp, W, c, B.z, [&] { return is_neighbor_serial(g.col, W.poff, W.pd, c); })) {
+    bool accept;
+    if (W.s == 0) accept = true;                               // Weight = MaxWeight on the first step
+    else if (c == W.prev) accept = (uint64_t)B.z < sp.T_ret;
+    else if ((uint64_t)B.z < sp.T_lo) accept = true;
+    else if ((uint64_t)B.z >= sp.T_hi) accept = false;
+    else if (W.pd >= coop.search) {
+      p.kind = 2;
+      p.c = c;
+      p.y = B.z;
+      return kDefer;
+    } else {
+      accept = (uint64_t)B.z < (is_neighbor_serial(g.col, W.poff, W.pd, c) ? sp.T_nb : sp.T_far);
+    }
+    if (accept) {
       next = c;
       return kMoved;
     }
     return (W.att + 1 >= kRejectCap) ? kFail : kRetry;
   }
+}
+
+// The thread-serial step (no warp cooperation).
+template <int A, bool CHECK = false>
+__device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
+  Pend p;
+  return step_begin<A, CHECK>(g, sp, W, next, p, Coop{0x7fffffff, 0x7fffffff});
+}
+
+// Completes a deferred step once the warp has filled p.res.
+__device__ __forceinline__ int step_finish(const DevGraph& g, const WalkSpec& sp, const Walker& W, const Pend& p,
+                                           int32_t& next) {
+  if (p.kind == 1) {
+    if (p.res < 0) return kStop;                               // no edge carries the label
+    next = ldg(g.col + W.off + p.res);
+    return kMoved;
+  }
+  if ((uint64_t)p.y < (p.res ? sp.T_nb : sp.T_far)) {
+    next = p.c;
+    return kMoved;
+  }
+  return (W.att + 1 >= kRejectCap) ? kFail : kRetry;
+}
+
+// Bytes of the aligned word at wa that lie in [lo, hi), as a byte mask.
+__device__ __forceinline__ uint32_t bytes_in(int64_t wa, int64_t lo, int64_t hi) {
+  if (wa + 4 <= lo || wa >= hi) return 0u;
+  uint32_t m = 0xffffffffu;
+  if (wa < lo) m &= 0xffffffffu << (8 * (int)(lo - wa));
+  if (wa + 4 > hi) m &= 0xffffffffu >> (8 * (int)(wa + 4 - hi));
+  return m;
+}
+
+// Matching bytes (0xff each) of the 16 labels at p, limited to [lo, hi).
+__device__ __forceinline__ uint4 match16(const uint8_t* __restrict__ labels, int64_t p, int64_t lo, int64_t hi,
+                                         uint32_t hrep) {
+  uint4 m = make_uint4(0u, 0u, 0u, 0u);
+  if (p < hi) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(labels + p));
+    m.x = __vcmpeq4(v.x, hrep) & bytes_in(p, lo, hi);
+    m.y = __vcmpeq4(v.y, hrep) & bytes_in(p + 4, lo, hi);
+    m.z = __vcmpeq4(v.z, hrep) & bytes_in(p + 8, lo, hi);
+    m.w = __vcmpeq4(v.w, hrep) & bytes_in(p + 12, lo, hi);
+  }
+  return m;
+}
+
+__device__ __forceinline__ uint32_t count16(uint4 m) {
+  return (uint32_t)((__popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w)) >> 3);
+}
+
+// Index (relative to lo) of the k-th matching label among the 16 at pos.
+__device__ __forceinline__ int32_t kth_in16(uint4 m, uint32_t k, int64_t pos, int64_t lo) {
+  int32_t j = -1;
+#pragma unroll
+  for (int wi = 0; wi < 4; ++wi) {
+    const uint32_t w = (wi == 0) ? m.x : (wi == 1) ? m.y : (wi == 2) ? m.z : m.w;
+    const uint32_t cw = (uint32_t)__popc(w) >> 3;
+    if (j < 0) {
+      if (k < cw) {
+        for (int b = 0; b < 4; ++b) {
+          if ((w >> (8 * b)) & 0xffu) {
+            if (k == 0) {
+              j = (int32_t)(pos + 4 * wi + b - lo);
+              break;
+            }
+            --k;
+          }
+        }
+      } else {
+        k -= cw;
+      }
+    }
+  }
+  return j;
+}
+
+// Within one 512-byte chunk whose per-lane match masks are m: the index of the
+// r-th match of the chunk (r < the chunk's total), found with a warp prefix sum.
+__device__ __forceinline__ int32_t select_in_chunk(uint4 m, uint32_t r, int64_t pos, int64_t lo, int lane) {
+  const uint32_t c = count16(m);
+  uint32_t incl = c;
+#pragma unroll
+  for (int o2 = 1; o2 < 32; o2 <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, incl, o2);
+    if (lane >= o2) incl += t;
+  }
+  const bool mine = r >= incl - c && r < incl;
+  const int32_t j = mine ? kth_in16(m, r - (incl - c), pos, lo) : -1;
+  const unsigned owner = __ballot_sync(kFull, mine);
+  return __shfl_sync(kFull, j, __ffs(owner) - 1);
+}
+
+// Warp-cooperative MetaPath Gather + ITS generation for the lanes in `who`:
+// the warp counts the row's labels equal to the step's label 512 bytes at a
+// time (16 per lane, byte compares and popcount, a warp sum), lane g keeping
+// the total of chunk group g; it draws r in [0, cnt) from the owner's draw,
+// finds the group holding the r-th match with a warp prefix sum, and rescans
+// only that group (a one-chunk row is not rescanned).  Sets p.res of each owner.
+__device__ __forceinline__ void warp_metapath(const uint8_t* __restrict__ labels, unsigned who, const Walker& W,
+                                              Pend& p) {
+  const int lane = threadIdx.x & 31;
+  while (who) {
+    const int o = __ffs(who) - 1;
+    who &= who - 1;
+    const int64_t lo = __shfl_sync(kFull, W.off, o);
+    const int64_t hi = lo + __shfl_sync(kFull, W.d, o);
+    const uint32_t hrep = __shfl_sync(kFull, p.hrep, o);
+    const unsigned long long r64 = __shfl_sync(kFull, p.r64, o);
+    const int64_t a0 = lo & ~int64_t(15);
+    const int64_t nch = (hi - a0 + 511) >> 9;           // 512-byte chunks
+    const int64_t gs = (nch + 31) >> 5;                  // chunks per group (32 groups at most)
+    uint32_t cnt = 0, grp = 0;
+    uint4 m0 = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t k = 0; k < nch; ++k) {
+      const uint4 m = match16(labels, a0 + (k << 9) + 16 * lane, lo, hi, hrep);
+      if (k == 0) m0 = m;
+      const uint32_t t = __reduce_add_sync(kFull, count16(m));
+      cnt += t;
+      if (lane == (int)(k / gs)) grp += t;
+    }
+    int32_t res = -1;
+    if (cnt > 0) {
+      uint32_t r = (uint32_t)__umul64hi(r64, (unsigned long long)cnt);
+      if (nch == 1) {
+        res = select_in_chunk(m0, r, a0 + 16 * lane, lo, lane);
+      } else {
+        // the group holding match r
+        uint32_t incl = grp;
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, incl, o2);
+          if (lane >= o2) incl += t;
+        }
+        const unsigned hit = __ballot_sync(kFull, r >= incl - grp && r < incl);
+        const int tg = __ffs(hit) - 1;
+        r -= __shfl_sync(kFull, incl - grp, tg);
+        const int64_t k_end = min(nch, (int64_t)(tg + 1) * gs);
+        for (int64_t k = (int64_t)tg * gs; k < k_end; ++k) {
+          const int64_t pos = a0 + (k << 9) + 16 * lane;
+          const uint4 m = match16(labels, pos, lo, hi, hrep);
+          const uint32_t t = __reduce_add_sync(kFull, count16(m));
+          if (r < t) {
+            res = select_in_chunk(m, r, pos, lo, lane);
+            break;
+          }
+          r -= t;
+        }
+      }
+    }
+    if (lane == o) p.res = res;
+  }
+}
+
+// Warp-cooperative IsNeighbor(c, prev) for the lanes in `who`: a 32-way search
+// of c in the sorted row of prev -- each round the lanes load the last element
+// of 32 equal segments and keep the first segment whose last element is >= c --
+// then one compare per lane over the final <= 32 elements.  Sets p.res (0/1).
+__device__ __forceinline__ void warp_neighbor(const int32_t* __restrict__ col, unsigned who, const Walker& W, Pend& p) {
+  const int lane = threadIdx.x & 31;
+  while (who) {
+    const int o = __ffs(who) - 1;
+    who &= who - 1;
+    const int32_t poff = __shfl_sync(kFull, W.poff, o);
+    const int32_t c = __shfl_sync(kFull, p.c, o);
+    int32_t lo = 0, n = __shfl_sync(kFull, W.pd, o);
+    int found = -1;
+    while (n > 32) {
+      const int32_t last = lo + (int32_t)(((int64_t)(lane + 1) * n) >> 5) - 1;
+      const int32_t x = ldg(col + poff + last);
+      const unsigned ge = __ballot_sync(kFull, x >= c);
+      if (ge == 0u) {
+        found = 0;  // c is beyond the last element
+        break;
+      }
+      const int t = __ffs(ge) - 1;
+      if (__shfl_sync(kFull, x, t) == c) {
+        found = 1;
+        break;
+      }
+      const int32_t seg_lo = lo + (int32_t)(((int64_t)t * n) >> 5);
+      const int32_t seg_hi = lo + (int32_t)(((int64_t)(t + 1) * n) >> 5);
+      lo = seg_lo;
+      n = seg_hi - seg_lo;
+    }
+    if (found < 0) found = __ballot_sync(kFull, lane < n && ldg(col + poff + lo + lane) == c) != 0u ? 1 : 0;
+    if (lane == o) p.res = found;
+  }
+}
+
+// Resolves the deferred work of a warp; every lane of the warp must call it.
+__device__ __forceinline__ void warp_resolve(const DevGraph& g, int r, const Walker& W, Pend& p) {
+  const unsigned meta = __ballot_sync(kFull, r == kDefer && p.kind == 1);
+  if (meta) warp_metapath(g.labels, meta, W, p);
+  const unsigned nb = __ballot_sync(kFull, r == kDefer && p.kind == 2);
+  if (nb) warp_neighbor(g.col, nb, W, p);
 }
 
 __device__ __forceinline__ void advance(Walker& W, int32_t next) {
@@ -167,6 +390,24 @@ __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& 
       case PPR: return step_serial<PPR, CHECK>(g, sp, W, next);
       case NODE2VEC: return step_serial<NODE2VEC, CHECK>(g, sp, W, next);
       case METAPATH: return step_serial<METAPATH, CHECK>(g, sp, W, next);
+      default: return kBroken;
+    }
+  }
+}
+
+// step_begin for a compile-time or per-request algorithm.
+template <int A, bool CHECK = false>
+__device__ __forceinline__ int step_begin_dispatch(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next,
+                                                   Pend& p, Coop coop) {
+  if constexpr (A != MIXED) {
+    return step_begin<A, CHECK>(g, sp, W, next, p, coop);
+  } else {
+    switch (sp.algo) {
+      case DEEPWALK: return step_begin<DEEPWALK, CHECK>(g, sp, W, next, p, coop);
+      case DEEPWALK_WEIGHTED: return step_begin<DEEPWALK_WEIGHTED, CHECK>(g, sp, W, next, p, coop);
+      case PPR: return step_begin<PPR, CHECK>(g, sp, W, next, p, coop);
+      case NODE2VEC: return step_begin<NODE2VEC, CHECK>(g, sp, W, next, p, coop);
+      case METAPATH: return step_begin<METAPATH, CHECK>(g, sp, W, next, p, coop);
       default: return kBroken;
     }
   }

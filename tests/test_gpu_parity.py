@@ -217,8 +217,8 @@ def test_results_independent_of_tuning(small):
     want = oracle_walk(g, trw.NODE2VEC, src, 40, seed=3, **kw)
     old = G.tuning()
     try:
-        for bt, ch, cd in [(128, 1, 8), (512, 7, 100000), (64, 128, 32)]:
-            G.set_tuning(block_threads=bt, chunk=ch, coop_degree=cd, blocks_per_sm=1)
+        for bt, ch, cd, sd in [(128, 1, 8, 33), (512, 7, 100000, 0x7fffffff), (64, 128, 32, 100), (96, 3, 1, 40)]:
+            G.set_tuning(block_threads=bt, chunk=ch, coop_degree=cd, search_degree=sd, blocks_per_sm=1)
             out = G.walk(trw.NODE2VEC, src, 40, seed=3, **kw)
             assert_paths_equal(out.paths, out.lengths, want)
     finally:
@@ -246,3 +246,31 @@ def test_directed_graph_parity():
                            **ALGO_KW[algo])
         out = G.walk(algo, src, 25, seed=31, **ALGO_KW[algo])
         assert_paths_equal(out.paths, out.lengths, want)
+
+
+@pytest.mark.parametrize("coop", [1, 33, 1 << 30], ids=["coop-all", "coop-33", "coop-off"])
+def test_warp_cooperative_paths_bit_exact(small, coop):
+    """MetaPath label scans and Node2Vec neighbour checks handed to the whole
+    warp (every row at coop 1) give the same paths as the oracle."""
+    g, G = small
+    src = np.concatenate([synth.vertex_sources(g.nv), synth.sources(999, g.nv, seed=8)])
+    old = G.tuning()
+    try:
+        G.set_tuning(coop_degree=coop, search_degree=max(coop, 33))
+        for algo in (trw.METAPATH, trw.NODE2VEC):
+            for kw in ([ALGO_KW[algo], {"n2v_p": 2.0, "n2v_q": 0.5}] if algo == trw.NODE2VEC else [ALGO_KW[algo]]):
+                want = oracle_walk(g, algo, src, 60, seed=13, **kw)
+                out = G.walk(algo, torch.from_numpy(src).cuda(), 60, seed=13, kernel=trw.KERNEL_PERSISTENT, **kw)
+                torch.cuda.synchronize()
+                assert_paths_equal(out.paths.cpu().numpy(), out.lengths.cpu().numpy(), want)
+        reqs = [dict(algo=trw.METAPATH, sources=src, max_len=50, seed=3, schema=np.array([2, 4, 1], np.uint8)),
+                dict(algo=trw.NODE2VEC, sources=src[:700], max_len=50, seed=4, n2v_p=0.5, n2v_q=2.0),
+                dict(algo=trw.PPR, sources=src[:300], max_len=100, seed=5, ppr_stop=0.2)]
+        outs = G.walk_batch(reqs)
+        torch.cuda.synchronize()
+        for r, o in zip(reqs, outs):
+            kw = {k: r[k] for k in ("schema", "n2v_p", "n2v_q", "ppr_stop") if k in r}
+            want = oracle_walk(g, r["algo"], r["sources"], r["max_len"], r["seed"], **kw)
+            assert_paths_equal(o.paths.cpu().numpy(), o.lengths.cpu().numpy(), want)
+    finally:
+        G.set_tuning(**old)

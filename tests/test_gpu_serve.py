@@ -150,6 +150,22 @@ def test_serve_admission_and_ids(served, server_factory):
     assert e.value.status == -1
 
 
+def test_serve_warp_cooperative_rows(served, server_factory):
+    g, G = served
+    old = G.tuning()
+    G.set_tuning(coop_degree=1, search_degree=33)  # MetaPath scans and neighbour checks go to the warp
+    try:
+        S = server_factory(G, max_requests=16)
+        rng = np.random.default_rng(5)
+        reqs = [make_request(g, i, rng) for i in range(10)]
+        live = [(r,) + submit(S, r) for r in reqs]
+        for r, rid, op, ol in live:
+            wait(S, rid)
+            check(g, r, op, ol)
+    finally:
+        G.set_tuning(**old)
+
+
 def test_serve_relaunch_after_idle(served, server_factory):
     g, G = served
     S = server_factory(G, max_requests=8, idle_timeout_us=200)
