@@ -297,6 +297,128 @@ def measure_per_algo(trw, torch, G, g, flush, sp):
     return out
 
 
+def serve_trace(g, n_requests, rate, seed=6):
+    """The serving mix (an open-loop Poisson trace): 90% single-source PPR with
+    n log-uniform in [1e3, 1e5] (endpoints), 5% weighted DeepWalk and 5%
+    Node2Vec with n log-uniform in [1e4, 1e6] walks of 80 moves from uniform
+    sources.  Returns arrival offsets (s) and request dicts."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    t = np.cumsum(gaps) - gaps[0]
+    reqs = []
+    for i in range(n_requests):
+        u = rng.random()
+        if u < 0.90:
+            n = int(10 ** rng.uniform(3, 5))
+            reqs.append(dict(algo=2, sources=synth.sources(1, g.nv, seed=1000 + i), walks_per_source=n, max_len=1000,
+                             seed=i, ppr_stop=0.2, endpoints=True))
+        else:
+            n = int(10 ** rng.uniform(4, 6))
+            algo = 1 if u < 0.95 else 3
+            kw = {"n2v_p": 0.5, "n2v_q": 2.0} if algo == 3 else {}
+            reqs.append(dict(algo=algo, sources=synth.sources(n, g.nv, seed=1000 + i), max_len=80, seed=i, **kw))
+    return t, reqs
+
+
+def _req_kwargs(r):
+    return {k: r[k] for k in ("ppr_stop", "n2v_p", "n2v_q", "walks_per_source", "endpoints") if k in r}
+
+
+def _out_buffers(torch, r, dev):
+    n = int(r["sources"].shape[0]) * r.get("walks_per_source", 1)
+    shape = (n,) if r.get("endpoints") else (n, r["max_len"] + 1)
+    return torch.empty(shape, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev)
+
+
+def measure_serve(trw, torch, G, g, n_requests=3000, rate=2000.0):
+    """p50/p99 submit-to-done latency of the serving loop on an open-loop
+    Poisson trace, against the plain baseline (one launch per request, FIFO,
+    one stream), and saturating steps/s with every request queued at once."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t_arr, reqs = serve_trace(g, n_requests, rate)
+    srcs = [torch.from_numpy(r["sources"]).to(dev) for r in reqs]
+    torch.cuda.synchronize()
+    out = {"requests": n_requests, "rate_per_s": rate,
+           "mix": "90% PPR single-source 1e3-1e5 walks (endpoints), 5% weighted DeepWalk, 5% Node2Vec 1e4-1e6 x 80"}
+
+    def run_server(open_loop):
+        S = trw.Server(G, max_requests=1024)
+        pending = {}
+        lat, moves = [], 0
+        done_bufs = []
+        t0 = time.perf_counter()
+        i = 0
+        while i < n_requests or pending:
+            now = time.perf_counter() - t0
+            while i < n_requests and (not open_loop or t_arr[i] <= now):
+                r = reqs[i]
+                op, ol = _out_buffers(torch, r, dev)
+                ts = time.perf_counter()
+                try:
+                    rid = S.submit(r["algo"], srcs[i], r["max_len"], r["seed"], op, ol, **_req_kwargs(r))
+                except trw.TRWError as e:
+                    if e.status == -7:  # busy: retry after polling
+                        break
+                    raise
+                pending[rid] = (ts, op, ol)
+                i += 1
+                now = time.perf_counter() - t0
+            for rid in list(pending):
+                if S.poll(rid) == trw.OK:
+                    ts, op, ol = pending.pop(rid)
+                    lat.append(time.perf_counter() - ts)
+                    done_bufs.append(ol)
+        wall = time.perf_counter() - t0
+        S.close()
+        torch.cuda.synchronize()
+        moves = int(sum(int((ol.to(torch.int64) - 1).sum().item()) for ol in done_bufs))
+        return np.array(lat), wall, moves
+
+    def run_plain():
+        stream = torch.cuda.Stream()
+        sp = stream.cuda_stream
+        lat, done_bufs = [], []
+        pending = []
+        t0 = time.perf_counter()
+        i = 0
+        while i < n_requests or pending:
+            now = time.perf_counter() - t0
+            while i < n_requests and t_arr[i] <= now:
+                r = reqs[i]
+                op, ol = _out_buffers(torch, r, dev)
+                ts = time.perf_counter()
+                torch.cuda.current_stream().synchronize()
+                G.walk(r["algo"], srcs[i], r["max_len"], r["seed"], kernel=trw.KERNEL_PLAIN, out_paths=op,
+                       out_lengths=ol, stream=sp, sync=False, **_req_kwargs(r))
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                pending.append((ts, ev, ol))
+                i += 1
+                now = time.perf_counter() - t0
+            while pending and pending[0][1].query():
+                ts, ev, ol = pending.pop(0)
+                lat.append(time.perf_counter() - ts)
+                done_bufs.append(ol)
+        wall = time.perf_counter() - t0
+        G.sync(sp)
+        moves = int(sum(int((ol.to(torch.int64) - 1).sum().item()) for ol in done_bufs))
+        return np.array(lat), wall, moves
+
+    def pct(a):
+        return {"p50_ms": round(1000 * float(np.percentile(a, 50)), 3), "p99_ms": round(1000 * float(np.percentile(a, 99)), 3),
+                "mean_ms": round(1000 * float(a.mean()), 3)}
+
+    lat, wall, moves = run_server(True)
+    out["served"] = dict(pct(lat), steps_per_s=round(moves / wall, 1), wall_s=round(wall, 3))
+    lat, wall, moves = run_plain()
+    out["plain_fifo"] = dict(pct(lat), steps_per_s=round(moves / wall, 1), wall_s=round(wall, 3))
+    lat, wall, moves = run_server(False)
+    out["saturating"] = {"steps_per_s": round(moves / wall, 1), "wall_s": round(wall, 3), "moves": moves}
+    out["p99_speedup_vs_plain"] = round(out["plain_fifo"]["p99_ms"] / out["served"]["p99_ms"], 3)
+    log(f"serve: {out}")
+    return out
+
+
 def measure_gather_ceiling(trw, g):
     """Dependent random 16-byte loads over a table the size of the alias
     records, at walk-kernel occupancy: the practical random-access ceiling."""
@@ -441,9 +563,12 @@ def run_ours(args, wl):
 
     per_algo = None
     gather = None
+    serve = None
     if rank == 0 and not args.no_extras:
         per_algo = measure_per_algo(trw, torch, G, g, flush, sp)
         gather = measure_gather_ceiling(trw, g)
+        if G.has_weights:
+            serve = measure_serve(trw, torch, G, g, n_requests=args.serve_requests)
         if roof is not None and gather is not None:
             roof["random_gather_ceiling_steps_per_s"] = gather["loads_per_s"]
             roof["frac_of_gather_ceiling"] = round(value / ws / gather["loads_per_s"], 4)
@@ -473,6 +598,7 @@ def run_ours(args, wl):
         "gpu_launches": 2 * args.steps,
         "roofline": roof,
         "per_algo": per_algo,
+        "serve": serve,
         "gather_ceiling": gather,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -492,6 +618,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-algorithm lines and the gather ceiling")
     ap.add_argument("--scale", type=int, default=0, help="override the R-MAT scale (smaller profiling cases)")
+    ap.add_argument("--serve-requests", type=int, default=3000, help="requests in the serving trace")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 steps")

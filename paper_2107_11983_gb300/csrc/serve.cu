@@ -8,11 +8,10 @@
 //     (the only reader of the host ring), cuts each new request into chunks of
 //     walks and pushes them into a device chunk queue;
 //   - every other warp is a worker: it pops chunks (CAS on the queue head),
-//     copies the request's descriptor into shared memory (field by field,
-//     past L1, so a reused slot is never read stale), runs the walks with the
-//     same step code as the batch kernels and refills a lane as soon as its
-//     walk ends.  A warp holds one request at a time and switches when its
-//     lanes have drained; different warps run different requests at once;
+//     copies the request's descriptor into one of its two shared-memory slots
+//     (field by field, past L1, so a reused table entry is never read stale),
+//     runs the walks with the same step code as the batch kernels and refills
+//     a lane as soon as its walk ends, from the newest request it holds;
 //   - when the last walk of a request ends, the lane that finished it fences
 //     and writes the request's done flag to host-mapped memory.
 // Every wait is bounded: with no work for idle_timeout_us the kernel exits,
@@ -36,22 +35,39 @@ using namespace trw;
 namespace {
 
 constexpr uint32_t kQueueCap = 1u << 16;
+constexpr int kMaxActive = 64;        // requests the dispatcher interleaves
 
 struct Chunk {
   unsigned long long k;   // request number
   uint32_t begin, end;    // walk range within the request
+  unsigned long long seq; // queue position it was written for (checked by the reader)
+  unsigned long long pad;
 };
 
 struct ServeState {       // device memory, persists across launches
   unsigned long long q_head;      // next queue entry to pop
   unsigned long long q_tail;      // entries pushed
   unsigned long long q_consumed;  // entries popped and read
-  unsigned long long disp_k;      // dispatcher: next request to cut
-  unsigned long long disp_pos;    // dispatcher: next walk of that request
+  unsigned long long disp_next;   // dispatcher: next published request to admit
+  int n_act;                      // dispatcher: requests with walks not yet queued
+  int rr;                         // dispatcher: round-robin cursor
+  unsigned long long act_k[kMaxActive];    // their request numbers
+  unsigned long long act_pos[kMaxActive];  // next walk to queue
+  unsigned long long act_n[kMaxActive];    // walks of the request
+  unsigned long long act_cw[kMaxActive];   // walks per chunk
   unsigned long long moves;       // total moves of finished walks
+  int exit_now;                   // set by the dispatcher: the launch is ending (cleared before each launch)
   int live_workers;               // worker warps of the running launch
   int err;                        // first failed self-check (kernel-wide)
   unsigned long long bad[4];      // what that check saw
+};
+
+// Everything the device keeps per request slot, uploaded at submit in one copy.
+struct SlotRec {
+  WalkSpec spec;                  // the request
+  unsigned long long finished;    // walks finished (zero at submit)
+  uint32_t cw;                    // walks per chunk
+  int err;                        // first error of the request (zero at submit)
 };
 
 struct ServeHost {        // host-mapped pinned memory
@@ -63,16 +79,14 @@ struct ServeHost {        // host-mapped pinned memory
 struct ServeDev {
   ServeState* state;
   Chunk* queue;                     // [kQueueCap]
-  const WalkSpec* specs;            // [R]
-  const uint32_t* chunk_walks;      // [R] walks per chunk for the request in each slot
-  unsigned long long* finished;     // [R] finished walks
-  int* err;                         // [R] first error of the request
+  SlotRec* slots;                   // [R]
   volatile ServeHost* host;         // device pointer to host-mapped control
   volatile unsigned long long* done;// [R] host-mapped: k + 1 once request k finished
   volatile int* done_err;           // [R] host-mapped: status of request k
   int R;
   step::Coop coop;                  // rows this long go to the whole warp
   long long idle_ns;
+  unsigned long long depth;         // queued chunks the dispatcher keeps ahead of the workers
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const volatile unsigned long long* p) {
@@ -97,53 +111,101 @@ __device__ __forceinline__ long long now_ns() {
   return (long long)t;
 }
 
-// Dispatcher: cut published requests into chunks.  One warp; lane 0 works.
-__device__ void dispatcher(const ServeDev& sv) {
+// Active-request set of the dispatcher, kept in shared memory during a launch
+// and saved to the persistent state when the launch ends.
+struct ActiveSet {
+  unsigned long long k[kMaxActive];
+  unsigned long long pos[kMaxActive];
+  unsigned long long n[kMaxActive];
+  unsigned long long cw[kMaxActive];
+};
+
+// Dispatcher: admits published requests into an active set and cuts them into
+// chunks round-robin, keeping at most sv.depth chunks queued, so a request
+// that arrives behind a large one waits for a bounded number of chunks, not
+// for the large request.  It alone decides when the launch ends: after
+// idle_timeout with nothing to hand out, or on the host's stop, it raises
+// exit_now for the workers.  One warp; lane 0 works.
+__device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
   const int lane = threadIdx.x & 31;
+  ServeState* st = sv.state;
+  int n_act = 0, rr = 0;
+  if (lane == 0) {
+    n_act = st->n_act;
+    rr = st->rr;
+    for (int i = 0; i < n_act; ++i) {
+      act->k[i] = st->act_k[i];
+      act->pos[i] = st->act_pos[i];
+      act->n[i] = st->act_n[i];
+      act->cw[i] = st->act_cw[i];
+    }
+  }
   long long idle_since = now_ns();
+  unsigned long long disp_next = st->disp_next;
+  unsigned long long tail = st->q_tail;
   for (;;) {
     int go = 1;
     if (lane == 0) {
-      bool progress = false;
-      ServeState* st = sv.state;
       const unsigned long long P = ld_acquire_sys(&sv.host->published);
-      unsigned long long k = st->disp_k, pos = st->disp_pos, tail = st->q_tail;
+      while (n_act < kMaxActive && disp_next < P) {
+        const int slot = (int)(disp_next % (unsigned long long)sv.R);
+        const unsigned long long n = (unsigned long long)__ldcg(&sv.slots[slot].spec.nwalks);
+        if (n > 0) {
+          act->k[n_act] = disp_next;
+          act->pos[n_act] = 0;
+          act->n[n_act] = n;
+          act->cw[n_act] = __ldcg(&sv.slots[slot].cw);
+          ++n_act;
+        }
+        ++disp_next;
+      }
       const unsigned long long consumed = ld_acquire_gpu(&st->q_consumed);
       int pushed = 0;
-      while (k < P && tail - consumed < kQueueCap && pushed < 4096) {
-        const int slot = (int)(k % (unsigned long long)sv.R);
-        const unsigned long long n = (unsigned long long)__ldcg(&sv.specs[slot].nwalks);
-        if (pos >= n) {
-          ++k;
-          pos = 0;
-          continue;
-        }
-        const unsigned long long cw = __ldcg(&sv.chunk_walks[slot]);
-        const unsigned long long end = pos + cw < n ? pos + cw : n;
-        Chunk c;
-        c.k = k;
-        c.begin = (uint32_t)pos;
-        c.end = (uint32_t)end;
-        __stcg(&sv.queue[tail % kQueueCap].k, c.k);
-        __stcg(reinterpret_cast<uint2*>(&sv.queue[tail % kQueueCap].begin), make_uint2(c.begin, c.end));
+      while (n_act > 0 && tail - consumed < sv.depth && pushed < 512) {
+        if (rr >= n_act) rr = 0;
+        const unsigned long long pos = act->pos[rr], n = act->n[rr];
+        const unsigned long long end = pos + act->cw[rr] < n ? pos + act->cw[rr] : n;
+        Chunk* c = &sv.queue[tail % kQueueCap];
+        __stcg(&c->k, act->k[rr]);
+        __stcg(reinterpret_cast<uint2*>(&c->begin), make_uint2((uint32_t)pos, (uint32_t)end));
+        __stcg(&c->seq, tail);
         ++tail;
         ++pushed;
-        pos = end;
-        progress = true;
+        if (end >= n) {  // fully queued: leaves the active set
+          --n_act;
+          act->k[rr] = act->k[n_act];
+          act->pos[rr] = act->pos[n_act];
+          act->n[rr] = act->n[n_act];
+          act->cw[rr] = act->cw[n_act];
+        } else {
+          act->pos[rr] = end;
+          ++rr;
+        }
       }
-      st->disp_k = k;
-      st->disp_pos = pos;
-      if (progress) {
+      if (pushed) {
         __threadfence();
         st_release_gpu(&st->q_tail, tail);
         idle_since = now_ns();
       } else {
         const long long t = now_ns();
+        const bool nothing_left = n_act == 0 && disp_next >= P;
         if (sv.host->stop) go = 0;
-        else if (t - idle_since > sv.idle_ns &&
-                 (ld_acquire_gpu(&st->q_consumed) == tail || atomicAdd(&st->live_workers, 0) == 0))
-          go = 0;  // nothing left to hand out, or nobody left to take it (the host relaunches)
-        else __nanosleep(2000);
+        else if (t - idle_since > sv.idle_ns && nothing_left && ld_acquire_gpu(&st->q_consumed) == tail) go = 0;
+        else __nanosleep(1000);
+      }
+      if (!go) {
+        // save the dispatcher's state for the next launch, then end this one
+        st->disp_next = disp_next;
+        st->n_act = n_act;
+        st->rr = rr;
+        for (int i = 0; i < n_act; ++i) {
+          st->act_k[i] = act->k[i];
+          st->act_pos[i] = act->pos[i];
+          st->act_n[i] = act->n[i];
+          st->act_cw[i] = act->cw[i];
+        }
+        __threadfence();
+        atomicExch(&st->exit_now, 1);
       }
     }
     go = __shfl_sync(0xffffffffu, go, 0);
@@ -216,22 +278,31 @@ __device__ __forceinline__ void record_bad(const ServeDev& sv, int bad, unsigned
   }
 }
 
-// Worker warps run walks of one request at a time: lanes are refilled from
-// chunks of that request; a chunk of another request waits until every lane
-// has finished, then the warp switches its descriptor.
-__global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
+// Worker warps hold up to two requests in two descriptor slots: the current
+// slot, which new walks come from, and the other, whose walks may still be
+// running.  Idle lanes therefore start walks of a new request at once; a chunk
+// of a third request waits until the other slot has drained.  Every lane keeps
+// the number of its own request and checks it against its slot before using
+// the slot (a mismatch is recorded and the walk ends without a write).
+__global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  WalkSpec* spec = reinterpret_cast<WalkSpec*>(smem_raw) + wid;
-  int32_t* stage_mem = reinterpret_cast<int32_t*>(smem_raw + sizeof(WalkSpec) * nwarps);
+  WalkSpec* spec = reinterpret_cast<WalkSpec*>(smem_raw) + 2 * wid;
+  unsigned long long* key =
+      reinterpret_cast<unsigned long long*>(smem_raw + sizeof(WalkSpec) * 2 * nwarps) + 2 * wid;
+  int32_t* stage_mem = reinterpret_cast<int32_t*>(smem_raw + (sizeof(WalkSpec) + 8) * 2 * nwarps);
+  ActiveSet* act =
+      reinterpret_cast<ActiveSet*>(smem_raw + (sizeof(WalkSpec) + 8) * 2 * nwarps + (size_t)blockDim.x * 32);
 
   if (blockIdx.x == 0 && wid == 0) {
-    dispatcher(sv);
+    dispatcher(sv, act);
     return;
   }
+  if (lane < 2) key[lane] = ~0ull;
   if (lane == 0) atomicAdd(&sv.state->live_workers, 1);
+  __syncwarp();
 
   const unsigned lt_mask = (1u << lane) - 1u;
   step::Stage st;
@@ -242,9 +313,13 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
   W.w = 0; W.s = 0; W.cur = 0; W.prev = -1; W.off = W.d = W.poff = W.pd = 0; W.att = 0;
   bool active = false;
   int64_t walk = 0;
-  unsigned long long cur_k = ~0ull;   // request whose descriptor is in spec (warp-uniform)
-  uint32_t wlo = 0, whi = 0;          // unassigned walks of cur_k (warp-uniform)
-  bool pend = false;                  // a popped chunk of another request (warp-uniform)
+  int ent = 0;                        // this lane's slot
+  unsigned long long my_k = ~0ull;    // this lane's request
+  int cur = 0;                        // slot receiving new walks (warp-uniform)
+  uint32_t wlo = 0, whi = 0;          // unassigned walks of key[cur] (warp-uniform)
+  bool pend = false;                  // a popped chunk not yet placed (warp-uniform)
+  bool has_ticket = false;            // lane 0: holds a queue ticket not yet served
+  unsigned long long ticket = 0;
   unsigned long long pk = 0;
   uint32_t pb = 0, pe = 0;
   long long idle_since = now_ns();
@@ -259,20 +334,26 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
           uint32_t cb = 0, ce = 0;
           int got = 0;
           if (lane == 0) {
+            // A ticket (fetch-and-add on the queue head, which always succeeds)
+            // names the next entry this warp reads once the tail passes it.
             ServeState* s = sv.state;
-            for (int tries = 0; tries < 64; ++tries) {
-              const unsigned long long h = *(volatile unsigned long long*)&s->q_head;
-              const unsigned long long t = ld_acquire_gpu(&s->q_tail);
-              if (h >= t) break;
-              if (atomicCAS(&s->q_head, h, h + 1) == h) {
-                const Chunk* c = &sv.queue[h % kQueueCap];
-                ck = ldcg_as(&c->k);
-                cb = ldcg_as(&c->begin);
-                ce = ldcg_as(&c->end);
-                __threadfence();
-                atomicAdd(&s->q_consumed, 1ull);
-                got = 1;
-                break;
+            if (!has_ticket) {
+              ticket = atomicAdd(&s->q_head, 1ull);
+              has_ticket = true;
+            }
+            if (ticket < ld_acquire_gpu(&s->q_tail)) {
+              const Chunk* c = &sv.queue[ticket % kQueueCap];
+              ck = ldcg_as(&c->k);
+              cb = ldcg_as(&c->begin);
+              ce = ldcg_as(&c->end);
+              const unsigned long long seq = ldcg_as(&c->seq);
+              __threadfence();
+              atomicAdd(&s->q_consumed, 1ull);
+              has_ticket = false;
+              got = 1;
+              if (seq != ticket) {  // overwritten before it was read: record, skip
+                record_bad(sv, 7, ticket, seq, ck, 0);
+                got = 0;
               }
             }
           }
@@ -281,44 +362,52 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
           ck = __shfl_sync(0xffffffffu, ck, 0);
           cb = __shfl_sync(0xffffffffu, cb, 0);
           ce = __shfl_sync(0xffffffffu, ce, 0);
-          if (ck == cur_k) {
+          if (ck == key[cur]) {  // more walks of the current request
             wlo = cb;
             whi = ce;
-          } else {
-            pend = true;
-            pk = ck;
-            pb = cb;
-            pe = ce;
-          }
-        }
-        if (pend) {
-          // switch only once the warp has drained the current request
-          if (__any_sync(0xffffffffu, active)) break;
-          int bad = 0;
-          if (lane == 0) {
-            load_spec(&sv.specs[(int)(pk % (unsigned long long)sv.R)], spec);
-            bad = spec_check(*spec, pk, pb, pe, ld_acquire_sys(&sv.host->published));
-            if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec->nwalks,
-                                reinterpret_cast<uintptr_t>(spec->out_paths));
-          }
-          bad = __shfl_sync(0xffffffffu, bad, 0);
-          __syncwarp();
-          pend = false;
-          if (bad) {
-            cur_k = ~0ull;
-            wlo = whi = 0;
             continue;
           }
-          cur_k = pk;
+          pend = true;
+          pk = ck;
+          pb = cb;
+          pe = ce;
+        }
+        const int other = 1 - cur;
+        if (key[other] == pk) {  // the other slot already holds the request
+          cur = other;
           wlo = pb;
           whi = pe;
+          pend = false;
+          continue;
         }
+        // a slot takes a new request only once none of its lanes is running
+        const bool other_busy = __ballot_sync(0xffffffffu, active && ent == other) != 0u;
+        const bool cur_busy = __ballot_sync(0xffffffffu, active && ent == cur) != 0u;
+        const int tgt = !other_busy ? other : (!cur_busy ? cur : -1);
+        if (tgt < 0) break;
+        int bad = 0;
+        if (lane == 0) {
+          load_spec(&sv.slots[(int)(pk % (unsigned long long)sv.R)].spec, &spec[tgt]);
+          bad = spec_check(spec[tgt], pk, pb, pe, ld_acquire_sys(&sv.host->published));
+          if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec[tgt].nwalks,
+                              reinterpret_cast<uintptr_t>(spec[tgt].out_paths));
+          key[tgt] = bad ? ~0ull : pk;
+        }
+        bad = __shfl_sync(0xffffffffu, bad, 0);
+        __syncwarp();
+        pend = false;
+        if (bad) continue;
+        cur = tgt;
+        wlo = pb;
+        whi = pe;
         continue;
       }
       const int take = (int)min((uint32_t)__popc(idle), whi - wlo);
       const int rank = __popc(idle & lt_mask);
       if (((idle >> lane) & 1u) && rank < take) {
-        const WalkSpec& sp = *spec;
+        const WalkSpec& sp = spec[cur];
+        ent = cur;
+        my_k = key[cur];
         walk = (int64_t)wlo + rank;
         const int32_t src = __ldcg(sp.sources + walk / sp.wps);
         W.w = sp.walk_offset + (uint32_t)walk;
@@ -338,12 +427,17 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
     }
 
     if (!__any_sync(0xffffffffu, active)) {
+      // Idle: wait for chunks until the dispatcher ends the launch (with an
+      // absolute bound of 1000 idle timeouts should it never do so).
       int go = 1;
       if (lane == 0) {
         const long long t = now_ns();
-        if (sv.host->stop) go = 0;
-        else if (t - idle_since > sv.idle_ns) go = 0;
-        else __nanosleep(1000);
+        // leave once the dispatcher ended the launch and no entry waits for this warp
+        if (*(volatile int*)&sv.state->exit_now &&
+            (!has_ticket || ticket >= ld_acquire_gpu(&sv.state->q_tail)))
+          go = 0;
+        else if (t - idle_since > 1000 * sv.idle_ns) go = 0;
+        else __nanosleep(2000);
       }
       if (!__shfl_sync(0xffffffffu, go, 0)) break;
       continue;
@@ -351,19 +445,25 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
     idle_since = now_ns();
 
     bool finishing = false;
-    const int slot = (int)(cur_k % (unsigned long long)sv.R);
-    const WalkSpec& sp = *spec;
+    const bool mine = active && key[ent] == my_k;
+    if (active && !mine) {
+      // the slot no longer holds this lane's request: record, stop, write nothing
+      record_bad(sv, 6, my_k, (unsigned long long)walk, key[ent], (unsigned long long)ent);
+      active = false;
+    }
+    const WalkSpec& sp = spec[ent];
     int r = step::kIdle;
     int32_t next = -1;
-    step::Pend pend;
-    pend.kind = 0;
-    pend.res = 0;
-    if (active) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend, sv.coop);
+    step::Pend pend_work;
+    pend_work.kind = 0;
+    pend_work.res = 0;
+    if (mine) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend_work, sv.coop);
     if (__any_sync(0xffffffffu, r == step::kDefer)) {
-      step::warp_resolve(g, r, W, pend);
-      if (r == step::kDefer) r = step::step_finish(g, sp, W, pend, next);
+      step::warp_resolve(g, r, W, pend_work);
+      if (r == step::kDefer) r = step::step_finish(g, sp, W, pend_work, next);
     }
-    if (active) {
+    if (mine) {
+      const int slot = (int)(my_k % (unsigned long long)sv.R);
       const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
       if (r == step::kMoved) {
         step::advance(W, next);
@@ -371,10 +471,10 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
       } else if (r == step::kRetry) {
         W.att += 1;
       } else {
-        if (r == step::kFail) atomicCAS(&sv.err[slot], 0, kErrRejectCap);
+        if (r == step::kFail) atomicCAS(&sv.slots[slot].err, 0, kErrRejectCap);
         if (r == step::kBroken) {
-          atomicCAS(&sv.err[slot], 0, kErrInternal);
-          record_bad(sv, 5, cur_k, (unsigned long long)walk, (unsigned long long)(uint32_t)W.cur,
+          atomicCAS(&sv.slots[slot].err, 0, kErrInternal);
+          record_bad(sv, 5, my_k, (unsigned long long)walk, (unsigned long long)(uint32_t)W.cur,
                      ((unsigned long long)(uint32_t)W.off << 32) | (uint32_t)W.d);
         }
         if (sp.endpoints) __stcs(sp.out_paths + walk, W.cur);
@@ -385,21 +485,28 @@ __global__ void __launch_bounds__(256) serve_kernel(DevGraph g, ServeDev sv) {
         active = false;
       }
     }
-    // Completion: every active lane belongs to cur_k.
-    const unsigned fin = __ballot_sync(0xffffffffu, finishing);
-    if (fin) {
+    // Completion, per slot: every finishing lane of slot e belongs to key[e].
+    const unsigned fin0 = __ballot_sync(0xffffffffu, finishing && ent == 0);
+    const unsigned fin1 = __ballot_sync(0xffffffffu, finishing && ent == 1);
+    if (fin0 | fin1) {
       __threadfence();  // outputs of the finishing lanes before their count
       __syncwarp();
       if (lane == 0) {
-        const unsigned long long cnt = (unsigned long long)__popc(fin);
-        const unsigned long long old = atomicAdd(&sv.finished[slot], cnt);
-        if (old + cnt == (unsigned long long)spec->nwalks) {
-          __threadfence();
-          const int e = atomicAdd(&sv.err[slot], 0);
-          sv.done_err[slot] = e;
-          __threadfence_system();
-          sv.done[slot] = cur_k + 1;
-          __threadfence_system();
+        for (int e = 0; e < 2; ++e) {
+          const unsigned fin = e == 0 ? fin0 : fin1;
+          if (!fin) continue;
+          const unsigned long long k = key[e];
+          const int slot = (int)(k % (unsigned long long)sv.R);
+          const unsigned long long cnt = (unsigned long long)__popc(fin);
+          const unsigned long long old = atomicAdd(&sv.slots[slot].finished, cnt);
+          if (old + cnt == (unsigned long long)spec[e].nwalks) {
+            __threadfence();
+            const int err = atomicAdd(&sv.slots[slot].err, 0);
+            sv.done_err[slot] = err;
+            __threadfence_system();
+            sv.done[slot] = k + 1;
+            __threadfence_system();
+          }
         }
       }
     }
@@ -424,10 +531,7 @@ struct trw_server {
   cudaStream_t copy_stream = nullptr;  // descriptor uploads
   ServeState* state = nullptr;
   Chunk* queue = nullptr;
-  WalkSpec* specs = nullptr;
-  uint32_t* chunk_walks = nullptr;
-  unsigned long long* finished = nullptr;
-  int* err = nullptr;
+  SlotRec* slots = nullptr;
   int32_t* src_pool = nullptr;         // device copies of request sources (ring allocator)
   int64_t src_cap = 0;
   ServeHost* host = nullptr;           // mapped
@@ -436,8 +540,7 @@ struct trw_server {
   ServeHost* host_dev = nullptr;
   unsigned long long* done_dev = nullptr;
   int* done_err_dev = nullptr;
-  WalkSpec* spec_stage = nullptr;      // pinned staging [R]
-  uint32_t* cw_stage = nullptr;        // pinned [R]
+  SlotRec* slot_stage = nullptr;       // pinned staging [R]
   // host bookkeeping, ring order
   unsigned long long next_k = 0;       // next request number
   unsigned long long oldest = 0;       // oldest request not yet collected
@@ -466,16 +569,12 @@ static void server_release(trw_server* s) {
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   cudaFree(s->state);
   cudaFree(s->queue);
-  cudaFree(s->specs);
-  cudaFree(s->chunk_walks);
-  cudaFree(s->finished);
-  cudaFree(s->err);
+  cudaFree(s->slots);
   cudaFree(s->src_pool);
   if (s->host) cudaFreeHost(s->host);
   if (s->done) cudaFreeHost(s->done);
   if (s->done_err) cudaFreeHost(s->done_err);
-  if (s->spec_stage) cudaFreeHost(s->spec_stage);
-  if (s->cw_stage) cudaFreeHost(s->cw_stage);
+  if (s->slot_stage) cudaFreeHost(s->slot_stage);
   delete s;
 }
 
@@ -510,17 +609,13 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   SV_TRY(cudaMalloc(&s->state, sizeof(ServeState)), "serve state");
   SV_TRY(cudaMemset(s->state, 0, sizeof(ServeState)), "serve state");
   SV_TRY(cudaMalloc(&s->queue, sizeof(Chunk) * kQueueCap), "chunk queue");
-  SV_TRY(cudaMalloc(&s->specs, sizeof(WalkSpec) * R), "slot table");
-  SV_TRY(cudaMemset(s->specs, 0, sizeof(WalkSpec) * R), "slot table");
-  SV_TRY(cudaMalloc(&s->chunk_walks, sizeof(uint32_t) * R), "slot table");
-  SV_TRY(cudaMalloc(&s->finished, sizeof(unsigned long long) * R), "slot table");
-  SV_TRY(cudaMalloc(&s->err, sizeof(int) * R), "slot table");
+  SV_TRY(cudaMalloc(&s->slots, sizeof(SlotRec) * R), "slot table");
+  SV_TRY(cudaMemset(s->slots, 0, sizeof(SlotRec) * R), "slot table");
   SV_TRY(cudaMalloc(&s->src_pool, sizeof(int32_t) * (size_t)s->src_cap), "source pool");
   SV_TRY(cudaHostAlloc(&s->host, sizeof(ServeHost), cudaHostAllocMapped), "mapped control");
   SV_TRY(cudaHostAlloc(&s->done, sizeof(unsigned long long) * R, cudaHostAllocMapped), "mapped flags");
   SV_TRY(cudaHostAlloc(&s->done_err, sizeof(int) * R, cudaHostAllocMapped), "mapped flags");
-  SV_TRY(cudaHostAlloc(&s->spec_stage, sizeof(WalkSpec) * R, cudaHostAllocDefault), "pinned staging");
-  SV_TRY(cudaHostAlloc(&s->cw_stage, sizeof(uint32_t) * R, cudaHostAllocDefault), "pinned staging");
+  SV_TRY(cudaHostAlloc(&s->slot_stage, sizeof(SlotRec) * R, cudaHostAllocDefault), "pinned staging");
   std::memset((void*)s->host, 0, sizeof(ServeHost));
   std::memset((void*)s->done, 0, sizeof(unsigned long long) * R);
   std::memset((void*)s->done_err, 0, sizeof(int) * R);
@@ -534,7 +629,7 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   s->collected.assign(R, 1);
   s->block_threads = 256;
   const int nwarps = s->block_threads / 32;
-  s->smem = sizeof(WalkSpec) * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t);
+  s->smem = (sizeof(WalkSpec) + 8) * 2 * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t) + sizeof(ActiveSet);
   int bps = 0;
   SV_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, serve_kernel, s->block_threads, s->smem), "occupancy");
   if (bps < 1) bps = 1;
@@ -551,16 +646,28 @@ static cudaError_t launch_if_idle(trw_server* s) {
   ServeDev sv;
   sv.state = s->state;
   sv.queue = s->queue;
-  sv.specs = s->specs;
-  sv.chunk_walks = s->chunk_walks;
-  sv.finished = s->finished;
-  sv.err = s->err;
+  sv.slots = s->slots;
   sv.host = s->host_dev;
   sv.done = s->done_dev;
   sv.done_err = s->done_err_dev;
   sv.R = s->R;
   sv.coop = step::Coop{s->g->tuning.coop_degree, s->g->tuning.search_degree};
   sv.idle_ns = (long long)s->cfg.idle_timeout_us * 1000;
+  {
+    // enough queued chunks to cover the workers' claims between dispatcher rounds
+    const unsigned long long workers = (unsigned long long)s->grid_blocks * (s->block_threads / 32);
+    unsigned long long depth = workers / 16;
+    if (depth < 64) depth = 64;
+    if (depth > 1024) depth = 1024;
+    sv.depth = depth;
+  }
+  cudaError_t e = cudaMemsetAsync(&s->state->exit_now, 0, sizeof(int), s->stream);
+  // Tickets taken past the tail by the last launch are void: restart the
+  // head at the tail (that launch ended with every pushed entry read).
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s->state->q_head, &s->state->q_tail, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                        s->stream);
+  if (e != cudaSuccess) return e;
   serve_kernel<<<s->grid_blocks, s->block_threads, s->smem, s->stream>>>(trw_dev_graph(s->g), sv);
   return cudaGetLastError();
 }
@@ -616,22 +723,24 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   sp.sources = s->src_pool + pos;
   sp.out_paths = out_paths;
   sp.out_lengths = out_lengths;
-  // walks per chunk: about 4096 expected moves
+  // Walks per chunk: about 20 expected moves per lane of the warp that takes
+  // the chunk, so that a request spreads over many warps and a small one is
+  // not serialised on a few lanes.
   double exp_moves = (double)max_len;
   if (algo == TRW_PPR && params && params->ppr_stop > 0) exp_moves = std::min(exp_moves, 1.0 / params->ppr_stop);
   if (exp_moves < 1) exp_moves = 1;
-  uint32_t cw = (uint32_t)std::max(16.0, std::min(2048.0, 4096.0 / exp_moves));
-  s->spec_stage[slot] = sp;
-  s->cw_stage[slot] = cw;
+  uint32_t cw = (uint32_t)std::max(32.0, std::min(2048.0, 640.0 / exp_moves));
+  SlotRec& rec = s->slot_stage[slot];
+  rec.spec = sp;
+  rec.finished = 0;
+  rec.cw = cw;
+  rec.err = 0;
   cudaStream_t cs = s->copy_stream;
   cudaError_t e = cudaSuccess;
   if (n_sources > 0)
     e = cudaMemcpyAsync(s->src_pool + pos, sources, sizeof(int32_t) * (size_t)n_sources,
                         src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->specs[slot], &s->spec_stage[slot], sizeof(WalkSpec), cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->chunk_walks[slot], &s->cw_stage[slot], sizeof(uint32_t), cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&s->finished[slot], 0, sizeof(unsigned long long), cs);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&s->err[slot], 0, sizeof(int), cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->slots[slot], &rec, sizeof(SlotRec), cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit upload");
   if (src_dev) {
