@@ -146,7 +146,9 @@ trw_status trw_prepare(trw_graph* g, uint32_t what);
  *   out_lengths    host or device, int32[nwalks]: vertices in walk i (>= 1).
  * A walk stops after max_len moves, on PPR's stop coin (flipped before each
  * move), at a vertex without out-edges, or when no edge carries the MetaPath
- * label of the step.  Synchronous on the graph's stream.
+ * label of the step.  Synchronous on the graph's stream.  Host outputs go
+ * through device staging; a large batch walks in slices whose copy-out
+ * overlaps the next slice's walk.
  * Errors: TRW_ERR_INVALID (a source out of range, max_len < 0, a missing
  * weight/label array, p or q <= 0, ppr_stop outside [0, 1], bad schema),
  * TRW_ERR_NOT_PREPARED, TRW_ERR_REJECT_CAP, TRW_ERR_OOM, TRW_ERR_CUDA.

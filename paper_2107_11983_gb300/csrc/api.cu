@@ -110,6 +110,11 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->misc);
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
+  for (int b = 0; b < 2; ++b) {
+    if (g->ev_walked[b]) cudaEventDestroy(g->ev_walked[b]);
+    if (g->ev_copied[b]) cudaEventDestroy(g->ev_copied[b]);
+  }
+  if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
   if (g->stream) cudaStreamDestroy(g->stream);
   delete g;
 }
@@ -173,6 +178,11 @@ extern "C" trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_
     }                                               \
   } while (0)
   LOAD_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  LOAD_CUDA(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  for (int b = 0; b < 2; ++b) {
+    LOAD_CUDA(cudaEventCreateWithFlags(&g->ev_walked[b], cudaEventDisableTiming), "cudaEventCreate");
+    LOAD_CUDA(cudaEventCreateWithFlags(&g->ev_copied[b], cudaEventDisableTiming), "cudaEventCreate");
+  }
   LOAD_CUDA(cudaEventCreate(&g->ev0), "cudaEventCreate");
   LOAD_CUDA(cudaEventCreate(&g->ev1), "cudaEventCreate");
   LOAD_TRY(alloc_dev((void**)&g->row_ptr, sizeof(int32_t) * ((size_t)nv + 1), "row_ptr"));
@@ -369,6 +379,64 @@ static trw_status collect_status(trw_graph* g, cudaStream_t stream) {
   return TRW_OK;
 }
 
+// Slices of at least this many walks overlap their copy-out with the next walk.
+static constexpr int64_t kSliceWalks = 1 << 19;
+
+// The synchronous walk of trw_walk_ex with host outputs, sliced: slice i walks
+// into staging buffer i % 2 on `stream`; its paths and lengths are copied to
+// the host on the graph's copy stream while slice i + 1 walks; slice i + 2
+// waits until the copy of slice i has drained its buffer.
+static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, const int32_t* d_src, int64_t n_sources,
+                              int64_t row, int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream) {
+  const int64_t wps = (int64_t)sp.wps;
+  const int64_t nwalks = sp.nwalks;
+  int64_t nslices = nwalks / kSliceWalks;
+  if (nslices < 2) nslices = 2;
+  if (nslices > 16) nslices = 16;
+  const int64_t src_per = (n_sources + nslices - 1) / nslices;
+  const int64_t walks_per = src_per * wps;
+  trw_status st = trw_grow((void**)&g->out_stage, &g->out_cap, sizeof(int32_t) * (size_t)(2 * walks_per * row));
+  if (st != TRW_OK) return st;
+  st = trw_grow((void**)&g->len_stage, &g->len_cap, sizeof(int32_t) * (size_t)(2 * walks_per));
+  if (st != TRW_OK) return st;
+  const DevGraph dg = trw_dev_graph(g);
+  const LaunchCfg cfg = trw_launch_cfg(g, sp.algo);
+  cudaStream_t cs = g->copy_stream;
+  CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), stream), "reset ctrl");
+  CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
+  int64_t done_src = 0;
+  for (int64_t i = 0; done_src < n_sources; ++i) {
+    const int b = (int)(i & 1);
+    const int64_t s0 = done_src, s1 = std::min(n_sources, s0 + src_per);
+    WalkSpec sl = sp;
+    sl.sources = d_src + s0;
+    sl.nwalks = (s1 - s0) * wps;
+    sl.walk_offset = sp.walk_offset + (uint32_t)(s0 * wps);
+    sl.out_paths = g->out_stage + (size_t)b * (size_t)(walks_per * row);
+    sl.out_lengths = g->len_stage + (size_t)b * (size_t)walks_per;
+    if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(stream, g->ev_copied[b], 0), "wait for a drained buffer");
+    CUDA_TRY(cudaMemsetAsync(&g->ctrl->head, 0, sizeof(unsigned long long), stream), "reset queue");
+    if (kernel == TRW_KERNEL_PLAIN) CUDA_TRY(launch_walk_plain(dg, sl, g->ctrl, stream, 256), "plain walk launch");
+    else CUDA_TRY(launch_walk_persistent(dg, sl, g->ctrl, stream, cfg), "persistent walk launch");
+    CUDA_TRY(cudaEventRecord(g->ev_walked[b], stream), "event");
+    CUDA_TRY(cudaStreamWaitEvent(cs, g->ev_walked[b], 0), "wait for a walked slice");
+    CUDA_TRY(cudaMemcpyAsync(out_paths + s0 * wps * row, sl.out_paths, sizeof(int32_t) * (size_t)(sl.nwalks * row),
+                             cudaMemcpyDeviceToHost, cs),
+             "copy paths");
+    CUDA_TRY(cudaMemcpyAsync(out_lengths + s0 * wps, sl.out_lengths, sizeof(int32_t) * (size_t)sl.nwalks,
+                             cudaMemcpyDeviceToHost, cs),
+             "copy lengths");
+    CUDA_TRY(cudaEventRecord(g->ev_copied[b], cs), "event");
+    done_src = s1;
+  }
+  CUDA_TRY(cudaEventRecord(g->ev1, stream), "event");
+  g->timed = true;
+  g->last.grid_blocks = cfg.grid_blocks;
+  g->last.block_threads = cfg.block_threads;
+  CUDA_TRY(cudaStreamSynchronize(cs), "copy stream");
+  return collect_status(g, stream);
+}
+
 extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
                                   int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
                                   int32_t* out_lengths, trw_kernel kernel, void* stream_v, int sync) {
@@ -409,6 +477,22 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
              "copy sources");
     d_src = g->src_stage;
   }
+  // Device sources with host outputs: check them before anything is copied out
+  // (an invalid batch must leave the caller's buffers untouched).
+  if (src_dev && (!out_dev || !len_dev)) {
+    CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), stream), "reset ctrl");
+    CUDA_TRY(launch_validate_sources(d_src, n_sources, (int32_t)g->nv, g->ctrl, stream), "validate sources");
+    Ctrl c;
+    CUDA_TRY(cudaMemcpyAsync(&c, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream), "read status");
+    CUDA_TRY(cudaStreamSynchronize(stream), "validate sources");
+    if (c.err != 0) return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
+  }
+  // Host outputs of a large batch: walk it in source-aligned slices into two
+  // device staging buffers and copy each slice out on a second stream while
+  // the next slice walks (a double-buffered dump of the paths).
+  const int64_t row = sp.endpoints ? 1 : (int64_t)max_len + 1;
+  if (!out_dev && !len_dev && sync && nwalks >= 2 * kSliceWalks)
+    return walk_sliced(g, sp, kernel, d_src, n_sources, row, out_paths, out_lengths, stream);
   if (!out_dev) {
     st = trw_grow((void**)&g->out_stage, &g->out_cap, sizeof(int32_t) * out_elems);
     if (st != TRW_OK) return st;

@@ -34,6 +34,9 @@ struct trw_graph {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
+  cudaStream_t copy_stream = nullptr;              // copy-out of sliced walks
+  cudaEvent_t ev_walked[2] = {nullptr, nullptr};   // slice walked into staging buffer b
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};   // staging buffer b copied out
   trw_tuning tuning{};
   trw_stats last{};
   int64_t device_bytes = 0;

@@ -144,6 +144,13 @@ def test_invalid_arguments_write_nothing(small):
         G.walk(trw.DEEPWALK, dsrc, L, seed=1, out_paths=dp, out_lengths=dl)
     assert e.value.status == -1
     assert bool((dp == sentinel).all()) and bool((dl == sentinel).all())
+    # device sources, host outputs: still nothing written
+    hp = np.full((3, L + 1), sentinel, np.int32)
+    hl = np.full(3, sentinel, np.int32)
+    with pytest.raises(trw.TRWError) as e:
+        G.walk(trw.DEEPWALK, dsrc, L, seed=1, out_paths=hp, out_lengths=hl)
+    assert e.value.status == -1
+    assert np.all(hp == sentinel) and np.all(hl == sentinel)
     src = np.array([0], np.int32)
     for kw in [dict(algo=trw.NODE2VEC, n2v_p=0.0), dict(algo=trw.NODE2VEC, n2v_q=-1.0),
                dict(algo=trw.PPR, ppr_stop=1.5), dict(algo=trw.METAPATH, schema=np.zeros(17, np.uint8)),
@@ -210,6 +217,25 @@ def test_mixed_batch_one_launch(small):
         assert_paths_equal(o.paths.cpu().numpy(), o.lengths.cpu().numpy(), want, endpoints=r.get("endpoints", False))
 
 
+def test_sliced_host_outputs_large_batch():
+    """A batch large enough to walk in slices (copy-out overlapped with the next
+    slice) gives the oracle's paths, with several walks per source and an offset."""
+    g = rmat_graph(14)
+    G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
+    G.prepare()
+    src = synth.sources(300_001, g.nv, seed=21)
+    al = oracle.prepare_alias(g.row_ptr, g.weights)
+    for algo, kw in [(trw.DEEPWALK_WEIGHTED, {}), (trw.NODE2VEC, {"n2v_p": 0.5, "n2v_q": 2.0})]:
+        want = oracle_walk(g, algo, src, 20, seed=23, alias=al if algo == trw.DEEPWALK_WEIGHTED else None,
+                           walks_per_source=4, walk_offset=77, **kw)
+        h_paths = torch.full((src.shape[0] * 4, 21), -1, dtype=torch.int32).pin_memory()
+        h_len = torch.full((src.shape[0] * 4,), -1, dtype=torch.int32).pin_memory()
+        G.walk(algo, src, 20, seed=23, walks_per_source=4, walk_offset=77, out_paths=h_paths.numpy(),
+               out_lengths=h_len.numpy(), **kw)
+        assert_paths_equal(h_paths.numpy(), h_len.numpy(), want)
+        assert G.last_stats()["moves"] == int((want.lengths - 1).sum())
+
+
 def test_results_independent_of_tuning(small):
     g, G = small
     src = synth.vertex_sources(g.nv)
@@ -274,3 +300,25 @@ def test_warp_cooperative_paths_bit_exact(small, coop):
             assert_paths_equal(o.paths.cpu().numpy(), o.lengths.cpu().numpy(), want)
     finally:
         G.set_tuning(**old)
+
+
+@pytest.mark.parametrize("algo", [trw.DEEPWALK_WEIGHTED, trw.NODE2VEC, trw.PPR], ids=["weighted", "node2vec", "ppr"])
+def test_pinned_host_outputs(small, algo):
+    """Page-locked host outputs and sources (the end-to-end path) equal the oracle."""
+    g, G = small
+    src = np.concatenate([synth.vertex_sources(g.nv), synth.sources(321, g.nv, seed=12)])
+    L = 80
+    kw = ALGO_KW[algo]
+    want = oracle_walk(g, algo, src, L, seed=17, alias=oracle_alias(SCALE) if algo == trw.DEEPWALK_WEIGHTED else None,
+                       **kw)
+    h_src = torch.from_numpy(src).pin_memory()
+    h_paths = torch.full((src.shape[0], L + 1), -1, dtype=torch.int32).pin_memory()
+    h_len = torch.full((src.shape[0],), -1, dtype=torch.int32).pin_memory()
+    G.walk(algo, h_src.numpy(), L, seed=17, out_paths=h_paths.numpy(), out_lengths=h_len.numpy(), **kw)
+    assert_paths_equal(h_paths.numpy(), h_len.numpy(), want)
+    # endpoints into pinned memory too
+    want = oracle_walk(g, algo, src, L, seed=18, alias=oracle_alias(SCALE) if algo == trw.DEEPWALK_WEIGHTED else None,
+                       endpoints_only=True, **kw)
+    h_end = torch.full((src.shape[0],), -1, dtype=torch.int32).pin_memory()
+    G.walk(algo, h_src.numpy(), L, seed=18, endpoints=True, out_paths=h_end.numpy(), out_lengths=h_len.numpy(), **kw)
+    assert_paths_equal(h_end.numpy(), h_len.numpy(), want, endpoints=True)
