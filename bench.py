@@ -34,22 +34,29 @@ WORKLOADS = {
                sources="vertices", seed=1),
     "c3": dict(name="node2vec-p0.5-q2-rmat-s24", scale=24, algo="node2vec", max_len=80, sources="vertices", seed=1,
                n2v_p=0.5, n2v_q=2.0),
+    "c4": dict(name="mixed-ppr1M-metapath-rmat-s23", scale=23, kind="mixed", seed=1),
+    "c5": dict(name="serve-rmat-s26-directed", scale=26, kind="serve", symmetric=False, algo="deepwalk_weighted",
+               max_len=80, seed=1),
 }
 METRIC = "walk steps/sec"
 UNIT = "steps/s"
 
 # Algorithmic bytes per move and per walk of each kernel, at 32-byte sector
-# granularity (the random-access roofline): a move reads the row-offset pair
-# (1.125 sectors on average: an 8-byte pair straddles a sector boundary one
-# time in eight) and the sampled record, and writes one 4-byte path entry.
+# granularity (the random-access roofline).  NAIVE: a move reads the row-offset
+# pair of the current vertex (1.125 sectors on average: an 8-byte pair
+# straddles a sector boundary one time in eight) and col[off + x], and writes
+# one 4-byte path entry.  ALIAS: a move reads one 32-byte record (threshold,
+# both destinations and their rows) and writes the path entry; the row-offset
+# pair is read once per walk, for the source.
 SECTOR = 32
 ROW_PAIR = 1.125 * SECTOR
 BYTES_PER_MOVE = {
-    "deepwalk": ROW_PAIR + SECTOR + 4,           # col[off + x]
+    "deepwalk": ROW_PAIR + SECTOR + 4,
     "ppr": ROW_PAIR + SECTOR + 4,
-    "deepwalk_weighted": ROW_PAIR + SECTOR + 4,  # 16-byte alias record {H, first, second}
+    "deepwalk_weighted": SECTOR + 4,
 }
-BYTES_PER_WALK = 12  # source read, length write, path[0] write
+BYTES_PER_WALK_BASE = 12  # source read, length write, path[0] write
+BYTES_PER_WALK = {"deepwalk_weighted": BYTES_PER_WALK_BASE + ROW_PAIR}
 
 
 def log(*a):
@@ -66,9 +73,10 @@ def dist_env():
 def build_graph(wl):
     t = time.time()
     g = synth.rmat(wl["scale"], symmetric=wl.get("symmetric", True))
-    if wl["algo"] == "deepwalk_weighted":
+    if wl.get("algo") == "deepwalk_weighted":
         g.weights = synth.edge_weights(g)
-    g.labels = synth.edge_labels(g)  # MetaPath line of the per-algorithm table
+    if wl.get("kind") != "serve":
+        g.labels = synth.edge_labels(g)  # MetaPath line of the per-algorithm table
     log(f"graph {g.name}: nv={g.nv} ne={g.ne} built in {time.time() - t:.1f}s")
     return g
 
@@ -179,28 +187,35 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
     src = synth.vertex_sources(g.nv)
     n = 2000
     done_moves, done_s, walks = 0, 0.0, 0
+    sectors, out_bytes = 0, 0
     pos = 0
     while done_s < seconds and pos < src.shape[0]:
         m = min(n, src.shape[0] - pos)
         t = time.perf_counter()
         res = oracle.walk(g.row_ptr, g.col, algo, src[pos:pos + m], wl["max_len"], wl["seed"], alias=alias,
-                          labels=g.labels, walk_offset=pos, **walk_kwargs(wl))
+                          labels=g.labels, walk_offset=pos, schema=wl.get("schema"), **walk_kwargs(wl))
         dt = time.perf_counter() - t
         assert res.status == 0
         done_moves += res.stats["moves"]
+        sectors += res.stats["sectors"]
+        out_bytes += res.stats["out_bytes"]
         done_s += dt
         walks += m
         pos += m
         n = min(n * 2, 200000)
     return {"value": done_moves / done_s, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {walks} of {src.shape[0]} walks ({done_moves} moves) of the workload, "
-                      f"single-threaded oracle, {done_s:.1f}s walking after {prep:.1f}s of alias preparation"}
+                      f"single-threaded oracle, {done_s:.1f}s walking after {prep:.1f}s of alias preparation",
+            "model_bytes_per_move": (32.0 * sectors + out_bytes) / max(1, done_moves)}
 
 
 def run_reference(args, wl):
     """Reference arm: the oracle on the host cores, a bounded sample per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
+        return
+    if "algo" not in wl or wl.get("kind"):
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on walk workloads only"}))
         return
     import oracle
 
@@ -230,6 +245,35 @@ def run_reference(args, wl):
                              "sample": f"{per_step} walks per step of the workload, single-threaded oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ roofline
+
+def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s):
+    """Roofline of the walk kernel: algorithmic bytes of one launch (the
+    closed form per move where the layout fixes it, else the oracle's sector
+    model measured on the CPU-baseline sample) over the kernel's event time,
+    against the measured HBM copy bandwidth; plus the fraction of the
+    random-gather ceiling."""
+    peak, peak_kind = measured_peak_hbm()
+    bpm = BYTES_PER_MOVE.get(wl["algo"])
+    source = "closed form (32-byte sectors of the device layout)"
+    if bpm is None and cpu is not None:
+        bpm = cpu["model_bytes_per_move"]
+        source = "oracle sector model on the CPU-baseline sample"
+    if bpm is None:
+        return None
+    alg_bytes = moves * bpm + walks * BYTES_PER_WALK.get(wl["algo"], BYTES_PER_WALK_BASE)
+    achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(f"walk_persistent/{wl['name']}"),
+            "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "walk_persistent",
+            "bytes_per_move": round(bpm, 2), "bytes_per_move_source": source,
+            "algorithmic_bytes_per_launch": int(alg_bytes)}
+    if gather is not None:
+        roof["random_gather_ceiling_steps_per_s"] = gather["loads_per_s"]
+        roof["frac_of_gather_ceiling"] = round(steps_per_s / gather["loads_per_s"], 4)
+    return roof
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -547,37 +591,22 @@ def run_ours(args, wl):
     e2e_value = moves * ws / e2e_s
     assert int((h_len.to(torch.int64) - 1).sum().item()) == moves
 
-    # roofline of the walk kernel
-    peak, peak_kind = measured_peak_hbm()
-    bpm = BYTES_PER_MOVE.get(wl["algo"])
     kms = statistics.mean(kern_ms)
-    roof = None
-    if bpm is not None:
-        alg_bytes = moves * bpm + n * BYTES_PER_WALK
-        achieved = alg_bytes / (kms / 1000.0) / 1e9
-        key = f"walk_persistent/{wl['name']}"
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(key),
-                "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "walk_persistent",
-                "bytes_per_move": bpm, "algorithmic_bytes_per_launch": int(alg_bytes)}
 
     per_algo = None
-    gather = None
     serve = None
+    gather = measure_gather_ceiling(trw, g) if rank == 0 else None
     if rank == 0 and not args.no_extras:
         per_algo = measure_per_algo(trw, torch, G, g, flush, sp)
-        gather = measure_gather_ceiling(trw, g)
         if G.has_weights:
             serve = measure_serve(trw, torch, G, g, n_requests=args.serve_requests)
-        if roof is not None and gather is not None:
-            roof["random_gather_ceiling_steps_per_s"] = gather["loads_per_s"]
-            roof["frac_of_gather_ceiling"] = round(value / ws / gather["loads_per_s"], 4)
 
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
     cpu = cpu_baseline(g, wl) if ws == 1 and not args.no_cpu_baseline else None
+    roof = roofline(wl, moves, n, kms, cpu, gather, value / ws)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * dev_s / args.steps, 4), "higher_is_better": True,
@@ -608,6 +637,190 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def _common_line(args, wl, value, ms_per_step, cfg_extra):
+    return {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": dict({"workload": wl["name"]}, **cfg_extra)}
+
+
+def run_mixed(args, wl):
+    """One persistent launch over a mixed batch: 1M PPR walks (stop 0.2, at most
+    1000 moves, uniform random sources, endpoints) and one MetaPath walk per
+    vertex (cyclic schema of 5 labels, 80 moves), against the plain kernel
+    launched once per request."""
+    import torch
+
+    import oracle
+    import paper_2107_11983_gb300 as trw
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = build_graph(wl)
+    G = trw.Graph(g.row_ptr, g.col, None, g.labels)
+    schema = synth.schema(5, 5, seed=1)
+    ppr_src_h = synth.sources(1_000_000, g.nv, seed=1)
+    mp_src_h = synth.vertex_sources(g.nv)
+    G.autotune(trw.METAPATH, 10, schema=schema)
+    reqs = [dict(algo=trw.PPR, sources=torch.from_numpy(ppr_src_h).to(dev), max_len=1000, seed=1, ppr_stop=0.2,
+                 endpoints=True),
+            dict(algo=trw.METAPATH, sources=torch.from_numpy(mp_src_h).to(dev), max_len=80, seed=1, schema=schema)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream or 1
+    for _ in range(args.warmup):
+        flush.zero_()
+        outs = G.walk_batch(reqs, stream=sp)
+    torch.cuda.synchronize()
+    moves = sum(int((o.lengths.to(torch.int64) - 1).sum().item()) for o in outs)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        outs = G.walk_batch(reqs, stream=sp, sync=False)
+        b.record(stream)
+        G.sync(sp)
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    kms = G.last_stats()["kernel_ms"]
+    value = moves / (statistics.mean(ms) / 1000.0)
+    # plain baseline: one plain launch per request
+    plain_ms = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for r in reqs:
+            kw = {k: r[k] for k in ("ppr_stop", "schema", "endpoints") if k in r}
+            G.walk(r["algo"], r["sources"], r["max_len"], r["seed"], kernel=trw.KERNEL_PLAIN, stream=sp, **kw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+    # end to end: host sources in, every output back on the host
+    reqs_h = [dict(r, sources=src) for r, src in zip(reqs, (ppr_src_h, mp_src_h))]
+    e2e_t = []
+    for _ in range(3):
+        t = time.perf_counter()
+        o = G.walk_batch(reqs_h, stream=sp)
+        host = [(x.paths.cpu(), x.lengths.cpu()) for x in o]
+        e2e_t.append(time.perf_counter() - t)
+    e2e_s = statistics.median(e2e_t)
+    d2h = sum(int(p.numel() + l.numel()) * 4 for p, l in host)
+    gather = measure_gather_ceiling(trw, g) if not args.no_extras else None
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on a sample of both requests, in proportion to their walks
+        t0 = time.perf_counter()
+        mv, sec, ob, walks = 0, 0, 0, 0
+        step = 0
+        while time.perf_counter() - t0 < 12.0:
+            lo = step * 20000
+            res = oracle.walk(g.row_ptr, g.col, oracle.METAPATH, mp_src_h[lo:lo + 20000], 80, 1, labels=g.labels,
+                              schema=schema, walk_offset=lo)
+            res2 = oracle.walk(g.row_ptr, g.col, oracle.PPR, ppr_src_h[lo // 8:lo // 8 + 2500], 1000, 1,
+                               ppr_stop=0.2, endpoints_only=True, walk_offset=lo // 8)
+            for r_ in (res, res2):
+                assert r_.status == 0
+                mv += r_.stats["moves"]
+                sec += r_.stats["sectors"]
+                ob += r_.stats["out_bytes"]
+            walks += 22500
+            step += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": mv / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{walks} walks (MetaPath:PPR = 8:1, the batch's proportion), {mv} moves, single-threaded, {dt:.1f}s",
+               "model_bytes_per_move": (32.0 * sec + ob) / max(1, mv)}
+    line = _common_line(args, wl, value, statistics.mean(ms), {
+        "graph": f"rmat-s{wl['scale']}-ef16-sym", "nv": g.nv, "ne": g.ne, "requests": "PPR 1,000,000 (stop 0.2, max 1000, endpoints) + MetaPath one per vertex (schema of 5, 80 moves)",
+        "moves_per_step": moves, "l2": "256 MiB buffer written between timed steps", "tuning": G.tuning()})
+    line["kernel_ms_per_step"] = round(kms, 4)
+    line["plain_launch"] = {"value": round(moves / (statistics.median(plain_ms) / 1000.0), 1), "unit": UNIT,
+                            "ms": round(statistics.median(plain_ms), 3),
+                            "speedup_persistent": round(statistics.median(plain_ms) / statistics.mean(ms), 3)}
+    line["e2e"] = {"value": round(moves / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int((ppr_src_h.size + mp_src_h.size) * 4),
+                   "d2h_bytes_per_step": d2h, "ms": round(1000 * e2e_s, 3)}
+    line["gpu_launches"] = 3 * args.steps
+    bpm = cpu["model_bytes_per_move"] if cpu else None
+    if bpm:
+        peak, kind = measured_peak_hbm()
+        ach = moves * bpm / (kms / 1000.0) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(ach / peak, 4), "traffic": None, "peak_kind": f"{kind} copy bandwidth",
+                            "kernel": "walk_persistent<MIXED>", "bytes_per_move": round(bpm, 2),
+                            "bytes_per_move_source": "oracle sector model on the CPU-baseline sample"}
+    line["gather_ceiling"] = gather
+    line["cpu_baseline"] = cpu
+    line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args, wl):
+    """The serving loop on the largest graph (R-MAT s26, directed, weights and
+    alias tables resident): latency of an open-loop trace, saturating steps/s,
+    and a batch weighted DeepWalk on the same graph for the roofline."""
+    import torch
+
+    import paper_2107_11983_gb300 as trw
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = build_graph(wl)
+    t = time.time()
+    G = trw.Graph(g.row_ptr, g.col, g.weights, None)
+    load_s = time.time() - t
+    t = time.time()
+    G.prepare()
+    prep_s = time.time() - t
+    log(f"loaded in {load_s:.1f}s, prepared in {prep_s:.1f}s, {G.device_bytes() / 1e9:.1f} GB on the device")
+    G.autotune(trw.DEEPWALK_WEIGHTED, 10)
+    # batch walk on the largest graph: 16,777,216 uniform sources x 80 moves
+    n = 1 << 24
+    src = torch.from_numpy(synth.sources(n, g.nv, seed=1)).to(dev)
+    out_p = torch.empty((n, 81), dtype=torch.int32, device=dev)
+    out_l = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream or 1
+    for _ in range(args.warmup):
+        G.walk(trw.DEEPWALK_WEIGHTED, src, 80, 1, out_paths=out_p, out_lengths=out_l, stream=sp)
+    moves = int((out_l.to(torch.int64) - 1).sum().item())
+    kms = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(args.steps):
+        flush.zero_()
+        G.walk(trw.DEEPWALK_WEIGHTED, src, 80, 1, out_paths=out_p, out_lengths=out_l, stream=sp)
+        kms.append(G.last_stats()["kernel_ms"])
+    clk = clocks.stop()
+    kms_m = statistics.mean(kms)
+    batch_value = moves / (kms_m / 1000.0)
+    gather = measure_gather_ceiling(trw, g)
+    roof = roofline(dict(wl, algo="deepwalk_weighted", name="deepwalk-weighted-alias-rmat-s26-directed"), moves, n,
+                    kms_m, None, gather, batch_value)
+    del out_p, out_l
+    torch.cuda.empty_cache()
+    serve = measure_serve(trw, torch, G, g, n_requests=args.serve_requests, rate=2000.0)
+    value = serve["saturating"]["steps_per_s"]
+    line = _common_line(args, wl, value, 0.0, {
+        "graph": f"rmat-s{wl['scale']}-ef16-directed", "nv": g.nv, "ne": g.ne, "device_bytes": G.device_bytes(),
+        "trace": f"{args.serve_requests} requests, Poisson 2000/s", "tuning": G.tuning()})
+    line["value_kind"] = "saturating served steps/s (every request queued at once)"
+    line["serve"] = serve
+    line["batch_largest_graph"] = {"workload": "weighted DeepWalk, 16,777,216 uniform sources x 80 moves",
+                                   "steps_per_s": round(batch_value, 1), "kernel_ms": round(kms_m, 3), "moves": moves}
+    line["preprocess"] = {"graph_load_s": round(load_s, 2), "alias_prepare_s": round(prep_s, 2)}
+    line["roofline"] = roof
+    line["gather_ceiling"] = gather
+    line["e2e"] = {"value": serve["served"]["steps_per_s"], "unit": UNIT, "h2d_bytes_per_step": None,
+                   "d2h_bytes_per_step": None, "note": "open-loop served trace, outputs on the device"}
+    line["gpu_launches"] = None
+    line["cpu_baseline"] = None
+    line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,6 +842,10 @@ def main():
         wl["scale"] = args.scale
     if args.impl == "reference":
         run_reference(args, wl)
+    elif wl.get("kind") == "mixed":
+        run_mixed(args, wl)
+    elif wl.get("kind") == "serve":
+        run_serve(args, wl)
     else:
         run_ours(args, wl)
 

@@ -253,9 +253,9 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   if (!g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
   const size_t ne = (size_t)g->ne;
   if (!g->alias) {
-    trw_status st = alloc_dev((void**)&g->alias, sizeof(uint4) * (ne + 1), "alias tables");
+    trw_status st = alloc_dev((void**)&g->alias, sizeof(AliasRec) * (ne + 1), "alias tables");
     if (st != TRW_OK) return st;
-    g->device_bytes += (int64_t)(sizeof(uint4) * ne);
+    g->device_bytes += (int64_t)(sizeof(AliasRec) * ne);
   }
   unsigned long long* q = nullptr;
   int32_t *sm = nullptr, *lg = nullptr;
@@ -637,12 +637,13 @@ extern "C" trw_status trw_last_stats(const trw_graph* g, trw_stats* s) {
 extern "C" trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int32_t* second) {
   if (!g || !H || !first || !second) return trw_fail(TRW_ERR_INVALID, "NULL argument");
   if (!g->prepared_alias) return trw_fail(TRW_ERR_NOT_PREPARED, "no alias tables");
-  std::vector<uint4> rec((size_t)g->ne);
-  if (g->ne > 0) CUDA_TRY(cudaMemcpy(rec.data(), g->alias, sizeof(uint4) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy alias");
+  std::vector<AliasRec> rec((size_t)g->ne);
+  if (g->ne > 0)
+    CUDA_TRY(cudaMemcpy(rec.data(), g->alias, sizeof(AliasRec) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy alias");
   for (int64_t i = 0; i < g->ne; ++i) {
-    H[i] = rec[(size_t)i].x;
-    first[i] = (int32_t)rec[(size_t)i].y;
-    second[i] = (int32_t)rec[(size_t)i].z;
+    H[i] = rec[(size_t)i].a.x;
+    first[i] = (int32_t)rec[(size_t)i].a.y;
+    second[i] = (int32_t)rec[(size_t)i].a.z;
   }
   return TRW_OK;
 }

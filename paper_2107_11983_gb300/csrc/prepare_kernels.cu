@@ -9,9 +9,9 @@
 // and l joins the back of the small list once q_l < S.  What remains forms
 // one-element buckets (H = 2^32 - 1 and second = first, which picks the same
 // edge for every 32-bit dart).  The sequence of list operations is fixed, so
-// the tables are exactly reproducible.  Records hold destination vertices
-// directly: {H, col[off + first], col[off + second], 0}.  A vertex whose
-// integer weights sum to zero gets {0, -1, -1, 0} records: a dead end.
+// the tables are exactly reproducible.  Records hold the destination vertices
+// directly, with their own CSR rows (see AliasRec).  A vertex whose integer
+// weights sum to zero gets records with both destinations -1: a dead end.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -50,9 +50,19 @@ __device__ __forceinline__ uint32_t frac32(unsigned long long q, unsigned long l
   return quo;
 }
 
+// Record of a bucket whose first element is destination u (taken with
+// probability H / 2^32) and whose second is v.
+__device__ __forceinline__ AliasRec make_rec(const int32_t* __restrict__ row_ptr, uint32_t H, int32_t u, int32_t v) {
+  const int32_t ou = row_ptr[u], ov = row_ptr[v];
+  AliasRec r;
+  r.a = make_uint4(H, (uint32_t)u, (uint32_t)v, (uint32_t)ou);
+  r.b = make_uint4((uint32_t)ov, (uint32_t)(row_ptr[u + 1] - ou), (uint32_t)(row_ptr[v + 1] - ov), 0u);
+  return r;
+}
+
 __global__ void prepare_alias_kernel(int32_t nv, const int32_t* __restrict__ row_ptr,
                                      const int32_t* __restrict__ col, const float* __restrict__ weights,
-                                     uint4* __restrict__ alias, unsigned long long* __restrict__ q,
+                                     AliasRec* __restrict__ alias, unsigned long long* __restrict__ q,
                                      int32_t* __restrict__ small, int32_t* __restrict__ large, Ctrl* ctrl) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t off = row_ptr[v];
@@ -70,7 +80,10 @@ __global__ void prepare_alias_kernel(int32_t nv, const int32_t* __restrict__ row
       continue;
     }
     if (S == 0) {
-      for (int32_t j = 0; j < d; ++j) alias[off + j] = make_uint4(0u, 0xffffffffu, 0xffffffffu, 0u);
+      AliasRec dead;
+      dead.a = make_uint4(0u, 0xffffffffu, 0xffffffffu, 0u);
+      dead.b = make_uint4(0u, 0u, 0u, 0u);
+      for (int32_t j = 0; j < d; ++j) alias[off + j] = dead;
       continue;
     }
     int32_t ns = 0, nl = 0;
@@ -87,7 +100,7 @@ __global__ void prepare_alias_kernel(int32_t nv, const int32_t* __restrict__ row
       const int32_t s = small[off + sh++];
       const int32_t l = large[off + lh];
       const unsigned long long qs = q[off + s];
-      alias[off + s] = make_uint4(frac32(qs, S), (uint32_t)col[off + s], (uint32_t)col[off + l], 0u);
+      alias[off + s] = make_rec(row_ptr, frac32(qs, S), col[off + s], col[off + l]);
       const unsigned long long ql = q[off + l] - (S - qs);
       q[off + l] = ql;
       if (ql < S) {
@@ -97,13 +110,11 @@ __global__ void prepare_alias_kernel(int32_t nv, const int32_t* __restrict__ row
     }
     for (; lh < nl; ++lh) {
       const int32_t j = large[off + lh];
-      const uint32_t c = (uint32_t)col[off + j];
-      alias[off + j] = make_uint4(0xffffffffu, c, c, 0u);
+      alias[off + j] = make_rec(row_ptr, 0xffffffffu, col[off + j], col[off + j]);
     }
     for (; sh < st; ++sh) {
       const int32_t j = small[off + sh];
-      const uint32_t c = (uint32_t)col[off + j];
-      alias[off + j] = make_uint4(0xffffffffu, c, c, 0u);
+      alias[off + j] = make_rec(row_ptr, 0xffffffffu, col[off + j], col[off + j]);
     }
   }
 }
@@ -131,7 +142,7 @@ __global__ void check_graph_kernel(int32_t nv, const int32_t* __restrict__ row_p
 }  // namespace
 
 cudaError_t launch_prepare_alias(int32_t nv, const int32_t* row_ptr, const int32_t* col, const float* weights,
-                                 uint4* alias, unsigned long long* q_scratch, int32_t* small_scratch,
+                                 AliasRec* alias, unsigned long long* q_scratch, int32_t* small_scratch,
                                  int32_t* large_scratch, Ctrl* ctrl, cudaStream_t st) {
   if (nv <= 0) return cudaSuccess;
   int64_t blocks = ((int64_t)nv + 127) / 128;

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
   st.gpos = 0;
   st.lo = 0;
   step::Walker W;
-  W.w = 0; W.s = 0; W.cur = 0; W.prev = -1; W.off = W.d = W.poff = W.pd = 0; W.att = 0;
+  step::walker_init(W, 0u, 0);
   bool active = false;
   int64_t walk = 0;
   int ent = 0;                        // this lane's slot
@@ -410,11 +410,7 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
         my_k = key[cur];
         walk = (int64_t)wlo + rank;
         const int32_t src = __ldcg(sp.sources + walk / sp.wps);
-        W.w = sp.walk_offset + (uint32_t)walk;
-        W.s = 0;
-        W.cur = src;
-        W.prev = -1;
-        W.att = 0;
+        step::walker_init(W, sp.walk_offset + (uint32_t)walk, src);
         if (!sp.endpoints) {
           st.gpos = walk * ((int64_t)sp.max_len + 1);
           st.lo = (int)(st.gpos & 7);

@@ -20,7 +20,7 @@ struct trw_graph {
   int32_t* col = nullptr;            // [ne]
   float* weights = nullptr;          // [ne] or null
   uint8_t* labels = nullptr;         // [ne + 64] or null
-  uint4* alias = nullptr;            // [ne] after trw_prepare(ALIAS)
+  trw::AliasRec* alias = nullptr;    // [ne] after trw_prepare(ALIAS)
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags
   int32_t* src_stage = nullptr;      // staging for host buffers (grow-only)

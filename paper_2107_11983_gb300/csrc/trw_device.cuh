@@ -18,11 +18,22 @@ constexpr int kErrInvalid = -1;
 constexpr int kErrRejectCap = -6;
 constexpr int kErrInternal = -9;
 
+// ALIAS record of one edge slot, one 32-byte sector: the bucket's threshold
+// H and both destinations, each with its own CSR row, so that an ALIAS move
+// needs one random read and the next step no row-offset lookup.
+//   a = {H, first dst, second dst, row offset of first dst}
+//   b = {row offset of second dst, degree of first dst, degree of second dst, 0}
+// A vertex with no positive weight has first = second = -1 in every record.
+struct __align__(32) AliasRec {
+  uint4 a;
+  uint4 b;
+};
+
 // A CSR graph resident in HBM.  Offsets and ids are int32 (nv, ne < 2^31).
 struct DevGraph {
   const int32_t* __restrict__ row_ptr;   // [nv + 1]
   const int32_t* __restrict__ col;       // [ne], rows sorted ascending when sorted != 0
-  const uint4* __restrict__ alias;       // [ne] {H, first dst, second dst, 0}, or null
+  const AliasRec* __restrict__ alias;    // [ne] after ALIAS preparation, or null
   const uint8_t* __restrict__ labels;    // [ne + 16] (padded for word loads), or null
   int32_t nv;
   int32_t ne;

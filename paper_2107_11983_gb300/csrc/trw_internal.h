@@ -29,7 +29,7 @@ cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const 
 
 // ALIAS preprocessing (Algorithm 3) on the device.
 cudaError_t launch_prepare_alias(int32_t nv, const int32_t* row_ptr, const int32_t* col, const float* weights,
-                                 uint4* alias, unsigned long long* q_scratch, int32_t* small_scratch,
+                                 AliasRec* alias, unsigned long long* q_scratch, int32_t* small_scratch,
                                  int32_t* large_scratch, Ctrl* ctrl, cudaStream_t st);
 
 // Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).

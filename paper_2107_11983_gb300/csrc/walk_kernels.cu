@@ -31,12 +31,7 @@ __global__ void __launch_bounds__(256) walk_plain(DevGraph g, WalkSpec sp, Ctrl*
     const int32_t src = sp.sources[i / sp.wps];
     if (src >= 0 && src < g.nv) {
       Walker W;
-      W.w = sp.walk_offset + (uint32_t)i;
-      W.s = 0;
-      W.cur = src;
-      W.prev = -1;
-      W.off = W.d = W.poff = W.pd = 0;
-      W.att = 0;
+      walker_init(W, sp.walk_offset + (uint32_t)i, src);
       const int64_t base = sp.endpoints ? i : i * ((int64_t)sp.max_len + 1);
       if (!sp.endpoints) sp.out_paths[base] = src;
       for (;;) {
@@ -82,7 +77,7 @@ __global__ void __launch_bounds__(512) walk_persistent(DevGraph g, WalkSpec sp0,
   st.gpos = 0;
   st.lo = 0;
   Walker W;
-  W.w = 0; W.s = 0; W.cur = 0; W.prev = -1; W.off = W.d = W.poff = W.pd = 0; W.att = 0;
+  walker_init(W, 0u, 0);
   bool active = false;
   int req = 0;
   int64_t walk = 0;  // walk index within its request
@@ -120,11 +115,7 @@ __global__ void __launch_bounds__(512) walk_persistent(DevGraph g, WalkSpec sp0,
         const WalkSpec& sp = (A == MIXED) ? specs[req] : sp0;
         const int32_t src = sp.sources[walk / sp.wps];
         if (src >= 0 && src < g.nv) {
-          W.w = sp.walk_offset + (uint32_t)walk;
-          W.s = 0;
-          W.cur = src;
-          W.prev = -1;
-          W.att = 0;
+          walker_init(W, sp.walk_offset + (uint32_t)walk, src);
           if (!sp.endpoints) {
             st.gpos = walk * ((int64_t)sp.max_len + 1);
             st.lo = (int)(st.gpos & 7);

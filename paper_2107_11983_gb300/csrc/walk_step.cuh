@@ -18,10 +18,25 @@ struct Walker {
   int32_t s;        // moves taken
   int32_t cur;
   int32_t prev;
-  int32_t off, d;   // CSR row of cur (valid once attempt 0 of the step loaded it)
+  int32_t off, d;   // CSR row of cur (valid once attempt 0 of the step loaded it, or when rowok)
   int32_t poff, pd; // CSR row of prev
   uint32_t att;     // rejection trial within the step
+  int32_t nxo, nxd; // row of the vertex an ALIAS move picked (from its record)
+  bool nxv;         // nxo/nxd hold the next vertex's row
+  bool rowok;       // off/d already hold cur's row
 };
+
+__device__ __forceinline__ void walker_init(Walker& W, uint32_t w, int32_t src) {
+  W.w = w;
+  W.s = 0;
+  W.cur = src;
+  W.prev = -1;
+  W.off = W.d = W.poff = W.pd = 0;
+  W.att = 0;
+  W.nxo = W.nxd = 0;
+  W.nxv = false;
+  W.rowok = false;
+}
 
 enum StepResult : int { kIdle = -1, kMoved = 0, kStop = 1, kRetry = 2, kFail = 3, kBroken = 4, kDefer = 5 };
 
@@ -116,9 +131,11 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
   const uint4 B = draw_block(sp, W.w, (uint32_t)W.s, W.att);
   if (A == PPR && (uint64_t)B.w < sp.T_stop) return kStop;     // Update: PPR stop coin
   if (W.att == 0) {
-    if (CHECK && (uint32_t)W.cur >= (uint32_t)g.nv) return kBroken;
-    W.off = ldg(g.row_ptr + W.cur);
-    W.d = ldg(g.row_ptr + W.cur + 1) - W.off;
+    if (!W.rowok) {
+      if (CHECK && (uint32_t)W.cur >= (uint32_t)g.nv) return kBroken;
+      W.off = ldg(g.row_ptr + W.cur);
+      W.d = ldg(g.row_ptr + W.cur + 1) - W.off;
+    }
     if (CHECK && (W.off < 0 || W.d < 0 || (int64_t)W.off + W.d > (int64_t)g.ne)) return kBroken;
   }
   if (W.d == 0) return kStop;                                  // dead end
@@ -127,11 +144,18 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     next = ldg(g.col + W.off + below(B, (uint32_t)W.d));
     return kMoved;
   } else if (A == DEEPWALK_WEIGHTED) {
-    // ALIAS generation from the stored C_v (no Gather for static walks).
-    const uint4 r = ldg(g.alias + W.off + below(B, (uint32_t)W.d));
-    const int32_t pick = (B.z < r.x) ? (int32_t)r.y : (int32_t)r.z;
+    // ALIAS generation from the stored C_v (no Gather for static walks); the
+    // record also carries the picked vertex's row for the next step.
+    const AliasRec* rec = g.alias + W.off + below(B, (uint32_t)W.d);
+    const uint4 ra = __ldg(&rec->a);
+    const uint4 rb = __ldg(&rec->b);
+    const bool first = B.z < ra.x;
+    const int32_t pick = first ? (int32_t)ra.y : (int32_t)ra.z;
     if (pick < 0) return kStop;                                // no positive weight
     next = pick;
+    W.nxo = first ? (int32_t)ra.w : (int32_t)rb.x;
+    W.nxd = first ? (int32_t)rb.y : (int32_t)rb.z;
+    W.nxv = true;
     return kMoved;
   } else if (A == METAPATH) {
     // Gather (0/1 weights by label) then ITS generation: the r-th match.
@@ -377,6 +401,12 @@ __device__ __forceinline__ void advance(Walker& W, int32_t next) {
   W.cur = next;
   W.s += 1;
   W.att = 0;
+  W.rowok = W.nxv;
+  if (W.nxv) {
+    W.off = W.nxo;
+    W.d = W.nxd;
+    W.nxv = false;
+  }
 }
 
 template <int A, bool CHECK = false>
