@@ -267,8 +267,8 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   if (st == TRW_OK) {
     e = cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), g->stream);
     if (e == cudaSuccess)
-      e = launch_prepare_alias((int32_t)g->nv, g->row_ptr, g->col, g->weights, g->alias, q, sm, lg, g->ctrl, g->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+      e = launch_prepare_alias((int32_t)g->nv, g->ne, g->row_ptr, g->col, g->weights, g->alias, q, sm, lg, g->ctrl,
+                               g->stream);
     if (e == cudaSuccess) e = cudaMemcpy(&c, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
   }
   cudaFree(q);

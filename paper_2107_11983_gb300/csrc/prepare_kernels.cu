@@ -12,7 +12,18 @@
 // the tables are exactly reproducible.  Records hold the destination vertices
 // directly, with their own CSR rows (see AliasRec).  A vertex whose integer
 // weights sum to zero gets records with both destinations -1: a dead end.
+//
+// Parallel form of the same sequence: a warp (a block for rows of kBigRow
+// edges or more) sums and classifies the row and lays the items out in queue
+// order with ballots; only the pairing itself is sequential, and it runs as
+// a lockstep warp loop over two register windows (pair_row); the records,
+// with their divisions and destination-row lookups, are then built by all
+// threads.  Large rows go first, largest first, since their pairings are the
+// longest sequential chains.
+#include <algorithm>
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "trw_device.cuh"
@@ -50,6 +61,15 @@ __device__ __forceinline__ uint32_t frac32(unsigned long long q, unsigned long l
   return quo;
 }
 
+constexpr int kPrepThreads = 256;
+constexpr int32_t kBigRow = 4096;  // rows this long are prepared by a whole block
+
+__device__ __forceinline__ unsigned long long shfl64_xor(unsigned long long v, int m) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
 // Record of a bucket whose first element is destination u (taken with
 // probability H / 2^32) and whose second is v.
 __device__ __forceinline__ AliasRec make_rec(const int32_t* __restrict__ row_ptr, uint32_t H, int32_t u, int32_t v) {
@@ -60,62 +80,294 @@ __device__ __forceinline__ AliasRec make_rec(const int32_t* __restrict__ row_ptr
   return r;
 }
 
-__global__ void prepare_alias_kernel(int32_t nv, const int32_t* __restrict__ row_ptr,
-                                     const int32_t* __restrict__ col, const float* __restrict__ weights,
-                                     AliasRec* __restrict__ alias, unsigned long long* __restrict__ q,
-                                     int32_t* __restrict__ small, int32_t* __restrict__ large, Ctrl* ctrl) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t off = row_ptr[v];
-    const int32_t d = row_ptr[v + 1] - off;
-    if (d == 0) continue;
-    unsigned long long S = 0;
-    bool ok = true;
-    for (int32_t j = 0; j < d; ++j) {
-      uint32_t W;
-      ok &= quantize(weights[off + j], W);
-      S += W;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long v, int src) {
+  const uint32_t lo = __shfl_sync(kFull, (uint32_t)v, src);
+  const uint32_t hi = __shfl_sync(kFull, (uint32_t)(v >> 32), src);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl64_xor(v, o);
+  return v;
+}
+
+// Scratch of one row at offset off: idx[p] is the item at position p of the
+// queue order (the small items 0..ns-1 first, then the large ones, each in
+// ascending item order), qv[p] its q, and part[p] the large index it is
+// paired with.
+struct Scratch {
+  unsigned long long* qv;
+  int32_t* idx;
+  int32_t* part;
+};
+
+// The FIFO pairing of one row, run by all 32 lanes of a warp in lockstep.
+// The small queue is the small items followed by the large items in the
+// order they turn small, which is their own order, so position p of idx is
+// the p-th item popped; qv[ns + k] receives the q of large k when it turns
+// small, before the loop can reach position ns + k.  The loop only moves
+// two cursors forward, so each lane holds one element of a 32-position
+// window per cursor: wI (the pop cursor i) and wL (the large cursor
+// ns + lh, whose entries are overwritten as larges turn small).  When both
+// cursors are in the same window the pop reads wL.  Returns the number of
+// pops; part[p] is written for every p below it and qv[p] holds the popped q.
+__device__ int32_t pair_row(int64_t off, int32_t d, int32_t ns, unsigned long long S, const Scratch& sc,
+                            int lane) {
+  const int32_t nl = d - ns;
+  if (ns == 0 || nl == 0) return 0;
+  unsigned long long* qv = sc.qv + off;
+  int32_t* part = sc.part + off;
+  int32_t i = 0, lh = 0, lpos = ns;
+  const int32_t lb0 = lpos & ~31;
+  unsigned long long wL = lb0 + lane < d ? qv[lb0 + lane] : 0ull;
+  unsigned long long wI = (lpos >> 5) != 0 ? qv[lane] : 0ull;  // block 0 holds only small items then
+  int32_t my_part = -1;
+  unsigned long long rem = shfl64(wL, lpos & 31);
+  while (i < ns + lh && lh < nl) {
+    const bool same = (i >> 5) == (lpos >> 5);
+    const unsigned long long qs = shfl64(same ? wL : wI, i & 31);
+    if (lane == (i & 31)) my_part = lh;
+    rem -= S - qs;
+    ++i;
+    if ((i & 31) == 0) {
+      part[i - 32 + lane] = my_part;
+      if ((i >> 5) != (lpos >> 5)) wI = i + lane < d ? qv[i + lane] : 0ull;
     }
-    if (!ok) {
-      atomicCAS(&ctrl->err, 0, kErrInvalid);
-      continue;
-    }
-    if (S == 0) {
-      AliasRec dead;
-      dead.a = make_uint4(0u, 0xffffffffu, 0xffffffffu, 0u);
-      dead.b = make_uint4(0u, 0u, 0u, 0u);
-      for (int32_t j = 0; j < d; ++j) alias[off + j] = dead;
-      continue;
-    }
-    int32_t ns = 0, nl = 0;
-    for (int32_t j = 0; j < d; ++j) {
-      uint32_t W;
-      quantize(weights[off + j], W);
-      const unsigned long long qj = (unsigned long long)d * W;
-      q[off + j] = qj;
-      if (qj < S) small[off + ns++] = j;
-      else large[off + nl++] = j;
-    }
-    int32_t sh = 0, st = ns, lh = 0;
-    while (sh < st && lh < nl) {
-      const int32_t s = small[off + sh++];
-      const int32_t l = large[off + lh];
-      const unsigned long long qs = q[off + s];
-      alias[off + s] = make_rec(row_ptr, frac32(qs, S), col[off + s], col[off + l]);
-      const unsigned long long ql = q[off + l] - (S - qs);
-      q[off + l] = ql;
-      if (ql < S) {
-        ++lh;
-        small[off + st++] = l;
+    if (rem < S) {
+      if (lane == (lpos & 31)) wL = rem;
+      ++lh;
+      ++lpos;
+      if ((lpos & 31) == 0) {
+        const int32_t b = lpos - 32;
+        if (b + lane < d) qv[b + lane] = wL;
+        if ((i >> 5) == (b >> 5)) wI = wL;
+        wL = lpos + lane < d ? qv[lpos + lane] : 0ull;
       }
+      if (lh < nl) rem = shfl64(wL, lpos & 31);
     }
-    for (; lh < nl; ++lh) {
-      const int32_t j = large[off + lh];
-      alias[off + j] = make_rec(row_ptr, 0xffffffffu, col[off + j], col[off + j]);
+  }
+  {
+    const int32_t b = i & ~31;
+    if (b + lane < i) part[b + lane] = my_part;
+  }
+  {
+    const int32_t b = lpos & ~31;
+    if (b + lane < lpos && b + lane < d) qv[b + lane] = wL;
+  }
+  return i;
+}
+
+// The record of the item at queue position p.
+__device__ __forceinline__ void emit(int64_t off, int32_t p, int32_t ns, int32_t npop, unsigned long long S,
+                                     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                     const Scratch& sc, AliasRec* __restrict__ alias) {
+  const int32_t j = sc.idx[off + p];
+  const int32_t u = col[off + j];
+  if (p < npop) {
+    const int32_t l = sc.idx[off + ns + sc.part[off + p]];
+    alias[off + j] = make_rec(row_ptr, frac32(sc.qv[off + p], S), u, col[off + l]);
+  } else {
+    alias[off + j] = make_rec(row_ptr, 0xffffffffu, u, u);
+  }
+}
+
+__device__ __forceinline__ AliasRec dead_rec() {
+  AliasRec r;
+  r.a = make_uint4(0u, 0xffffffffu, 0xffffffffu, 0u);
+  r.b = make_uint4(0u, 0u, 0u, 0u);
+  return r;
+}
+
+// One row of fewer than kBigRow edges, by one warp.
+__device__ void warp_row(int64_t off, int32_t d, const int32_t* __restrict__ row_ptr,
+                         const int32_t* __restrict__ col, const float* __restrict__ weights, const Scratch& sc,
+                         AliasRec* __restrict__ alias, Ctrl* ctrl, int lane) {
+  unsigned long long S = 0;
+  bool ok = true;
+  for (int32_t j = lane; j < d; j += 32) {
+    uint32_t W;
+    ok &= quantize(weights[off + j], W);
+    S += W;
+  }
+  S = warp_sum64(S);
+  if (!__all_sync(kFull, ok)) {
+    if (lane == 0) atomicCAS(&ctrl->err, 0, kErrInvalid);
+    return;
+  }
+  if (S == 0) {
+    for (int32_t j = lane; j < d; j += 32) alias[off + j] = dead_rec();
+    return;
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  int32_t ns = 0;
+  for (int32_t b = 0; b < d; b += 32) {
+    const int32_t j = b + lane;
+    uint32_t W = 0;
+    if (j < d) quantize(weights[off + j], W);
+    ns += __popc(__ballot_sync(kFull, j < d && (unsigned long long)d * W < S));
+  }
+  int32_t cs = 0, cl = ns;
+  for (int32_t b = 0; b < d; b += 32) {
+    const int32_t j = b + lane;
+    uint32_t W = 0;
+    if (j < d) quantize(weights[off + j], W);
+    const unsigned long long q = (unsigned long long)d * W;
+    const bool small = j < d && q < S;
+    const unsigned ms = __ballot_sync(kFull, small), ml = __ballot_sync(kFull, j < d && !small);
+    if (j < d) {
+      const int32_t p = small ? cs + __popc(ms & lt) : cl + __popc(ml & lt);
+      sc.idx[off + p] = j;
+      sc.qv[off + p] = q;
     }
-    for (; sh < st; ++sh) {
-      const int32_t j = small[off + sh];
-      alias[off + j] = make_rec(row_ptr, 0xffffffffu, col[off + j], col[off + j]);
+    cs += __popc(ms);
+    cl += __popc(ml);
+  }
+  __syncwarp();
+  const int32_t npop = pair_row(off, d, ns, S, sc, lane);
+  __syncwarp();
+  for (int32_t p = lane; p < d; p += 32) emit(off, p, ns, npop, S, row_ptr, col, sc, alias);
+}
+
+// One row of kBigRow or more edges, by the whole block (kPrepThreads
+// threads); warp 0 runs the pairing.
+__device__ void block_row(int64_t off, int32_t d, const int32_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ col, const float* __restrict__ weights, const Scratch& sc,
+                          AliasRec* __restrict__ alias, Ctrl* ctrl) {
+  constexpr int kWarps = kPrepThreads / 32;
+  __shared__ unsigned long long s_sum[kWarps];
+  __shared__ int32_t s_cnt[2][kWarps];
+  __shared__ int32_t s_ok, s_npop;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long S = 0;
+  bool ok = true;
+  for (int32_t j = threadIdx.x; j < d; j += kPrepThreads) {
+    uint32_t W;
+    ok &= quantize(weights[off + j], W);
+    S += W;
+  }
+  S = warp_sum64(S);
+  ok = __all_sync(kFull, ok);
+  if (threadIdx.x == 0) s_ok = 1;
+  __syncthreads();
+  if (lane == 0) {
+    s_sum[warp] = S;
+    if (!ok) s_ok = 0;
+  }
+  __syncthreads();
+  S = 0;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) S += s_sum[k];
+  const bool all_ok = s_ok != 0;
+  __syncthreads();
+  if (!all_ok) {
+    if (threadIdx.x == 0) atomicCAS(&ctrl->err, 0, kErrInvalid);
+    return;
+  }
+  if (S == 0) {
+    for (int32_t j = threadIdx.x; j < d; j += kPrepThreads) alias[off + j] = dead_rec();
+    return;
+  }
+  // Small-item count.
+  int32_t ns_part = 0;
+  for (int32_t j = threadIdx.x; j < d; j += kPrepThreads) {
+    uint32_t W;
+    quantize(weights[off + j], W);
+    ns_part += (unsigned long long)d * W < S ? 1 : 0;
+  }
+  ns_part = __reduce_add_sync(kFull, ns_part);
+  if (lane == 0) s_cnt[0][warp] = ns_part;
+  __syncthreads();
+  int32_t ns = 0;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) ns += s_cnt[0][k];
+  __syncthreads();
+  // Ordered compaction, kPrepThreads items per round.
+  const unsigned lt = (1u << lane) - 1u;
+  int32_t cs = 0, cl = ns;
+  for (int32_t b = 0; b < d; b += kPrepThreads) {
+    const int32_t j = b + threadIdx.x;
+    uint32_t W = 0;
+    if (j < d) quantize(weights[off + j], W);
+    const unsigned long long q = (unsigned long long)d * W;
+    const bool small = j < d && q < S;
+    const unsigned ms = __ballot_sync(kFull, small), ml = __ballot_sync(kFull, j < d && !small);
+    if (lane == 0) {
+      s_cnt[0][warp] = __popc(ms);
+      s_cnt[1][warp] = __popc(ml);
     }
+    __syncthreads();
+    int32_t bs = cs, bl = cl, ts = 0, tl = 0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) {
+      if (k < warp) {
+        bs += s_cnt[0][k];
+        bl += s_cnt[1][k];
+      }
+      ts += s_cnt[0][k];
+      tl += s_cnt[1][k];
+    }
+    if (j < d) {
+      const int32_t p = small ? bs + __popc(ms & lt) : bl + __popc(ml & lt);
+      sc.idx[off + p] = j;
+      sc.qv[off + p] = q;
+    }
+    cs += ts;
+    cl += tl;
+    __syncthreads();
+  }
+  if (warp == 0) {
+    const int32_t npop = pair_row(off, d, ns, S, sc, lane);
+    if (lane == 0) s_npop = npop;
+  }
+  __syncthreads();
+  const int32_t npop = s_npop;
+  for (int32_t p = threadIdx.x; p < d; p += kPrepThreads) emit(off, p, ns, npop, S, row_ptr, col, sc, alias);
+  __syncthreads();
+}
+
+// Rows of kBigRow edges or more first, one per block, largest first (the
+// list is sorted by degree on the host); then every other row, one per warp,
+// claimed 32 rows at a time.
+__global__ void __launch_bounds__(kPrepThreads) prepare_alias_kernel(
+    int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const float* __restrict__ weights, AliasRec* __restrict__ alias, Scratch sc, const int32_t* __restrict__ big,
+    int32_t nbig, unsigned int* counters, Ctrl* ctrl) {
+  __shared__ int32_t s_r;
+  for (;;) {
+    if (threadIdx.x == 0) s_r = (int32_t)atomicAdd(&counters[0], 1u);
+    __syncthreads();
+    const int32_t r = s_r;
+    __syncthreads();
+    if (r >= nbig) break;
+    const int32_t v = big[r];
+    const int32_t off = row_ptr[v];
+    block_row(off, row_ptr[v + 1] - off, row_ptr, col, weights, sc, alias, ctrl);
+  }
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned int base = 0;
+    if (lane == 0) base = atomicAdd(&counters[1], 32u);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= (unsigned)nv) break;
+    const int32_t end = min((int32_t)base + 32, nv);
+    for (int32_t v = (int32_t)base; v < end; ++v) {
+      const int32_t off = row_ptr[v];
+      const int32_t d = row_ptr[v + 1] - off;
+      if (d == 0 || d >= kBigRow) continue;
+      warp_row(off, d, row_ptr, col, weights, sc, alias, ctrl, lane);
+    }
+  }
+}
+
+// Rows of kBigRow edges or more, as (degree << 32 | vertex) keys.
+__global__ void collect_big_rows(int32_t nv, const int32_t* __restrict__ row_ptr, unsigned long long* keys,
+                                 unsigned int* count) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d >= kBigRow) keys[atomicAdd(count, 1u)] = ((unsigned long long)d << 32) | (unsigned long long)v;
   }
 }
 
@@ -141,15 +393,55 @@ __global__ void check_graph_kernel(int32_t nv, const int32_t* __restrict__ row_p
 
 }  // namespace
 
-cudaError_t launch_prepare_alias(int32_t nv, const int32_t* row_ptr, const int32_t* col, const float* weights,
-                                 AliasRec* alias, unsigned long long* q_scratch, int32_t* small_scratch,
-                                 int32_t* large_scratch, Ctrl* ctrl, cudaStream_t st) {
+cudaError_t launch_prepare_alias(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                                 const float* weights, AliasRec* alias, unsigned long long* q_scratch,
+                                 int32_t* idx_scratch, int32_t* part_scratch, Ctrl* ctrl, cudaStream_t st) {
   if (nv <= 0) return cudaSuccess;
-  int64_t blocks = ((int64_t)nv + 127) / 128;
+  // Rows of kBigRow edges or more: collected on the device, sorted by degree
+  // (largest first) on the host so that the longest pairings start first.
+  const size_t max_big = (size_t)(ne / kBigRow) + 1;
+  unsigned long long* keys = nullptr;
+  int32_t* big = nullptr;
+  unsigned int* counters = nullptr;  // [0] big-row claims, [1] row claims, [2] big-row count
+  cudaError_t e = cudaMalloc(&keys, sizeof(unsigned long long) * max_big);
+  if (e == cudaSuccess) e = cudaMalloc(&big, sizeof(int32_t) * max_big);
+  if (e == cudaSuccess) e = cudaMalloc(&counters, sizeof(unsigned int) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * 4, st);
+  int64_t blocks = ((int64_t)nv + 255) / 256;
   if (blocks > 65535) blocks = 65535;
-  prepare_alias_kernel<<<(unsigned)blocks, 128, 0, st>>>(nv, row_ptr, col, weights, alias, q_scratch, small_scratch,
-                                                         large_scratch, ctrl);
-  return cudaGetLastError();
+  if (e == cudaSuccess) {
+    collect_big_rows<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, keys, counters + 2);
+    e = cudaGetLastError();
+  }
+  unsigned int nbig = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nbig, counters + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && nbig > max_big) e = cudaErrorUnknown;  // cannot happen: each big row holds kBigRow edges
+  std::vector<unsigned long long> hk(nbig);
+  std::vector<int32_t> hb(nbig);
+  if (e == cudaSuccess && nbig > 0) {
+    e = cudaMemcpy(hk.data(), keys, sizeof(unsigned long long) * nbig, cudaMemcpyDeviceToHost);
+    std::sort(hk.begin(), hk.end(), [](unsigned long long a, unsigned long long b) { return a > b; });
+    for (unsigned int k = 0; k < nbig; ++k) hb[k] = (int32_t)(hk[k] & 0xffffffffu);
+    if (e == cudaSuccess) e = cudaMemcpy(big, hb.data(), sizeof(int32_t) * nbig, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    int dev = 0, sms = 1, occ = 1;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, prepare_alias_kernel, kPrepThreads, 0);
+    if (e == cudaSuccess) {
+      const Scratch sc{q_scratch, idx_scratch, part_scratch};
+      prepare_alias_kernel<<<(unsigned)(sms * (occ > 0 ? occ : 1)), kPrepThreads, 0, st>>>(
+          nv, row_ptr, col, weights, alias, sc, big, (int32_t)nbig, counters, ctrl);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(keys);
+  cudaFree(big);
+  cudaFree(counters);
+  return e;
 }
 
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl, int* d_unsorted,

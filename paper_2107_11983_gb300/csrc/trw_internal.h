@@ -27,10 +27,11 @@ cudaError_t launch_walk_persistent(const DevGraph& g, const WalkSpec& sp, Ctrl* 
 cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const int64_t* d_prefix, int nreq,
                               int64_t total, Ctrl* ctrl, cudaStream_t st, const LaunchCfg& cfg);
 
-// ALIAS preprocessing (Algorithm 3) on the device.
-cudaError_t launch_prepare_alias(int32_t nv, const int32_t* row_ptr, const int32_t* col, const float* weights,
-                                 AliasRec* alias, unsigned long long* q_scratch, int32_t* small_scratch,
-                                 int32_t* large_scratch, Ctrl* ctrl, cudaStream_t st);
+// ALIAS preprocessing (Algorithm 3) on the device; synchronises st.  The
+// three scratch arrays hold ne elements each.
+cudaError_t launch_prepare_alias(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                                 const float* weights, AliasRec* alias, unsigned long long* q_scratch,
+                                 int32_t* idx_scratch, int32_t* part_scratch, Ctrl* ctrl, cudaStream_t st);
 
 // Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl,

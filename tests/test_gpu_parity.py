@@ -58,6 +58,65 @@ def test_alias_tables_match_oracle(small):
     assert ne == H.shape[0]
 
 
+def _rows_graph(degrees, seed=11):
+    """Directed CSR graph whose rows have the given degrees (random sorted
+    distinct neighbours), with a different weight pattern per row."""
+    rng = np.random.default_rng(seed)
+    nv = max(max(degrees) + 1, len(degrees))
+    row_ptr = np.zeros(nv + 1, dtype=np.int64)
+    cols, ws = [], []
+    for v in range(nv):
+        d = degrees[v] if v < len(degrees) else int(rng.integers(0, 9))
+        c = np.sort(rng.choice(nv, size=d, replace=False)).astype(np.int32)
+        kind = v % 7
+        if kind == 0:
+            w = rng.uniform(1, 100, d)
+        elif kind == 1:
+            w = np.full(d, 3.0)
+        elif kind == 2:  # one heavy edge absorbs every small one
+            w = np.ones(d)
+            if d:
+                w[rng.integers(d)] = 1e4
+        elif kind == 3:  # heavy-tailed: larges turn small again and again
+            w = rng.geometric(0.3, d).astype(np.float64) ** 3
+        elif kind == 4:  # half zeros
+            w = rng.uniform(0, 1, d) * (rng.uniform(0, 1, d) < 0.5)
+        elif kind == 5:
+            w = np.where(np.arange(d) % 7 == 0, 1000.0, 1.0)
+        else:  # quantisation extremes, S above 2^32
+            w = rng.choice([1e-6, 0.5, 65535.0, 2.0], d)
+        row_ptr[v + 1] = row_ptr[v] + d
+        cols.append(c)
+        ws.append(w.astype(np.float32))
+    return synth.Graph(row_ptr, np.concatenate(cols), np.concatenate(ws))
+
+
+def test_alias_tables_long_rows_match_oracle():
+    # Rows on both sides of the whole-block threshold (4096 edges) and far
+    # above it, each weight pattern at several lengths.
+    degrees = [20000, 4095, 4096, 4097, 9001, 12000, 6000, 40000, 4096, 5000, 8191, 8192, 30000, 4100, 0, 1, 31, 32,
+               33, 1000]
+    g = _rows_graph(degrees)
+    G = trw.Graph(g.row_ptr, g.col, g.weights, None)
+    G.prepare()
+    al = oracle.prepare_alias(g.row_ptr, g.weights)
+    H, first, second = G.debug_alias()
+    full = al.H == (1 << 32)
+    assert np.array_equal(H[~full], al.H[~full].astype(np.uint32))
+    assert np.all(H[full] == 0xFFFFFFFF)
+    off = np.repeat(g.row_ptr[:-1], np.diff(g.row_ptr))
+    live = ~np.repeat(al.dead.astype(bool), np.diff(g.row_ptr))
+    assert np.array_equal(first[live], g.col[off + al.A_first][live])
+    sec_slot = np.where(al.A_second >= 0, al.A_second, al.A_first)
+    assert np.array_equal(second[live], g.col[off + sec_slot][live])
+    assert np.all(first[~live] == -1) and np.all(second[~live] == -1)
+    # and the walks over them
+    src = np.concatenate([np.arange(len(degrees), dtype=np.int32), synth.sources(3001, g.nv, seed=4)])
+    out = G.walk(trw.DEEPWALK_WEIGHTED, src, 40, seed=9)
+    want = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, 40, 9, alias=al)
+    assert_paths_equal(out.paths, out.lengths, want)
+
+
 def test_alias_dead_and_zero_weights():
     # vertex 0: all zero weights (dead for weighted walks); vertex 1: one zero weight
     g = synth.from_edges(4, [(0, 1), (0, 2), (1, 0), (1, 2), (1, 3), (2, 3), (3, 0)])
