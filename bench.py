@@ -657,6 +657,12 @@ def run_mixed(args, wl):
     dev = torch.device("cuda", torch.cuda.current_device())
     g = build_graph(wl)
     G = trw.Graph(g.row_ptr, g.col, None, g.labels)
+    index_ms = None
+    if not args.no_label_index:
+        torch.cuda.synchronize()
+        t = time.time()
+        G.prepare(trw.PREP_LABEL_INDEX)
+        index_ms = 1000 * (time.time() - t)
     schema = synth.schema(5, 5, seed=1)
     ppr_src_h = synth.sources(1_000_000, g.nv, seed=1)
     mp_src_h = synth.vertex_sources(g.nv)
@@ -672,7 +678,8 @@ def run_mixed(args, wl):
         flush.zero_()
         outs = G.walk_batch(reqs, stream=sp)
     torch.cuda.synchronize()
-    moves = sum(int((o.lengths.to(torch.int64) - 1).sum().item()) for o in outs)
+    moves_by_req = [int((o.lengths.to(torch.int64) - 1).sum().item()) for o in outs]
+    moves = sum(moves_by_req)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
@@ -710,6 +717,28 @@ def run_mixed(args, wl):
         e2e_t.append(time.perf_counter() - t)
     e2e_s = statistics.median(e2e_t)
     d2h = sum(int(p.numel() + l.numel()) * 4 for p, l in host)
+    scan = None
+    if index_ms is not None and not args.no_extras:
+        # the same batch with the paper's per-step label scan (no index)
+        Gs = trw.Graph(g.row_ptr, g.col, None, g.labels)
+        if not args.no_autotune:
+            Gs.autotune(trw.METAPATH, 10, schema=schema)
+        for _ in range(2):
+            flush.zero_()
+            Gs.walk_batch(reqs, stream=sp)
+        sms = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Gs.walk_batch(reqs, stream=sp, sync=False)
+            b.record(stream)
+            Gs.sync(sp)
+            sms.append(a.elapsed_time(b))
+        scan = {"value": round(moves / (statistics.median(sms) / 1000.0), 1), "unit": UNIT,
+                "ms": round(statistics.median(sms), 3), "tuning": Gs.tuning(),
+                "speedup_index": round(statistics.median(sms) / statistics.mean(ms), 2)}
+        del Gs
     gather = measure_gather_ceiling(trw, g) if not args.no_extras else None
     cpu = None
     if not args.no_cpu_baseline:
@@ -736,7 +765,8 @@ def run_mixed(args, wl):
                "model_bytes_per_move": (32.0 * sec + ob) / max(1, mv)}
     line = _common_line(args, wl, value, statistics.mean(ms), {
         "graph": f"rmat-s{wl['scale']}-ef16-sym", "nv": g.nv, "ne": g.ne, "requests": "PPR 1,000,000 (stop 0.2, max 1000, endpoints) + MetaPath one per vertex (schema of 5, 80 moves)",
-        "moves_per_step": moves, "l2": "256 MiB buffer written between timed steps", "tuning": G.tuning()})
+        "moves_per_step": moves, "l2": "256 MiB buffer written between timed steps", "tuning": G.tuning(),
+        "metapath_gather": "label scan" if index_ms is None else "label index (bit-identical to the scan)"})
     line["kernel_ms_per_step"] = round(kms, 4)
     line["plain_launch"] = {"value": round(moves / (statistics.median(plain_ms) / 1000.0), 1), "unit": UNIT,
                             "ms": round(statistics.median(plain_ms), 3),
@@ -744,8 +774,29 @@ def run_mixed(args, wl):
     line["e2e"] = {"value": round(moves / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int((ppr_src_h.size + mp_src_h.size) * 4),
                    "d2h_bytes_per_step": d2h, "ms": round(1000 * e2e_s, 3)}
     line["gpu_launches"] = 3 * args.steps
+    line["preprocess"] = {"label_index_ms": None if index_ms is None else round(index_ms, 2)}
+    line["metapath_scan"] = scan
     bpm = cpu["model_bytes_per_move"] if cpu else None
-    if bpm:
+    if index_ms is not None:
+        # closed form: PPR moves are NAIVE moves (row pair, one col sector,
+        # nothing written: endpoints); an indexed MetaPath move reads one
+        # 32-byte record and writes a path entry; each MetaPath walk reads its
+        # source's vertex record; each walk reads its source and writes its
+        # length and first (PPR: only) output
+        n_ppr, n_mp = ppr_src_h.size, mp_src_h.size
+        alg = (moves_by_req[0] * (ROW_PAIR + SECTOR) + moves_by_req[1] * (SECTOR + 4)
+               + (n_ppr + n_mp) * BYTES_PER_WALK_BASE + n_mp * SECTOR)
+        peak, kind = measured_peak_hbm()
+        ach = alg / (kms / 1000.0) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(ach / peak, 4), "traffic": None, "peak_kind": f"{kind} copy bandwidth",
+                            "kernel": "walk_persistent<MIXED>", "bytes_per_move": round(alg / max(1, moves), 2),
+                            "bytes_per_move_source": "closed form (32-byte sectors of the device layout, label index)",
+                            "algorithmic_bytes_per_launch": int(alg)}
+        if gather is not None:
+            line["roofline"]["random_gather_ceiling_steps_per_s"] = gather["loads_per_s"]
+            line["roofline"]["frac_of_gather_ceiling"] = round(value / gather["loads_per_s"], 4)
+    elif bpm:
         peak, kind = measured_peak_hbm()
         ach = moves * bpm / (kms / 1000.0) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
@@ -834,6 +885,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-algorithm lines and the gather ceiling")
     ap.add_argument("--scale", type=int, default=0, help="override the R-MAT scale (smaller profiling cases)")
+    ap.add_argument("--no-label-index", action="store_true",
+                    help="mixed workload: MetaPath scans labels at every step instead of the label index")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tuning (profiling runs: the first launches are then the timed ones)")
     ap.add_argument("--serve-requests", type=int, default=3000, help="requests in the serving trace")

@@ -120,6 +120,8 @@ trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_ptr, const 
 void trw_graph_free(trw_graph* g);
 
 #define TRW_PREP_ALIAS 1u        /* build the ALIAS tables for TRW_DEEPWALK_WEIGHTED */
+#define TRW_PREP_LABEL_INDEX 2u  /* build the MetaPath label index (labelled graphs) */
+#define TRW_LABEL_INDEX_MAX_LABELS 30
 
 /*
  * Preprocessing for static walks (Algorithm 3): for every vertex v, apply the
@@ -128,8 +130,22 @@ void trw_graph_free(trw_graph* g);
  * integers round-half-even(w * 2^16); the tables come from Vose's method on
  * those integers with first-in first-out work lists, so every table entry is
  * exact up to one floor of H.  A vertex whose edges all quantise to zero
- * becomes a dead end for weighted walks.  Runs on the device; synchronous.
- * Errors: TRW_ERR_INVALID (no weights loaded), TRW_ERR_OOM, TRW_ERR_CUDA.
+ * becomes a dead end for weighted walks.
+ *
+ * TRW_PREP_LABEL_INDEX (not in the paper, whose MetaPath Gather scans the
+ * labels of E_v at every step, Section 2.2): every row is stably partitioned
+ * by edge label, and each edge slot gets a record holding its destination
+ * and the bounds of the destination's label groups.  A MetaPath move then
+ * reads one record instead of scanning the row; the r-th edge of a label
+ * group is the row's r-th matching edge in CSR order, so every walk is
+ * identical with and without the index.  Labels must lie in
+ * [0, TRW_LABEL_INDEX_MAX_LABELS); the records take (NL + 2) int32 rounded up
+ * to 8, 16 or 32 words per edge and per vertex (NL = largest label + 1).
+ * Preparing an index that exists already does nothing.
+ *
+ * Runs on the device; synchronous.  Errors: TRW_ERR_INVALID (no weights, or
+ * no labels, loaded for the requested table; a label too large for the
+ * index; an unknown flag), TRW_ERR_OOM, TRW_ERR_CUDA.
  */
 trw_status trw_prepare(trw_graph* g, uint32_t what);
 
@@ -268,6 +284,14 @@ int64_t trw_graph_device_bytes(const trw_graph* g);
  * H (probability threshold; 0xFFFFFFFF marks a one-element bucket),
  * first/second destination vertex (-1, -1 for a dead vertex).  For tests. */
 trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int32_t* second);
+
+/*
+ * Copy of the MetaPath label index (tests): *stride receives the words per
+ * record (0 when not prepared); when vrec and erec are both non-NULL they
+ * receive nv * stride and ne * stride int32 (host).  Errors: TRW_ERR_INVALID
+ * (NULL graph or stride), TRW_ERR_CUDA.
+ */
+trw_status trw_debug_label_index(const trw_graph* g, int32_t* stride, int32_t* vrec, int32_t* erec);
 
 /* Philox4x32-10 blocks computed on the device: out[4*i..4*i+3] for counter
  * ctr[4*i..4*i+3] and key (key0, key1).  Host buffers.  For tests. */

@@ -24,6 +24,8 @@ DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH = 0, 1, 2, 3, 4
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT = 0, 1, 2
 OUT_PATHS, OUT_ENDPOINTS = 0, 1
 PREP_ALIAS = 1
+PREP_LABEL_INDEX = 2
+LABEL_INDEX_MAX_LABELS = 30
 MAX_SCHEMA = 16
 MAX_BATCH = 64
 
@@ -93,6 +95,7 @@ _SIGS = {
     "trw_graph_ne": (ctypes.c_int64, [_VP]),
     "trw_graph_device_bytes": (ctypes.c_int64, [_VP]),
     "trw_debug_alias": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "trw_debug_label_index": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "trw_debug_philox": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, _VP]),
     "trw_serve_config_default": (None, [_VP]),
     "trw_serve_create": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -249,6 +252,8 @@ class Graph:
             pass
 
     def prepare(self, what: int = PREP_ALIAS):
+        """trw_prepare: PREP_ALIAS (weighted DeepWalk tables) and/or
+        PREP_LABEL_INDEX (MetaPath label index)."""
         _check(load_library().trw_prepare(self._h, what), "trw_prepare")
 
     def device_bytes(self) -> int:
@@ -365,6 +370,20 @@ class Graph:
         b = np.empty(self.ne, dtype=np.int32)
         _check(load_library().trw_debug_alias(self._h, H.ctypes.data, a.ctypes.data, b.ctypes.data), "trw_debug_alias")
         return H, a, b
+
+    def debug_label_index(self):
+        """(stride, vertex records [nv, stride], edge records [ne, stride]) of
+        the MetaPath label index, or None when it is not prepared."""
+        lib = load_library()
+        st = ctypes.c_int32(0)
+        _check(lib.trw_debug_label_index(self._h, ctypes.byref(st), None, None), "trw_debug_label_index")
+        if st.value == 0:
+            return None
+        v = np.empty((self.nv, st.value), dtype=np.int32)
+        e = np.empty((self.ne, st.value), dtype=np.int32)
+        _check(lib.trw_debug_label_index(self._h, ctypes.byref(st), v.ctypes.data, e.ctypes.data),
+               "trw_debug_label_index")
+        return st.value, v, e
 
 
 def gather_ceiling(table_bytes: int, record_bytes: int = 16, hops: int = 80, chains: int = 1) -> dict:

@@ -101,6 +101,8 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->weights);
   cudaFree(g->labels);
   cudaFree(g->alias);
+  cudaFree(g->lvrec);
+  cudaFree(g->lerec);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);
@@ -238,6 +240,10 @@ DevGraph trw_dev_graph(const trw_graph* g) {
   d.col = g->col;
   d.alias = g->alias;
   d.labels = g->labels;
+  d.lidx.vrec = g->lvrec;
+  d.lidx.erec = g->lerec;
+  d.lidx.stride = g->lstride;
+  d.lidx.nl = g->lnl;
   d.nv = (int32_t)g->nv;
   d.ne = (int32_t)g->ne;
   return d;
@@ -245,11 +251,7 @@ DevGraph trw_dev_graph(const trw_graph* g) {
 
 // ------------------------------------------------------------------ prepare
 
-extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
-  if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
-  if (what & ~TRW_PREP_ALIAS) return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
-  if (!(what & TRW_PREP_ALIAS)) return TRW_OK;
-  std::lock_guard<std::mutex> lk(g->mu);
+static trw_status prepare_alias(trw_graph* g) {
   if (!g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
   const size_t ne = (size_t)g->ne;
   if (!g->alias) {
@@ -281,6 +283,59 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
     return trw_fail(TRW_ERR_INVALID, "an edge weight is negative or not finite");
   }
   g->prepared_alias = true;
+  return TRW_OK;
+}
+
+static trw_status prepare_label_index(trw_graph* g) {
+  if (!g->labels) return trw_fail(TRW_ERR_INVALID, "the label index needs edge labels");
+  if (g->lerec) return TRW_OK;
+  unsigned int* d_max = reinterpret_cast<unsigned int*>(static_cast<char*>(g->misc) + 64);
+  unsigned int mx = 0;
+  cudaError_t e = cudaMemsetAsync(d_max, 0, sizeof(unsigned int), g->stream);
+  if (e == cudaSuccess) e = launch_label_max(g->labels, g->ne, d_max, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&mx, d_max, sizeof(unsigned int), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "label maximum");
+  const int32_t nl = (int32_t)mx + 1;
+  if (nl > TRW_LABEL_INDEX_MAX_LABELS)
+    return trw_fail(TRW_ERR_INVALID, "label %u is too large for the label index (at most %d labels)", mx,
+                    TRW_LABEL_INDEX_MAX_LABELS);
+  const int32_t stride = nl + 2 <= 8 ? 8 : nl + 2 <= 16 ? 16 : 32;
+  int32_t *vrec = nullptr, *erec = nullptr;
+  const size_t vbytes = sizeof(int32_t) * (size_t)stride * (size_t)g->nv;
+  const size_t ebytes = sizeof(int32_t) * (size_t)stride * (size_t)g->ne;
+  trw_status st = alloc_dev((void**)&vrec, vbytes, "label index");
+  if (st == TRW_OK) st = alloc_dev((void**)&erec, ebytes, "label index");
+  if (st == TRW_OK) {
+    e = launch_prepare_labels((int32_t)g->nv, g->ne, g->row_ptr, g->col, g->labels, nl, stride, vrec, erec,
+                              g->stream);
+    if (e != cudaSuccess) st = trw_cuda_fail(e, "prepare label index");
+  }
+  if (st != TRW_OK) {
+    cudaFree(vrec);
+    cudaFree(erec);
+    return st;
+  }
+  g->lvrec = vrec;
+  g->lerec = erec;
+  g->lstride = stride;
+  g->lnl = nl;
+  g->device_bytes += (int64_t)(vbytes + ebytes);
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
+  if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX))
+    return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
+  std::lock_guard<std::mutex> lk(g->mu);
+  if ((what & TRW_PREP_ALIAS) && !g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
+  if ((what & TRW_PREP_LABEL_INDEX) && !g->labels) return trw_fail(TRW_ERR_INVALID, "the label index needs edge labels");
+  if (what & TRW_PREP_ALIAS) {
+    trw_status st = prepare_alias(g);
+    if (st != TRW_OK) return st;
+  }
+  if (what & TRW_PREP_LABEL_INDEX) return prepare_label_index(g);
   return TRW_OK;
 }
 
@@ -348,7 +403,7 @@ LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
   LaunchCfg c;
   c.block_threads = g->tuning.block_threads;
   int bps = g->tuning.blocks_per_sm;
-  const bool coop = algo == MIXED || (algo == METAPATH && g->tuning.coop_degree < 0x7fffffff) ||
+  const bool coop = algo == MIXED || (algo == METAPATH && !g->lerec && g->tuning.coop_degree < 0x7fffffff) ||
                     (algo == NODE2VEC && g->tuning.search_degree < 0x7fffffff);
   const int occ = persistent_blocks_per_sm(algo, c.block_threads, coop);
   if (bps <= 0 || bps > occ) bps = occ;
@@ -356,6 +411,7 @@ LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
   c.chunk = g->tuning.chunk;
   c.coop_degree = g->tuning.coop_degree;
   c.search_degree = g->tuning.search_degree;
+  if (algo == METAPATH && g->lerec) c.coop_degree = 0x7fffffff;  // indexed: no label scans to share
   return c;
 }
 
@@ -645,6 +701,18 @@ extern "C" trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* 
     first[i] = (int32_t)rec[(size_t)i].a.y;
     second[i] = (int32_t)rec[(size_t)i].a.z;
   }
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_debug_label_index(const trw_graph* g, int32_t* stride, int32_t* vrec, int32_t* erec) {
+  if (!g || !stride) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  *stride = g->lerec ? g->lstride : 0;
+  if (!g->lerec || !vrec || !erec) return TRW_OK;
+  const size_t sw = (size_t)g->lstride;
+  if (g->nv > 0)
+    CUDA_TRY(cudaMemcpy(vrec, g->lvrec, sizeof(int32_t) * sw * (size_t)g->nv, cudaMemcpyDeviceToHost), "copy index");
+  if (g->ne > 0)
+    CUDA_TRY(cudaMemcpy(erec, g->lerec, sizeof(int32_t) * sw * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy index");
   return TRW_OK;
 }
 

@@ -53,7 +53,7 @@ extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params
     const int threads_c[] = {128, 256, 512};
     const int chunk_c[] = {8, 32, 128};
     std::vector<int> deg_c;
-    if (algo == TRW_METAPATH) deg_c = {64, 256, 1024, kOff};
+    if (algo == TRW_METAPATH && !g->lerec) deg_c = {64, 256, 1024, kOff};
     else if (algo == TRW_NODE2VEC) deg_c = {64, 1024, kOff};
     else deg_c = {kOff};
     for (int threads : threads_c) {

@@ -371,6 +371,89 @@ __global__ void collect_big_rows(int32_t nv, const int32_t* __restrict__ row_ptr
   }
 }
 
+// ------------------------------------------------------ MetaPath label index
+// (see LabelIndex).  One warp per row: labels are counted per value with
+// __match_any_sync (the lowest lane of each equal-label group adds the
+// group's size), the exclusive prefix over labels gives the group starts,
+// and a second pass scatters the destinations in CSR order, each lane at its
+// group's cursor plus its rank among the equal labels of lower lanes.
+
+__global__ void label_max_kernel(const uint8_t* __restrict__ labels, int64_t ne, unsigned int* out) {
+  unsigned int m = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned int)labels[e]);
+  m = __reduce_max_sync(kFull, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+constexpr int kLabelWarps = 8;
+
+__global__ void __launch_bounds__(kLabelWarps * 32) label_rows_kernel(
+    int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const uint8_t* __restrict__ labels, int32_t nl, int32_t stride, int32_t* __restrict__ vrec,
+    int32_t* __restrict__ erec) {
+  __shared__ int32_t s_cur[kLabelWarps][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t* cur = s_cur[wib];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t v = (int64_t)blockIdx.x * kLabelWarps + wib; v < nv; v += (int64_t)gridDim.x * kLabelWarps) {
+    const int32_t off = row_ptr[v];
+    const int32_t d = row_ptr[v + 1] - off;
+    cur[lane] = 0;
+    __syncwarp();
+    for (int32_t b = 0; b < d; b += 32) {
+      const int32_t j = b + lane;
+      const bool valid = j < d;
+      const uint32_t x = valid ? labels[off + j] : 0xffu;
+      const unsigned m = __match_any_sync(kFull, x);
+      if (valid && lane == __ffs(m) - 1) cur[x] += __popc(m);
+      __syncwarp();
+    }
+    const int32_t cnt = lane < nl ? cur[lane] : 0;
+    int32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int32_t start = off + incl - cnt;  // g(v, lane) for lane < nl
+    const int32_t prev_start = __shfl_up_sync(kFull, start, 1);
+    __syncwarp();
+    if (lane < nl) cur[lane] = start;
+    // record word k: v, then g(v, 0..nl), then padding (the row end)
+    if (lane < stride) {
+      int32_t word;
+      if (lane == 0) word = (int32_t)v;
+      else if (lane - 1 < nl) word = prev_start;
+      else word = off + d;
+      vrec[v * stride + lane] = word;
+    }
+    __syncwarp();
+    for (int32_t b = 0; b < d; b += 32) {
+      const int32_t j = b + lane;
+      const bool valid = j < d;
+      const uint32_t x = valid ? labels[off + j] : 0xffu;
+      const int32_t c = valid ? col[off + j] : 0;
+      const unsigned m = __match_any_sync(kFull, x);
+      if (valid) erec[(int64_t)(cur[x] + __popc(m & lt)) * stride] = c;
+      __syncwarp();
+      if (valid && lane == __ffs(m) - 1) cur[x] += __popc(m);
+      __syncwarp();
+    }
+  }
+}
+
+// Edge record e = the vertex record of the destination stored in its word 0.
+__global__ void label_gather_kernel(int64_t ne, int32_t stride, const int32_t* __restrict__ vrec,
+                                    int32_t* __restrict__ erec) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    int4* dst = reinterpret_cast<int4*>(erec + e * stride);
+    const int32_t v = erec[e * stride];
+    const int4* src = reinterpret_cast<const int4*>(vrec + (int64_t)v * stride);
+    for (int k = 0; k < stride / 4; ++k) dst[k] = __ldg(src + k);
+  }
+}
+
 // Every id in [0, nv); flags a row that is not strictly increasing.
 __global__ void check_graph_kernel(int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                    Ctrl* ctrl, int* unsorted) {
@@ -441,6 +524,32 @@ cudaError_t launch_prepare_alias(int32_t nv, int64_t ne, const int32_t* row_ptr,
   cudaFree(keys);
   cudaFree(big);
   cudaFree(counters);
+  return e;
+}
+
+cudaError_t launch_label_max(const uint8_t* labels, int64_t ne, unsigned int* d_out, cudaStream_t st) {
+  if (ne <= 0) return cudaSuccess;
+  int64_t blocks = (ne + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  label_max_kernel<<<(unsigned)blocks, 256, 0, st>>>(labels, ne, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_labels(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                                  const uint8_t* labels, int32_t nl, int32_t stride, int32_t* vrec, int32_t* erec,
+                                  cudaStream_t st) {
+  if (nv <= 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)nv + kLabelWarps - 1) / kLabelWarps;
+  if (blocks > 65535) blocks = 65535;
+  label_rows_kernel<<<(unsigned)blocks, kLabelWarps * 32, 0, st>>>(nv, row_ptr, col, labels, nl, stride, vrec, erec);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && ne > 0) {
+    int64_t eb = (ne + 255) / 256;
+    if (eb > 65535) eb = 65535;
+    label_gather_kernel<<<(unsigned)eb, 256, 0, st>>>(ne, stride, vrec, erec);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
 

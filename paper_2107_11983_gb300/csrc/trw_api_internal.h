@@ -21,6 +21,10 @@ struct trw_graph {
   float* weights = nullptr;          // [ne] or null
   uint8_t* labels = nullptr;         // [ne + 64] or null
   trw::AliasRec* alias = nullptr;    // [ne] after trw_prepare(ALIAS)
+  int32_t* lvrec = nullptr;          // MetaPath label index (trw_prepare(LABEL_INDEX)): vertex records
+  int32_t* lerec = nullptr;          // and edge records, lstride words each
+  int32_t lstride = 0;
+  int32_t lnl = 0;                   // labels in the index (largest label + 1)
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags
   int32_t* src_stage = nullptr;      // staging for host buffers (grow-only)

@@ -29,12 +29,29 @@ struct __align__(32) AliasRec {
   uint4 b;
 };
 
+// MetaPath label index (an optional preparation; walks are identical with
+// and without it).  Each row is stably partitioned by label, so the group of
+// label l in row v, [g(v, l), g(v, l + 1)), lists the edges labelled l in CSR
+// order and its r-th entry is the r-th matching edge of the row.  A vertex
+// record is lstride int32 words {v, g(v, 0), ..., g(v, NL)} (NL labels,
+// g(v, 0) = row_ptr[v], g(v, NL) = row_ptr[v + 1]); the edge record at
+// partitioned slot e is the vertex record of that edge's destination, so a
+// MetaPath move reads one record and learns both the next vertex and the
+// bounds of its label groups for the next step.
+struct LabelIndex {
+  const int32_t* __restrict__ vrec;      // [nv * stride], or null when not prepared
+  const int32_t* __restrict__ erec;      // [ne * stride]
+  int32_t stride;                        // words per record: 8, 16 or 32 (NL + 2 rounded up)
+  int32_t nl;                            // NL; a schema label >= NL has an empty group everywhere
+};
+
 // A CSR graph resident in HBM.  Offsets and ids are int32 (nv, ne < 2^31).
 struct DevGraph {
   const int32_t* __restrict__ row_ptr;   // [nv + 1]
   const int32_t* __restrict__ col;       // [ne], rows sorted ascending when sorted != 0
   const AliasRec* __restrict__ alias;    // [ne] after ALIAS preparation, or null
   const uint8_t* __restrict__ labels;    // [ne + 16] (padded for word loads), or null
+  LabelIndex lidx;
   int32_t nv;
   int32_t ne;
 };

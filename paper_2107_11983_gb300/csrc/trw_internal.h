@@ -33,6 +33,14 @@ cudaError_t launch_prepare_alias(int32_t nv, int64_t ne, const int32_t* row_ptr,
                                  const float* weights, AliasRec* alias, unsigned long long* q_scratch,
                                  int32_t* idx_scratch, int32_t* part_scratch, Ctrl* ctrl, cudaStream_t st);
 
+// MetaPath label index (LabelIndex): the largest label into *d_out (atomicMax;
+// zero it first), then the vertex and edge records for nl labels at stride
+// words per record; the second call synchronises st.
+cudaError_t launch_label_max(const uint8_t* labels, int64_t ne, unsigned int* d_out, cudaStream_t st);
+cudaError_t launch_prepare_labels(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                                  const uint8_t* labels, int32_t nl, int32_t stride, int32_t* vrec, int32_t* erec,
+                                  cudaStream_t st);
+
 // Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl,
                                int* d_unsorted, cudaStream_t st);

@@ -101,6 +101,13 @@ __device__ __forceinline__ int32_t label_select_serial(const uint8_t* __restrict
   return -1;
 }
 
+// Word k (0..7) of a 32-byte record held as two uint4 (selects, no local memory).
+__device__ __forceinline__ uint32_t word8(const uint4& a, const uint4& b, uint32_t k) {
+  const uint4& v = k < 4 ? a : b;
+  const uint32_t i = k & 3;
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
 // IsNeighbor(c, prev): lower-bound search of c in the sorted row of prev.
 __device__ __forceinline__ bool is_neighbor_serial(const int32_t* __restrict__ col, int32_t poff, int32_t pd,
                                                    int32_t c) {
@@ -133,8 +140,20 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
   if (W.att == 0) {
     if (!W.rowok) {
       if (CHECK && (uint32_t)W.cur >= (uint32_t)g.nv) return kBroken;
-      W.off = ldg(g.row_ptr + W.cur);
-      W.d = ldg(g.row_ptr + W.cur + 1) - W.off;
+      if (A == METAPATH && g.lidx.vrec) {
+        // Indexed MetaPath: (off, d) is the group of this step's label.
+        const uint32_t h = schema_label(sp, (uint32_t)W.s % sp.schema_len);
+        if (h < (uint32_t)g.lidx.nl) {
+          const int32_t* vr = g.lidx.vrec + (int64_t)W.cur * g.lidx.stride;
+          W.off = ldg(vr + 1 + h);
+          W.d = ldg(vr + 2 + h) - W.off;
+        } else {
+          W.off = W.d = 0;
+        }
+      } else {
+        W.off = ldg(g.row_ptr + W.cur);
+        W.d = ldg(g.row_ptr + W.cur + 1) - W.off;
+      }
     }
     if (CHECK && (W.off < 0 || W.d < 0 || (int64_t)W.off + W.d > (int64_t)g.ne)) return kBroken;
   }
@@ -158,6 +177,32 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     W.nxv = true;
     return kMoved;
   } else if (A == METAPATH) {
+    if (g.lidx.erec) {
+      // Indexed: the r-th entry of the label group is the r-th match; its
+      // record holds the next vertex and the bounds of its label groups.
+      const uint32_t h2 = schema_label(sp, (uint32_t)(W.s + 1) % sp.schema_len);
+      const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
+      int32_t lo, hi;
+      if (h2 >= (uint32_t)g.lidx.nl) {
+        next = ldg(g.lidx.erec + e * g.lidx.stride);
+        lo = hi = 0;
+      } else if (g.lidx.stride == 8) {
+        const uint4* rp = reinterpret_cast<const uint4*>(g.lidx.erec + e * 8);
+        const uint4 ra = __ldg(rp), rb = __ldg(rp + 1);
+        next = (int32_t)ra.x;
+        lo = (int32_t)word8(ra, rb, 1 + h2);
+        hi = (int32_t)word8(ra, rb, 2 + h2);
+      } else {
+        const int32_t* rp = g.lidx.erec + e * g.lidx.stride;
+        next = ldg(rp);
+        lo = ldg(rp + 1 + h2);
+        hi = ldg(rp + 2 + h2);
+      }
+      W.nxo = lo;
+      W.nxd = hi - lo;
+      W.nxv = true;
+      return kMoved;
+    }
     // Gather (0/1 weights by label) then ITS generation: the r-th match.
     const uint32_t h = schema_label(sp, (uint32_t)W.s % sp.schema_len);
     const uint32_t hrep = h * 0x01010101u;
