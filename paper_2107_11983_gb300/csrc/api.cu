@@ -415,6 +415,26 @@ LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
   return c;
 }
 
+LaunchCfg trw_launch_cfg_batch(const trw_graph* g, const WalkSpec* specs, int n) {
+  // The cooperative variant only when a request can hand work to its warp.
+  bool coop = false;
+  for (int r = 0; r < n; ++r) {
+    if (specs[r].algo == NODE2VEC && g->tuning.search_degree < 0x7fffffff) coop = true;
+    if (specs[r].algo == METAPATH && !g->lerec && g->tuning.coop_degree < 0x7fffffff) coop = true;
+  }
+  LaunchCfg c;
+  c.block_threads = g->tuning.block_threads;
+  const int occ = persistent_blocks_per_sm(MIXED, c.block_threads, coop);
+  int bps = g->tuning.blocks_per_sm;
+  if (bps <= 0 || bps > occ) bps = occ;
+  c.grid_blocks = g->num_sms * bps;
+  c.chunk = g->tuning.chunk;
+  c.coop_degree = g->tuning.coop_degree;
+  c.search_degree = g->tuning.search_degree;
+  c.batch_coop = coop;
+  return c;
+}
+
 static trw_status collect_status(trw_graph* g, cudaStream_t stream) {
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return trw_cuda_fail(e, "walk kernel");
@@ -647,7 +667,7 @@ extern "C" trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw
   for (int r = 0; r < n_requests; ++r)
     if (specs[r].nwalks > 0)
       CUDA_TRY(launch_validate_sources(specs[r].sources, n_sources[r], (int32_t)g->nv, g->ctrl, stream), "validate");
-  const LaunchCfg cfg = trw_launch_cfg(g, MIXED);
+  const LaunchCfg cfg = trw_launch_cfg_batch(g, specs.data(), n_requests);
   CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
   CUDA_TRY(launch_walk_batch(trw_dev_graph(g), reinterpret_cast<const WalkSpec*>(g->batch_specs),
                              reinterpret_cast<const int64_t*>(g->batch_specs + spec_bytes), n_requests, total, g->ctrl,

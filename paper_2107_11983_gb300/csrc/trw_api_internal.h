@@ -54,4 +54,5 @@ trw_status trw_grow(void** p, size_t* cap, size_t need);
 trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* p, int64_t n_sources, int32_t max_len,
                          uint64_t seed, trw::WalkSpec* sp);
 trw::LaunchCfg trw_launch_cfg(const trw_graph* g, int algo);
+trw::LaunchCfg trw_launch_cfg_batch(const trw_graph* g, const trw::WalkSpec* specs, int n);
 trw::DevGraph trw_dev_graph(const trw_graph* g);

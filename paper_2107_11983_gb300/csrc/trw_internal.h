@@ -14,6 +14,7 @@ struct LaunchCfg {
   int chunk = 32;            // walks per warp claim
   int coop_degree = 256;     // MetaPath label rows this long or longer: warp-cooperative Gather
   int search_degree = 0x7fffffff;  // Node2Vec rows of prev this long or longer: warp search
+  bool batch_coop = true;    // mixed batches: the variant with the warp-cooperative scan and search
 };
 
 // Occupancy-derived resident blocks per SM of the persistent kernel for algo

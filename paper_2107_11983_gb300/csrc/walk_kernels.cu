@@ -216,7 +216,9 @@ int persistent_blocks_per_sm(int algo, int block_threads, bool coop) {
     case METAPATH:
       return coop ? blocks_per_sm_of(walk_persistent<METAPATH, true>, block_threads)
                   : blocks_per_sm_of(walk_persistent<METAPATH, false>, block_threads);
-    default: return blocks_per_sm_of(walk_persistent<MIXED, true>, block_threads);
+    default:
+      return coop ? blocks_per_sm_of(walk_persistent<MIXED, true>, block_threads)
+                  : blocks_per_sm_of(walk_persistent<MIXED, false>, block_threads);
   }
 }
 
@@ -286,9 +288,13 @@ cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const 
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   WalkSpec dummy{};
-  walk_persistent<MIXED, true><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total,
-                                                                         ctrl, cfg.chunk,
-                                                                         Coop{cfg.coop_degree, cfg.search_degree});
+  const Coop coop{cfg.coop_degree, cfg.search_degree};
+  if (cfg.batch_coop)
+    walk_persistent<MIXED, true><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total,
+                                                                           ctrl, cfg.chunk, coop);
+  else
+    walk_persistent<MIXED, false><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total,
+                                                                            ctrl, cfg.chunk, coop);
   return cudaGetLastError();
 }
 
