@@ -188,7 +188,7 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
     src = synth.vertex_sources(g.nv)
     n = 2000
     done_moves, done_s, walks = 0, 0.0, 0
-    sectors, out_bytes = 0, 0
+    sectors, out_bytes, attempts, checks = 0, 0, 0, 0
     pos = 0
     while done_s < seconds and pos < src.shape[0]:
         m = min(n, src.shape[0] - pos)
@@ -200,6 +200,8 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
         done_moves += res.stats["moves"]
         sectors += res.stats["sectors"]
         out_bytes += res.stats["out_bytes"]
+        attempts += res.stats["attempts"]
+        checks += res.stats["checks"]
         done_s += dt
         walks += m
         pos += m
@@ -207,7 +209,11 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
     return {"value": done_moves / done_s, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {walks} of {src.shape[0]} walks ({done_moves} moves) of the workload, "
                       f"single-threaded oracle, {done_s:.1f}s walking after {prep:.1f}s of alias preparation",
-            "model_bytes_per_move": (32.0 * sectors + out_bytes) / max(1, done_moves)}
+            "model_bytes_per_move": (32.0 * sectors + out_bytes) / max(1, done_moves),
+            # Node2Vec with the neighbour hash: the row pair of cur, one col sector per
+            # attempt, one bucket sector per IsNeighbor that decides an attempt
+            "model_bytes_per_move_hashed": ROW_PAIR + (SECTOR * (attempts + checks) + out_bytes) / max(1, done_moves),
+            "attempts_per_move": attempts / max(1, done_moves), "checks_per_move": checks / max(1, done_moves)}
 
 
 def run_reference(args, wl):
@@ -250,7 +256,7 @@ def run_reference(args, wl):
 
 # ------------------------------------------------------------------ roofline
 
-def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s):
+def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False):
     """Roofline of the walk kernel: algorithmic bytes of one launch (the
     closed form per move where the layout fixes it, else the oracle's sector
     model measured on the CPU-baseline sample) over the kernel's event time,
@@ -259,7 +265,11 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s):
     peak, peak_kind = measured_peak_hbm()
     bpm = BYTES_PER_MOVE.get(wl["algo"])
     source = "closed form (32-byte sectors of the device layout)"
-    if bpm is None and cpu is not None:
+    if bpm is None and cpu is not None and hashed:
+        bpm = cpu["model_bytes_per_move_hashed"]
+        source = ("row pair + one 32-byte sector per attempt and per deciding IsNeighbor (neighbour hash), "
+                  "counts from the oracle on the CPU-baseline sample")
+    elif bpm is None and cpu is not None:
         bpm = cpu["model_bytes_per_move"]
         source = "oracle sector model on the CPU-baseline sample"
     if bpm is None:
@@ -304,9 +314,11 @@ def time_walk(trw, torch, G, flush, sp, algo, src, L, seed, kernel, reps=3, **kw
     return ms, moves
 
 
-def measure_per_algo(trw, torch, G, g, flush, sp):
+def measure_per_algo(trw, torch, G, g, flush, sp, G_paper=None):
     """Steps/s of every algorithm, persistent kernel vs the plain one-launch
-    baseline, on the workload's graph (labels drawn for MetaPath)."""
+    baseline, on the workload's graph (labels drawn for MetaPath).  With
+    G_paper (the same graph without label index and neighbour hash), Node2Vec
+    and MetaPath are also timed on the paper's binary search and label scan."""
     import synth as sy
 
     dev = flush.device
@@ -334,6 +346,12 @@ def measure_per_algo(trw, torch, G, g, flush, sp):
             ms, moves = time_walk(trw, torch, G, flush, sp, algo, src, L, 1, kern, **kw)
             row[kname] = {"steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3), "moves": moves}
         row["speedup"] = round(row["persistent"]["steps_per_s"] / row["plain"]["steps_per_s"], 3)
+        if G_paper is not None and algo in (trw.NODE2VEC, trw.METAPATH):
+            G_paper.autotune(algo, 10, **tune_kw)
+            ms, moves = time_walk(trw, torch, G_paper, flush, sp, algo, src, L, 1, trw.KERNEL_PERSISTENT, **kw)
+            row["paper_path"] = {"what": "binary search" if algo == trw.NODE2VEC else "label scan",
+                                 "steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3),
+                                 "speedup_prepared": round(row["persistent"]["steps_per_s"] * ms / 1000.0 / moves, 2)}
         row["walks"] = int(src.shape[0])
         row["max_len"] = L
         out[name] = row
@@ -503,6 +521,12 @@ def run_ours(args, wl):
         t = time.time()
         G.prepare()
         prep_ms = 1000 * (time.time() - t)
+    hash_ms = None
+    if algo == trw.NODE2VEC and not args.no_neighbor_hash:
+        torch.cuda.synchronize()
+        t = time.time()
+        G.prepare(trw.PREP_NEIGHBOR_HASH)
+        hash_ms = 1000 * (time.time() - t)
     kw = walk_kwargs(wl)
     L = wl["max_len"]
     t = time.time()
@@ -599,7 +623,15 @@ def run_ours(args, wl):
     serve = None
     gather = measure_gather_ceiling(trw, g) if rank == 0 else None
     if rank == 0 and not args.no_extras:
-        per_algo = measure_per_algo(trw, torch, G, g, flush, sp)
+        # every algorithm on this graph: with the label index and neighbour
+        # hash, and the paper's label scan and binary search beside them
+        G_paper = trw.Graph(g.row_ptr, g.col, None, g.labels)
+        if G.has_labels and not args.no_label_index:
+            G.prepare(trw.PREP_LABEL_INDEX)
+        if not args.no_neighbor_hash:
+            G.prepare(trw.PREP_NEIGHBOR_HASH)
+        per_algo = measure_per_algo(trw, torch, G, g, flush, sp, G_paper)
+        del G_paper
         if G.has_weights:
             serve = measure_serve(trw, torch, G, g, n_requests=args.serve_requests)
 
@@ -608,7 +640,7 @@ def run_ours(args, wl):
             dist.destroy_process_group()
         return
     cpu = cpu_baseline(g, wl) if ws == 1 and not args.no_cpu_baseline else None
-    roof = roofline(wl, moves, n, kms, cpu, gather, value / ws)
+    roof = roofline(wl, moves, n, kms, cpu, gather, value / ws, hashed=hash_ms is not None)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * dev_s / args.steps, 4), "higher_is_better": True,
@@ -617,12 +649,15 @@ def run_ours(args, wl):
                    "walks_per_gpu": n, "max_len": L, "moves_per_gpu_step": moves,
                    "parallelism": f"walk shards x{ws}, graph replicated",
                    "l2": "256 MiB buffer written between timed steps (outside the events)",
-                   "tuning": G.tuning()},
+                   "tuning": G.tuning(),
+                   **({"is_neighbor": "binary search" if hash_ms is None else
+                       "neighbour hash (bit-identical to the binary search)"} if algo == trw.NODE2VEC else {})},
         "kernel_ms_per_step": round(kms, 4),
         "wall_s": round(wall, 3),
         "plain_launch": {"value": round(plain_value, 1), "unit": UNIT, "ms": round(statistics.median(plain_ms), 4),
                          "speedup_persistent": round(value / ws / plain_value, 3)},
         "preprocess": {"graph_load_s": round(load_s, 3), "alias_prepare_ms": None if prep_ms is None else round(prep_ms, 2),
+                       "neighbor_hash_ms": None if hash_ms is None else round(hash_ms, 2),
                        "autotune_s": round(tune_s, 2)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(n * 4),
                 "d2h_bytes_per_step": int(n * (L + 1) * 4 + n * 4), "ms": round(1000 * e2e_s, 3)},
@@ -893,6 +928,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-algorithm lines and the gather ceiling")
     ap.add_argument("--scale", type=int, default=0, help="override the R-MAT scale (smaller profiling cases)")
+    ap.add_argument("--no-neighbor-hash", action="store_true",
+                    help="Node2Vec: binary search of the previous vertex's row instead of the neighbour hash")
     ap.add_argument("--no-label-index", action="store_true",
                     help="mixed workload: MetaPath scans labels at every step instead of the label index")
     ap.add_argument("--no-autotune", action="store_true",

@@ -122,6 +122,8 @@ void trw_graph_free(trw_graph* g);
 #define TRW_PREP_ALIAS 1u        /* build the ALIAS tables for TRW_DEEPWALK_WEIGHTED */
 #define TRW_PREP_LABEL_INDEX 2u  /* build the MetaPath label index (labelled graphs) */
 #define TRW_LABEL_INDEX_MAX_LABELS 30
+#define TRW_PREP_NEIGHBOR_HASH 4u /* build the neighbour hash for Node2Vec's IsNeighbor */
+#define TRW_NEIGHBOR_HASH_MIN_DEGREE 8
 
 /*
  * Preprocessing for static walks (Algorithm 3): for every vertex v, apply the
@@ -142,6 +144,15 @@ void trw_graph_free(trw_graph* g);
  * [0, TRW_LABEL_INDEX_MAX_LABELS); the records take (NL + 2) int32 rounded up
  * to 8, 16 or 32 words per edge and per vertex (NL = largest label + 1).
  * Preparing an index that exists already does nothing.
+ *
+ * TRW_PREP_NEIGHBOR_HASH (not in the paper, whose Node2Vec IsNeighbor is a
+ * binary search in the sorted row of the previous vertex, Section 4): the
+ * edges of every row of at least TRW_NEIGHBOR_HASH_MIN_DEGREE entries go
+ * into an open-addressing hash table of 32-byte buckets (16 bytes of table
+ * per edge at most, load <= 1/2), and IsNeighbor(c, prev) for such a row
+ * reads about one bucket instead of log2(d_prev) row entries.  Membership is
+ * exact, so every walk is identical with and without it.  Preparing a hash
+ * that exists already does nothing.
  *
  * Runs on the device; synchronous.  Errors: TRW_ERR_INVALID (no weights, or
  * no labels, loaded for the requested table; a label too large for the
@@ -292,6 +303,15 @@ trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int3
  * (NULL graph or stride), TRW_ERR_CUDA.
  */
 trw_status trw_debug_label_index(const trw_graph* g, int32_t* stride, int32_t* vrec, int32_t* erec);
+
+/*
+ * IsNeighbor(v[i], u[i]) for n pairs as the walk kernels evaluate it (the
+ * neighbour hash where prepared, else the binary search of u's sorted row):
+ * out[i] = 1 when v[i] is in N(u[i]).  Host arrays; every u[i] in [0, nv).
+ * Errors: TRW_ERR_INVALID (NULL argument, n < 0, a u out of range),
+ * TRW_ERR_OOM, TRW_ERR_CUDA.
+ */
+trw_status trw_debug_is_neighbor(const trw_graph* g, const int32_t* u, const int32_t* v, int64_t n, uint8_t* out);
 
 /* Philox4x32-10 blocks computed on the device: out[4*i..4*i+3] for counter
  * ctr[4*i..4*i+3] and key (key0, key1).  Host buffers.  For tests. */

@@ -54,7 +54,7 @@ class _Params(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("moves", ctypes.c_int64), ("attempts", ctypes.c_int64), ("stop_len", ctypes.c_int64),
                 ("stop_coin", ctypes.c_int64), ("stop_dead", ctypes.c_int64), ("stop_schema", ctypes.c_int64),
-                ("sectors", ctypes.c_int64), ("out_bytes", ctypes.c_int64)]
+                ("sectors", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("checks", ctypes.c_int64)]
 
 
 def _bind(path: str):

@@ -210,6 +210,8 @@ typedef struct {
   int64_t stop_len, stop_coin, stop_dead, stop_schema;
   int64_t sectors;        /* distinct 32-byte sectors read, summed over steps (layout model) */
   int64_t out_bytes;      /* bytes of path output written */
+  int64_t checks;         /* Node2Vec: IsNeighbor results that decided an attempt (the dart fell
+                             between the neighbour and far thresholds) */
 } orc_stats;
 
 /* Sector model of the device layout, used only for the roofline: 4-byte
@@ -354,9 +356,13 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
             T = 4294967296ULL; /* Weight = MaxWeight on the first step */
           } else {
             const int32_t u = path[s - 1];
-            if (c == u) T = T_ret;
-            else if (is_neighbor(g, c, u, sec)) T = T_nb;
-            else T = T_far;
+            if (c == u) {
+              T = T_ret;
+            } else {
+              const uint64_t lo = T_nb < T_far ? T_nb : T_far, hi = T_nb < T_far ? T_far : T_nb;
+              if (st && (uint64_t)B[2] >= lo && (uint64_t)B[2] < hi) st->checks++;
+              T = is_neighbor(g, c, u, sec) ? T_nb : T_far;
+            }
           }
           if ((uint64_t)B[2] < T) { next = c; accepted = 1; break; }
         }

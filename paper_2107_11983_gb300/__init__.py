@@ -26,6 +26,7 @@ OUT_PATHS, OUT_ENDPOINTS = 0, 1
 PREP_ALIAS = 1
 PREP_LABEL_INDEX = 2
 LABEL_INDEX_MAX_LABELS = 30
+PREP_NEIGHBOR_HASH = 4
 MAX_SCHEMA = 16
 MAX_BATCH = 64
 
@@ -96,6 +97,7 @@ _SIGS = {
     "trw_graph_device_bytes": (ctypes.c_int64, [_VP]),
     "trw_debug_alias": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "trw_debug_label_index": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "trw_debug_is_neighbor": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP]),
     "trw_debug_philox": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, _VP]),
     "trw_serve_config_default": (None, [_VP]),
     "trw_serve_create": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -252,8 +254,8 @@ class Graph:
             pass
 
     def prepare(self, what: int = PREP_ALIAS):
-        """trw_prepare: PREP_ALIAS (weighted DeepWalk tables) and/or
-        PREP_LABEL_INDEX (MetaPath label index)."""
+        """trw_prepare: PREP_ALIAS (weighted DeepWalk tables), PREP_LABEL_INDEX
+        (MetaPath label index) and/or PREP_NEIGHBOR_HASH (Node2Vec IsNeighbor)."""
         _check(load_library().trw_prepare(self._h, what), "trw_prepare")
 
     def device_bytes(self) -> int:
@@ -384,6 +386,15 @@ class Graph:
         _check(lib.trw_debug_label_index(self._h, ctypes.byref(st), v.ctypes.data, e.ctypes.data),
                "trw_debug_label_index")
         return st.value, v, e
+
+    def debug_is_neighbor(self, u, v) -> np.ndarray:
+        """IsNeighbor(v[i], u[i]) as the walk kernels evaluate it (bool array)."""
+        u = np.ascontiguousarray(u, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.int32)
+        out = np.empty(u.shape[0], dtype=np.uint8)
+        _check(load_library().trw_debug_is_neighbor(self._h, u.ctypes.data, v.ctypes.data, u.shape[0],
+                                                    out.ctypes.data), "trw_debug_is_neighbor")
+        return out.astype(bool)
 
 
 def gather_ceiling(table_bytes: int, record_bytes: int = 16, hops: int = 80, chains: int = 1) -> dict:

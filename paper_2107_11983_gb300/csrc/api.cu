@@ -103,6 +103,7 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->alias);
   cudaFree(g->lvrec);
   cudaFree(g->lerec);
+  cudaFree(g->nh_slots);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);
@@ -244,6 +245,10 @@ DevGraph trw_dev_graph(const trw_graph* g) {
   d.lidx.erec = g->lerec;
   d.lidx.stride = g->lstride;
   d.lidx.nl = g->lnl;
+  d.nh.slots = g->nh_slots;
+  d.nh.mask = g->nh_mask;
+  d.nh.max_probe = g->nh_max_probe;
+  d.nh.min_degree = TRW_NEIGHBOR_HASH_MIN_DEGREE;
   d.nv = (int32_t)g->nv;
   d.ne = (int32_t)g->ne;
   return d;
@@ -324,9 +329,29 @@ static trw_status prepare_label_index(trw_graph* g) {
   return TRW_OK;
 }
 
+static trw_status prepare_neighbor_hash(trw_graph* g) {
+  if (g->nh_slots) return TRW_OK;
+  unsigned long long* slots = nullptr;
+  unsigned long long mask = 0;
+  int32_t probe = 0;
+  size_t bytes = 0;
+  cudaError_t e = launch_neighbor_hash((int32_t)g->nv, g->ne, g->row_ptr, g->col, TRW_NEIGHBOR_HASH_MIN_DEGREE, &slots,
+                                       &mask, &probe, &bytes, g->stream);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return trw_fail(TRW_ERR_OOM, "out of device memory for the neighbour hash");
+  }
+  if (e != cudaSuccess) return trw_cuda_fail(e, "prepare neighbour hash");
+  g->nh_slots = slots;
+  g->nh_mask = mask;
+  g->nh_max_probe = probe;
+  g->device_bytes += (int64_t)bytes;
+  return TRW_OK;
+}
+
 extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
-  if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX))
+  if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX | TRW_PREP_NEIGHBOR_HASH))
     return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
   std::lock_guard<std::mutex> lk(g->mu);
   if ((what & TRW_PREP_ALIAS) && !g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
@@ -335,7 +360,11 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
     trw_status st = prepare_alias(g);
     if (st != TRW_OK) return st;
   }
-  if (what & TRW_PREP_LABEL_INDEX) return prepare_label_index(g);
+  if (what & TRW_PREP_LABEL_INDEX) {
+    trw_status st = prepare_label_index(g);
+    if (st != TRW_OK) return st;
+  }
+  if (what & TRW_PREP_NEIGHBOR_HASH) return prepare_neighbor_hash(g);
   return TRW_OK;
 }
 
@@ -404,7 +433,7 @@ LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
   c.block_threads = g->tuning.block_threads;
   int bps = g->tuning.blocks_per_sm;
   const bool coop = algo == MIXED || (algo == METAPATH && !g->lerec && g->tuning.coop_degree < 0x7fffffff) ||
-                    (algo == NODE2VEC && g->tuning.search_degree < 0x7fffffff);
+                    (algo == NODE2VEC && !g->nh_slots && g->tuning.search_degree < 0x7fffffff);
   const int occ = persistent_blocks_per_sm(algo, c.block_threads, coop);
   if (bps <= 0 || bps > occ) bps = occ;
   c.grid_blocks = g->num_sms * bps;
@@ -412,6 +441,7 @@ LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
   c.coop_degree = g->tuning.coop_degree;
   c.search_degree = g->tuning.search_degree;
   if (algo == METAPATH && g->lerec) c.coop_degree = 0x7fffffff;  // indexed: no label scans to share
+  if (g->nh_slots) c.search_degree = 0x7fffffff;                  // hashed: no row searches to share
   return c;
 }
 
@@ -419,7 +449,7 @@ LaunchCfg trw_launch_cfg_batch(const trw_graph* g, const WalkSpec* specs, int n)
   // The cooperative variant only when a request can hand work to its warp.
   bool coop = false;
   for (int r = 0; r < n; ++r) {
-    if (specs[r].algo == NODE2VEC && g->tuning.search_degree < 0x7fffffff) coop = true;
+    if (specs[r].algo == NODE2VEC && !g->nh_slots && g->tuning.search_degree < 0x7fffffff) coop = true;
     if (specs[r].algo == METAPATH && !g->lerec && g->tuning.coop_degree < 0x7fffffff) coop = true;
   }
   LaunchCfg c;
@@ -430,7 +460,7 @@ LaunchCfg trw_launch_cfg_batch(const trw_graph* g, const WalkSpec* specs, int n)
   c.grid_blocks = g->num_sms * bps;
   c.chunk = g->tuning.chunk;
   c.coop_degree = g->tuning.coop_degree;
-  c.search_degree = g->tuning.search_degree;
+  c.search_degree = g->nh_slots ? 0x7fffffff : g->tuning.search_degree;
   c.batch_coop = coop;
   return c;
 }
@@ -733,6 +763,33 @@ extern "C" trw_status trw_debug_label_index(const trw_graph* g, int32_t* stride,
     CUDA_TRY(cudaMemcpy(vrec, g->lvrec, sizeof(int32_t) * sw * (size_t)g->nv, cudaMemcpyDeviceToHost), "copy index");
   if (g->ne > 0)
     CUDA_TRY(cudaMemcpy(erec, g->lerec, sizeof(int32_t) * sw * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy index");
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_debug_is_neighbor(const trw_graph* g, const int32_t* u, const int32_t* v, int64_t n,
+                                            uint8_t* out) {
+  if (!g || n < 0 || (n > 0 && (!u || !v || !out))) return trw_fail(TRW_ERR_INVALID, "bad arguments");
+  for (int64_t i = 0; i < n; ++i)
+    if (u[i] < 0 || u[i] >= g->nv) return trw_fail(TRW_ERR_INVALID, "vertex %d out of range", u[i]);
+  if (n == 0) return TRW_OK;
+  int32_t *du = nullptr, *dv = nullptr;
+  uint8_t* dout = nullptr;
+  trw_status st = alloc_dev((void**)&du, sizeof(int32_t) * (size_t)n, "pairs");
+  if (st == TRW_OK) st = alloc_dev((void**)&dv, sizeof(int32_t) * (size_t)n, "pairs");
+  if (st == TRW_OK) st = alloc_dev((void**)&dout, (size_t)n, "pairs");
+  cudaError_t e = cudaSuccess;
+  if (st == TRW_OK) {
+    e = cudaMemcpy(du, u, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dv, v, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_debug_is_neighbor(trw_dev_graph(g), du, dv, n, dout, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)n, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(du);
+  cudaFree(dv);
+  cudaFree(dout);
+  if (st != TRW_OK) return st;
+  if (e != cudaSuccess) return trw_cuda_fail(e, "is_neighbor");
   return TRW_OK;
 }
 

@@ -54,7 +54,7 @@ extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params
     const int chunk_c[] = {8, 32, 128};
     std::vector<int> deg_c;
     if (algo == TRW_METAPATH && !g->lerec) deg_c = {64, 256, 1024, kOff};
-    else if (algo == TRW_NODE2VEC) deg_c = {64, 1024, kOff};
+    else if (algo == TRW_NODE2VEC && !g->nh_slots) deg_c = {64, 1024, kOff};
     else deg_c = {kOff};
     for (int threads : threads_c) {
       for (int cd : deg_c) {

@@ -362,6 +362,74 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_alias_kernel(
   }
 }
 
+// Edges in rows of at least min_degree entries (count[0]).
+__global__ void count_hash_edges(int32_t nv, const int32_t* __restrict__ row_ptr, int32_t min_degree,
+                                 unsigned long long* count) {
+  unsigned long long c = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d >= min_degree) c += (unsigned long long)d;
+  }
+  c = warp_sum64(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// Inserts key (u, v): the first empty slot from the key's bucket on, bucket by
+// bucket; probe[0] keeps the longest sequence (in buckets), probe[1] flags a
+// sequence that visited every bucket.
+__device__ __forceinline__ void hash_insert(unsigned long long* slots, unsigned long long mask, int32_t u, int32_t v,
+                                            unsigned int* probe) {
+  const unsigned long long key = edge_key(u, v);
+  unsigned long long b = mix64(key) & mask;
+  for (unsigned long long n = 1;; ++n) {
+    for (int k = 0; k < 4; ++k) {
+      const unsigned long long old = atomicCAS(slots + (b << 2) + k, kHashEmpty, key);
+      if (old == kHashEmpty || old == key) {
+        atomicMax(probe, (unsigned int)n);
+        return;
+      }
+    }
+    if (n > mask) {
+      atomicExch(probe + 1, 1u);
+      return;
+    }
+    b = (b + 1) & mask;
+  }
+}
+
+// Same schedule as the alias preparation: rows of kBigRow edges or more by
+// whole blocks, largest first, then the other rows one warp each.
+__global__ void __launch_bounds__(kPrepThreads) hash_insert_kernel(
+    int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int32_t min_degree,
+    const int32_t* __restrict__ big, int32_t nbig, unsigned int* counters, unsigned long long* slots,
+    unsigned long long mask, unsigned int* probe) {
+  __shared__ int32_t s_r;
+  for (;;) {
+    if (threadIdx.x == 0) s_r = (int32_t)atomicAdd(&counters[0], 1u);
+    __syncthreads();
+    const int32_t r = s_r;
+    __syncthreads();
+    if (r >= nbig) break;
+    const int32_t v = big[r];
+    const int32_t off = row_ptr[v], d = row_ptr[v + 1] - off;
+    if (d < min_degree) continue;
+    for (int32_t j = threadIdx.x; j < d; j += kPrepThreads) hash_insert(slots, mask, v, col[off + j], probe);
+  }
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned int base = 0;
+    if (lane == 0) base = atomicAdd(&counters[1], 32u);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= (unsigned)nv) break;
+    const int32_t end = min((int32_t)base + 32, nv);
+    for (int32_t v = (int32_t)base; v < end; ++v) {
+      const int32_t off = row_ptr[v], d = row_ptr[v + 1] - off;
+      if (d < min_degree || d >= kBigRow) continue;
+      for (int32_t j = lane; j < d; j += 32) hash_insert(slots, mask, v, col[off + j], probe);
+    }
+  }
+}
+
 // Rows of kBigRow edges or more, as (degree << 32 | vertex) keys.
 __global__ void collect_big_rows(int32_t nv, const int32_t* __restrict__ row_ptr, unsigned long long* keys,
                                  unsigned int* count) {
@@ -474,57 +542,126 @@ __global__ void check_graph_kernel(int32_t nv, const int32_t* __restrict__ row_p
   }
 }
 
+// Rows of kBigRow edges or more, collected on the device and sorted by
+// degree (largest first) on the host, so that the longest rows start first;
+// plus zeroed claim counters ([0] big rows, [1] other rows).
+struct BigRows {
+  int32_t* list = nullptr;
+  unsigned int n = 0;
+  unsigned int* counters = nullptr;
+  unsigned long long* keys = nullptr;
+  ~BigRows() {
+    cudaFree(list);
+    cudaFree(counters);
+    cudaFree(keys);
+  }
+};
+
+cudaError_t collect_big(int32_t nv, int64_t ne, const int32_t* row_ptr, cudaStream_t st, BigRows& br) {
+  const size_t max_big = (size_t)(ne / kBigRow) + 1;
+  cudaError_t e = cudaMalloc(&br.keys, sizeof(unsigned long long) * max_big);
+  if (e == cudaSuccess) e = cudaMalloc(&br.list, sizeof(int32_t) * max_big);
+  if (e == cudaSuccess) e = cudaMalloc(&br.counters, sizeof(unsigned int) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(br.counters, 0, sizeof(unsigned int) * 4, st);
+  int64_t blocks = ((int64_t)nv + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  if (e == cudaSuccess) {
+    collect_big_rows<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, br.keys, br.counters + 2);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&br.n, br.counters + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && br.n > max_big) e = cudaErrorUnknown;  // cannot happen: each big row holds kBigRow edges
+  if (e == cudaSuccess && br.n > 0) {
+    std::vector<unsigned long long> hk(br.n);
+    std::vector<int32_t> hb(br.n);
+    e = cudaMemcpy(hk.data(), br.keys, sizeof(unsigned long long) * br.n, cudaMemcpyDeviceToHost);
+    std::sort(hk.begin(), hk.end(), [](unsigned long long a, unsigned long long b) { return a > b; });
+    for (unsigned int k = 0; k < br.n; ++k) hb[k] = (int32_t)(hk[k] & 0xffffffffu);
+    if (e == cudaSuccess) e = cudaMemcpy(br.list, hb.data(), sizeof(int32_t) * br.n, cudaMemcpyHostToDevice);
+  }
+  return e;
+}
+
+template <typename K>
+cudaError_t persistent_grid(K kernel, int threads, unsigned* grid) {
+  int dev = 0, sms = 1, occ = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
+  *grid = (unsigned)(sms * (occ > 0 ? occ : 1));
+  return e;
+}
+
 }  // namespace
 
 cudaError_t launch_prepare_alias(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
                                  const float* weights, AliasRec* alias, unsigned long long* q_scratch,
                                  int32_t* idx_scratch, int32_t* part_scratch, Ctrl* ctrl, cudaStream_t st) {
   if (nv <= 0) return cudaSuccess;
-  // Rows of kBigRow edges or more: collected on the device, sorted by degree
-  // (largest first) on the host so that the longest pairings start first.
-  const size_t max_big = (size_t)(ne / kBigRow) + 1;
-  unsigned long long* keys = nullptr;
-  int32_t* big = nullptr;
-  unsigned int* counters = nullptr;  // [0] big-row claims, [1] row claims, [2] big-row count
-  cudaError_t e = cudaMalloc(&keys, sizeof(unsigned long long) * max_big);
-  if (e == cudaSuccess) e = cudaMalloc(&big, sizeof(int32_t) * max_big);
-  if (e == cudaSuccess) e = cudaMalloc(&counters, sizeof(unsigned int) * 4);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * 4, st);
-  int64_t blocks = ((int64_t)nv + 255) / 256;
-  if (blocks > 65535) blocks = 65535;
+  BigRows br;
+  cudaError_t e = collect_big(nv, ne, row_ptr, st, br);
+  unsigned grid = 1;
+  if (e == cudaSuccess) e = persistent_grid(prepare_alias_kernel, kPrepThreads, &grid);
   if (e == cudaSuccess) {
-    collect_big_rows<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, keys, counters + 2);
+    const Scratch sc{q_scratch, idx_scratch, part_scratch};
+    prepare_alias_kernel<<<grid, kPrepThreads, 0, st>>>(nv, row_ptr, col, weights, alias, sc, br.list,
+                                                        (int32_t)br.n, br.counters, ctrl);
     e = cudaGetLastError();
   }
-  unsigned int nbig = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&nbig, counters + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && nbig > max_big) e = cudaErrorUnknown;  // cannot happen: each big row holds kBigRow edges
-  std::vector<unsigned long long> hk(nbig);
-  std::vector<int32_t> hb(nbig);
-  if (e == cudaSuccess && nbig > 0) {
-    e = cudaMemcpy(hk.data(), keys, sizeof(unsigned long long) * nbig, cudaMemcpyDeviceToHost);
-    std::sort(hk.begin(), hk.end(), [](unsigned long long a, unsigned long long b) { return a > b; });
-    for (unsigned int k = 0; k < nbig; ++k) hb[k] = (int32_t)(hk[k] & 0xffffffffu);
-    if (e == cudaSuccess) e = cudaMemcpy(big, hb.data(), sizeof(int32_t) * nbig, cudaMemcpyHostToDevice);
-  }
-  if (e == cudaSuccess) {
-    int dev = 0, sms = 1, occ = 1;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, prepare_alias_kernel, kPrepThreads, 0);
-    if (e == cudaSuccess) {
-      const Scratch sc{q_scratch, idx_scratch, part_scratch};
-      prepare_alias_kernel<<<(unsigned)(sms * (occ > 0 ? occ : 1)), kPrepThreads, 0, st>>>(
-          nv, row_ptr, col, weights, alias, sc, big, (int32_t)nbig, counters, ctrl);
-      e = cudaGetLastError();
-    }
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(keys);
-  cudaFree(big);
-  cudaFree(counters);
   return e;
+}
+
+cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                                 int32_t min_degree, unsigned long long** slots_out, unsigned long long* mask_out,
+                                 int32_t* max_probe_out, size_t* bytes_out, cudaStream_t st) {
+  *slots_out = nullptr;
+  *mask_out = 0;
+  *max_probe_out = 0;
+  *bytes_out = 0;
+  unsigned long long* d_count = nullptr;
+  cudaError_t e = cudaMalloc(&d_count, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 2, st);
+  int64_t blocks = ((int64_t)nv + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  if (e == cudaSuccess && nv > 0) {
+    count_hash_edges<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, min_degree, d_count);
+    e = cudaGetLastError();
+  }
+  unsigned long long count = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // buckets: a power of two with at least twice the keys' slots (load <= 1/2)
+  unsigned long long nb = 1;
+  while (nb * 4 < 2 * count) nb <<= 1;
+  unsigned long long* slots = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&slots, sizeof(unsigned long long) * 4 * nb);
+  if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0xff, sizeof(unsigned long long) * 4 * nb, st);
+  BigRows br;
+  if (e == cudaSuccess && nv > 0) e = collect_big(nv, ne, row_ptr, st, br);
+  unsigned grid = 1;
+  if (e == cudaSuccess) e = persistent_grid(hash_insert_kernel, kPrepThreads, &grid);
+  if (e == cudaSuccess && nv > 0 && count > 0) {
+    unsigned int* probe = reinterpret_cast<unsigned int*>(d_count + 1);
+    hash_insert_kernel<<<grid, kPrepThreads, 0, st>>>(nv, row_ptr, col, min_degree, br.list, (int32_t)br.n,
+                                                      br.counters, slots, nb - 1, probe);
+    e = cudaGetLastError();
+  }
+  unsigned int probes[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(probes, d_count + 1, sizeof(probes), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_count);
+  if (e == cudaSuccess && probes[1] != 0) e = cudaErrorUnknown;  // a probe ran past every bucket: cannot happen
+  if (e != cudaSuccess) {
+    cudaFree(slots);
+    return e;
+  }
+  *slots_out = slots;
+  *mask_out = nb - 1;
+  *max_probe_out = (int32_t)(probes[0] > 0 ? probes[0] : 1);
+  *bytes_out = sizeof(unsigned long long) * 4 * nb;
+  return cudaSuccess;
 }
 
 cudaError_t launch_label_max(const uint8_t* labels, int64_t ne, unsigned int* d_out, cudaStream_t st) {

@@ -45,6 +45,35 @@ struct LabelIndex {
   int32_t nl;                            // NL; a schema label >= NL has an empty group everywhere
 };
 
+// Neighbour hash (an optional preparation; walks are identical with and
+// without it): the edges (u, v) of every row u of at least min_degree entries
+// as 64-bit keys u << 32 | v in an open-addressing table of 4-key buckets
+// (one 32-byte sector), probed bucket by bucket from mix64(key) & mask.
+// Keys fill each bucket from its first slot, so a lookup that meets an empty
+// slot is done; max_probe bounds the buckets any lookup visits.
+struct NeighborHash {
+  const unsigned long long* __restrict__ slots;  // [(mask + 1) * 4], or null when not prepared
+  unsigned long long mask;                       // buckets - 1 (a power of two minus one)
+  int32_t max_probe;                             // longest probe sequence of the build, in buckets
+  int32_t min_degree;                            // rows shorter than this are searched in place
+};
+
+constexpr unsigned long long kHashEmpty = 0xffffffffffffffffull;
+
+// MurmurHash3's 64-bit finaliser (Appleby): a bijective mix of the key bits.
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ unsigned long long edge_key(int32_t u, int32_t v) {
+  return ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
+}
+
 // A CSR graph resident in HBM.  Offsets and ids are int32 (nv, ne < 2^31).
 struct DevGraph {
   const int32_t* __restrict__ row_ptr;   // [nv + 1]
@@ -52,6 +81,7 @@ struct DevGraph {
   const AliasRec* __restrict__ alias;    // [ne] after ALIAS preparation, or null
   const uint8_t* __restrict__ labels;    // [ne + 16] (padded for word loads), or null
   LabelIndex lidx;
+  NeighborHash nh;
   int32_t nv;
   int32_t ne;
 };

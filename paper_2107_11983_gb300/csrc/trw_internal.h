@@ -42,10 +42,19 @@ cudaError_t launch_prepare_labels(int32_t nv, int64_t ne, const int32_t* row_ptr
                                   const uint8_t* labels, int32_t nl, int32_t stride, int32_t* vrec, int32_t* erec,
                                   cudaStream_t st);
 
+// Neighbour hash (NeighborHash) of the rows of at least min_degree entries:
+// allocates the table (*slots_out, *bytes_out bytes; the caller frees it) and
+// reports its mask and longest probe sequence; synchronises st.
+cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                                 int32_t min_degree, unsigned long long** slots_out, unsigned long long* mask_out,
+                                 int32_t* max_probe_out, size_t* bytes_out, cudaStream_t st);
+
 // Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl,
                                int* d_unsorted, cudaStream_t st);
 
+cudaError_t launch_debug_is_neighbor(const DevGraph& g, const int32_t* u, const int32_t* v, int64_t n, uint8_t* out,
+                                     cudaStream_t st);
 cudaError_t launch_debug_philox(const uint32_t* d_ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* d_out,
                                 cudaStream_t st);
 

@@ -177,6 +177,15 @@ __global__ void validate_sources(const int32_t* __restrict__ src, int64_t n, int
   }
 }
 
+__global__ void debug_is_neighbor(DevGraph g, const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t n,
+                                  uint8_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = u[i];
+    const int32_t off = g.row_ptr[a];
+    out[i] = step::is_neighbor(g, a, off, g.row_ptr[a + 1] - off, v[i]) ? 1 : 0;
+  }
+}
+
 __global__ void debug_philox(const uint4* __restrict__ ctr, int64_t n, uint32_t k0, uint32_t k1,
                              uint4* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,6 +304,15 @@ cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const 
   else
     walk_persistent<MIXED, false><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total,
                                                                             ctrl, cfg.chunk, coop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_is_neighbor(const DevGraph& g, const int32_t* u, const int32_t* v, int64_t n, uint8_t* out,
+                                     cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  debug_is_neighbor<<<(unsigned)blocks, 256, 0, st>>>(g, u, v, n, out);
   return cudaGetLastError();
 }
 

@@ -124,6 +124,26 @@ __device__ __forceinline__ bool is_neighbor_serial(const int32_t* __restrict__ c
   return lo < pd && ldg(col + poff + lo) == c;
 }
 
+// IsNeighbor(c, u) by the neighbour hash: one bucket (one sector) per probe.
+__device__ __forceinline__ bool is_neighbor_hashed(const NeighborHash& h, int32_t u, int32_t c) {
+  const unsigned long long key = edge_key(u, c);
+  unsigned long long b = mix64(key) & h.mask;
+  for (int32_t probe = 0; probe < h.max_probe; ++probe) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(h.slots + (b << 2));
+    const ulonglong2 s0 = __ldg(p), s1 = __ldg(p + 1);
+    if (s0.x == key || s0.y == key || s1.x == key || s1.y == key) return true;
+    if (s0.x == kHashEmpty || s0.y == kHashEmpty || s1.x == kHashEmpty || s1.y == kHashEmpty) return false;
+    b = (b + 1) & h.mask;
+  }
+  return false;
+}
+
+// IsNeighbor(c, prev): the hash for rows it holds, else the row's binary search.
+__device__ __forceinline__ bool is_neighbor(const DevGraph& g, int32_t prev, int32_t poff, int32_t pd, int32_t c) {
+  if (g.nh.slots && pd >= g.nh.min_degree) return is_neighbor_hashed(g.nh, prev, c);
+  return is_neighbor_serial(g.col, poff, pd, c);
+}
+
 // One unit of work for one walker: a full step, or one rejection trial of a
 // Node2Vec step.  Rows at least coop long are not scanned or searched by the
 // lane alone: the step returns kDefer with the work in p, the warp resolves it
@@ -227,13 +247,13 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     else if (c == W.prev) accept = (uint64_t)B.z < sp.T_ret;
     else if ((uint64_t)B.z < sp.T_lo) accept = true;
     else if ((uint64_t)B.z >= sp.T_hi) accept = false;
-    else if (W.pd >= coop.search) {
+    else if (W.pd >= coop.search && !g.nh.slots) {
       p.kind = 2;
       p.c = c;
       p.y = B.z;
       return kDefer;
     } else {
-      accept = (uint64_t)B.z < (is_neighbor_serial(g.col, W.poff, W.pd, c) ? sp.T_nb : sp.T_far);
+      accept = (uint64_t)B.z < (is_neighbor(g, W.prev, W.poff, W.pd, c) ? sp.T_nb : sp.T_far);
     }
     if (accept) {
       next = c;

@@ -25,7 +25,7 @@ MUTANTS = [
      "const uint64_t T_stop = orc_threshold(1.0 - p->ppr_stop);"),
     ("metapath: schema index off by one", "p->schema[s % p->schema_len]", "p->schema[(s + 1) % p->schema_len]"),
     ("metapath: CDF search takes <=", "if (x < cdf[mid]) hi = mid;", "if (x <= cdf[mid]) hi = mid;"),
-    ("node2vec: return edge gets the far weight", "if (c == u) T = T_ret;", "if (c == u) T = T_far;"),
+    ("node2vec: return edge gets the far weight", "T = T_ret;", "T = T_far;"),
     ("node2vec: IsNeighbor direction reversed", "is_neighbor(g, c, u, sec)", "is_neighbor(g, u, c, sec)"),
     ("node2vec: prev taken as cur", "const int32_t u = path[s - 1];", "const int32_t u = path[s];"),
     ("node2vec: p* ignores 1/a", "pstar = w_ret > w_nb ? w_ret : w_nb;", "pstar = w_nb;"),
