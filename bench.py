@@ -30,15 +30,34 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOADS = {
-    "c1": dict(name="deepwalk-rmat-s14", scale=14, algo="deepwalk", max_len=80, sources="vertices", seed=1),
+    "c1": dict(name="deepwalk-rmat-s14", scale=14, algo="deepwalk", max_len=80, sources="vertices", seed=1,
+               tables=("row_records",)),
     "c2": dict(name="deepwalk-weighted-alias-rmat-s22", scale=22, algo="deepwalk_weighted", max_len=80,
-               sources="vertices", seed=1),
+               sources="vertices", seed=1, tables=()),
     "c3": dict(name="node2vec-p0.5-q2-rmat-s24", scale=24, algo="node2vec", max_len=80, sources="vertices", seed=1,
-               n2v_p=0.5, n2v_q=2.0),
-    "c4": dict(name="mixed-ppr1M-metapath-rmat-s23", scale=23, kind="mixed", seed=1),
+               n2v_p=0.5, n2v_q=2.0, tables=("neighbor_hash",)),
+    "c4": dict(name="mixed-ppr1M-metapath-rmat-s23", scale=23, kind="mixed", seed=1, tables=("label_index",)),
     "c5": dict(name="serve-rmat-s26-directed", scale=26, kind="serve", symmetric=False, algo="deepwalk_weighted",
-               max_len=80, seed=1),
+               max_len=80, seed=1, tables=("row_records", "neighbor_hash")),
 }
+# Optional device tables beyond the paper's own preprocessing (walks are
+# identical with and without them), chosen per workload where they pay:
+# row records when the row-offset array does not sit in L2 or the walk is
+# latency-bound, the neighbour hash for Node2Vec, the label index for MetaPath.
+TABLE_FLAGS = {"row_records": 8, "neighbor_hash": 4, "label_index": 2}
+
+
+def tables_of(wl, args) -> int:
+    if args.paper_paths:
+        return 0
+    flags = 0
+    for t in wl.get("tables", ()):
+        flags |= TABLE_FLAGS[t]
+    return flags
+
+
+def table_names(flags: int):
+    return [k for k, v in TABLE_FLAGS.items() if flags & v]
 METRIC = "walk steps/sec"
 UNIT = "steps/s"
 
@@ -256,7 +275,7 @@ def run_reference(args, wl):
 
 # ------------------------------------------------------------------ roofline
 
-def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False):
+def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False, records=False):
     """Roofline of the walk kernel: algorithmic bytes of one launch (the
     closed form per move where the layout fixes it, else the oracle's sector
     model measured on the CPU-baseline sample) over the kernel's event time,
@@ -265,6 +284,12 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False
     peak, peak_kind = measured_peak_hbm()
     bpm = BYTES_PER_MOVE.get(wl["algo"])
     source = "closed form (32-byte sectors of the device layout)"
+    per_walk = BYTES_PER_WALK.get(wl["algo"], BYTES_PER_WALK_BASE)
+    if records and wl["algo"] in ("deepwalk", "ppr"):
+        # one 16-byte row record (one sector) per move; the source's row pair once per walk
+        bpm = SECTOR + 4
+        per_walk = BYTES_PER_WALK_BASE + ROW_PAIR
+        source = "closed form (32-byte sectors of the device layout, row records)"
     if bpm is None and cpu is not None and hashed:
         bpm = cpu["model_bytes_per_move_hashed"]
         source = ("row pair + one 32-byte sector per attempt and per deciding IsNeighbor (neighbour hash), "
@@ -274,7 +299,7 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False
         source = "oracle sector model on the CPU-baseline sample"
     if bpm is None:
         return None
-    alg_bytes = moves * bpm + walks * BYTES_PER_WALK.get(wl["algo"], BYTES_PER_WALK_BASE)
+    alg_bytes = moves * bpm + walks * per_walk
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": ncu_traffic(f"walk_persistent/{wl['name']}"),
@@ -482,6 +507,46 @@ def measure_serve(trw, torch, G, g, n_requests=3000, rate=2000.0):
     return out
 
 
+def measure_replay(trw, torch, G, sp, algo, src, L, seed, kw, k=50):
+    """Back-to-back steps with no L2 flush between them: one CUDA-graph replay
+    of a captured plan per step against one library call per step (the
+    launch-overhead comparison; per-step device time over k steps)."""
+    req = dict(algo=algo, sources=src, max_len=L, seed=seed, **kw)
+    P = G.plan([req])
+    stream = torch.cuda.current_stream()
+    out = {}
+    try:
+        for _ in range(3):
+            P.launch(sp)
+        P.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            P.launch(sp)
+        b.record(stream)
+        P.sync()
+        torch.cuda.synchronize()
+        out["graph_replay_ms"] = round(a.elapsed_time(b) / k, 4)
+    finally:
+        P.close()
+    n = int(src.shape[0])
+    op = torch.empty((n, L + 1), dtype=torch.int32, device=src.device)
+    ol = torch.empty(n, dtype=torch.int32, device=src.device)
+    for _ in range(3):
+        G.walk(algo, src, L, seed, out_paths=op, out_lengths=ol, stream=sp, sync=False, **kw)
+    G.sync(sp)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(k):
+        G.walk(algo, src, L, seed, out_paths=op, out_lengths=ol, stream=sp, sync=False, **kw)
+    b.record(stream)
+    G.sync(sp)
+    torch.cuda.synchronize()
+    out["direct_call_ms"] = round(a.elapsed_time(b) / k, 4)
+    out["steps"] = k
+    return out
+
+
 def measure_gather_ceiling(trw, g):
     """Dependent random 16-byte loads over a table the size of the alias
     records, at walk-kernel occupancy: the practical random-access ceiling."""
@@ -521,12 +586,14 @@ def run_ours(args, wl):
         t = time.time()
         G.prepare()
         prep_ms = 1000 * (time.time() - t)
-    hash_ms = None
-    if algo == trw.NODE2VEC and not args.no_neighbor_hash:
+    tables = tables_of(wl, args)
+    tables_ms = None
+    if tables:
         torch.cuda.synchronize()
         t = time.time()
-        G.prepare(trw.PREP_NEIGHBOR_HASH)
-        hash_ms = 1000 * (time.time() - t)
+        G.prepare(tables)
+        tables_ms = 1000 * (time.time() - t)
+    hashed = bool(tables & TABLE_FLAGS["neighbor_hash"])
     kw = walk_kwargs(wl)
     L = wl["max_len"]
     t = time.time()
@@ -621,15 +688,18 @@ def run_ours(args, wl):
 
     per_algo = None
     serve = None
+    replay = None
     gather = measure_gather_ceiling(trw, g) if rank == 0 else None
     if rank == 0 and not args.no_extras:
         # every algorithm on this graph: with the label index and neighbour
         # hash, and the paper's label scan and binary search beside them
         G_paper = trw.Graph(g.row_ptr, g.col, None, g.labels)
-        if G.has_labels and not args.no_label_index:
+        if G.has_labels and not args.paper_paths:
             G.prepare(trw.PREP_LABEL_INDEX)
-        if not args.no_neighbor_hash:
+        if not args.paper_paths:
             G.prepare(trw.PREP_NEIGHBOR_HASH)
+        replay = measure_replay(trw, torch, G, sp, algo, src, L, wl["seed"], kw)
+        replay["value"] = round(moves / (replay["graph_replay_ms"] / 1000.0), 1)
         per_algo = measure_per_algo(trw, torch, G, g, flush, sp, G_paper)
         del G_paper
         if G.has_weights:
@@ -640,7 +710,8 @@ def run_ours(args, wl):
             dist.destroy_process_group()
         return
     cpu = cpu_baseline(g, wl) if ws == 1 and not args.no_cpu_baseline else None
-    roof = roofline(wl, moves, n, kms, cpu, gather, value / ws, hashed=hash_ms is not None)
+    roof = roofline(wl, moves, n, kms, cpu, gather, value / ws, hashed=hashed,
+                    records=bool(tables & TABLE_FLAGS["row_records"]))
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * dev_s / args.steps, 4), "higher_is_better": True,
@@ -650,18 +721,18 @@ def run_ours(args, wl):
                    "parallelism": f"walk shards x{ws}, graph replicated",
                    "l2": "256 MiB buffer written between timed steps (outside the events)",
                    "tuning": G.tuning(),
-                   **({"is_neighbor": "binary search" if hash_ms is None else
-                       "neighbour hash (bit-identical to the binary search)"} if algo == trw.NODE2VEC else {})},
+                   "prepared_tables": table_names(tables) + (["alias"] if algo == trw.DEEPWALK_WEIGHTED else [])},
         "kernel_ms_per_step": round(kms, 4),
         "wall_s": round(wall, 3),
         "plain_launch": {"value": round(plain_value, 1), "unit": UNIT, "ms": round(statistics.median(plain_ms), 4),
                          "speedup_persistent": round(value / ws / plain_value, 3)},
         "preprocess": {"graph_load_s": round(load_s, 3), "alias_prepare_ms": None if prep_ms is None else round(prep_ms, 2),
-                       "neighbor_hash_ms": None if hash_ms is None else round(hash_ms, 2),
+                       "tables_ms": None if tables_ms is None else round(tables_ms, 2),
                        "autotune_s": round(tune_s, 2)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(n * 4),
                 "d2h_bytes_per_step": int(n * (L + 1) * 4 + n * 4), "ms": round(1000 * e2e_s, 3)},
         "gpu_launches": 2 * args.steps,
+        "plan_replay": replay,
         "roofline": roof,
         "per_algo": per_algo,
         "serve": serve,
@@ -694,7 +765,7 @@ def run_mixed(args, wl):
     g = build_graph(wl)
     G = trw.Graph(g.row_ptr, g.col, None, g.labels)
     index_ms = None
-    if not args.no_label_index:
+    if tables_of(wl, args) & TABLE_FLAGS["label_index"]:
         torch.cuda.synchronize()
         t = time.time()
         G.prepare(trw.PREP_LABEL_INDEX)
@@ -868,7 +939,13 @@ def run_serve(args, wl):
     t = time.time()
     G.prepare()
     prep_s = time.time() - t
-    log(f"loaded in {load_s:.1f}s, prepared in {prep_s:.1f}s, {G.device_bytes() / 1e9:.1f} GB on the device")
+    tables = tables_of(wl, args)
+    t = time.time()
+    if tables:
+        G.prepare(tables)
+    tables_s = time.time() - t
+    log(f"loaded in {load_s:.1f}s, prepared in {prep_s:.1f}s + {tables_s:.1f}s, "
+        f"{G.device_bytes() / 1e9:.1f} GB on the device")
     if not args.no_autotune:
         G.autotune(trw.DEEPWALK_WEIGHTED, 10)
     # batch walk on the largest graph: 16,777,216 uniform sources x 80 moves
@@ -907,7 +984,8 @@ def run_serve(args, wl):
     line["serve"] = serve
     line["batch_largest_graph"] = {"workload": "weighted DeepWalk, 16,777,216 uniform sources x 80 moves",
                                    "steps_per_s": round(batch_value, 1), "kernel_ms": round(kms_m, 3), "moves": moves}
-    line["preprocess"] = {"graph_load_s": round(load_s, 2), "alias_prepare_s": round(prep_s, 2)}
+    line["preprocess"] = {"graph_load_s": round(load_s, 2), "alias_prepare_s": round(prep_s, 2),
+                          "tables_s": round(tables_s, 2), "prepared_tables": table_names(tables) + ["alias"]}
     line["roofline"] = roof
     line["gather_ceiling"] = gather
     line["e2e"] = {"value": serve["served"]["steps_per_s"], "unit": UNIT, "h2d_bytes_per_step": None,
@@ -928,10 +1006,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-algorithm lines and the gather ceiling")
     ap.add_argument("--scale", type=int, default=0, help="override the R-MAT scale (smaller profiling cases)")
-    ap.add_argument("--no-neighbor-hash", action="store_true",
-                    help="Node2Vec: binary search of the previous vertex's row instead of the neighbour hash")
-    ap.add_argument("--no-label-index", action="store_true",
-                    help="mixed workload: MetaPath scans labels at every step instead of the label index")
+    ap.add_argument("--paper-paths", action="store_true",
+                    help="no optional device tables: MetaPath label scans, Node2Vec binary searches, NAIVE moves "
+                         "through the row offsets (the paper's method as written; walks are identical)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tuning (profiling runs: the first launches are then the timed ones)")
     ap.add_argument("--serve-requests", type=int, default=3000, help="requests in the serving trace")

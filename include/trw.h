@@ -124,6 +124,7 @@ void trw_graph_free(trw_graph* g);
 #define TRW_LABEL_INDEX_MAX_LABELS 30
 #define TRW_PREP_NEIGHBOR_HASH 4u /* build the neighbour hash for Node2Vec's IsNeighbor */
 #define TRW_NEIGHBOR_HASH_MIN_DEGREE 8
+#define TRW_PREP_ROW_RECORDS 8u   /* build row records for NAIVE moves and O-REJ candidates */
 
 /*
  * Preprocessing for static walks (Algorithm 3): for every vertex v, apply the
@@ -153,6 +154,15 @@ void trw_graph_free(trw_graph* g);
  * reads about one bucket instead of log2(d_prev) row entries.  Membership is
  * exact, so every walk is identical with and without it.  Preparing a hash
  * that exists already does nothing.
+ *
+ * TRW_PREP_ROW_RECORDS (not in the paper, whose NAIVE move reads the row of
+ * the current vertex and then one edge of it, Section 2.3): a 16-byte record
+ * per edge slot {destination, its row offset, its degree, 0}, so that a NAIVE
+ * move (DeepWalk, PPR) or an O-REJ candidate (Node2Vec) reads one record and
+ * the next step needs no row-offset lookup: one dependent random read per
+ * move instead of two.  16 bytes of device memory per edge; every walk is
+ * identical with and without them.  Preparing records that exist already
+ * does nothing.
  *
  * Runs on the device; synchronous.  Errors: TRW_ERR_INVALID (no weights, or
  * no labels, loaded for the requested table; a label too large for the
@@ -228,6 +238,39 @@ trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw_algo* algo
                           const int32_t* const* sources, const int64_t* n_sources, const int32_t* max_lens,
                           const uint64_t* seeds, int32_t* const* out_paths, int32_t* const* out_lengths,
                           void* stream, int sync);
+
+/*
+ * Batch plans (no counterpart in the paper, whose executor is a CPU loop): the
+ * mixed batch of trw_walk_batch, with the same arguments and the same device
+ * buffers, captured once as a CUDA graph (control reset, one source check
+ * over every request, the persistent walk launch) and
+ * replayed by trw_plan_launch with a single graph launch.  Every replay
+ * re-walks the batch into the same outputs; the walks of a replay are those
+ * of trw_walk_batch with the plan's current seeds.  The plan keeps the
+ * graph's launch configuration and prepared tables as they were at creation;
+ * destroy plans before their graph.  The buffers must stay valid while the
+ * plan exists.
+ *   trw_plan_create   validates and captures; nothing runs.
+ *                     Errors: those of trw_walk_batch, TRW_ERR_OOM, TRW_ERR_CUDA.
+ *   trw_plan_set_seed changes request r's seed for the next launch (waits for
+ *                     the previous launch of the plan to finish).
+ *   trw_plan_launch   enqueues one replay on stream (NULL: the graph's
+ *                     stream); asynchronous.
+ *   trw_plan_sync     waits for the last launch and returns its status
+ *                     (TRW_ERR_INVALID for a source outside [0, nv): nothing
+ *                     was written; TRW_ERR_REJECT_CAP); *moves (may be NULL)
+ *                     receives the moves it made.
+ *   trw_plan_destroy  waits for the last launch and frees the plan.
+ */
+typedef struct trw_plan trw_plan;
+trw_status trw_plan_create(trw_graph* g, int32_t n_requests, const trw_algo* algos, const trw_params* params,
+                           const int32_t* const* sources, const int64_t* n_sources, const int32_t* max_lens,
+                           const uint64_t* seeds, int32_t* const* out_paths, int32_t* const* out_lengths,
+                           trw_plan** plan);
+trw_status trw_plan_set_seed(trw_plan* plan, int32_t request, uint64_t seed);
+trw_status trw_plan_launch(trw_plan* plan, void* stream);
+trw_status trw_plan_sync(trw_plan* plan, int64_t* moves);
+void trw_plan_destroy(trw_plan* plan);
 
 /*
  * trw_walk_batch with no allocation (the paper has no counterpart: this is an

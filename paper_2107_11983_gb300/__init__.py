@@ -27,6 +27,8 @@ PREP_ALIAS = 1
 PREP_LABEL_INDEX = 2
 LABEL_INDEX_MAX_LABELS = 30
 PREP_NEIGHBOR_HASH = 4
+PREP_ROW_RECORDS = 8
+PREP_ALL = PREP_ALIAS | PREP_LABEL_INDEX | PREP_NEIGHBOR_HASH | PREP_ROW_RECORDS
 MAX_SCHEMA = 16
 MAX_BATCH = 64
 
@@ -88,6 +90,11 @@ _SIGS = {
     "trw_walk_batch": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                       ctypes.c_int]),
     "trw_walk_batch_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "trw_plan_create": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "trw_plan_set_seed": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_uint64]),
+    "trw_plan_launch": (ctypes.c_int, [_VP, _VP]),
+    "trw_plan_sync": (ctypes.c_int, [_VP, _VP]),
+    "trw_plan_destroy": (None, [_VP]),
     "trw_get_tuning": (ctypes.c_int, [_VP, _VP]),
     "trw_set_tuning": (ctypes.c_int, [_VP, _VP]),
     "trw_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int32, _VP]),
@@ -255,7 +262,8 @@ class Graph:
 
     def prepare(self, what: int = PREP_ALIAS):
         """trw_prepare: PREP_ALIAS (weighted DeepWalk tables), PREP_LABEL_INDEX
-        (MetaPath label index) and/or PREP_NEIGHBOR_HASH (Node2Vec IsNeighbor)."""
+        (MetaPath label index), PREP_NEIGHBOR_HASH (Node2Vec IsNeighbor) and/or
+        PREP_ROW_RECORDS (one read per NAIVE move or O-REJ candidate)."""
         _check(load_library().trw_prepare(self._h, what), "trw_prepare")
 
     def device_bytes(self) -> int:
@@ -296,11 +304,8 @@ class Graph:
         sa = _stream_arg(stream) if stream is not None else (int(_torch().cuda.current_stream().cuda_stream) or 1)
         _check(load_library().trw_sync(self._h, sa), "trw_sync")
 
-    def walk_batch(self, requests: Sequence[dict], stream=None, sync: bool = True):
-        """One persistent launch over a mixed batch.  Each request is a dict with
-        algo, sources (CUDA tensor), max_len, seed and optional parameters; outputs
-        are allocated as CUDA tensors and returned as a list of WalkOutput."""
-        lib = load_library()
+    def _batch_args(self, requests: Sequence[dict]):
+        """ctypes arrays of a mixed batch; outputs allocated as CUDA tensors."""
         torch = _torch()
         nreq = len(requests)
         if not 1 <= nreq <= MAX_BATCH:
@@ -336,12 +341,22 @@ class Graph:
             seeds[i] = int(r["seed"]) & ((1 << 64) - 1)
             outs[i], outl[i] = op.data_ptr(), ol.data_ptr()
             results.append(WalkOutput(op, ol))
-        st = lib.trw_walk_batch(self._h, nreq, algos, params, srcs, ns, lens, seeds, outs, outl,
-                                _stream_arg(stream, *[k for k in keep if _is_torch(k)]), 1 if sync else 0)
+        return (nreq, algos, params, srcs, ns, lens, seeds, outs, outl), keep, results
+
+    def walk_batch(self, requests: Sequence[dict], stream=None, sync: bool = True):
+        """One persistent launch over a mixed batch.  Each request is a dict with
+        algo, sources (CUDA tensor), max_len, seed and optional parameters; outputs
+        are allocated as CUDA tensors and returned as a list of WalkOutput."""
+        args, keep, results = self._batch_args(requests)
+        st = load_library().trw_walk_batch(self._h, *args, _stream_arg(stream, *[k for k in keep if _is_torch(k)]),
+                                           1 if sync else 0)
         _check(st, "trw_walk_batch")
         return results
 
-    # ------------------------------------------------------------- tuning
+    def plan(self, requests: Sequence[dict]) -> "Plan":
+        """The mixed batch captured once as a CUDA graph (trw_plan_create)."""
+        return Plan(self, requests)
+
     def tuning(self) -> dict:
         t = Tuning()
         _check(load_library().trw_get_tuning(self._h, ctypes.byref(t)))
@@ -413,6 +428,43 @@ def philox_device(ctr, key0: int, key1: int) -> np.ndarray:
     out = np.empty_like(c)
     _check(load_library().trw_debug_philox(c.ctypes.data, c.shape[0], key0, key1, out.ctypes.data), "philox")
     return out
+
+
+class Plan:
+    """A mixed batch captured as a CUDA graph (trw_plan_*): every launch()
+    re-walks the batch into the same output tensors (.outputs)."""
+
+    def __init__(self, graph: Graph, requests: Sequence[dict]):
+        lib = load_library()
+        args, self._keep, self.outputs = graph._batch_args(requests)
+        _torch().cuda.current_stream().synchronize()  # sources copied on torch's stream
+        self.graph = graph
+        h = ctypes.c_void_p(0)
+        _check(lib.trw_plan_create(graph._h, *args, ctypes.byref(h)), "trw_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load_library().trw_plan_launch(self._h, _stream_arg(stream)), "trw_plan_launch")
+
+    def sync(self) -> int:
+        """Waits for the last launch; returns its moves (raises on a device error)."""
+        moves = ctypes.c_int64(0)
+        _check(load_library().trw_plan_sync(self._h, ctypes.byref(moves)), "trw_plan_sync")
+        return moves.value
+
+    def set_seed(self, request: int, seed: int):
+        _check(load_library().trw_plan_set_seed(self._h, request, int(seed) & ((1 << 64) - 1)), "trw_plan_set_seed")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().trw_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

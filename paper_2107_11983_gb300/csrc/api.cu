@@ -104,6 +104,7 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->lvrec);
   cudaFree(g->lerec);
   cudaFree(g->nh_slots);
+  cudaFree(g->rrec);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);
@@ -241,6 +242,7 @@ DevGraph trw_dev_graph(const trw_graph* g) {
   d.col = g->col;
   d.alias = g->alias;
   d.labels = g->labels;
+  d.rrec = g->rrec;
   d.lidx.vrec = g->lvrec;
   d.lidx.erec = g->lerec;
   d.lidx.stride = g->lstride;
@@ -349,9 +351,26 @@ static trw_status prepare_neighbor_hash(trw_graph* g) {
   return TRW_OK;
 }
 
+static trw_status prepare_row_records(trw_graph* g) {
+  if (g->rrec) return TRW_OK;
+  int4* rec = nullptr;
+  const size_t bytes = sizeof(int4) * (size_t)g->ne;
+  trw_status st = alloc_dev((void**)&rec, bytes, "row records");
+  if (st != TRW_OK) return st;
+  cudaError_t e = launch_row_records(g->ne, g->row_ptr, g->col, rec, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    cudaFree(rec);
+    return trw_cuda_fail(e, "prepare row records");
+  }
+  g->rrec = rec;
+  g->device_bytes += (int64_t)bytes;
+  return TRW_OK;
+}
+
 extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
-  if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX | TRW_PREP_NEIGHBOR_HASH))
+  if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX | TRW_PREP_NEIGHBOR_HASH | TRW_PREP_ROW_RECORDS))
     return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
   std::lock_guard<std::mutex> lk(g->mu);
   if ((what & TRW_PREP_ALIAS) && !g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
@@ -364,7 +383,11 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
     trw_status st = prepare_label_index(g);
     if (st != TRW_OK) return st;
   }
-  if (what & TRW_PREP_NEIGHBOR_HASH) return prepare_neighbor_hash(g);
+  if (what & TRW_PREP_NEIGHBOR_HASH) {
+    trw_status st = prepare_neighbor_hash(g);
+    if (st != TRW_OK) return st;
+  }
+  if (what & TRW_PREP_ROW_RECORDS) return prepare_row_records(g);
   return TRW_OK;
 }
 

@@ -522,6 +522,17 @@ __global__ void label_gather_kernel(int64_t ne, int32_t stride, const int32_t* _
   }
 }
 
+// ---------------------------------------------------------------- row records
+
+__global__ void row_records_kernel(int64_t ne, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                   int4* __restrict__ rec) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = col[e];
+    const int32_t o = row_ptr[c];
+    rec[e] = make_int4(c, o, row_ptr[c + 1] - o, 0);
+  }
+}
+
 // Every id in [0, nv); flags a row that is not strictly increasing.
 __global__ void check_graph_kernel(int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                    Ctrl* ctrl, int* unsorted) {
@@ -688,6 +699,14 @@ cudaError_t launch_prepare_labels(int32_t nv, int64_t ne, const int32_t* row_ptr
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
+}
+
+cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, int4* rec, cudaStream_t st) {
+  if (ne <= 0) return cudaSuccess;
+  int64_t blocks = (ne + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  row_records_kernel<<<(unsigned)blocks, 256, 0, st>>>(ne, row_ptr, col, rec);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl, int* d_unsorted,

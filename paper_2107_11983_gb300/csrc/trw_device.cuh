@@ -80,6 +80,7 @@ struct DevGraph {
   const int32_t* __restrict__ col;       // [ne], rows sorted ascending when sorted != 0
   const AliasRec* __restrict__ alias;    // [ne] after ALIAS preparation, or null
   const uint8_t* __restrict__ labels;    // [ne + 16] (padded for word loads), or null
+  const int4* __restrict__ rrec;         // [ne] row records {dst, row_ptr[dst], deg(dst), 0}, or null
   LabelIndex lidx;
   NeighborHash nh;
   int32_t nv;

@@ -49,6 +49,9 @@ cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr,
                                  int32_t min_degree, unsigned long long** slots_out, unsigned long long* mask_out,
                                  int32_t* max_probe_out, size_t* bytes_out, cudaStream_t st);
 
+// Row records {col[e], row_ptr[col[e]], deg(col[e]), 0} of every edge slot.
+cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, int4* rec, cudaStream_t st);
+
 // Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl,
                                int* d_unsorted, cudaStream_t st);

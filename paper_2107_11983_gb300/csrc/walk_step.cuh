@@ -179,8 +179,18 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
   }
   if (W.d == 0) return kStop;                                  // dead end
   if (A == DEEPWALK || A == PPR) {
-    // NAIVE: E_v[x], x uniform in [0, d_v).
-    next = ldg(g.col + W.off + below(B, (uint32_t)W.d));
+    // NAIVE: E_v[x], x uniform in [0, d_v).  A row record also carries the
+    // picked vertex's row for the next step.
+    const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
+    if (g.rrec) {
+      const int4 r = __ldg(g.rrec + e);
+      next = r.x;
+      W.nxo = r.y;
+      W.nxd = r.z;
+      W.nxv = true;
+    } else {
+      next = ldg(g.col + e);
+    }
     return kMoved;
   } else if (A == DEEPWALK_WEIGHTED) {
     // ALIAS generation from the stored C_v (no Gather for static walks); the
@@ -241,7 +251,10 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     next = ldg(g.col + W.off + j);
     return kMoved;
   } else {  // NODE2VEC, O-REJ
-    const int32_t c = ldg(g.col + W.off + below(B, (uint32_t)W.d));
+    const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
+    int4 rr = make_int4(0, 0, 0, 0);
+    if (g.rrec) rr = __ldg(g.rrec + e);
+    const int32_t c = g.rrec ? rr.x : ldg(g.col + e);
     bool accept;
     if (W.s == 0) accept = true;                               // Weight = MaxWeight on the first step
     else if (c == W.prev) accept = (uint64_t)B.z < sp.T_ret;
@@ -257,6 +270,11 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     }
     if (accept) {
       next = c;
+      if (g.rrec) {
+        W.nxo = rr.y;
+        W.nxd = rr.z;
+        W.nxv = true;
+      }
       return kMoved;
     }
     return (W.att + 1 >= kRejectCap) ? kFail : kRetry;

@@ -145,7 +145,7 @@ def test_index_rejections():
         nol.prepare(trw.PREP_LABEL_INDEX)
     assert e.value.status == -1
     with pytest.raises(trw.TRWError) as e:
-        nol.prepare(8)
+        nol.prepare(64)
     assert e.value.status == -1
 
 
