@@ -451,18 +451,19 @@ def measure_serve(trw, torch, G, g, n_requests=3000, rate=2000.0):
                 pending[rid] = (ts, op, ol)
                 i += 1
                 now = time.perf_counter() - t0
-            for rid in list(pending):
-                if S.poll(rid) == trw.OK:
-                    ts, op, ol = pending.pop(rid)
-                    lat.append(time.perf_counter() - ts)
-                    done_bufs.append(ol)
+            for rid, status in S.reap():
+                if status != 0:
+                    raise trw.TRWError(status, f"request {rid}")
+                ts, op, ol = pending.pop(rid)
+                lat.append(time.perf_counter() - ts)
+                done_bufs.append(ol)
         wall = time.perf_counter() - t0
         S.close()
         torch.cuda.synchronize()
         moves = int(sum(int((ol.to(torch.int64) - 1).sum().item()) for ol in done_bufs))
         return np.array(lat), wall, moves
 
-    def run_plain():
+    def run_plain(open_loop=True):
         stream = torch.cuda.Stream()
         sp = stream.cuda_stream
         lat, done_bufs = [], []
@@ -471,7 +472,7 @@ def measure_serve(trw, torch, G, g, n_requests=3000, rate=2000.0):
         i = 0
         while i < n_requests or pending:
             now = time.perf_counter() - t0
-            while i < n_requests and t_arr[i] <= now:
+            while i < n_requests and (not open_loop or t_arr[i] <= now):
                 r = reqs[i]
                 op, ol = _out_buffers(torch, r, dev)
                 ts = time.perf_counter()
@@ -502,6 +503,10 @@ def measure_serve(trw, torch, G, g, n_requests=3000, rate=2000.0):
     out["plain_fifo"] = dict(pct(lat), steps_per_s=round(moves / wall, 1), wall_s=round(wall, 3))
     lat, wall, moves = run_server(False)
     out["saturating"] = {"steps_per_s": round(moves / wall, 1), "wall_s": round(wall, 3), "moves": moves}
+    lat, wall, moves = run_plain(False)
+    out["plain_fifo_saturating"] = {"steps_per_s": round(moves / wall, 1), "wall_s": round(wall, 3), "moves": moves}
+    out["saturating_speedup_vs_plain"] = round(out["saturating"]["steps_per_s"] /
+                                               out["plain_fifo_saturating"]["steps_per_s"], 3)
     out["p99_speedup_vs_plain"] = round(out["plain_fifo"]["p99_ms"] / out["served"]["p99_ms"], 3)
     log(f"serve: {out}")
     return out

@@ -386,9 +386,13 @@ trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg, trw_serve
  * DEVICE buffers that stay valid until poll returns TRW_OK or an error, and
  * that no other stream still writes when submit is called: the server runs
  * on its own streams and does not order itself after the caller's).
- * sources may be host or device; it is copied at submit.  Returns
- * TRW_ERR_BUSY when admitting it would exceed the configured walk, byte or
- * slot limits (nothing is queued), else queues it and writes *req_id.
+ * sources may be host or device; every source is checked at submit
+ * (TRW_ERR_INVALID for one outside [0, nv): nothing queued or written).  Host
+ * sources are copied into the server's pool before submit returns; device
+ * sources are read in place, so they must stay valid and unchanged until the
+ * request is reported.  Submit does not wait for the walk kernel.  Returns TRW_ERR_BUSY when admitting it would exceed the
+ * configured walk, byte or slot limits (nothing is queued), else queues it
+ * and writes *req_id.
  */
 trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* params, const int32_t* sources,
                             int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
@@ -398,6 +402,13 @@ trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* para
  * while it runs, TRW_ERR_NOT_FOUND for an unknown or already collected id,
  * or the request's error status. */
 trw_status trw_serve_poll(trw_server* s, uint64_t req_id);
+
+/* Collect up to max finished requests (oldest first) in one call:
+ * ids[i] and statuses[i] (TRW_OK or the request's error status) for
+ * i < *n_out; each is released as by trw_serve_poll.  *n_out = 0 when none
+ * has finished.  Errors: TRW_ERR_INVALID (bad arguments), TRW_ERR_CUDA,
+ * TRW_ERR_INTERNAL (a failed device self-check). */
+trw_status trw_serve_reap(trw_server* s, uint64_t* ids, int32_t* statuses, int32_t max, int32_t* n_out);
 
 /* Wait (bounded by timeout_ms) until every submitted request has finished. */
 trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms);

@@ -111,6 +111,7 @@ _SIGS = {
     "trw_serve_submit": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.c_uint64, _VP, _VP, _VP]),
     "trw_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "trw_serve_reap": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
     "trw_serve_drain": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "trw_serve_destroy": (None, [_VP]),
     "trw_gather_ceiling": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
@@ -504,7 +505,7 @@ class Server:
         st = lib.trw_serve_submit(self._h, algo, ctypes.byref(p), _ptr(src), int(src.shape[0]), max_len,
                                   seed & ((1 << 64) - 1), _ptr(out_paths), _ptr(out_lengths), ctypes.byref(rid))
         _check(st, "trw_serve_submit")
-        self._keep[rid.value] = (out_paths, out_lengths)
+        self._keep[rid.value] = (src, out_paths, out_lengths)  # device sources are read after submit returns
         return rid.value
 
     def poll(self, rid: int) -> int:
@@ -515,6 +516,19 @@ class Server:
         self._keep.pop(rid, None)
         _check(st, f"request {rid}")
         return OK
+
+    def reap(self, max_requests: int = 256):
+        """Finished requests, oldest first, as (request id, status) pairs (status 0
+        is OK, else the request's error status); empty when none has finished."""
+        ids = (ctypes.c_uint64 * max_requests)()
+        sts = (ctypes.c_int32 * max_requests)()
+        n = ctypes.c_int32(0)
+        _check(load_library().trw_serve_reap(self._h, ids, sts, max_requests, ctypes.byref(n)), "trw_serve_reap")
+        out = []
+        for i in range(n.value):
+            self._keep.pop(int(ids[i]), None)
+            out.append((int(ids[i]), int(sts[i])))
+        return out
 
     def drain(self, timeout_ms: int = 60000):
         _check(load_library().trw_serve_drain(self._h, timeout_ms), "trw_serve_drain")

@@ -1,9 +1,11 @@
 // Serving loop with continuous batching.
 //
 // Requests (any algorithm, any size) arrive while others run.  The host
-// writes a request's descriptor into a device slot table and publishes it by
-// bumping a counter in host-mapped memory.  A resident persistent kernel does
-// the rest:
+// copies a request's descriptor into a device slot table and publishes it by
+// copying the new request count into a device counter, both on a copy
+// stream (copy engines, no SM: the resident kernel holds every SM), so a
+// submit never waits for the device.  A resident persistent kernel does the
+// rest:
 //   - warp 0 of block 0 is the dispatcher: it reads the published counter
 //     (the only reader of the host ring), cuts each new request into chunks of
 //     walks and pushes them into a device chunk queue;
@@ -44,11 +46,17 @@ struct Chunk {
   unsigned long long pad;
 };
 
+// The counters that many warps touch at once sit on cache lines of their own
+// (tickets on q_head, polls of q_tail, pops on q_consumed, the published
+// count and the exit flag), so that polling one does not slow the atomics on
+// another.
 struct ServeState {       // device memory, persists across launches
-  unsigned long long q_head;      // next queue entry to pop
-  unsigned long long q_tail;      // entries pushed
-  unsigned long long q_consumed;  // entries popped and read
-  unsigned long long disp_next;   // dispatcher: next published request to admit
+  alignas(128) unsigned long long q_head;      // next queue entry to pop (tickets)
+  alignas(128) unsigned long long q_tail;      // entries pushed
+  alignas(128) unsigned long long q_consumed;  // entries popped and read
+  alignas(128) unsigned long long published;   // requests 0..published-1 are visible (written by host copies)
+  alignas(128) int exit_now;      // set by the dispatcher: the launch is ending (cleared before each launch)
+  alignas(128) unsigned long long disp_next;   // dispatcher: next published request to admit
   int n_act;                      // dispatcher: requests with walks not yet queued
   int rr;                         // dispatcher: round-robin cursor
   unsigned long long act_k[kMaxActive];    // their request numbers
@@ -56,7 +64,6 @@ struct ServeState {       // device memory, persists across launches
   unsigned long long act_n[kMaxActive];    // walks of the request
   unsigned long long act_cw[kMaxActive];   // walks per chunk
   unsigned long long moves;       // total moves of finished walks
-  int exit_now;                   // set by the dispatcher: the launch is ending (cleared before each launch)
   int live_workers;               // worker warps of the running launch
   int err;                        // first failed self-check (kernel-wide)
   unsigned long long bad[4];      // what that check saw
@@ -71,8 +78,7 @@ struct SlotRec {
 };
 
 struct ServeHost {        // host-mapped pinned memory
-  unsigned long long published;   // requests 0..published-1 are visible to the device
-  unsigned int stop;
+  unsigned int stop;              // the host asks the kernel to end
   unsigned int pad;
 };
 
@@ -88,12 +94,6 @@ struct ServeDev {
   long long idle_ns;
   unsigned long long depth;         // queued chunks the dispatcher keeps ahead of the workers
 };
-
-__device__ __forceinline__ unsigned long long ld_acquire_sys(const volatile unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
   unsigned long long v;
@@ -145,8 +145,9 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
   unsigned long long tail = st->q_tail;
   for (;;) {
     int go = 1;
+    unsigned long long P = 0;
     if (lane == 0) {
-      const unsigned long long P = ld_acquire_sys(&sv.host->published);
+      P = ld_acquire_gpu(&st->published);
       while (n_act < kMaxActive && disp_next < P) {
         const int slot = (int)(disp_next % (unsigned long long)sv.R);
         const unsigned long long n = (unsigned long long)__ldcg(&sv.slots[slot].spec.nwalks);
@@ -159,31 +160,63 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
         }
         ++disp_next;
       }
-      const unsigned long long consumed = ld_acquire_gpu(&st->q_consumed);
-      int pushed = 0;
-      while (n_act > 0 && tail - consumed < sv.depth && pushed < 512) {
+    }
+    // Chunks go out in bursts of up to 32 consecutive chunks of one request,
+    // one per lane, round-robin over the active requests.
+    const unsigned long long consumed = lane == 0 ? ld_acquire_gpu(&st->q_consumed) : 0ull;
+    int pushed = 0;
+    for (;;) {
+      int burst = 0;
+      unsigned long long bk = 0, bpos = 0, bn = 0, bcw = 0;
+      if (lane == 0 && n_act > 0 && tail - consumed < sv.depth && pushed < 1024) {
         if (rr >= n_act) rr = 0;
-        const unsigned long long pos = act->pos[rr], n = act->n[rr];
-        const unsigned long long end = pos + act->cw[rr] < n ? pos + act->cw[rr] : n;
-        Chunk* c = &sv.queue[tail % kQueueCap];
-        __stcg(&c->k, act->k[rr]);
-        __stcg(reinterpret_cast<uint2*>(&c->begin), make_uint2((uint32_t)pos, (uint32_t)end));
-        __stcg(&c->seq, tail);
-        ++tail;
-        ++pushed;
-        if (end >= n) {  // fully queued: leaves the active set
+        bk = act->k[rr];
+        bpos = act->pos[rr];
+        bn = act->n[rr];
+        bcw = act->cw[rr];
+        const unsigned long long left = (bn - bpos + bcw - 1) / bcw;
+        const unsigned long long room = sv.depth - (tail - consumed);
+        burst = (int)(left < 32 ? left : 32);
+        if ((unsigned long long)burst > room) burst = (int)room;
+      }
+      burst = __shfl_sync(0xffffffffu, burst, 0);
+      if (burst == 0) break;
+      bk = __shfl_sync(0xffffffffu, bk, 0);
+      bpos = __shfl_sync(0xffffffffu, bpos, 0);
+      bn = __shfl_sync(0xffffffffu, bn, 0);
+      bcw = __shfl_sync(0xffffffffu, bcw, 0);
+      const unsigned long long t0 = __shfl_sync(0xffffffffu, tail, 0);
+      if (lane < burst) {
+        const unsigned long long b = bpos + (unsigned long long)lane * bcw;
+        const unsigned long long e = b + bcw < bn ? b + bcw : bn;
+        Chunk* c = &sv.queue[(t0 + lane) % kQueueCap];
+        __stcg(&c->k, bk);
+        __stcg(reinterpret_cast<uint2*>(&c->begin), make_uint2((uint32_t)b, (uint32_t)e));
+        __stcg(&c->seq, t0 + lane);
+      }
+      if (lane == 0) {
+        tail = t0 + burst;
+        pushed += burst;
+        const unsigned long long npos = bpos + (unsigned long long)burst * bcw;
+        if (npos >= bn) {  // fully queued: leaves the active set
           --n_act;
           act->k[rr] = act->k[n_act];
           act->pos[rr] = act->pos[n_act];
           act->n[rr] = act->n[n_act];
           act->cw[rr] = act->cw[n_act];
         } else {
-          act->pos[rr] = end;
+          act->pos[rr] = npos;
           ++rr;
         }
       }
+    }
+    pushed = __shfl_sync(0xffffffffu, pushed, 0);
+    if (pushed) {
+      __threadfence();  // every lane's chunk entries before the tail
+      __syncwarp();
+    }
+    if (lane == 0) {
       if (pushed) {
-        __threadfence();
         st_release_gpu(&st->q_tail, tail);
         idle_since = now_ns();
       } else {
@@ -388,7 +421,7 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
         int bad = 0;
         if (lane == 0) {
           load_spec(&sv.slots[(int)(pk % (unsigned long long)sv.R)].spec, &spec[tgt]);
-          bad = spec_check(spec[tgt], pk, pb, pe, ld_acquire_sys(&sv.host->published));
+          bad = spec_check(spec[tgt], pk, pb, pe, ld_acquire_gpu(&sv.state->published));
           if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec[tgt].nwalks,
                               reinterpret_cast<uintptr_t>(spec[tgt].out_paths));
           key[tgt] = bad ? ~0ull : pk;
@@ -428,12 +461,16 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
       int go = 1;
       if (lane == 0) {
         const long long t = now_ns();
+        const unsigned long long tl = ld_acquire_gpu(&sv.state->q_tail);
         // leave once the dispatcher ended the launch and no entry waits for this warp
-        if (*(volatile int*)&sv.state->exit_now &&
-            (!has_ticket || ticket >= ld_acquire_gpu(&sv.state->q_tail)))
+        if (*(volatile int*)&sv.state->exit_now && (!has_ticket || ticket >= tl))
           go = 0;
         else if (t - idle_since > 1000 * sv.idle_ns) go = 0;
-        else __nanosleep(2000);
+        else {
+          // warps whose ticket is near the tail poll often, the rest back off
+          const unsigned long long dist = has_ticket && ticket > tl ? ticket - tl : 0;
+          __nanosleep(dist < 64 ? 256u : dist < 512 ? 2000u : 8000u);
+        }
       }
       if (!__shfl_sync(0xffffffffu, go, 0)) break;
       continue;
@@ -537,6 +574,9 @@ struct trw_server {
   unsigned long long* done_dev = nullptr;
   int* done_err_dev = nullptr;
   SlotRec* slot_stage = nullptr;       // pinned staging [R]
+  unsigned long long* pub_stage = nullptr;  // pinned [R]: the count that publishes request k is pub_stage[k % R]
+  int32_t* check_buf = nullptr;        // pinned: host copy of device sources for the range check
+  int64_t check_cap = 0;
   // host bookkeeping, ring order
   unsigned long long next_k = 0;       // next request number
   unsigned long long oldest = 0;       // oldest request not yet collected
@@ -571,6 +611,8 @@ static void server_release(trw_server* s) {
   if (s->done) cudaFreeHost(s->done);
   if (s->done_err) cudaFreeHost(s->done_err);
   if (s->slot_stage) cudaFreeHost(s->slot_stage);
+  if (s->pub_stage) cudaFreeHost(s->pub_stage);
+  if (s->check_buf) cudaFreeHost(s->check_buf);
   delete s;
 }
 
@@ -612,6 +654,7 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   SV_TRY(cudaHostAlloc(&s->done, sizeof(unsigned long long) * R, cudaHostAllocMapped), "mapped flags");
   SV_TRY(cudaHostAlloc(&s->done_err, sizeof(int) * R, cudaHostAllocMapped), "mapped flags");
   SV_TRY(cudaHostAlloc(&s->slot_stage, sizeof(SlotRec) * R, cudaHostAllocDefault), "pinned staging");
+  SV_TRY(cudaHostAlloc(&s->pub_stage, sizeof(unsigned long long) * R, cudaHostAllocDefault), "pinned staging");
   std::memset((void*)s->host, 0, sizeof(ServeHost));
   std::memset((void*)s->done, 0, sizeof(unsigned long long) * R);
   std::memset((void*)s->done_err, 0, sizeof(int) * R);
@@ -668,6 +711,13 @@ static cudaError_t launch_if_idle(trw_server* s) {
   return cudaGetLastError();
 }
 
+// Every id in [0, nv) (branch-free, so the loop vectorises).
+static bool sources_in_range(const int32_t* src, int64_t n, int64_t nv) {
+  uint32_t bad = 0;
+  for (int64_t i = 0; i < n; ++i) bad |= (uint32_t)((uint32_t)src[i] >= (uint32_t)nv);
+  return bad == 0;
+}
+
 // Collect finished requests at the front of the ring (frees their slots and source ranges).
 static void retire_front(trw_server* s) {
   while (s->oldest < s->next_k && s->collected[s->oldest % s->R]) ++s->oldest;
@@ -684,15 +734,17 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   if (sp.nwalks > 0 && (!trw_is_device_ptr(out_paths) || !trw_is_device_ptr(out_lengths)))
     return trw_fail(TRW_ERR_INVALID, "serve outputs must be device buffers");
   const bool src_dev = trw_is_device_ptr(sources);
-  if (!src_dev)
-    for (int64_t i = 0; i < n_sources; ++i)
-      if (sources[i] < 0 || sources[i] >= s->g->nv) return trw_fail(TRW_ERR_INVALID, "source %lld out of range", (long long)i);
+  if (!src_dev && !sources_in_range(sources, n_sources, s->g->nv))
+    return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
   const int64_t out_bytes =
       (int64_t)sizeof(int32_t) * (sp.endpoints ? sp.nwalks : sp.nwalks * ((int64_t)max_len + 1)) + 4 * sp.nwalks;
+  // Host sources are copied into the server's source pool; device sources
+  // are read in place (they stay valid until the request is reported).
+  const int64_t pool_n = src_dev ? 0 : n_sources;
   std::lock_guard<std::mutex> lk(s->mu);
   retire_front(s);
   if (s->next_k - s->oldest >= (unsigned long long)s->R) return trw_fail(TRW_ERR_BUSY, "all %d request slots in use", s->R);
-  if (n_sources > s->src_cap || s->inflight_walks + sp.nwalks > s->cfg.max_inflight_walks)
+  if (pool_n > s->src_cap || s->inflight_walks + sp.nwalks > s->cfg.max_inflight_walks)
     return trw_fail(TRW_ERR_BUSY, "walk admission limit %lld reached", (long long)s->cfg.max_inflight_walks);
   if (s->inflight_bytes + out_bytes > s->cfg.max_inflight_bytes)
     return trw_fail(TRW_ERR_BUSY, "output byte admission limit reached");
@@ -701,70 +753,83 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   int64_t pos = -1;
   if (s->oldest == s->next_k) {
     s->src_head = 0;
-    if (n_sources <= s->src_cap) pos = 0;
+    if (pool_n <= s->src_cap) pos = 0;
   } else {
     const int64_t lo_live = s->req_src_pos[s->oldest % s->R];
     if (lo_live < s->src_head) {  // free: [src_head, cap) and [0, lo_live)
-      if (s->src_head + n_sources <= s->src_cap) pos = s->src_head;
-      else if (n_sources <= lo_live) pos = 0;
+      if (s->src_head + pool_n <= s->src_cap) pos = s->src_head;
+      else if (pool_n <= lo_live) pos = 0;
     } else if (lo_live > s->src_head) {  // free: [src_head, lo_live)
-      if (s->src_head + n_sources <= lo_live) pos = s->src_head;
-    } else if (n_sources == 0) {
+      if (s->src_head + pool_n <= lo_live) pos = s->src_head;
+    } else if (pool_n == 0) {
       pos = s->src_head;
     }
   }
   if (pos < 0) return trw_fail(TRW_ERR_BUSY, "source pool full");
+  if (src_dev && n_sources > 0) {
+    // device sources: one copy to pinned memory and a host range check
+    // before anything is queued
+    if (n_sources > s->check_cap) {
+      if (s->check_buf) cudaFreeHost(s->check_buf);
+      s->check_buf = nullptr;
+      s->check_cap = 0;
+      const cudaError_t ea = cudaHostAlloc(&s->check_buf, sizeof(int32_t) * (size_t)n_sources, cudaHostAllocDefault);
+      if (ea != cudaSuccess) return trw_cuda_fail(ea, "serve source check buffer");
+      s->check_cap = n_sources;
+    }
+    cudaError_t ec = cudaMemcpyAsync(s->check_buf, sources, sizeof(int32_t) * (size_t)n_sources,
+                                     cudaMemcpyDeviceToHost, s->copy_stream);
+    if (ec == cudaSuccess) ec = cudaStreamSynchronize(s->copy_stream);
+    if (ec != cudaSuccess) return trw_cuda_fail(ec, "serve source check");
+    if (!sources_in_range(s->check_buf, n_sources, s->g->nv))
+      return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
+  }
   const unsigned long long k = s->next_k;
   const int slot = (int)(k % (unsigned long long)s->R);
-  sp.sources = s->src_pool + pos;
+  sp.sources = src_dev ? sources : s->src_pool + pos;
   sp.out_paths = out_paths;
   sp.out_lengths = out_lengths;
-  // Walks per chunk: about 20 expected moves per lane of the warp that takes
-  // the chunk, so that a request spreads over many warps and a small one is
-  // not serialised on a few lanes.
+  // Walks per chunk: one walk per lane (32) while the request fits in the
+  // resident lanes, so its latency is its longest walk; a larger request
+  // takes about 20 expected moves per lane per chunk, fewer chunks to hand out.
   double exp_moves = (double)max_len;
   if (algo == TRW_PPR && params && params->ppr_stop > 0) exp_moves = std::min(exp_moves, 1.0 / params->ppr_stop);
   if (exp_moves < 1) exp_moves = 1;
-  uint32_t cw = (uint32_t)std::max(32.0, std::min(2048.0, 640.0 / exp_moves));
+  const int64_t lanes = (int64_t)s->grid_blocks * s->block_threads;
+  uint32_t cw = sp.nwalks <= lanes ? 32u : (uint32_t)std::max(32.0, std::min(2048.0, 640.0 / exp_moves));
   SlotRec& rec = s->slot_stage[slot];
   rec.spec = sp;
   rec.finished = 0;
   rec.cw = cw;
   rec.err = 0;
+  // Nothing below waits for the device: the sources, the slot record and
+  // then the new request count go up on the copy stream, in submission
+  // order.  The pinned record and count are not reused before the request is
+  // collected, when their copies have long completed.
   cudaStream_t cs = s->copy_stream;
-  cudaError_t e = cudaSuccess;
-  if (n_sources > 0)
-    e = cudaMemcpyAsync(s->src_pool + pos, sources, sizeof(int32_t) * (size_t)n_sources,
-                        src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->slots[slot], &rec, sizeof(SlotRec), cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-  if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit upload");
-  if (src_dev) {
-    // device sources are validated on the host side of the copy: check the pool copy
-    std::vector<int32_t> tmp((size_t)n_sources);
-    if (n_sources > 0) {
-      e = cudaMemcpy(tmp.data(), s->src_pool + pos, sizeof(int32_t) * (size_t)n_sources, cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit check");
-      for (int64_t i = 0; i < n_sources; ++i)
-        if (tmp[(size_t)i] < 0 || tmp[(size_t)i] >= s->g->nv) return trw_fail(TRW_ERR_INVALID, "source %lld out of range", (long long)i);
-    }
-  }
   s->done[slot] = 0;
   s->done_err[slot] = 0;
+  cudaError_t e = cudaSuccess;
+  if (pool_n > 0)
+    e = cudaMemcpyAsync(s->src_pool + pos, sources, sizeof(int32_t) * (size_t)pool_n, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->slots[slot], &rec, sizeof(SlotRec), cudaMemcpyHostToDevice, cs);
+  s->pub_stage[slot] = k + 1;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s->state->published, &s->pub_stage[slot], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                        cs);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit upload");
   s->req_walks[slot] = sp.nwalks;
   s->req_bytes[slot] = out_bytes;
   s->req_src_pos[slot] = pos;
-  s->req_src_n[slot] = n_sources;
+  s->req_src_n[slot] = pool_n;
   s->collected[slot] = 0;
   s->inflight_walks += sp.nwalks;
   s->inflight_bytes += out_bytes;
-  s->src_head = pos + n_sources;
+  s->src_head = pos + pool_n;
   s->next_k = k + 1;
   if (sp.nwalks == 0) {
     s->done[slot] = k + 1;  // nothing to run
   }
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  reinterpret_cast<volatile unsigned long long*>(&s->host->published)[0] = k + 1;
   std::atomic_thread_fence(std::memory_order_seq_cst);
   e = launch_if_idle(s);
   if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel launch");
@@ -805,6 +870,7 @@ static trw_status poll_locked(trw_server* s, uint64_t k) {
   s->inflight_bytes -= s->req_bytes[slot];
   retire_front(s);
   if (err == kErrRejectCap) return trw_fail(TRW_ERR_REJECT_CAP, "request %llu: a rejection step hit the cap", (unsigned long long)k);
+  if (err == kErrInvalid) return trw_fail(TRW_ERR_INVALID, "request %llu: a source vertex is outside [0, nv)", (unsigned long long)k);
   if (err != 0) return trw_fail(TRW_ERR_INTERNAL, "request %llu: device status %d", (unsigned long long)k, err);
   return TRW_OK;
 }
@@ -813,6 +879,42 @@ extern "C" trw_status trw_serve_poll(trw_server* s, uint64_t req_id) {
   if (!s) return trw_fail(TRW_ERR_INVALID, "NULL server");
   std::lock_guard<std::mutex> lk(s->mu);
   return poll_locked(s, req_id);
+}
+
+extern "C" trw_status trw_serve_reap(trw_server* s, uint64_t* ids, int32_t* statuses, int32_t max, int32_t* n_out) {
+  if (!s || !n_out || max < 0 || (max > 0 && (!ids || !statuses))) return trw_fail(TRW_ERR_INVALID, "bad arguments");
+  *n_out = 0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int32_t n = 0;
+  bool pending = false;
+  for (unsigned long long k = s->oldest; k < s->next_k && n < max; ++k) {
+    const int slot = (int)(k % (unsigned long long)s->R);
+    if (s->collected[slot]) continue;
+    const unsigned long long d = reinterpret_cast<volatile unsigned long long*>(s->done)[slot];
+    if (d != k + 1) {
+      pending = true;
+      continue;
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const int err = reinterpret_cast<volatile int*>(s->done_err)[slot];
+    s->collected[slot] = 1;
+    s->inflight_walks -= s->req_walks[slot];
+    s->inflight_bytes -= s->req_bytes[slot];
+    ids[n] = k;
+    statuses[n] = err == 0 ? TRW_OK
+                  : err == kErrRejectCap ? TRW_ERR_REJECT_CAP
+                  : err == kErrInvalid ? TRW_ERR_INVALID
+                                       : TRW_ERR_INTERNAL;
+    ++n;
+  }
+  retire_front(s);
+  *n_out = n;
+  if (pending && n == 0) {
+    cudaError_t e = launch_if_idle(s);
+    if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel relaunch");
+    if ((++s->polls & 63) == 0) return check_state(s);
+  }
+  return TRW_OK;
 }
 
 extern "C" trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms) {

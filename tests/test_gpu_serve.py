@@ -176,3 +176,44 @@ def test_serve_relaunch_after_idle(served, server_factory):
         check(g, r, op, ol)
         time.sleep(0.05)  # longer than the idle timeout: the resident kernel exits
     S.drain(10000)
+
+
+def test_serve_device_source_check_and_reap(served, server_factory):
+    """Device sources are checked at submit: an out-of-range one is refused
+    with ERR_INVALID and nothing written, while the requests around it run;
+    reap collects every finished request in one call."""
+    g, G = served
+    S = server_factory(G, max_requests=32)
+    rng = np.random.default_rng(9)
+    reqs = [make_request(g, i, rng) for i in range(12)]
+    bad_src = torch.from_numpy(synth.sources(2000, g.nv, seed=77)).cuda()
+    bad_src[1234] = g.nv
+    bad = dict(algo=trw.DEEPWALK, sources=bad_src, max_len=40, seed=3)
+    live = {}
+    for i, r in enumerate(reqs):
+        rr = dict(r, sources=torch.from_numpy(r["sources"]).cuda())
+        rid, op, ol = submit(S, rr)
+        live[rid] = (r, op, ol)
+        if i == 5:
+            bop = torch.full((2000, 41), -1, dtype=torch.int32, device="cuda")
+            bol = torch.full((2000,), -1, dtype=torch.int32, device="cuda")
+            with pytest.raises(trw.TRWError) as e:
+                S.submit(bad["algo"], bad["sources"], bad["max_len"], bad["seed"], bop, bol)
+            assert e.value.status == -1
+    statuses = {}
+    t = time.time()
+    while len(statuses) < len(live):
+        for rid, st in S.reap(max_requests=4):
+            assert rid not in statuses
+            statuses[rid] = st
+        assert time.time() - t < 60, "requests did not finish"
+        time.sleep(0.0005)
+    torch.cuda.synchronize()
+    assert bool((bol == -1).all()) and bool((bop == -1).all())
+    for rid, (r, op, ol) in live.items():
+        assert statuses[rid] == 0
+        check(g, r, op, ol)
+    assert S.reap() == []
+    with pytest.raises(trw.TRWError) as e:
+        S.poll(next(iter(live)))  # already collected by reap
+    assert e.value.status == -8
