@@ -365,14 +365,14 @@ def measure_per_algo(trw, torch, G, g, flush, sp, G_paper=None):
         row = {}
         t0 = time.time()
         tune_kw = {k: v for k, v in kw.items() if k != "endpoints"}
-        row["tuning"] = G.autotune(algo, 10, **tune_kw)
+        row["tuning"] = G.autotune(algo, L, **tune_kw)
         row["autotune_s"] = round(time.time() - t0, 2)
         for kname, kern in (("persistent", trw.KERNEL_PERSISTENT), ("plain", trw.KERNEL_PLAIN)):
             ms, moves = time_walk(trw, torch, G, flush, sp, algo, src, L, 1, kern, **kw)
             row[kname] = {"steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3), "moves": moves}
         row["speedup"] = round(row["persistent"]["steps_per_s"] / row["plain"]["steps_per_s"], 3)
         if G_paper is not None and algo in (trw.NODE2VEC, trw.METAPATH):
-            G_paper.autotune(algo, 10, **tune_kw)
+            G_paper.autotune(algo, L, **tune_kw)
             ms, moves = time_walk(trw, torch, G_paper, flush, sp, algo, src, L, 1, trw.KERNEL_PERSISTENT, **kw)
             row["paper_path"] = {"what": "binary search" if algo == trw.NODE2VEC else "label scan",
                                  "steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3),
@@ -603,7 +603,7 @@ def run_ours(args, wl):
     L = wl["max_len"]
     t = time.time()
     if not args.no_autotune:
-        G.autotune(algo, 10, **kw)
+        G.autotune(algo, wl["max_len"], **kw)
     tune_s = time.time() - t
     src_host = synth.vertex_sources(g.nv)
     n = src_host.shape[0]
@@ -779,7 +779,7 @@ def run_mixed(args, wl):
     ppr_src_h = synth.sources(1_000_000, g.nv, seed=1)
     mp_src_h = synth.vertex_sources(g.nv)
     if not args.no_autotune:
-        G.autotune(trw.METAPATH, 10, schema=schema)
+        G.autotune(trw.METAPATH, 80, schema=schema)
     reqs = [dict(algo=trw.PPR, sources=torch.from_numpy(ppr_src_h).to(dev), max_len=1000, seed=1, ppr_stop=0.2,
                  endpoints=True),
             dict(algo=trw.METAPATH, sources=torch.from_numpy(mp_src_h).to(dev), max_len=80, seed=1, schema=schema)]
@@ -841,7 +841,7 @@ def run_mixed(args, wl):
         # the same batch with the paper's per-step label scan (no index)
         Gs = trw.Graph(g.row_ptr, g.col, None, g.labels)
         if not args.no_autotune:
-            Gs.autotune(trw.METAPATH, 10, schema=schema)
+            Gs.autotune(trw.METAPATH, 80, schema=schema)
         for _ in range(2):
             flush.zero_()
             Gs.walk_batch(reqs, stream=sp)
@@ -952,7 +952,7 @@ def run_serve(args, wl):
     log(f"loaded in {load_s:.1f}s, prepared in {prep_s:.1f}s + {tables_s:.1f}s, "
         f"{G.device_bytes() / 1e9:.1f} GB on the device")
     if not args.no_autotune:
-        G.autotune(trw.DEEPWALK_WEIGHTED, 10)
+        G.autotune(trw.DEEPWALK_WEIGHTED, 80)
     # batch walk on the largest graph: 16,777,216 uniform sources x 80 moves
     n = 1 << 24
     src = torch.from_numpy(synth.sources(n, g.nv, seed=1)).to(dev)

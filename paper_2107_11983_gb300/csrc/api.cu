@@ -585,8 +585,8 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
   const bool len_dev = trw_is_device_ptr(out_lengths);
   if (!sync && (!src_dev || !out_dev || !len_dev))
     return trw_fail(TRW_ERR_INVALID, "asynchronous walks need device buffers");
-  if (!src_dev) {
-    for (int64_t i = 0; i < n_sources; ++i)
+  if (!src_dev && !trw_sources_in_range(sources, n_sources, g->nv)) {
+    for (int64_t i = 0; i < n_sources; ++i)  // name the first offender
       if (sources[i] < 0 || sources[i] >= g->nv)
         return trw_fail(TRW_ERR_INVALID, "source %lld = %d is outside [0, %lld)", (long long)i, sources[i], (long long)g->nv);
   }

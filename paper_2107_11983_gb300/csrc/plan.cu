@@ -1,10 +1,12 @@
 // Batch plans: one mixed-batch walk (the work-queue launch of
 // trw_walk_batch) captured once as a CUDA graph and replayed by a single
 // cudaGraphLaunch.  The graph holds three nodes: the reset of the plan's
-// control block, one validation kernel over every request's sources, and the
-// persistent walk kernel.  The request table lives in device memory owned by
-// the plan; trw_plan_set_seed rewrites one entry there between launches, so a
-// new seed takes effect without re-capturing.
+// control block, the source check, and the persistent walk kernel.  A plan of
+// several requests runs the mixed-batch kernel over a request table in device
+// memory owned by the plan, and trw_plan_set_seed rewrites one entry there
+// between launches.  A plan of one request runs that algorithm's own kernel
+// with the request passed by value (fewer registers than the mixed one), and
+// a new seed re-captures the graph.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -25,6 +27,9 @@ using namespace trw;
 struct trw_plan {
   trw_graph* g = nullptr;
   int32_t nreq = 0;
+  int64_t n_src0 = 0;          // one-request plans: the request's source count
+  trw::LaunchCfg cfg{};
+  trw::DevGraph dg{};
   int64_t total = 0;
   char* d_table = nullptr;   // WalkSpec[nreq] then int64 prefix[nreq + 1]
   char* h_table = nullptr;   // pinned host copy
@@ -74,6 +79,43 @@ void plan_release(trw_plan* p) {
     }                                                  \
   } while (0)
 
+// (Re)captures the plan's graph from its request table (host copy).
+static cudaError_t capture(trw_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  const WalkSpec* h_specs = reinterpret_cast<const WalkSpec*>(p->h_table);
+  const size_t spec_bytes = sizeof(WalkSpec) * (size_t)p->nreq;
+  const WalkSpec* d_specs = reinterpret_cast<const WalkSpec*>(p->d_table);
+  const int64_t* d_prefix = reinterpret_cast<const int64_t*>(p->d_table + spec_bytes);
+  int64_t max_src = 0;
+  for (int r = 0; r < p->nreq; ++r)
+    max_src = std::max<int64_t>(max_src, h_specs[r].wps ? h_specs[r].nwalks / (int64_t)h_specs[r].wps : 0);
+  int64_t vblocks = (max_src + 255) / 256;
+  if (vblocks < 1) vblocks = 1;
+  if (vblocks > 4096) vblocks = 4096;
+  cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), p->cap);
+  if (p->nreq == 1) {
+    if (e == cudaSuccess) e = launch_validate_sources(h_specs[0].sources, p->n_src0, p->dg.nv, p->ctrl, p->cap);
+    if (e == cudaSuccess && h_specs[0].nwalks > 0) e = launch_walk_persistent(p->dg, h_specs[0], p->ctrl, p->cap, p->cfg);
+  } else {
+    if (e == cudaSuccess) {
+      validate_batch<<<(unsigned)vblocks, 256, 0, p->cap>>>(d_specs, p->nreq, p->dg.nv, p->ctrl);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_walk_batch(p->dg, d_specs, d_prefix, p->nreq, p->total, p->ctrl, p->cap, p->cfg);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(p->cap, &graph);
+  p->graph = graph;
+  if (e != cudaSuccess) return e;
+  if (ec != cudaSuccess) return ec;
+  return cudaGraphInstantiate(&p->exec, p->graph, 0);
+}
+
 extern "C" trw_status trw_plan_create(trw_graph* g, int32_t n_requests, const trw_algo* algos,
                                       const trw_params* params, const int32_t* const* sources,
                                       const int64_t* n_sources, const int32_t* max_lens, const uint64_t* seeds,
@@ -113,33 +155,13 @@ extern "C" trw_status trw_plan_create(trw_graph* g, int32_t n_requests, const tr
   PLAN_CUDA(cudaMalloc((void**)&p->ctrl, sizeof(Ctrl)), "plan control block");
   PLAN_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "plan stream");
   PLAN_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming), "plan event");
-  LaunchCfg cfg;
-  DevGraph dg;
   {
     std::lock_guard<std::mutex> lk(g->mu);
-    cfg = trw_launch_cfg_batch(g, specs.data(), n_requests);
-    dg = trw_dev_graph(g);
+    p->cfg = n_requests == 1 ? trw_launch_cfg(g, specs[0].algo) : trw_launch_cfg_batch(g, specs.data(), n_requests);
+    p->dg = trw_dev_graph(g);
   }
-  const WalkSpec* d_specs = reinterpret_cast<const WalkSpec*>(p->d_table);
-  const int64_t* d_prefix = reinterpret_cast<const int64_t*>(p->d_table + spec_bytes);
-  int64_t max_src = 0;
-  for (int r = 0; r < n_requests; ++r) max_src = std::max<int64_t>(max_src, n_sources[r]);
-  int64_t vblocks = (max_src + 255) / 256;
-  if (vblocks < 1) vblocks = 1;
-  if (vblocks > 4096) vblocks = 4096;
-  PLAN_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-  cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), p->cap);
-  if (e == cudaSuccess) {
-    validate_batch<<<(unsigned)vblocks, 256, 0, p->cap>>>(d_specs, n_requests, (int32_t)g->nv, p->ctrl);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = launch_walk_batch(dg, d_specs, d_prefix, n_requests, p->total, p->ctrl, p->cap, cfg);
-  cudaGraph_t graph = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(p->cap, &graph);
-  p->graph = graph;
-  PLAN_CUDA(e, "capture batch walk");
-  PLAN_CUDA(ec, "end capture");
-  PLAN_CUDA(cudaGraphInstantiate(&p->exec, p->graph, 0), "instantiate plan");
+  p->n_src0 = n_sources[0];
+  PLAN_CUDA(capture(p), "capture plan");
   *out = p;
   return TRW_OK;
 }
@@ -154,6 +176,7 @@ extern "C" trw_status trw_plan_set_seed(trw_plan* p, int32_t request, uint64_t s
   sp->key1 = (uint32_t)(seed >> 32);
   CUDA_TRY(cudaMemcpy(reinterpret_cast<WalkSpec*>(p->d_table) + request, sp, sizeof(WalkSpec), cudaMemcpyHostToDevice),
            "plan seed");
+  if (p->nreq == 1) CUDA_TRY(capture(p), "plan re-capture");  // the request is a kernel argument
   return TRW_OK;
 }
 

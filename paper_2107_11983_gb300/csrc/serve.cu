@@ -711,13 +711,6 @@ static cudaError_t launch_if_idle(trw_server* s) {
   return cudaGetLastError();
 }
 
-// Every id in [0, nv) (branch-free, so the loop vectorises).
-static bool sources_in_range(const int32_t* src, int64_t n, int64_t nv) {
-  uint32_t bad = 0;
-  for (int64_t i = 0; i < n; ++i) bad |= (uint32_t)((uint32_t)src[i] >= (uint32_t)nv);
-  return bad == 0;
-}
-
 // Collect finished requests at the front of the ring (frees their slots and source ranges).
 static void retire_front(trw_server* s) {
   while (s->oldest < s->next_k && s->collected[s->oldest % s->R]) ++s->oldest;
@@ -734,7 +727,7 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   if (sp.nwalks > 0 && (!trw_is_device_ptr(out_paths) || !trw_is_device_ptr(out_lengths)))
     return trw_fail(TRW_ERR_INVALID, "serve outputs must be device buffers");
   const bool src_dev = trw_is_device_ptr(sources);
-  if (!src_dev && !sources_in_range(sources, n_sources, s->g->nv))
+  if (!src_dev && !trw_sources_in_range(sources, n_sources, s->g->nv))
     return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
   const int64_t out_bytes =
       (int64_t)sizeof(int32_t) * (sp.endpoints ? sp.nwalks : sp.nwalks * ((int64_t)max_len + 1)) + 4 * sp.nwalks;
@@ -781,7 +774,7 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
                                      cudaMemcpyDeviceToHost, s->copy_stream);
     if (ec == cudaSuccess) ec = cudaStreamSynchronize(s->copy_stream);
     if (ec != cudaSuccess) return trw_cuda_fail(ec, "serve source check");
-    if (!sources_in_range(s->check_buf, n_sources, s->g->nv))
+    if (!trw_sources_in_range(s->check_buf, n_sources, s->g->nv))
       return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
   }
   const unsigned long long k = s->next_k;

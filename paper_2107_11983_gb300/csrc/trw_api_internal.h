@@ -52,6 +52,13 @@ struct trw_graph {
 };
 
 trw_status trw_fail(trw_status st, const char* fmt, ...);
+
+// Every id of src[0..n) in [0, nv) (branch-free, so the loop vectorises).
+inline bool trw_sources_in_range(const int32_t* src, int64_t n, int64_t nv) {
+  uint32_t bad = 0;
+  for (int64_t i = 0; i < n; ++i) bad |= (uint32_t)((uint32_t)src[i] >= (uint32_t)nv);
+  return bad == 0;
+}
 trw_status trw_cuda_fail(cudaError_t e, const char* what);
 bool trw_is_device_ptr(const void* p);
 trw_status trw_grow(void** p, size_t* cap, size_t need);

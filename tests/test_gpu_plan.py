@@ -108,3 +108,26 @@ def test_plan_on_a_stream_and_invalid_source():
         check(g, ok[0], P.outputs[0])
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("algo", [trw.DEEPWALK_WEIGHTED, trw.NODE2VEC, trw.METAPATH], ids=["weighted", "node2vec", "metapath"])
+def test_single_request_plan(algo):
+    """A one-request plan runs the algorithm's own kernel; a seed change
+    re-captures it."""
+    g = rmat_graph(SCALE)
+    G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
+    G.prepare()
+    kw = {trw.NODE2VEC: dict(n2v_p=0.5, n2v_q=2.0), trw.METAPATH: dict(schema=np.array([2, 0, 4], np.uint8))}.get(algo, {})
+    r = dict(algo=algo, sources=synth.sources(5000, g.nv, seed=12), max_len=50, seed=31, **kw)
+    P = G.plan([r])
+    try:
+        P.launch()
+        moves = P.sync()
+        assert moves == check(g, r, P.outputs[0])
+        P.set_seed(0, 4242)
+        P.launch()
+        P.launch()
+        P.sync()
+        check(g, r, P.outputs[0], seed=4242)
+    finally:
+        P.close()
