@@ -35,7 +35,7 @@ WORKLOADS = {
     "c2": dict(name="deepwalk-weighted-alias-rmat-s22", scale=22, algo="deepwalk_weighted", max_len=80,
                sources="vertices", seed=1, tables=()),
     "c3": dict(name="node2vec-p0.5-q2-rmat-s24", scale=24, algo="node2vec", max_len=80, sources="vertices", seed=1,
-               n2v_p=0.5, n2v_q=2.0, tables=("neighbor_hash",)),
+               n2v_p=0.5, n2v_q=2.0, tables=("neighbor_hash", "row_records")),
     "c4": dict(name="mixed-ppr1M-metapath-rmat-s23", scale=23, kind="mixed", seed=1, tables=("label_index",)),
     "c5": dict(name="serve-rmat-s26-directed", scale=26, kind="serve", symmetric=False, algo="deepwalk_weighted",
                max_len=80, seed=1, tables=("row_records", "neighbor_hash")),
@@ -275,7 +275,8 @@ def run_reference(args, wl):
 
 # ------------------------------------------------------------------ roofline
 
-def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False, records=False):
+def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False, records=False,
+             kernel="walk_persistent"):
     """Roofline of the walk kernel: algorithmic bytes of one launch (the
     closed form per move where the layout fixes it, else the oracle's sector
     model measured on the CPU-baseline sample) over the kernel's event time,
@@ -302,8 +303,8 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False
     alg_bytes = moves * bpm + walks * per_walk
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(f"walk_persistent/{wl['name']}"),
-            "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "walk_persistent",
+            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(f"{kernel}/{wl['name']}"),
+            "peak_kind": f"{peak_kind} copy bandwidth", "kernel": kernel,
             "bytes_per_move": round(bpm, 2), "bytes_per_move_source": source,
             "algorithmic_bytes_per_launch": int(alg_bytes)}
     if gather is not None:
@@ -643,6 +644,7 @@ def run_ours(args, wl):
         evs[i][1].record(stream)
         G.sync(sp)  # collects the device status and the library's kernel-only event time
         kern_ms.append(G.last_stats()["kernel_ms"])
+    kernel_ran = "walk_plain" if G.last_stats()["kernel"] == trw.KERNEL_PLAIN else "walk_persistent"
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
@@ -716,7 +718,7 @@ def run_ours(args, wl):
         return
     cpu = cpu_baseline(g, wl) if ws == 1 and not args.no_cpu_baseline else None
     roof = roofline(wl, moves, n, kms, cpu, gather, value / ws, hashed=hashed,
-                    records=bool(tables & TABLE_FLAGS["row_records"]))
+                    records=bool(tables & TABLE_FLAGS["row_records"]), kernel=kernel_ran)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * dev_s / args.steps, 4), "higher_is_better": True,

@@ -68,7 +68,8 @@ typedef enum {
 
 /* Kernel choice for trw_walk_ex. */
 typedef enum {
-  TRW_KERNEL_AUTO = 0,          /* the persistent kernel */
+  TRW_KERNEL_AUTO = 0,          /* the persistent kernel; the plain one for a batch that fits in one
+                                   resident wave and needs no warp-cooperative path */
   TRW_KERNEL_PLAIN = 1,         /* baseline: one launch, one thread per walk, no refill */
   TRW_KERNEL_PERSISTENT = 2     /* persistent kernel, device work queue, refill, staging */
 } trw_kernel;
@@ -325,6 +326,8 @@ typedef struct {
   double kernel_ms;             /* device time of the walk kernel (CUDA events) */
   int32_t grid_blocks;          /* launch shape used */
   int32_t block_threads;
+  int32_t kernel;               /* TRW_KERNEL_PLAIN or TRW_KERNEL_PERSISTENT: the kernel that ran */
+  int32_t reserved;
 } trw_stats;
 trw_status trw_last_stats(const trw_graph* g, trw_stats* s);
 
@@ -409,6 +412,14 @@ trw_status trw_serve_poll(trw_server* s, uint64_t req_id);
  * has finished.  Errors: TRW_ERR_INVALID (bad arguments), TRW_ERR_CUDA,
  * TRW_ERR_INTERNAL (a failed device self-check). */
 trw_status trw_serve_reap(trw_server* s, uint64_t* ids, int32_t* statuses, int32_t max, int32_t* n_out);
+
+/* Device timeline of request req_id (tracing; the paper has no counterpart):
+ * t_ns[0] when the kernel's dispatcher took it in, t_ns[1] when a worker
+ * first loaded it (its walks start), t_ns[2] when its last walk finished, on
+ * the device's global nanosecond clock (0: not reached yet).  Valid while the
+ * request's slot has not been reused (fewer than max_requests later submits).
+ * Errors: TRW_ERR_INVALID, TRW_ERR_NOT_FOUND, TRW_ERR_CUDA. */
+trw_status trw_serve_trace(trw_server* s, uint64_t req_id, uint64_t* t_ns);
 
 /* Wait (bounded by timeout_ms) until every submitted request has finished. */
 trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms);

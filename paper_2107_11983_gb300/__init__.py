@@ -62,7 +62,8 @@ class Tuning(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("walks", ctypes.c_int64), ("moves", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
-                ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,6 +113,7 @@ _SIGS = {
                                         ctypes.c_uint64, _VP, _VP, _VP]),
     "trw_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "trw_serve_reap": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
+    "trw_serve_trace": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP]),
     "trw_serve_drain": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "trw_serve_destroy": (None, [_VP]),
     "trw_gather_ceiling": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
@@ -529,6 +531,13 @@ class Server:
             self._keep.pop(int(ids[i]), None)
             out.append((int(ids[i]), int(sts[i])))
         return out
+
+    def trace(self, rid: int) -> dict:
+        """Device timeline of a request (ns on the device clock; 0 = not yet):
+        admitted by the dispatcher, first walks started, last walk finished."""
+        t = (ctypes.c_uint64 * 3)()
+        _check(load_library().trw_serve_trace(self._h, rid, t), "trw_serve_trace")
+        return {"admit_ns": int(t[0]), "first_ns": int(t[1]), "done_ns": int(t[2])}
 
     def drain(self, timeout_ms: int = 60000):
         _check(load_library().trw_serve_drain(self._h, timeout_ms), "trw_serve_drain")

@@ -562,6 +562,7 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
   g->timed = true;
   g->last.grid_blocks = cfg.grid_blocks;
   g->last.block_threads = cfg.block_threads;
+  g->last.kernel = kernel == TRW_KERNEL_PLAIN ? TRW_KERNEL_PLAIN : TRW_KERNEL_PERSISTENT;
   CUDA_TRY(cudaStreamSynchronize(cs), "copy stream");
   return collect_status(g, stream);
 }
@@ -595,6 +596,16 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
   g->last.kernel_ms = 0;
   g->timed = false;
   if (nwalks == 0) return TRW_OK;
+  if (kernel == TRW_KERNEL_AUTO) {
+    // Refill only pays when there are more walks than resident lanes: a batch
+    // that fits in one wave of the persistent configuration (and needs no
+    // warp-cooperative path) runs the one-launch kernel, which has less to do
+    // per step.
+    const LaunchCfg cfg = trw_launch_cfg(g, sp.algo);
+    const bool coop = (sp.algo == METAPATH && cfg.coop_degree < 0x7fffffff) ||
+                      (sp.algo == NODE2VEC && cfg.search_degree < 0x7fffffff);
+    kernel = !coop && nwalks <= (int64_t)cfg.grid_blocks * cfg.block_threads ? TRW_KERNEL_PLAIN : TRW_KERNEL_PERSISTENT;
+  }
 
   const int32_t* d_src = sources;
   int32_t* d_out = out_paths;
@@ -640,6 +651,7 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
   else CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, offsetof(Ctrl, err), stream), "reset ctrl");
   if (src_dev) CUDA_TRY(launch_validate_sources(d_src, n_sources, (int32_t)g->nv, g->ctrl, stream), "validate sources");
   CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
+  g->last.kernel = kernel == TRW_KERNEL_PLAIN ? TRW_KERNEL_PLAIN : TRW_KERNEL_PERSISTENT;
   if (kernel == TRW_KERNEL_PLAIN) {
     CUDA_TRY(launch_walk_plain(dg, sp, g->ctrl, stream, 256), "plain walk launch");
     g->last.grid_blocks = (int32_t)((nwalks + 255) / 256);
@@ -728,6 +740,7 @@ extern "C" trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw
            "batch walk launch");
   CUDA_TRY(cudaEventRecord(g->ev1, stream), "event");
   g->timed = true;
+  g->last.kernel = TRW_KERNEL_PERSISTENT;
   g->last.grid_blocks = cfg.grid_blocks;
   g->last.block_threads = cfg.block_threads;
   if (!sync) return TRW_OK;

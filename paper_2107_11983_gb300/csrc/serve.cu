@@ -75,6 +75,9 @@ struct SlotRec {
   unsigned long long finished;    // walks finished (zero at submit)
   uint32_t cw;                    // walks per chunk
   int err;                        // first error of the request (zero at submit)
+  unsigned long long t_admit;     // device clock (ns): the dispatcher took the request in
+  unsigned long long t_first;     // a worker loaded its descriptor (first walks start)
+  unsigned long long t_done;      // its last walk finished
 };
 
 struct ServeHost {        // host-mapped pinned memory
@@ -151,6 +154,7 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
       while (n_act < kMaxActive && disp_next < P) {
         const int slot = (int)(disp_next % (unsigned long long)sv.R);
         const unsigned long long n = (unsigned long long)__ldcg(&sv.slots[slot].spec.nwalks);
+        sv.slots[slot].t_admit = (unsigned long long)now_ns();
         if (n > 0) {
           act->k[n_act] = disp_next;
           act->pos[n_act] = 0;
@@ -420,6 +424,7 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
         if (tgt < 0) break;
         int bad = 0;
         if (lane == 0) {
+          atomicCAS(&sv.slots[(int)(pk % (unsigned long long)sv.R)].t_first, 0ull, (unsigned long long)now_ns());
           load_spec(&sv.slots[(int)(pk % (unsigned long long)sv.R)].spec, &spec[tgt]);
           bad = spec_check(spec[tgt], pk, pb, pe, ld_acquire_gpu(&sv.state->published));
           if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec[tgt].nwalks,
@@ -533,6 +538,7 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
           const unsigned long long cnt = (unsigned long long)__popc(fin);
           const unsigned long long old = atomicAdd(&sv.slots[slot].finished, cnt);
           if (old + cnt == (unsigned long long)spec[e].nwalks) {
+            sv.slots[slot].t_done = (unsigned long long)now_ns();
             __threadfence();
             const int err = atomicAdd(&sv.slots[slot].err, 0);
             sv.done_err[slot] = err;
@@ -795,6 +801,7 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   rec.finished = 0;
   rec.cw = cw;
   rec.err = 0;
+  rec.t_admit = rec.t_first = rec.t_done = 0;
   // Nothing below waits for the device: the sources, the slot record and
   // then the new request count go up on the copy stream, in submission
   // order.  The pinned record and count are not reused before the request is
@@ -907,6 +914,20 @@ extern "C" trw_status trw_serve_reap(trw_server* s, uint64_t* ids, int32_t* stat
     if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel relaunch");
     if ((++s->polls & 63) == 0) return check_state(s);
   }
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_serve_trace(trw_server* s, uint64_t req_id, uint64_t* t_ns) {
+  if (!s || !t_ns) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (req_id >= s->next_k || req_id + (unsigned long long)s->R < s->next_k)
+    return trw_fail(TRW_ERR_NOT_FOUND, "request %llu is not in the slot table", (unsigned long long)req_id);
+  const int slot = (int)(req_id % (unsigned long long)s->R);
+  unsigned long long t[3];
+  cudaError_t e = cudaMemcpyAsync(t, &s->slots[slot].t_admit, sizeof(t), cudaMemcpyDeviceToHost, s->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "serve trace");
+  for (int i = 0; i < 3; ++i) t_ns[i] = t[i];
   return TRW_OK;
 }
 

@@ -381,3 +381,20 @@ def test_pinned_host_outputs(small, algo):
     h_end = torch.full((src.shape[0],), -1, dtype=torch.int32).pin_memory()
     G.walk(algo, h_src.numpy(), L, seed=18, endpoints=True, out_paths=h_end.numpy(), out_lengths=h_len.numpy(), **kw)
     assert_paths_equal(h_end.numpy(), h_len.numpy(), want, endpoints=True)
+
+
+def test_auto_kernel_choice(small):
+    """KERNEL_AUTO runs the one-launch kernel for a batch that fits in one
+    resident wave, the persistent kernel beyond it; results are the oracle's
+    either way."""
+    g, G = small
+    few = synth.sources(100, g.nv, seed=41)
+    out = G.walk(trw.DEEPWALK, few, 30, seed=3)
+    assert G.last_stats()["kernel"] == trw.KERNEL_PLAIN
+    assert_paths_equal(out.paths, out.lengths, oracle_walk(g, trw.DEEPWALK, few, 30, seed=3))
+    many = synth.sources(2_000_000, g.nv, seed=42)
+    out = G.walk(trw.PPR, torch.from_numpy(many).cuda(), 50, seed=4, ppr_stop=0.2, endpoints=True)
+    torch.cuda.synchronize()
+    assert G.last_stats()["kernel"] == trw.KERNEL_PERSISTENT
+    want = oracle_walk(g, trw.PPR, many, 50, seed=4, ppr_stop=0.2, endpoints_only=True)
+    assert_paths_equal(out.paths.cpu().numpy(), out.lengths.cpu().numpy(), want, endpoints=True)

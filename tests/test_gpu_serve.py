@@ -217,3 +217,21 @@ def test_serve_device_source_check_and_reap(served, server_factory):
     with pytest.raises(trw.TRWError) as e:
         S.poll(next(iter(live)))  # already collected by reap
     assert e.value.status == -8
+
+
+def test_serve_trace_timeline(served, server_factory):
+    """Every served request carries a device timeline: admitted, started and
+    finished, in that order."""
+    g, G = served
+    S = server_factory(G, max_requests=16)
+    rng = np.random.default_rng(11)
+    reqs = [make_request(g, i, rng) for i in range(6)]
+    live = [(r,) + submit(S, r) for r in reqs]
+    for r, rid, op, ol in live:
+        wait(S, rid)
+        check(g, r, op, ol)
+        t = S.trace(rid)
+        assert 0 < t["admit_ns"] <= t["first_ns"] <= t["done_ns"], t
+    with pytest.raises(trw.TRWError) as e:
+        S.trace(10 ** 6)
+    assert e.value.status == -8
