@@ -119,6 +119,10 @@ static void graph_release(trw_graph* g) {
     if (g->ev_copied[b]) cudaEventDestroy(g->ev_copied[b]);
   }
   if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+  if (g->stream2) cudaStreamDestroy(g->stream2);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  cudaFree(g->ctrl2);
   if (g->stream) cudaStreamDestroy(g->stream);
   delete g;
 }
@@ -183,6 +187,9 @@ extern "C" trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_
   } while (0)
   LOAD_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking), "cudaStreamCreate");
   LOAD_CUDA(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  LOAD_CUDA(cudaStreamCreateWithFlags(&g->stream2, cudaStreamNonBlocking), "cudaStreamCreate");
+  LOAD_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+  LOAD_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "cudaEventCreate");
   for (int b = 0; b < 2; ++b) {
     LOAD_CUDA(cudaEventCreateWithFlags(&g->ev_walked[b], cudaEventDisableTiming), "cudaEventCreate");
     LOAD_CUDA(cudaEventCreateWithFlags(&g->ev_copied[b], cudaEventDisableTiming), "cudaEventCreate");
@@ -192,6 +199,7 @@ extern "C" trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_
   LOAD_TRY(alloc_dev((void**)&g->row_ptr, sizeof(int32_t) * ((size_t)nv + 1), "row_ptr"));
   LOAD_TRY(alloc_dev((void**)&g->col, sizeof(int32_t) * ((size_t)ne + 4), "col"));
   LOAD_TRY(alloc_dev((void**)&g->ctrl, sizeof(Ctrl), "ctrl"));
+  LOAD_TRY(alloc_dev((void**)&g->ctrl2, sizeof(Ctrl), "ctrl"));
   LOAD_TRY(alloc_dev((void**)&g->misc, 256, "misc"));
   LOAD_CUDA(cudaMemcpy(g->row_ptr, rp32.data(), sizeof(int32_t) * ((size_t)nv + 1), cudaMemcpyHostToDevice), "copy row_ptr");
   if (ne > 0) LOAD_CUDA(cudaMemcpy(g->col, col, sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice), "copy col");
@@ -512,9 +520,12 @@ static trw_status collect_status(trw_graph* g, cudaStream_t stream) {
 static constexpr int64_t kSliceWalks = 1 << 19;
 
 // The synchronous walk of trw_walk_ex with host outputs, sliced: slice i walks
-// into staging buffer i % 2 on `stream`; its paths and lengths are copied to
-// the host on the graph's copy stream while slice i + 1 walks; slice i + 2
-// waits until the copy of slice i has drained its buffer.
+// into staging buffer b = i % 2 on compute stream b (the caller's stream or
+// the graph's second one, each with its own control block), so that the
+// blocks of slice i + 1 start on the SMs that slice i's tail leaves idle; its
+// paths and lengths are copied to the host on the graph's copy stream while
+// the next slices walk; slice i + 2 waits until the copy of slice i has
+// drained its buffer.
 static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, const int32_t* d_src, int64_t n_sources,
                               int64_t row, int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream) {
   const int64_t wps = (int64_t)sp.wps;
@@ -531,11 +542,17 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
   const DevGraph dg = trw_dev_graph(g);
   const LaunchCfg cfg = trw_launch_cfg(g, sp.algo);
   cudaStream_t cs = g->copy_stream;
+  cudaStream_t ks[2] = {stream, g->stream2};
+  Ctrl* kc[2] = {g->ctrl, g->ctrl2};
   CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), stream), "reset ctrl");
+  CUDA_TRY(cudaMemsetAsync(g->ctrl2, 0, sizeof(Ctrl), stream), "reset ctrl");
   CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
+  CUDA_TRY(cudaEventRecord(g->ev_fork, stream), "event");
+  CUDA_TRY(cudaStreamWaitEvent(g->stream2, g->ev_fork, 0), "fork");
   int64_t done_src = 0;
   for (int64_t i = 0; done_src < n_sources; ++i) {
     const int b = (int)(i & 1);
+    cudaStream_t kst = ks[b];
     const int64_t s0 = done_src, s1 = std::min(n_sources, s0 + src_per);
     WalkSpec sl = sp;
     sl.sources = d_src + s0;
@@ -543,11 +560,11 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
     sl.walk_offset = sp.walk_offset + (uint32_t)(s0 * wps);
     sl.out_paths = g->out_stage + (size_t)b * (size_t)(walks_per * row);
     sl.out_lengths = g->len_stage + (size_t)b * (size_t)walks_per;
-    if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(stream, g->ev_copied[b], 0), "wait for a drained buffer");
-    CUDA_TRY(cudaMemsetAsync(&g->ctrl->head, 0, sizeof(unsigned long long), stream), "reset queue");
-    if (kernel == TRW_KERNEL_PLAIN) CUDA_TRY(launch_walk_plain(dg, sl, g->ctrl, stream, 256), "plain walk launch");
-    else CUDA_TRY(launch_walk_persistent(dg, sl, g->ctrl, stream, cfg), "persistent walk launch");
-    CUDA_TRY(cudaEventRecord(g->ev_walked[b], stream), "event");
+    if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(kst, g->ev_copied[b], 0), "wait for a drained buffer");
+    CUDA_TRY(cudaMemsetAsync(&kc[b]->head, 0, sizeof(unsigned long long), kst), "reset queue");
+    if (kernel == TRW_KERNEL_PLAIN) CUDA_TRY(launch_walk_plain(dg, sl, kc[b], kst, 256), "plain walk launch");
+    else CUDA_TRY(launch_walk_persistent(dg, sl, kc[b], kst, cfg), "persistent walk launch");
+    CUDA_TRY(cudaEventRecord(g->ev_walked[b], kst), "event");
     CUDA_TRY(cudaStreamWaitEvent(cs, g->ev_walked[b], 0), "wait for a walked slice");
     CUDA_TRY(cudaMemcpyAsync(out_paths + s0 * wps * row, sl.out_paths, sizeof(int32_t) * (size_t)(sl.nwalks * row),
                              cudaMemcpyDeviceToHost, cs),
@@ -558,13 +575,25 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
     CUDA_TRY(cudaEventRecord(g->ev_copied[b], cs), "event");
     done_src = s1;
   }
+  CUDA_TRY(cudaEventRecord(g->ev_join, g->stream2), "event");
+  CUDA_TRY(cudaStreamWaitEvent(stream, g->ev_join, 0), "join");
   CUDA_TRY(cudaEventRecord(g->ev1, stream), "event");
   g->timed = true;
   g->last.grid_blocks = cfg.grid_blocks;
   g->last.block_threads = cfg.block_threads;
   g->last.kernel = kernel == TRW_KERNEL_PLAIN ? TRW_KERNEL_PLAIN : TRW_KERNEL_PERSISTENT;
   CUDA_TRY(cudaStreamSynchronize(cs), "copy stream");
-  return collect_status(g, stream);
+  // the second control block's moves and status join the first's
+  Ctrl c2;
+  CUDA_TRY(cudaStreamSynchronize(stream), "walk kernel");
+  CUDA_TRY(cudaMemcpy(&c2, g->ctrl2, sizeof(Ctrl), cudaMemcpyDeviceToHost), "read status");
+  trw_status rs = collect_status(g, stream);
+  g->last.moves += (int64_t)c2.moves;
+  if (rs != TRW_OK) return rs;
+  if (c2.err == kErrRejectCap) return trw_fail(TRW_ERR_REJECT_CAP, "a rejection step exceeded %d trials", TRW_REJECT_CAP);
+  if (c2.err == kErrInvalid) return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
+  if (c2.err != 0) return trw_fail(TRW_ERR_INTERNAL, "device status %d", c2.err);
+  return TRW_OK;
 }
 
 extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,

@@ -43,6 +43,9 @@ struct trw_graph {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
   cudaStream_t copy_stream = nullptr;              // copy-out of sliced walks
+  cudaStream_t stream2 = nullptr;                  // odd slices of sliced walks (tails overlap)
+  trw::Ctrl* ctrl2 = nullptr;                      // their control block
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_walked[2] = {nullptr, nullptr};   // slice walked into staging buffer b
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};   // staging buffer b copied out
   trw_tuning tuning{};
