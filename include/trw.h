@@ -148,13 +148,13 @@ void trw_graph_free(trw_graph* g);
  * Preparing an index that exists already does nothing.
  *
  * TRW_PREP_NEIGHBOR_HASH (not in the paper, whose Node2Vec IsNeighbor is a
- * binary search in the sorted row of the previous vertex, Section 4): the
- * edges of every row of at least TRW_NEIGHBOR_HASH_MIN_DEGREE entries go
- * into an open-addressing hash table of 32-byte buckets (16 bytes of table
- * per edge at most, load <= 1/2), and IsNeighbor(c, prev) for such a row
- * reads about one bucket instead of log2(d_prev) row entries.  Membership is
- * exact, so every walk is identical with and without it.  Preparing a hash
- * that exists already does nothing.
+ * binary search in the sorted row of the previous vertex, Section 4): every
+ * row of at least TRW_NEIGHBOR_HASH_MIN_DEGREE entries gets an
+ * open-addressing hash table of its neighbours (2 d slots at load 1/2, laid
+ * out like the rows: 8 bytes of device memory per edge), and IsNeighbor(c,
+ * prev) for such a row reads about one sector instead of log2(d_prev) row
+ * entries.  Membership is exact, so every walk is identical with and without
+ * it.  Preparing a hash that exists already does nothing.
  *
  * TRW_PREP_ROW_RECORDS (not in the paper, whose NAIVE move reads the row of
  * the current vertex and then one edge of it, Section 2.3): a 16-byte record

@@ -256,8 +256,6 @@ DevGraph trw_dev_graph(const trw_graph* g) {
   d.lidx.stride = g->lstride;
   d.lidx.nl = g->lnl;
   d.nh.slots = g->nh_slots;
-  d.nh.mask = g->nh_mask;
-  d.nh.max_probe = g->nh_max_probe;
   d.nh.min_degree = TRW_NEIGHBOR_HASH_MIN_DEGREE;
   d.nv = (int32_t)g->nv;
   d.ne = (int32_t)g->ne;
@@ -341,20 +339,17 @@ static trw_status prepare_label_index(trw_graph* g) {
 
 static trw_status prepare_neighbor_hash(trw_graph* g) {
   if (g->nh_slots) return TRW_OK;
-  unsigned long long* slots = nullptr;
-  unsigned long long mask = 0;
-  int32_t probe = 0;
-  size_t bytes = 0;
-  cudaError_t e = launch_neighbor_hash((int32_t)g->nv, g->ne, g->row_ptr, g->col, TRW_NEIGHBOR_HASH_MIN_DEGREE, &slots,
-                                       &mask, &probe, &bytes, g->stream);
-  if (e == cudaErrorMemoryAllocation) {
-    cudaGetLastError();
-    return trw_fail(TRW_ERR_OOM, "out of device memory for the neighbour hash");
+  int32_t* slots = nullptr;
+  const size_t bytes = sizeof(int32_t) * 2 * (size_t)g->ne;
+  trw_status st = alloc_dev((void**)&slots, bytes, "neighbour hash");
+  if (st != TRW_OK) return st;
+  const cudaError_t e =
+      launch_neighbor_hash((int32_t)g->nv, g->ne, g->row_ptr, g->col, TRW_NEIGHBOR_HASH_MIN_DEGREE, slots, g->stream);
+  if (e != cudaSuccess) {
+    cudaFree(slots);
+    return trw_cuda_fail(e, "prepare neighbour hash");
   }
-  if (e != cudaSuccess) return trw_cuda_fail(e, "prepare neighbour hash");
   g->nh_slots = slots;
-  g->nh_mask = mask;
-  g->nh_max_probe = probe;
   g->device_bytes += (int64_t)bytes;
   return TRW_OK;
 }

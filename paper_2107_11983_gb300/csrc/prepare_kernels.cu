@@ -362,47 +362,26 @@ __global__ void __launch_bounds__(kPrepThreads) prepare_alias_kernel(
   }
 }
 
-// Edges in rows of at least min_degree entries (count[0]).
-__global__ void count_hash_edges(int32_t nv, const int32_t* __restrict__ row_ptr, int32_t min_degree,
-                                 unsigned long long* count) {
-  unsigned long long c = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t d = row_ptr[v + 1] - row_ptr[v];
-    if (d >= min_degree) c += (unsigned long long)d;
+// Inserts neighbour v into the table of cap slots at tab: the first empty
+// slot from slot_of(v, cap) on, wrapping; probe[0] flags a table found full
+// (cannot happen at load 1/2).
+__device__ __forceinline__ void row_hash_insert(int32_t* tab, uint32_t cap, int32_t v, unsigned int* probe) {
+  uint32_t b = slot_of(v, cap);
+  for (uint32_t n = 0; n < cap; ++n) {
+    const int32_t old = atomicCAS(tab + b, kHashEmpty, v);
+    if (old == kHashEmpty || old == v) return;
+    b = b + 1 == cap ? 0u : b + 1;
   }
-  c = warp_sum64(c);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
-}
-
-// Inserts key (u, v): the first empty slot from the key's bucket on, bucket by
-// bucket; probe[0] keeps the longest sequence (in buckets), probe[1] flags a
-// sequence that visited every bucket.
-__device__ __forceinline__ void hash_insert(unsigned long long* slots, unsigned long long mask, int32_t u, int32_t v,
-                                            unsigned int* probe) {
-  const unsigned long long key = edge_key(u, v);
-  unsigned long long b = mix64(key) & mask;
-  for (unsigned long long n = 1;; ++n) {
-    for (int k = 0; k < 4; ++k) {
-      const unsigned long long old = atomicCAS(slots + (b << 2) + k, kHashEmpty, key);
-      if (old == kHashEmpty || old == key) {
-        atomicMax(probe, (unsigned int)n);
-        return;
-      }
-    }
-    if (n > mask) {
-      atomicExch(probe + 1, 1u);
-      return;
-    }
-    b = (b + 1) & mask;
-  }
+  atomicExch(probe, 1u);
 }
 
 // Same schedule as the alias preparation: rows of kBigRow edges or more by
-// whole blocks, largest first, then the other rows one warp each.
+// whole blocks, largest first, then the other rows one warp each.  Each row
+// fills only its own table, which the warp or block has just cleared, so the
+// compare-and-swaps stay in L2.
 __global__ void __launch_bounds__(kPrepThreads) hash_insert_kernel(
     int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int32_t min_degree,
-    const int32_t* __restrict__ big, int32_t nbig, unsigned int* counters, unsigned long long* slots,
-    unsigned long long mask, unsigned int* probe) {
+    const int32_t* __restrict__ big, int32_t nbig, unsigned int* counters, int32_t* slots, unsigned int* probe) {
   __shared__ int32_t s_r;
   for (;;) {
     if (threadIdx.x == 0) s_r = (int32_t)atomicAdd(&counters[0], 1u);
@@ -413,7 +392,11 @@ __global__ void __launch_bounds__(kPrepThreads) hash_insert_kernel(
     const int32_t v = big[r];
     const int32_t off = row_ptr[v], d = row_ptr[v + 1] - off;
     if (d < min_degree) continue;
-    for (int32_t j = threadIdx.x; j < d; j += kPrepThreads) hash_insert(slots, mask, v, col[off + j], probe);
+    int32_t* tab = slots + 2 * (int64_t)off;
+    for (int32_t j = threadIdx.x; j < 2 * d; j += kPrepThreads) tab[j] = kHashEmpty;
+    __syncthreads();
+    for (int32_t j = threadIdx.x; j < d; j += kPrepThreads) row_hash_insert(tab, 2u * (uint32_t)d, col[off + j], probe);
+    __syncthreads();
   }
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -425,7 +408,11 @@ __global__ void __launch_bounds__(kPrepThreads) hash_insert_kernel(
     for (int32_t v = (int32_t)base; v < end; ++v) {
       const int32_t off = row_ptr[v], d = row_ptr[v + 1] - off;
       if (d < min_degree || d >= kBigRow) continue;
-      for (int32_t j = lane; j < d; j += 32) hash_insert(slots, mask, v, col[off + j], probe);
+      int32_t* tab = slots + 2 * (int64_t)off;
+      for (int32_t j = lane; j < 2 * d; j += 32) tab[j] = kHashEmpty;
+      __syncwarp();
+      for (int32_t j = lane; j < d; j += 32) row_hash_insert(tab, 2u * (uint32_t)d, col[off + j], probe);
+      __syncwarp();
     }
   }
 }
@@ -625,54 +612,26 @@ cudaError_t launch_prepare_alias(int32_t nv, int64_t ne, const int32_t* row_ptr,
 }
 
 cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
-                                 int32_t min_degree, unsigned long long** slots_out, unsigned long long* mask_out,
-                                 int32_t* max_probe_out, size_t* bytes_out, cudaStream_t st) {
-  *slots_out = nullptr;
-  *mask_out = 0;
-  *max_probe_out = 0;
-  *bytes_out = 0;
-  unsigned long long* d_count = nullptr;
-  cudaError_t e = cudaMalloc(&d_count, sizeof(unsigned long long) * 2);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 2, st);
-  int64_t blocks = ((int64_t)nv + 255) / 256;
-  if (blocks > 65535) blocks = 65535;
-  if (e == cudaSuccess && nv > 0) {
-    count_hash_edges<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, min_degree, d_count);
-    e = cudaGetLastError();
-  }
-  unsigned long long count = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  // buckets: a power of two with at least twice the keys' slots (load <= 1/2)
-  unsigned long long nb = 1;
-  while (nb * 4 < 2 * count) nb <<= 1;
-  unsigned long long* slots = nullptr;
-  if (e == cudaSuccess) e = cudaMalloc(&slots, sizeof(unsigned long long) * 4 * nb);
-  if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0xff, sizeof(unsigned long long) * 4 * nb, st);
+                                 int32_t min_degree, int32_t* slots, cudaStream_t st) {
+  if (nv <= 0 || ne <= 0) return cudaSuccess;
+  unsigned int* d_probe = nullptr;
+  cudaError_t e = cudaMalloc(&d_probe, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_probe, 0, sizeof(unsigned int), st);
   BigRows br;
-  if (e == cudaSuccess && nv > 0) e = collect_big(nv, ne, row_ptr, st, br);
+  if (e == cudaSuccess) e = collect_big(nv, ne, row_ptr, st, br);
   unsigned grid = 1;
   if (e == cudaSuccess) e = persistent_grid(hash_insert_kernel, kPrepThreads, &grid);
-  if (e == cudaSuccess && nv > 0 && count > 0) {
-    unsigned int* probe = reinterpret_cast<unsigned int*>(d_count + 1);
+  if (e == cudaSuccess) {
     hash_insert_kernel<<<grid, kPrepThreads, 0, st>>>(nv, row_ptr, col, min_degree, br.list, (int32_t)br.n,
-                                                      br.counters, slots, nb - 1, probe);
+                                                      br.counters, slots, d_probe);
     e = cudaGetLastError();
   }
-  unsigned int probes[2] = {0, 0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(probes, d_count + 1, sizeof(probes), cudaMemcpyDeviceToHost, st);
+  unsigned int full = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&full, d_probe, sizeof(full), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(d_count);
-  if (e == cudaSuccess && probes[1] != 0) e = cudaErrorUnknown;  // a probe ran past every bucket: cannot happen
-  if (e != cudaSuccess) {
-    cudaFree(slots);
-    return e;
-  }
-  *slots_out = slots;
-  *mask_out = nb - 1;
-  *max_probe_out = (int32_t)(probes[0] > 0 ? probes[0] : 1);
-  *bytes_out = sizeof(unsigned long long) * 4 * nb;
-  return cudaSuccess;
+  cudaFree(d_probe);
+  if (e == cudaSuccess && full != 0) e = cudaErrorUnknown;  // a table found full: cannot happen at load 1/2
+  return e;
 }
 
 cudaError_t launch_label_max(const uint8_t* labels, int64_t ne, unsigned int* d_out, cudaStream_t st) {

@@ -26,9 +26,7 @@ struct trw_graph {
   int32_t lstride = 0;
   int32_t lnl = 0;                   // labels in the index (largest label + 1)
   int4* rrec = nullptr;              // row records (trw_prepare(ROW_RECORDS))
-  unsigned long long* nh_slots = nullptr;  // neighbour hash (trw_prepare(NEIGHBOR_HASH))
-  unsigned long long nh_mask = 0;
-  int32_t nh_max_probe = 0;
+  int32_t* nh_slots = nullptr;       // neighbour hash (trw_prepare(NEIGHBOR_HASH)): 2 ne int32
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags
   int32_t* src_stage = nullptr;      // staging for host buffers (grow-only)

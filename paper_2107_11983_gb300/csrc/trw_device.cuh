@@ -46,32 +46,32 @@ struct LabelIndex {
 };
 
 // Neighbour hash (an optional preparation; walks are identical with and
-// without it): the edges (u, v) of every row u of at least min_degree entries
-// as 64-bit keys u << 32 | v in an open-addressing table of 4-key buckets
-// (one 32-byte sector), probed bucket by bucket from mix64(key) & mask.
-// Keys fill each bucket from its first slot, so a lookup that meets an empty
-// slot is done; max_probe bounds the buckets any lookup visits.
+// without it).  Every row u of at least min_degree entries owns an
+// open-addressing table of 2 d(u) int32 slots at offset 2 row_ptr[u] of one
+// array (so a lookup needs only the row it already holds): each neighbour v
+// sits in the first empty slot at or after slot_of(v, 2 d(u)), wrapping
+// within the row's table; empty slots hold -1, and the load factor is 1/2.
 struct NeighborHash {
-  const unsigned long long* __restrict__ slots;  // [(mask + 1) * 4], or null when not prepared
-  unsigned long long mask;                       // buckets - 1 (a power of two minus one)
-  int32_t max_probe;                             // longest probe sequence of the build, in buckets
-  int32_t min_degree;                            // rows shorter than this are searched in place
+  const int32_t* __restrict__ slots;     // [2 ne], or null when not prepared
+  int32_t min_degree;                    // rows shorter than this are searched in place
 };
 
-constexpr unsigned long long kHashEmpty = 0xffffffffffffffffull;
+constexpr int32_t kHashEmpty = -1;
 
-// MurmurHash3's 64-bit finaliser (Appleby): a bijective mix of the key bits.
-__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
+// MurmurHash3's 32-bit finaliser (Appleby): a bijective mix of the key bits.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t k) {
+  k ^= k >> 16;
+  k *= 0x85ebca6bu;
+  k ^= k >> 13;
+  k *= 0xc2b2ae35u;
+  k ^= k >> 16;
   return k;
 }
 
-__device__ __forceinline__ unsigned long long edge_key(int32_t u, int32_t v) {
-  return ((unsigned long long)(uint32_t)u << 32) | (uint32_t)v;
+// First probe of key v in a table of cap slots: the mixed key scaled to
+// [0, cap) by a 32x32-bit high product.
+__host__ __device__ __forceinline__ uint32_t slot_of(int32_t v, uint32_t cap) {
+  return (uint32_t)(((uint64_t)mix32((uint32_t)v) * cap) >> 32);
 }
 
 // A CSR graph resident in HBM.  Offsets and ids are int32 (nv, ne < 2^31).

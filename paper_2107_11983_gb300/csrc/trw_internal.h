@@ -42,12 +42,10 @@ cudaError_t launch_prepare_labels(int32_t nv, int64_t ne, const int32_t* row_ptr
                                   const uint8_t* labels, int32_t nl, int32_t stride, int32_t* vrec, int32_t* erec,
                                   cudaStream_t st);
 
-// Neighbour hash (NeighborHash) of the rows of at least min_degree entries:
-// allocates the table (*slots_out, *bytes_out bytes; the caller frees it) and
-// reports its mask and longest probe sequence; synchronises st.
+// Neighbour hash (NeighborHash) of the rows of at least min_degree entries,
+// built into slots (2 ne int32, allocated by the caller); synchronises st.
 cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
-                                 int32_t min_degree, unsigned long long** slots_out, unsigned long long* mask_out,
-                                 int32_t* max_probe_out, size_t* bytes_out, cudaStream_t st);
+                                 int32_t min_degree, int32_t* slots, cudaStream_t st);
 
 // Row records {col[e], row_ptr[col[e]], deg(col[e]), 0} of every edge slot.
 cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, int4* rec, cudaStream_t st);

@@ -124,23 +124,24 @@ __device__ __forceinline__ bool is_neighbor_serial(const int32_t* __restrict__ c
   return lo < pd && ldg(col + poff + lo) == c;
 }
 
-// IsNeighbor(c, u) by the neighbour hash: one bucket (one sector) per probe.
-__device__ __forceinline__ bool is_neighbor_hashed(const NeighborHash& h, int32_t u, int32_t c) {
-  const unsigned long long key = edge_key(u, c);
-  unsigned long long b = mix64(key) & h.mask;
-  for (int32_t probe = 0; probe < h.max_probe; ++probe) {
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(h.slots + (b << 2));
-    const ulonglong2 s0 = __ldg(p), s1 = __ldg(p + 1);
-    if (s0.x == key || s0.y == key || s1.x == key || s1.y == key) return true;
-    if (s0.x == kHashEmpty || s0.y == kHashEmpty || s1.x == kHashEmpty || s1.y == kHashEmpty) return false;
-    b = (b + 1) & h.mask;
+// IsNeighbor(c, u) by u's table of the neighbour hash (u's row at poff,
+// pd entries): about 1.5 probes, nearly always within one sector.
+__device__ __forceinline__ bool is_neighbor_hashed(const NeighborHash& h, int32_t poff, int32_t pd, int32_t c) {
+  const uint32_t cap = 2u * (uint32_t)pd;
+  const int32_t* tab = h.slots + 2 * (int64_t)poff;
+  uint32_t b = slot_of(c, cap);
+  for (uint32_t probe = 0; probe < cap; ++probe) {
+    const int32_t v = ldg(tab + b);
+    if (v == c) return true;
+    if (v == kHashEmpty) return false;
+    b = b + 1 == cap ? 0u : b + 1;
   }
   return false;
 }
 
 // IsNeighbor(c, prev): the hash for rows it holds, else the row's binary search.
 __device__ __forceinline__ bool is_neighbor(const DevGraph& g, int32_t prev, int32_t poff, int32_t pd, int32_t c) {
-  if (g.nh.slots && pd >= g.nh.min_degree) return is_neighbor_hashed(g.nh, prev, c);
+  if (g.nh.slots && pd >= g.nh.min_degree) return is_neighbor_hashed(g.nh, poff, pd, c);
   return is_neighbor_serial(g.col, poff, pd, c);
 }
 
