@@ -484,7 +484,9 @@ LaunchCfg trw_launch_cfg_batch(const trw_graph* g, const WalkSpec* specs, int n)
   int bps = g->tuning.blocks_per_sm;
   if (bps <= 0 || bps > occ) bps = occ;
   c.grid_blocks = g->num_sms * bps;
-  c.chunk = g->tuning.chunk;
+  // A claim of a mixed batch also looks up each walk's request: a warp takes
+  // at least one walk per lane per claim, whatever a single-algorithm tuning chose.
+  c.chunk = std::max(32, g->tuning.chunk);
   c.coop_degree = g->tuning.coop_degree;
   c.search_degree = g->nh_slots ? 0x7fffffff : g->tuning.search_degree;
   c.batch_coop = coop;
