@@ -513,6 +513,38 @@ def measure_serve(trw, torch, G, g, n_requests=3000, rate=2000.0):
     return out
 
 
+def serve_cpu_baseline(g, seconds: float = 12.0):
+    """The oracle on a bounded sample of the serving trace: the PPR and
+    Node2Vec requests in arrival order, at most 2000 walks of each, until about
+    `seconds` of walking (weighted DeepWalk requests are left out: the
+    oracle's alias preparation of the 1.06B-edge graph alone outlasts the
+    budget)."""
+    import oracle
+
+    _, reqs = serve_trace(g, 3000, 2000.0)
+    moves, walks, used, dt = 0, 0, 0, 0.0
+    for r in reqs:
+        if r["algo"] == 1:
+            continue
+        wps = r.get("walks_per_source", 1)
+        n_src = max(1, min(r["sources"].shape[0], 2000 // wps))
+        kw = {k: v for k, v in r.items() if k in ("ppr_stop", "n2v_p", "n2v_q")}
+        t = time.perf_counter()
+        res = oracle.walk(g.row_ptr, g.col, {2: oracle.PPR, 3: oracle.NODE2VEC}[r["algo"]], r["sources"][:n_src],
+                          r["max_len"], r["seed"], walks_per_source=min(wps, 2000), endpoints_only=r.get("endpoints", False),
+                          **kw)
+        dt += time.perf_counter() - t
+        assert res.status == 0
+        moves += res.stats["moves"]
+        walks += n_src * min(wps, 2000)
+        used += 1
+        if dt > seconds:
+            break
+    return {"value": moves / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{used} PPR and Node2Vec requests of the trace in arrival order, at most 2000 walks each "
+                      f"({walks} walks, {moves} moves), single-threaded oracle, {dt:.1f}s walking"}
+
+
 def measure_replay(trw, torch, G, sp, algo, src, L, seed, kw, k=50):
     """Back-to-back steps with no L2 flush between them: one CUDA-graph replay
     of a captured plan per step against one library call per step (the
@@ -998,7 +1030,7 @@ def run_serve(args, wl):
     line["e2e"] = {"value": serve["served"]["steps_per_s"], "unit": UNIT, "h2d_bytes_per_step": None,
                    "d2h_bytes_per_step": None, "note": "open-loop served trace, outputs on the device"}
     line["gpu_launches"] = None
-    line["cpu_baseline"] = None
+    line["cpu_baseline"] = None if args.no_cpu_baseline else serve_cpu_baseline(g)
     line["clocks"] = clk
     print(json.dumps(line), flush=True)
 

@@ -5,8 +5,8 @@
 // several requests runs the mixed-batch kernel over a request table in device
 // memory owned by the plan, and trw_plan_set_seed rewrites one entry there
 // between launches.  A plan of one request runs that algorithm's own kernel
-// with the request passed by value (fewer registers than the mixed one), and
-// a new seed re-captures the graph.
+// (the one trw_walk's automatic choice would run) with the request passed by
+// value, and a new seed re-captures the graph.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -99,8 +99,17 @@ static cudaError_t capture(trw_plan* p) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), p->cap);
   if (p->nreq == 1) {
-    if (e == cudaSuccess) e = launch_validate_sources(h_specs[0].sources, p->n_src0, p->dg.nv, p->ctrl, p->cap);
-    if (e == cudaSuccess && h_specs[0].nwalks > 0) e = launch_walk_persistent(p->dg, h_specs[0], p->ctrl, p->cap, p->cfg);
+    // the kernel trw_walk's automatic choice would run: the one-launch kernel
+    // for a request that fits in one resident wave and needs no warp
+    // cooperation, else the persistent one
+    const WalkSpec& s0 = h_specs[0];
+    const bool coop = (s0.algo == METAPATH && p->cfg.coop_degree < 0x7fffffff) ||
+                      (s0.algo == NODE2VEC && p->cfg.search_degree < 0x7fffffff);
+    const bool one_wave = !coop && s0.nwalks <= (int64_t)p->cfg.grid_blocks * p->cfg.block_threads;
+    if (e == cudaSuccess) e = launch_validate_sources(s0.sources, p->n_src0, p->dg.nv, p->ctrl, p->cap);
+    if (e == cudaSuccess && s0.nwalks > 0)
+      e = one_wave ? launch_walk_plain(p->dg, s0, p->ctrl, p->cap, 256)
+                   : launch_walk_persistent(p->dg, s0, p->ctrl, p->cap, p->cfg);
   } else {
     if (e == cudaSuccess) {
       validate_batch<<<(unsigned)vblocks, 256, 0, p->cap>>>(d_specs, p->nreq, p->dg.nv, p->ctrl);
