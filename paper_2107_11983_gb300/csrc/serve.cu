@@ -21,6 +21,7 @@
 // Queue and dispatcher state live in device memory, so nothing is lost
 // between launches.
 #include <atomic>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <cstdint>
@@ -58,11 +59,12 @@ struct ServeState {       // device memory, persists across launches
   alignas(128) int exit_now;      // set by the dispatcher: the launch is ending (cleared before each launch)
   alignas(128) unsigned long long disp_next;   // dispatcher: next published request to admit
   int n_act;                      // dispatcher: requests with walks not yet queued
-  int rr;                         // dispatcher: round-robin cursor
+  int rr;                         // (unused)
   unsigned long long act_k[kMaxActive];    // their request numbers
   unsigned long long act_pos[kMaxActive];  // next walk to queue
   unsigned long long act_n[kMaxActive];    // walks of the request
   unsigned long long act_cw[kMaxActive];   // walks per chunk
+  unsigned long long act_w[kMaxActive];    // expected moves per walk
   unsigned long long moves;       // total moves of finished walks
   int live_workers;               // worker warps of the running launch
   int err;                        // first failed self-check (kernel-wide)
@@ -75,6 +77,8 @@ struct SlotRec {
   unsigned long long finished;    // walks finished (zero at submit)
   uint32_t cw;                    // walks per chunk
   int err;                        // first error of the request (zero at submit)
+  uint32_t exp_moves;             // expected moves per walk (the dispatcher's work estimate)
+  uint32_t pad;
   unsigned long long t_admit;     // device clock (ns): the dispatcher took the request in
   unsigned long long t_first;     // a worker loaded its descriptor (first walks start)
   unsigned long long t_done;      // its last walk finished
@@ -121,12 +125,15 @@ struct ActiveSet {
   unsigned long long pos[kMaxActive];
   unsigned long long n[kMaxActive];
   unsigned long long cw[kMaxActive];
+  unsigned long long w[kMaxActive];
 };
 
 // Dispatcher: admits published requests into an active set and cuts them into
-// chunks round-robin, keeping at most sv.depth chunks queued, so a request
-// that arrives behind a large one waits for a bounded number of chunks, not
-// for the large request.  It alone decides when the launch ends: after
+// chunks, shortest remaining work first (walks not yet queued times expected
+// moves per walk), keeping at most sv.depth chunks queued: a request that
+// arrives behind a large one waits for a bounded number of chunks, not for
+// the large request, and of two large requests the one nearer completion
+// finishes first instead of both finishing late.  It alone decides when the launch ends: after
 // idle_timeout with nothing to hand out, or on the host's stop, it raises
 // exit_now for the workers.  One warp; lane 0 works.
 __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
@@ -141,6 +148,7 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
       act->pos[i] = st->act_pos[i];
       act->n[i] = st->act_n[i];
       act->cw[i] = st->act_cw[i];
+      act->w[i] = st->act_w[i];
     }
   }
   long long idle_since = now_ns();
@@ -160,20 +168,30 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
           act->pos[n_act] = 0;
           act->n[n_act] = n;
           act->cw[n_act] = __ldcg(&sv.slots[slot].cw);
+          act->w[n_act] = __ldcg(&sv.slots[slot].exp_moves);
           ++n_act;
         }
         ++disp_next;
       }
     }
     // Chunks go out in bursts of up to 32 consecutive chunks of one request,
-    // one per lane, round-robin over the active requests.
+    // one per lane.
     const unsigned long long consumed = lane == 0 ? ld_acquire_gpu(&st->q_consumed) : 0ull;
     int pushed = 0;
     for (;;) {
       int burst = 0;
       unsigned long long bk = 0, bpos = 0, bn = 0, bcw = 0;
       if (lane == 0 && n_act > 0 && tail - consumed < sv.depth && pushed < 1024) {
-        if (rr >= n_act) rr = 0;
+        // shortest remaining work first: walks not yet queued x expected moves
+        rr = 0;
+        unsigned long long best = ~0ull;
+        for (int i = 0; i < n_act; ++i) {
+          const unsigned long long work = (act->n[i] - act->pos[i]) * act->w[i];
+          if (work < best) {
+            best = work;
+            rr = i;
+          }
+        }
         bk = act->k[rr];
         bpos = act->pos[rr];
         bn = act->n[rr];
@@ -208,9 +226,9 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
           act->pos[rr] = act->pos[n_act];
           act->n[rr] = act->n[n_act];
           act->cw[rr] = act->cw[n_act];
+          act->w[rr] = act->w[n_act];
         } else {
           act->pos[rr] = npos;
-          ++rr;
         }
       }
     }
@@ -240,6 +258,7 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
           st->act_pos[i] = act->pos[i];
           st->act_n[i] = act->n[i];
           st->act_cw[i] = act->cw[i];
+          st->act_w[i] = act->w[i];
         }
         __threadfence();
         atomicExch(&st->exit_now, 1);
@@ -801,6 +820,8 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   rec.finished = 0;
   rec.cw = cw;
   rec.err = 0;
+  rec.exp_moves = (uint32_t)std::max(1.0, std::ceil(exp_moves));
+  rec.pad = 0;
   rec.t_admit = rec.t_first = rec.t_done = 0;
   // Nothing below waits for the device: the sources, the slot record and
   // then the new request count go up on the copy stream, in submission
