@@ -128,6 +128,20 @@ struct ActiveSet {
   unsigned long long w[kMaxActive];
 };
 
+// A worker warp's queue bookkeeping, kept in shared memory between refills so
+// that none of it is live in registers while the lanes step their walks.
+struct WarpState {
+  unsigned long long ticket;      // lane 0: queue ticket held (has_ticket)
+  unsigned long long pk;          // popped chunk not yet placed (pend): request
+  long long idle_since;           // last time the warp had a walk to step
+  uint32_t wlo, whi;              // unassigned walks of key[cur]
+  uint32_t pb, pe;                // popped chunk not yet placed: walk range
+  int cur;                        // slot receiving new walks
+  int pend;
+  int has_ticket;
+  int pad;
+};
+
 // Dispatcher: admits published requests into an active set and cuts them into
 // chunks, shortest remaining work first (walks not yet queued times expected
 // moves per walk), keeping at most sv.depth chunks queued: a request that
@@ -174,14 +188,14 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
         ++disp_next;
       }
     }
-    // Chunks go out in bursts of up to 32 consecutive chunks of one request,
-    // one per lane.
+    // Chunks go out in bursts of up to 128 consecutive chunks of one request,
+    // up to four per lane.
     const unsigned long long consumed = lane == 0 ? ld_acquire_gpu(&st->q_consumed) : 0ull;
     int pushed = 0;
     for (;;) {
       int burst = 0;
       unsigned long long bk = 0, bpos = 0, bn = 0, bcw = 0;
-      if (lane == 0 && n_act > 0 && tail - consumed < sv.depth && pushed < 1024) {
+      if (lane == 0 && n_act > 0 && tail - consumed < sv.depth && pushed < 4096) {
         // shortest remaining work first: walks not yet queued x expected moves
         rr = 0;
         unsigned long long best = ~0ull;
@@ -198,7 +212,7 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
         bcw = act->cw[rr];
         const unsigned long long left = (bn - bpos + bcw - 1) / bcw;
         const unsigned long long room = sv.depth - (tail - consumed);
-        burst = (int)(left < 32 ? left : 32);
+        burst = (int)(left < 128 ? left : 128);
         if ((unsigned long long)burst > room) burst = (int)room;
       }
       burst = __shfl_sync(0xffffffffu, burst, 0);
@@ -208,13 +222,13 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
       bn = __shfl_sync(0xffffffffu, bn, 0);
       bcw = __shfl_sync(0xffffffffu, bcw, 0);
       const unsigned long long t0 = __shfl_sync(0xffffffffu, tail, 0);
-      if (lane < burst) {
-        const unsigned long long b = bpos + (unsigned long long)lane * bcw;
+      for (int i = lane; i < burst; i += 32) {  // up to four entries per lane
+        const unsigned long long b = bpos + (unsigned long long)i * bcw;
         const unsigned long long e = b + bcw < bn ? b + bcw : bn;
-        Chunk* c = &sv.queue[(t0 + lane) % kQueueCap];
+        Chunk* c = &sv.queue[(t0 + i) % kQueueCap];
         __stcg(&c->k, bk);
         __stcg(reinterpret_cast<uint2*>(&c->begin), make_uint2((uint32_t)b, (uint32_t)e));
-        __stcg(&c->seq, t0 + lane);
+        __stcg(&c->seq, t0 + i);
       }
       if (lane == 0) {
         tail = t0 + burst;
@@ -340,7 +354,11 @@ __device__ __forceinline__ void record_bad(const ServeDev& sv, int bad, unsigned
 // of a third request waits until the other slot has drained.  Every lane keeps
 // the number of its own request and checks it against its slot before using
 // the slot (a mismatch is recorded and the walk ends without a write).
-__global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) {
+// COOP compiles in the warp-cooperative MetaPath scan and Node2Vec search
+// (needed only when a graph without the label index or neighbour hash is
+// tuned to use them); without it the kernel fits four blocks per SM.
+template <bool COOP>
+__global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, ServeDev sv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -351,13 +369,26 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
   int32_t* stage_mem = reinterpret_cast<int32_t*>(smem_raw + (sizeof(WalkSpec) + 8) * 2 * nwarps);
   ActiveSet* act =
       reinterpret_cast<ActiveSet*>(smem_raw + (sizeof(WalkSpec) + 8) * 2 * nwarps + (size_t)blockDim.x * 32);
+  WarpState* wsp = reinterpret_cast<WarpState*>(reinterpret_cast<unsigned char*>(act) + sizeof(ActiveSet)) + wid;
 
   if (blockIdx.x == 0 && wid == 0) {
     dispatcher(sv, act);
     return;
   }
   if (lane < 2) key[lane] = ~0ull;
-  if (lane == 0) atomicAdd(&sv.state->live_workers, 1);
+  if (lane == 0) {
+    atomicAdd(&sv.state->live_workers, 1);
+    WarpState w0;
+    w0.ticket = 0;
+    w0.pk = 0;
+    w0.idle_since = now_ns();
+    w0.wlo = w0.whi = w0.pb = w0.pe = 0;
+    w0.cur = 0;
+    w0.pend = 0;
+    w0.has_ticket = 0;
+    w0.pad = 0;
+    *wsp = w0;
+  }
   __syncwarp();
 
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -371,18 +402,19 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
   int64_t walk = 0;
   int ent = 0;                        // this lane's slot
   unsigned long long my_k = ~0ull;    // this lane's request
-  int cur = 0;                        // slot receiving new walks (warp-uniform)
-  uint32_t wlo = 0, whi = 0;          // unassigned walks of key[cur] (warp-uniform)
-  bool pend = false;                  // a popped chunk not yet placed (warp-uniform)
-  bool has_ticket = false;            // lane 0: holds a queue ticket not yet served
-  unsigned long long ticket = 0;
-  unsigned long long pk = 0;
-  uint32_t pb = 0, pe = 0;
-  long long idle_since = now_ns();
   unsigned long long moves_acc = 0;
 
   for (;;) {
     unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (idle != 0u) {
+    // the warp's bookkeeping, loaded for this refill and stored back below
+    int cur = wsp->cur;
+    uint32_t wlo = wsp->wlo, whi = wsp->whi;
+    bool pend = wsp->pend != 0;
+    bool has_ticket = wsp->has_ticket != 0;   // lane 0's
+    unsigned long long ticket = wsp->ticket;
+    unsigned long long pk = wsp->pk;
+    uint32_t pb = wsp->pb, pe = wsp->pe;
     while (idle != 0u) {
       if (wlo >= whi) {
         if (!pend) {
@@ -478,6 +510,20 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
       wlo += (uint32_t)take;
       idle = __ballot_sync(0xffffffffu, !active);
     }
+    __syncwarp();
+    if (lane == 0) {
+      wsp->cur = cur;
+      wsp->wlo = wlo;
+      wsp->whi = whi;
+      wsp->pend = pend ? 1 : 0;
+      wsp->has_ticket = has_ticket ? 1 : 0;
+      wsp->ticket = ticket;
+      wsp->pk = pk;
+      wsp->pb = pb;
+      wsp->pe = pe;
+    }
+    __syncwarp();
+    }
 
     if (!__any_sync(0xffffffffu, active)) {
       // Idle: wait for chunks until the dispatcher ends the launch (with an
@@ -486,10 +532,12 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
       if (lane == 0) {
         const long long t = now_ns();
         const unsigned long long tl = ld_acquire_gpu(&sv.state->q_tail);
+        const bool has_ticket = wsp->has_ticket != 0;
+        const unsigned long long ticket = wsp->ticket;
         // leave once the dispatcher ended the launch and no entry waits for this warp
         if (*(volatile int*)&sv.state->exit_now && (!has_ticket || ticket >= tl))
           go = 0;
-        else if (t - idle_since > 1000 * sv.idle_ns) go = 0;
+        else if (t - wsp->idle_since > 1000 * sv.idle_ns) go = 0;
         else {
           // warps whose ticket is near the tail poll often, the rest back off
           const unsigned long long dist = has_ticket && ticket > tl ? ticket - tl : 0;
@@ -499,7 +547,7 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
       if (!__shfl_sync(0xffffffffu, go, 0)) break;
       continue;
     }
-    idle_since = now_ns();
+    if (lane == 0) wsp->idle_since = now_ns();
 
     bool finishing = false;
     const bool mine = active && key[ent] == my_k;
@@ -514,10 +562,14 @@ __global__ void __launch_bounds__(256, 3) serve_kernel(DevGraph g, ServeDev sv) 
     step::Pend pend_work;
     pend_work.kind = 0;
     pend_work.res = 0;
-    if (mine) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend_work, sv.coop);
-    if (__any_sync(0xffffffffu, r == step::kDefer)) {
-      step::warp_resolve(g, r, W, pend_work);
-      if (r == step::kDefer) r = step::step_finish(g, sp, W, pend_work, next);
+    if constexpr (COOP) {
+      if (mine) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend_work, sv.coop);
+      if (__any_sync(0xffffffffu, r == step::kDefer)) {
+        step::warp_resolve(g, r, W, pend_work);
+        if (r == step::kDefer) r = step::step_finish(g, sp, W, pend_work, next);
+      }
+    } else {
+      if (mine) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend_work, step::Coop{0x7fffffff, 0x7fffffff});
     }
     if (mine) {
       const int slot = (int)(my_k % (unsigned long long)sv.R);
@@ -610,7 +662,8 @@ struct trw_server {
   int64_t inflight_walks = 0, inflight_bytes = 0;
   int64_t src_head = 0;                // ring allocator: next free position
   int block_threads = 256;
-  int grid_blocks = 0;
+  int grid_blocks = 0;                 // the variant without warp cooperation
+  int grid_blocks_coop = 0;            // the variant with it
   size_t smem = 0;
   uint64_t polls = 0;
   std::mutex mu;
@@ -693,11 +746,17 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   s->collected.assign(R, 1);
   s->block_threads = 256;
   const int nwarps = s->block_threads / 32;
-  s->smem = (sizeof(WalkSpec) + 8) * 2 * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t) + sizeof(ActiveSet);
-  int bps = 0;
-  SV_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, serve_kernel, s->block_threads, s->smem), "occupancy");
+  s->smem = (sizeof(WalkSpec) + 8) * 2 * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t) + sizeof(ActiveSet) +
+            sizeof(WarpState) * nwarps;
+  int bps = 0, bps_coop = 0;
+  SV_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, serve_kernel<false>, s->block_threads, s->smem),
+         "occupancy");
+  SV_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps_coop, serve_kernel<true>, s->block_threads, s->smem),
+         "occupancy");
   if (bps < 1) bps = 1;
+  if (bps_coop < 1) bps_coop = 1;
   s->grid_blocks = g->num_sms * bps;
+  s->grid_blocks_coop = g->num_sms * bps_coop;
   *out = s;
   return TRW_OK;
 }
@@ -720,9 +779,9 @@ static cudaError_t launch_if_idle(trw_server* s) {
   {
     // enough queued chunks to cover the workers' claims between dispatcher rounds
     const unsigned long long workers = (unsigned long long)s->grid_blocks * (s->block_threads / 32);
-    unsigned long long depth = workers / 16;
+    unsigned long long depth = workers / 4;
     if (depth < 64) depth = 64;
-    if (depth > 1024) depth = 1024;
+    if (depth > 4096) depth = 4096;
     sv.depth = depth;
   }
   cudaError_t e = cudaMemsetAsync(&s->state->exit_now, 0, sizeof(int), s->stream);
@@ -732,7 +791,15 @@ static cudaError_t launch_if_idle(trw_server* s) {
     e = cudaMemcpyAsync(&s->state->q_head, &s->state->q_tail, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                         s->stream);
   if (e != cudaSuccess) return e;
-  serve_kernel<<<s->grid_blocks, s->block_threads, s->smem, s->stream>>>(trw_dev_graph(s->g), sv);
+  // the cooperative variant only when the tuning asks for a warp path that no
+  // prepared table replaces
+  const trw_graph* g = s->g;
+  const bool coop = (g->tuning.coop_degree < 0x7fffffff && !g->lerec) ||
+                    (g->tuning.search_degree < 0x7fffffff && !g->nh_slots);
+  if (coop)
+    serve_kernel<true><<<s->grid_blocks_coop, s->block_threads, s->smem, s->stream>>>(trw_dev_graph(g), sv);
+  else
+    serve_kernel<false><<<s->grid_blocks, s->block_threads, s->smem, s->stream>>>(trw_dev_graph(g), sv);
   return cudaGetLastError();
 }
 
@@ -809,12 +876,14 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   sp.out_lengths = out_lengths;
   // Walks per chunk: one walk per lane (32) while the request fits in the
   // resident lanes, so its latency is its longest walk; a larger request
-  // takes about 20 expected moves per lane per chunk, fewer chunks to hand out.
+  // takes about 20 expected moves per lane per chunk.  (Chunks sized to two
+  // per worker warp made large requests slower: the tail imbalance cost more
+  // than the dispatcher's work saved.)
   double exp_moves = (double)max_len;
   if (algo == TRW_PPR && params && params->ppr_stop > 0) exp_moves = std::min(exp_moves, 1.0 / params->ppr_stop);
   if (exp_moves < 1) exp_moves = 1;
   const int64_t lanes = (int64_t)s->grid_blocks * s->block_threads;
-  uint32_t cw = sp.nwalks <= lanes ? 32u : (uint32_t)std::max(32.0, std::min(2048.0, 640.0 / exp_moves));
+  const uint32_t cw = sp.nwalks <= lanes ? 32u : (uint32_t)std::max(32.0, std::min(2048.0, 640.0 / exp_moves));
   SlotRec& rec = s->slot_stage[slot];
   rec.spec = sp;
   rec.finished = 0;
