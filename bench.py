@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -119,7 +120,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        out = os.environ.get("TRW_BENCH_OUT") or os.path.join(tempfile.gettempdir(), "trw_bench")
+        self.path = os.path.join(out, f"clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
