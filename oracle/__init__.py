@@ -25,6 +25,8 @@ _lib = None
 
 DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH = 0, 1, 2, 3, 4
 OK, ERR_INVALID, ERR_OOM, ERR_REJECT_CAP = 0, -1, -2, -6
+# Sampling methods of weighted DeepWalk (Section 2.3); DEFAULT is ALIAS.
+SAMPLER_DEFAULT, SAMPLER_ITS, SAMPLER_REJ, SAMPLER_OREJ = 0, 1, 2, 3
 ALGO_NAMES = {DEEPWALK: "deepwalk", DEEPWALK_WEIGHTED: "deepwalk_weighted", PPR: "ppr",
               NODE2VEC: "node2vec", METAPATH: "metapath"}
 
@@ -41,14 +43,15 @@ def build(force: bool = False) -> str:
 class _Graph(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
                 ("H", ctypes.c_void_p), ("A_first", ctypes.c_void_p), ("A_second", ctypes.c_void_p),
-                ("dead", ctypes.c_void_p), ("labels", ctypes.c_void_p)]
+                ("dead", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("cdf", ctypes.c_void_p), ("pmax", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("walks_per_source", ctypes.c_int32), ("ppr_stop", ctypes.c_double),
                 ("n2v_p", ctypes.c_double), ("n2v_q", ctypes.c_double), ("schema", ctypes.c_void_p),
                 ("schema_len", ctypes.c_int32), ("endpoints_only", ctypes.c_int32),
-                ("walk_offset", ctypes.c_int64)]
+                ("walk_offset", ctypes.c_int64), ("sampler", ctypes.c_int32), ("max_weight", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -70,6 +73,12 @@ def _bind(path: str):
     lib.orc_alias_build.restype = ctypes.c_int
     lib.orc_prepare_alias.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp, vp]
     lib.orc_prepare_alias.restype = ctypes.c_int
+    lib.orc_prepare_its.argtypes = [ctypes.c_int64, vp, vp, vp]
+    lib.orc_prepare_its.restype = ctypes.c_int
+    lib.orc_prepare_rej.argtypes = [ctypes.c_int64, vp, vp, vp]
+    lib.orc_prepare_rej.restype = ctypes.c_int
+    lib.orc_rej_threshold.argtypes = [ctypes.c_uint32, ctypes.c_uint64]
+    lib.orc_rej_threshold.restype = ctypes.c_uint64
     lib.orc_walk.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Params), vp, ctypes.c_int64,
                              ctypes.c_int32, ctypes.c_uint64, vp, vp, ctypes.POINTER(_Stats)]
     lib.orc_walk.restype = ctypes.c_int
@@ -156,6 +165,33 @@ def prepare_alias(row_ptr: np.ndarray, weights: np.ndarray, lib=None) -> AliasTa
     return AliasTables(H, A1, A2, dead)
 
 
+def prepare_its(row_ptr: np.ndarray, weights: np.ndarray, lib=None) -> np.ndarray:
+    """Algorithm 3 for ITS: the per-row prefix sums P' of the integer weights, uint64[ne]."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    weights = np.ascontiguousarray(weights, dtype=np.float32)
+    cdf = np.zeros(int(row_ptr[-1]), dtype=np.uint64)
+    if (lib or _load()).orc_prepare_its(row_ptr.shape[0] - 1, row_ptr.ctypes.data, weights.ctypes.data,
+                                        cdf.ctypes.data) != OK:
+        raise ValueError("invalid edge weight")
+    return cdf
+
+
+def prepare_rej(row_ptr: np.ndarray, weights: np.ndarray, lib=None) -> np.ndarray:
+    """Algorithm 3 for REJ: p*_v, the largest integer weight of each row, uint32[nv]."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    weights = np.ascontiguousarray(weights, dtype=np.float32)
+    pmax = np.zeros(row_ptr.shape[0] - 1, dtype=np.uint32)
+    if (lib or _load()).orc_prepare_rej(row_ptr.shape[0] - 1, row_ptr.ctypes.data, weights.ctypes.data,
+                                        pmax.ctypes.data) != OK:
+        raise ValueError("invalid edge weight")
+    return pmax
+
+
+def rej_threshold(W: int, pstar: int, lib=None) -> int:
+    """Acceptance threshold of a rejection dart: floor(W * 2^32 / p*), 2^32 once W >= p*."""
+    return int((lib or _load()).orc_rej_threshold(int(W), int(pstar)))
+
+
 @dataclass
 class WalkResult:
     paths: np.ndarray     # int32[nwalks, max_len+1] (or [nwalks] for endpoints)
@@ -167,6 +203,7 @@ class WalkResult:
 def walk(row_ptr, col, algo: int, sources, max_len: int, seed: int, *, alias: Optional[AliasTables] = None,
          labels=None, ppr_stop: float = 0.0, n2v_p: float = 1.0, n2v_q: float = 1.0, schema=None,
          walks_per_source: int = 1, endpoints_only: bool = False, walk_offset: int = 0,
+         sampler: int = SAMPLER_DEFAULT, weights=None, its=None, pmax=None, max_weight: float = 0.0,
          lib=None) -> WalkResult:
     """Run the oracle walker; returns paths, lengths, counters and the status code."""
     lib = lib or _load()
@@ -185,6 +222,18 @@ def walk(row_ptr, col, algo: int, sources, max_len: int, seed: int, *, alias: Op
         labels = np.ascontiguousarray(labels, dtype=np.uint8)
         keep.append(labels)
         g.labels = labels.ctypes.data
+    if weights is not None:
+        weights = np.ascontiguousarray(weights, dtype=np.float32)
+        keep.append(weights)
+        g.weights = weights.ctypes.data
+    if its is not None:
+        its = np.ascontiguousarray(its, dtype=np.uint64)
+        keep.append(its)
+        g.cdf = its.ctypes.data
+    if pmax is not None:
+        pmax = np.ascontiguousarray(pmax, dtype=np.uint32)
+        keep.append(pmax)
+        g.pmax = pmax.ctypes.data
     p = _Params()
     p.algo = algo
     p.walks_per_source = walks_per_source
@@ -198,6 +247,8 @@ def walk(row_ptr, col, algo: int, sources, max_len: int, seed: int, *, alias: Op
         p.schema_len = schema.shape[0]
     p.endpoints_only = int(endpoints_only)
     p.walk_offset = walk_offset
+    p.sampler = sampler
+    p.max_weight = max_weight
     nwalks = sources.shape[0] * walks_per_source
     width = 1 if endpoints_only else max_len + 1
     paths = np.full((nwalks, width) if not endpoints_only else (nwalks,), -1, dtype=np.int32)

@@ -30,6 +30,15 @@
  *   - Node2Vec's IsNeighbor(c, u) means c is an out-neighbour of u.
  *   - The alias table is built by Vose's method on integer weights, with
  *     first-in first-out work lists (the paper leaves the construction open).
+ *   - Weighted DeepWalk may also sample by ITS, REJ or O-REJ (Section 2.3),
+ *     all on the same integer weights W_e.  Static ITS stores the row's
+ *     prefix sums P' and draws x uniform in [0, p'_{d-1}); static REJ stores
+ *     p*_v = max W_e of the row; O-REJ takes a user bound P >= max W_e
+ *     (MaxWeight, quantised like a weight) and has no initialisation.  A dart
+ *     (x, y) hits when the 32-bit word y is below floor(W_x * 2^32 / p*),
+ *     clamped to 2^32 when W_x >= p*.  A row whose weights are all zero is a
+ *     dead end for ITS and REJ (their initialisation sees it); O-REJ cannot
+ *     see it and runs into the trial cap.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -38,6 +47,8 @@
 
 enum { ORC_DEEPWALK = 0, ORC_DEEPWALK_WEIGHTED = 1, ORC_PPR = 2, ORC_NODE2VEC = 3, ORC_METAPATH = 4 };
 enum { ORC_OK = 0, ORC_ERR_INVALID = -1, ORC_ERR_OOM = -2, ORC_ERR_REJECT_CAP = -6 };
+/* Sampling method of weighted DeepWalk (the other walks take 0). */
+enum { ORC_SAMPLER_DEFAULT = 0, ORC_SAMPLER_ITS = 1, ORC_SAMPLER_REJ = 2, ORC_SAMPLER_OREJ = 3 };
 
 #define ORC_REJECT_CAP 65536
 
@@ -180,6 +191,49 @@ int orc_prepare_alias(int64_t nv, const int64_t* row_ptr, const float* weights, 
   return ORC_OK;
 }
 
+/*
+ * Algorithm 3 with the ITS initialisation (Section 2.3): for every vertex v,
+ * the cumulative sums of its integer weights, P'_i = W_0 + ... + W_i, stored
+ * per edge slot (off + i).  Returns 0 or -1 on a bad weight.
+ */
+int orc_prepare_its(int64_t nv, const int64_t* row_ptr, const float* weights, uint64_t* cdf) {
+  for (int64_t v = 0; v < nv; ++v) {
+    uint64_t acc = 0;
+    for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      int64_t wq = orc_quantize_weight(weights[e]);
+      if (wq < 0) return ORC_ERR_INVALID;
+      acc += (uint64_t)wq;
+      cdf[e] = acc;
+    }
+  }
+  return ORC_OK;
+}
+
+/*
+ * Algorithm 3 with the REJ initialisation (Section 2.3): p*_v, the largest
+ * integer weight of E_v (0 for a vertex without edges or with only zero
+ * weights).  Returns 0 or -1 on a bad weight.
+ */
+int orc_prepare_rej(int64_t nv, const int64_t* row_ptr, const float* weights, uint32_t* pmax) {
+  for (int64_t v = 0; v < nv; ++v) {
+    uint32_t m = 0;
+    for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+      int64_t wq = orc_quantize_weight(weights[e]);
+      if (wq < 0) return ORC_ERR_INVALID;
+      if ((uint32_t)wq > m) m = (uint32_t)wq;
+    }
+    pmax[v] = m;
+  }
+  return ORC_OK;
+}
+
+/* Fixed-point acceptance threshold of a rejection dart with weight W under the
+ * bound pstar > 0: floor(W / pstar * 2^32), exactly, and 2^32 once W >= pstar. */
+uint64_t orc_rej_threshold(uint32_t W, uint64_t pstar) {
+  if ((uint64_t)W >= pstar) return 4294967296ULL;
+  return ((uint64_t)W << 32) / pstar;
+}
+
 /* ------------------------------------------------------------------ walks */
 
 typedef struct {
@@ -191,6 +245,9 @@ typedef struct {
   const int32_t* A_second;
   const uint8_t* dead;
   const uint8_t* labels;    /* MetaPath edge labels, or NULL */
+  const float* weights;     /* edge weights (REJ, O-REJ darts), or NULL */
+  const uint64_t* cdf;      /* ITS prefix sums from orc_prepare_its, or NULL */
+  const uint32_t* pmax;     /* REJ bounds p*_v from orc_prepare_rej, or NULL */
 } orc_graph;
 
 typedef struct {
@@ -202,11 +259,13 @@ typedef struct {
   int32_t schema_len;
   int32_t endpoints_only;     /* 1: out_paths holds one vertex (the end) per walk */
   int64_t walk_offset;        /* index of the first walk in the Philox counter */
+  int32_t sampler;            /* weighted DeepWalk: ORC_SAMPLER_* (0 = ALIAS); 0 for the others */
+  double max_weight;          /* O-REJ: the user's bound on the edge weights (MaxWeight) */
 } orc_params;
 
 typedef struct {
   int64_t moves;          /* total moves (steps) of all walks */
-  int64_t attempts;       /* Node2Vec: total rejection trials */
+  int64_t attempts;       /* Node2Vec, REJ, O-REJ: total rejection trials */
   int64_t stop_len, stop_coin, stop_dead, stop_schema;
   int64_t sectors;        /* distinct 32-byte sectors read, summed over steps (layout model) */
   int64_t out_bytes;      /* bytes of path output written */
@@ -215,8 +274,9 @@ typedef struct {
 } orc_stats;
 
 /* Sector model of the device layout, used only for the roofline: 4-byte
- * row offsets and column ids, 16-byte packed alias records, 1-byte labels. */
-enum { SEC_ROW = 0, SEC_COL = 1, SEC_ALIAS = 2, SEC_LABEL = 3 };
+ * row offsets and column ids, 16-byte packed alias records, 1-byte labels,
+ * 8-byte ITS prefix sums, 4-byte REJ bounds and edge weights. */
+enum { SEC_ROW = 0, SEC_COL = 1, SEC_ALIAS = 2, SEC_LABEL = 3, SEC_CDF = 4, SEC_PMAX = 5, SEC_WEIGHT = 6 };
 typedef struct { int64_t n; int64_t key[512]; } sector_set;
 static void sec_touch(sector_set* s, int array, int64_t byte_off) {
   int64_t k = ((int64_t)array << 58) | (byte_off >> 5);
@@ -278,7 +338,24 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
   const uint64_t T_nb = orc_threshold(w_nb / pstar);
   const uint64_t T_far = orc_threshold(w_far / pstar);
   if (p->algo == ORC_METAPATH && (p->schema_len < 1 || !p->schema || !g->labels)) return ORC_ERR_INVALID;
-  if (p->algo == ORC_DEEPWALK_WEIGHTED && !g->H) return ORC_ERR_INVALID;
+  if (p->sampler != ORC_SAMPLER_DEFAULT && p->algo != ORC_DEEPWALK_WEIGHTED) return ORC_ERR_INVALID;
+  if (p->sampler < ORC_SAMPLER_DEFAULT || p->sampler > ORC_SAMPLER_OREJ) return ORC_ERR_INVALID;
+  if (p->algo == ORC_DEEPWALK_WEIGHTED) {
+    if (p->sampler == ORC_SAMPLER_DEFAULT && !g->H) return ORC_ERR_INVALID;
+    if (p->sampler == ORC_SAMPLER_ITS && !g->cdf) return ORC_ERR_INVALID;
+    if (p->sampler == ORC_SAMPLER_REJ && (!g->pmax || !g->weights)) return ORC_ERR_INVALID;
+    if (p->sampler == ORC_SAMPLER_OREJ && !g->weights) return ORC_ERR_INVALID;
+  }
+  /* O-REJ's bound P: round-half-even(MaxWeight * 2^16), clamped to 2^32 - 1
+   * like a weight; it must be at least 1. */
+  uint64_t P_user = 0;
+  if (p->algo == ORC_DEEPWALK_WEIGHTED && p->sampler == ORC_SAMPLER_OREJ) {
+    if (!isfinite(p->max_weight) || !(p->max_weight > 0)) return ORC_ERR_INVALID;
+    double t = rint(p->max_weight * 65536.0);
+    if (t > 4294967295.0) t = 4294967295.0;
+    if (t < 1.0) return ORC_ERR_INVALID;
+    P_user = (uint64_t)t;
+  }
 
   int32_t* path = (int32_t*)malloc(((size_t)max_len + 1) * sizeof(int32_t));
   int64_t dmax = 0;
@@ -311,6 +388,40 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
         const uint64_t x = uniform_below(B, (uint64_t)d);
         next = g->col[off + (int64_t)x];
         if (sec) sec_touch(sec, SEC_COL, (off + (int64_t)x) * 4);
+      } else if (p->algo == ORC_DEEPWALK_WEIGHTED && p->sampler == ORC_SAMPLER_ITS) {
+        /* Static walk, ITS generation from the stored P': x uniform in
+         * [0, p'_{d-1}), then the smallest i with x < p'_i. */
+        const uint64_t* P = g->cdf + off;
+        if (sec) sec_touch(sec, SEC_CDF, (off + d - 1) * 8);
+        if (P[d - 1] == 0) { if (st) st->stop_dead++; break; }
+        const uint64_t x = uniform_below(B, P[d - 1]);
+        int64_t lo = 0, hi = d - 1;
+        while (lo < hi) {
+          int64_t mid = lo + (hi - lo) / 2;
+          if (sec) sec_touch(sec, SEC_CDF, (off + mid) * 8);
+          if (x < P[mid]) hi = mid; else lo = mid + 1;
+        }
+        next = g->col[off + lo];
+        if (sec) sec_touch(sec, SEC_COL, (off + lo) * 4);
+      } else if (p->algo == ORC_DEEPWALK_WEIGHTED && p->sampler != ORC_SAMPLER_DEFAULT) {
+        /* REJ (p* stored by the preprocessing) or O-REJ (the user's bound):
+         * throw darts (x, y), x uniform in [0, d_v), until y < p_x / p*. */
+        uint64_t pstar = P_user;
+        if (p->sampler == ORC_SAMPLER_REJ) {
+          pstar = g->pmax[cur];
+          if (sec) sec_touch(sec, SEC_PMAX, (int64_t)cur * 4);
+          if (pstar == 0) { if (st) st->stop_dead++; break; }
+        }
+        int accepted = 0;
+        for (uint32_t a = 0; a < ORC_REJECT_CAP; ++a) {
+          if (a > 0) draw_block(seed, w, (uint32_t)s, a, B);
+          if (st) st->attempts++;
+          const int64_t x = (int64_t)uniform_below(B, (uint64_t)d);
+          const uint32_t Wx = (uint32_t)orc_quantize_weight(g->weights[off + x]);
+          if (sec) { sec_touch(sec, SEC_WEIGHT, (off + x) * 4); sec_touch(sec, SEC_COL, (off + x) * 4); }
+          if ((uint64_t)B[2] < orc_rej_threshold(Wx, pstar)) { next = g->col[off + x]; accepted = 1; break; }
+        }
+        if (!accepted) { rc = ORC_ERR_REJECT_CAP; break; }
       } else if (p->algo == ORC_DEEPWALK_WEIGHTED) {
         /* Static walk: C_v was stored by the preprocessing, no Gather. */
         if (g->dead[cur]) { if (st) st->stop_dead++; break; }

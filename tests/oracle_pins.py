@@ -13,7 +13,13 @@ paper or the mathematics fixes:
   * the PPR end-vertex law by a linear solve of the absorbing chain, and the
     geometric length law (mean 5 vertices at stop 0.2, Section 6.2);
   * the O-REJ expected number of trials d * p* / sum(p) (Section 2.3);
-  * special cases that must reduce exactly to NAIVE sampling.
+  * special cases that must reduce exactly to NAIVE sampling;
+  * weighted DeepWalk under ITS, REJ and O-REJ: the first move of every walk
+    recomputed independently (numpy prefix sums and searchsorted for ITS,
+    the dart sequence with the cross-multiplied acceptance test for REJ and
+    O-REJ), path laws by chi-square, the expected trials d * p* / sum(p)
+    on a graph whose rows share one weight multiset, and the acceptance
+    threshold by its counting definition.
 """
 from __future__ import annotations
 
@@ -371,6 +377,13 @@ def pin_reductions(lib=None):
     eq = oracle.prepare_alias(g.row_ptr, np.full(g.ne, 3.0, dtype=np.float32), lib=lib)
     same(oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, L, seed=3, alias=eq, lib=lib),
          "alias with equal weights")
+    w3 = np.full(g.ne, 3.0, dtype=np.float32)
+    same(oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, L, seed=3, sampler=oracle.SAMPLER_ITS,
+                     its=oracle.prepare_its(g.row_ptr, w3, lib=lib), lib=lib), "its with equal weights")
+    same(oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, L, seed=3, sampler=oracle.SAMPLER_REJ,
+                     pmax=oracle.prepare_rej(g.row_ptr, w3, lib=lib), weights=w3, lib=lib), "rej with equal weights")
+    same(oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, L, seed=3, sampler=oracle.SAMPLER_OREJ,
+                     weights=w3, max_weight=3.0, lib=lib), "o-rej with equal weights at the bound")
     same(oracle.walk(g.row_ptr, g.col, oracle.METAPATH, src, L, seed=3, labels=np.zeros(g.ne, np.uint8),
                      schema=[0], lib=lib), "metapath on one label")
     same(oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src, L, seed=3, n2v_p=1.0, n2v_q=1.0, lib=lib),
@@ -432,5 +445,180 @@ def pin_sharding(lib=None):
         assert np.array_equal(part.paths[j, :ln], full.paths[i, :ln])
 
 
+# ------------------------------------------- ITS, REJ and O-REJ (Section 2.3)
+
+def _wq(w):
+    """Integer weights by numpy: round-half-even(w * 2^16), clamped."""
+    return np.minimum(np.rint(np.asarray(w, dtype=np.float32).astype(np.float64) * 65536.0), TWO32 - 1).astype(
+        np.int64)
+
+
+def _r64(B):
+    return int(B[0]) | (int(B[1]) << 32)
+
+
+def pin_rej_threshold(lib=None):
+    """T = rej_threshold(W, p*) is the number of 32-bit words y with
+    (y + 1) / 2^32 <= W / p*: word T - 1 passes and word T fails."""
+    cases = [(1, 3), (2, 3), (5, 7), (65536, 6553600), (6553599, 6553600), (123457, 999983), (TWO32 - 2, TWO32 - 1),
+             (1, TWO32 - 1), (7, 7), (9, 7), (0, 5), (65536 * 3, 65536 * 4)]
+    for W, ps in cases:
+        T = oracle.rej_threshold(W, ps, lib=lib)
+        if W >= ps:
+            assert T == TWO32, (W, ps)
+            continue
+        assert 0 <= T < TWO32
+        if T > 0:
+            assert T * ps <= W * TWO32, (W, ps, T)          # y = T - 1 passes
+        assert (T + 1) * ps > W * TWO32, (W, ps, T)          # y = T fails
+
+
+def pin_its_first_move(lib=None):
+    """Every ITS walk's first move equals numpy's searchsorted over the
+    cumulative integer weights at x = floor(r64 * S / 2^64)."""
+    g = small_rmat()
+    cdf = oracle.prepare_its(g.row_ptr, g.weights, lib=lib)
+    src = synth.vertex_sources(g.nv)
+    seed = 0x1234567890ABCDEF
+    res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, 1, seed, sampler=oracle.SAMPLER_ITS, its=cdf,
+                      lib=lib)
+    assert res.status == 0
+    Wq = _wq(g.weights)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i, v in enumerate(src):
+        lo, hi = int(g.row_ptr[v]), int(g.row_ptr[v + 1])
+        if hi == lo:
+            assert res.lengths[i] == 1
+            continue
+        P = np.cumsum(Wq[lo:hi])
+        S = int(P[-1])
+        B = oracle.philox4x32_10([i, 0, 0, 0], key)
+        x = (_r64(B) * S) >> 64
+        j = int(np.searchsorted(P, x, side="right"))
+        assert res.lengths[i] == 2 and res.paths[i, 1] == g.col[lo + j], (i, v)
+
+
+def _darts(g, Wq, v, key, walk, step, pstar):
+    """REJ dart sequence of one step with the acceptance test written as
+    (y + 1) * p* <= W_x * 2^32; returns (edge slot, trials)."""
+    lo, hi = int(g.row_ptr[v]), int(g.row_ptr[v + 1])
+    d = hi - lo
+    for a in range(65536):
+        B = oracle.philox4x32_10([walk, step, a, 0], key)
+        x = (_r64(B) * d) >> 64
+        if (int(B[2]) + 1) * pstar <= int(Wq[lo + x]) * TWO32:
+            return lo + x, a + 1
+    raise AssertionError("trial cap")
+
+
+def pin_rej_first_move(lib=None):
+    """Every REJ and O-REJ walk's first move, and the trials it took, from the
+    dart sequence recomputed in Python (p* the row maximum by numpy for REJ,
+    the quantised bound for O-REJ)."""
+    g = small_rmat()
+    pm = oracle.prepare_rej(g.row_ptr, g.weights, lib=lib)
+    src = synth.vertex_sources(g.nv)[:400]
+    seed = 77
+    key = [seed, 0]
+    Wq = _wq(g.weights)
+    for sampler, bound in ((oracle.SAMPLER_REJ, None), (oracle.SAMPLER_OREJ, 130.5)):
+        res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, 1, seed, sampler=sampler, weights=g.weights,
+                          pmax=pm if sampler == oracle.SAMPLER_REJ else None, max_weight=bound or 0.0, lib=lib)
+        assert res.status == 0
+        trials = 0
+        for i, v in enumerate(src):
+            lo, hi = int(g.row_ptr[v]), int(g.row_ptr[v + 1])
+            if hi == lo:
+                assert res.lengths[i] == 1
+                continue
+            ps = int(Wq[lo:hi].max()) if bound is None else int(np.rint(bound * 65536))
+            e, t = _darts(g, Wq, int(v), key, i, 0, ps)
+            trials += t
+            assert res.lengths[i] == 2 and res.paths[i, 1] == g.col[e], (sampler, i)
+        assert res.stats["attempts"] == trials, sampler
+
+
+def _sweep_laws(g, lib):
+    cdf = oracle.prepare_its(g.row_ptr, g.weights, lib=lib)
+    pm = oracle.prepare_rej(g.row_ptr, g.weights, lib=lib)
+    return [(oracle.SAMPLER_ITS, {"its": cdf}), (oracle.SAMPLER_REJ, {"pmax": pm, "weights": g.weights}),
+            (oracle.SAMPLER_OREJ, {"weights": g.weights, "max_weight": 12.0})]
+
+
+def pin_law_samplers(lib=None):
+    """Three-move path laws of ITS, REJ and O-REJ equal the weighted law
+    w_e / sum(w) of Section 2.2 (chi-square on the directed graph, whose
+    weights are exact in fixed point)."""
+    g = dir_graph()
+
+    def law(path):
+        v = path[-1]
+        nb = nbrs(g, v)
+        ws = [DIR_WEIGHTS[(v, c)] for c in nb]
+        return {c: w / sum(ws) for c, w in zip(nb, ws)}
+
+    want = enumerate_paths(0, 3, law)
+    for sampler, kw in _sweep_laws(g, lib):
+        res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, [0], 3, seed=31 + sampler, walks_per_source=N_LAW,
+                          sampler=sampler, lib=lib, **kw)
+        assert res.status == 0, sampler
+        p = chi2_pvalue(path_counts(res), want, N_LAW)
+        assert p > 1e-3, (sampler, p)
+
+
+def pin_rej_trials_closed_form(lib=None):
+    """On a circulant graph whose every row holds the weights {1, 3, 4}, the
+    mean trials per move are d * p* / sum(p) (Section 2.3): 3 * 4 / 8 = 1.5 for
+    REJ (p* = 4) and 3 * 8 / 8 = 3 for O-REJ with the bound 8."""
+    n = 64
+    edges = [(v, (v + k) % n) for v in range(n) for k in (1, 2, 3)]
+    g = synth.from_edges(n, edges, symmetric=False)
+    wmap = {(v, (v + k) % n): float(w) for v in range(n) for k, w in ((1, 1), (2, 3), (3, 4))}
+    g.weights = np.array([wmap[(v, int(c))] for v in range(n) for c in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]],
+                         dtype=np.float32)
+    pm = oracle.prepare_rej(g.row_ptr, g.weights, lib=lib)
+    L, walks = 20, 4000
+    for sampler, kw, e in ((oracle.SAMPLER_REJ, {"pmax": pm}, 1.5), (oracle.SAMPLER_OREJ, {"max_weight": 8.0}, 3.0)):
+        res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, np.arange(n), L, seed=5, walks_per_source=walks // n,
+                          sampler=sampler, weights=g.weights, lib=lib, **kw)
+        assert res.status == 0
+        moves = res.stats["moves"]
+        assert moves == walks // n * n * L
+        q = 1.0 / e
+        var = (1 - q) / q ** 2
+        got = res.stats["attempts"] / moves
+        assert abs(got - e) < 6 * np.sqrt(var / moves), (sampler, got, e)
+
+
+def pin_zero_weights(lib=None):
+    """Zero-weight edges are never taken; a row of only zero weights is a dead
+    end for ALIAS, ITS and REJ, and exhausts O-REJ's trial cap."""
+    edges = [(0, 1), (0, 2), (0, 3), (0, 4), (1, 0), (1, 2), (2, 1), (3, 0), (4, 0)]
+    g = synth.from_edges(5, edges, symmetric=False)
+    wmap = {(0, 1): 0.0, (0, 2): 2.0, (0, 3): 0.0, (0, 4): 5.0, (1, 0): 1.0, (1, 2): 1.0, (2, 1): 1.0,
+            (3, 0): 1.0, (4, 0): 0.0}
+    w = np.array([wmap[(v, int(c))] for v in range(5) for c in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]], np.float32)
+    al = oracle.prepare_alias(g.row_ptr, w, lib=lib)
+    cdf = oracle.prepare_its(g.row_ptr, w, lib=lib)
+    pm = oracle.prepare_rej(g.row_ptr, w, lib=lib)
+    assert list(pm) == [5 * 65536, 65536, 65536, 65536, 0]
+    for sampler, kw in ((oracle.SAMPLER_DEFAULT, {"alias": al}), (oracle.SAMPLER_ITS, {"its": cdf}),
+                        (oracle.SAMPLER_REJ, {"pmax": pm, "weights": w})):
+        res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, [0], 5, seed=4, walks_per_source=2000,
+                          sampler=sampler, lib=lib, **kw)
+        assert res.status == 0, sampler
+        firsts = Counter(int(x) for x in res.paths[:, 1])
+        assert set(firsts) == {2, 4}, (sampler, firsts)
+        for row, ln in zip(res.paths, res.lengths):
+            if 4 in row[:ln]:
+                assert row[ln - 1] == 4 and ln == list(row[:ln]).index(4) + 1, "a zero row ends the walk"
+            else:
+                assert ln == 6
+    res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, [4], 3, seed=4, sampler=oracle.SAMPLER_OREJ,
+                      weights=w, max_weight=5.0, lib=lib)
+    assert res.status == oracle.ERR_REJECT_CAP
+
+
 ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
-            pin_law_metapath, pin_ppr, pin_rejection_trials, pin_reductions, pin_invariants, pin_sharding]
+            pin_law_metapath, pin_ppr, pin_rejection_trials, pin_reductions, pin_invariants, pin_sharding, pin_rej_threshold, pin_its_first_move,
+            pin_rej_first_move, pin_law_samplers, pin_rej_trials_closed_form, pin_zero_weights]

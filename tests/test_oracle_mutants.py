@@ -30,6 +30,20 @@ MUTANTS = [
     ("node2vec: prev taken as cur", "const int32_t u = path[s - 1];", "const int32_t u = path[s];"),
     ("node2vec: p* ignores 1/a", "pstar = w_ret > w_nb ? w_ret : w_nb;", "pstar = w_nb;"),
     ("walk: one move short", "if (s == max_len) {", "if (s + 1 == max_len) {"),
+    ("its: exclusive prefix sums", "acc += (uint64_t)wq;\n      cdf[e] = acc;", "cdf[e] = acc;\n      acc += (uint64_t)wq;"),
+    ("its: CDF search takes <=", "if (x < P[mid]) hi = mid;", "if (x <= P[mid]) hi = mid;"),
+    ("its: x drawn below the second-last prefix", "const uint64_t x = uniform_below(B, P[d - 1]);",
+     "const uint64_t x = uniform_below(B, d > 1 ? P[d - 2] : P[0]);"),
+    ("rej: p* of the first neighbour", "pstar = g->pmax[cur];", "pstar = g->pmax[g->col[off]];"),
+    ("rej: p* is the smallest weight", "if ((uint32_t)wq > m) m = (uint32_t)wq;",
+     "if (e == row_ptr[v] || (uint32_t)wq < m) m = (uint32_t)wq;"),
+    ("rej: threshold rounded up", "return ((uint64_t)W << 32) / pstar;",
+     "return (((uint64_t)W << 32) + pstar - 1) / pstar;"),
+    ("rej: dart reuses the first draw", "if (a > 0) draw_block(seed, w, (uint32_t)s, a, B);\n          if (st) st->attempts++;\n          const int64_t x = (int64_t)uniform_below(B, (uint64_t)d);\n          const uint32_t Wx",
+     "if (a > 0) draw_block(seed, w, (uint32_t)s, a > 1 ? a - 1 : a, B);\n          if (st) st->attempts++;\n          const int64_t x = (int64_t)uniform_below(B, (uint64_t)d);\n          const uint32_t Wx"),
+    ("o-rej: bound truncated", "double t = rint(p->max_weight * 65536.0);", "double t = floor(p->max_weight * 65536.0 / 2);"),
+    ("zero row: not a dead end for REJ", "if (pstar == 0) { if (st) st->stop_dead++; break; }",
+     "if (pstar == 0) pstar = 1;"),
 ]
 
 
