@@ -428,6 +428,72 @@ def measure_per_algo(trw, torch, G, g, flush, sp, G_paper=None):
     return out
 
 
+SWEEP_BOUND = 100.0  # O-REJ's MaxWeight: the synthetic weights lie in [1, 100)
+
+
+def measure_sampler_sweep(trw, torch, g, flush, sp, gather, walks_cpu=20000):
+    """Weighted DeepWalk under ALIAS, ITS, REJ and O-REJ (Section 2.3) on the
+    workload's graph: one walk of 80 moves per vertex, persistent kernel,
+    each sampler tuned for itself.  Per sampler: steps/s, its preparation
+    (time and device bytes), and on a CPU sample of the same walks the
+    oracle's rate, trials per move and sector-model bytes per move, from
+    which the roofline fraction follows."""
+    import oracle
+    import synth as sy
+
+    dev = flush.device
+    G = trw.Graph(g.row_ptr, g.col, g.weights)
+    verts_h = sy.vertex_sources(g.nv)
+    verts = torch.from_numpy(verts_h).to(dev)
+    L = 80
+    peak, peak_kind = measured_peak_hbm()
+    out = {}
+    for name, s, flag in (("alias", trw.SAMPLER_DEFAULT, trw.PREP_ALIAS), ("its", trw.SAMPLER_ITS, trw.PREP_ITS),
+                          ("rej", trw.SAMPLER_REJ, trw.PREP_REJ), ("orej", trw.SAMPLER_OREJ, 0)):
+        row = {}
+        b0 = G.device_bytes()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        if flag:
+            G.prepare(flag)
+        torch.cuda.synchronize()
+        row["prepare_ms"] = round(1000 * (time.perf_counter() - t), 2) if flag else 0.0
+        row["table_bytes"] = int(G.device_bytes() - b0)
+        kw = {"sampler": s, "max_weight": SWEEP_BOUND} if s else {}
+        row["tuning"] = G.autotune(trw.DEEPWALK_WEIGHTED, L, **kw)
+        ms, moves = time_walk(trw, torch, G, flush, sp, trw.DEEPWALK_WEIGHTED, verts, L, 1, trw.KERNEL_PERSISTENT,
+                              **kw)
+        row.update({"steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3), "moves": moves})
+        if gather:
+            row["frac_of_gather_ceiling"] = round(row["steps_per_s"] / gather["loads_per_s"], 4)
+        if name == "alias":
+            bpm = SECTOR + 4
+            row["bytes_per_move_source"] = "closed form: one 32-byte record and the path entry"
+        else:
+            # the oracle on the first walks of the batch (same walk indices)
+            tabs = {"its": oracle.prepare_its(g.row_ptr, g.weights)} if s == trw.SAMPLER_ITS else (
+                {"pmax": oracle.prepare_rej(g.row_ptr, g.weights)} if s == trw.SAMPLER_REJ else {})
+            t = time.perf_counter()
+            res = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, verts_h[:walks_cpu], L, 1, sampler=s,
+                              weights=g.weights, max_weight=SWEEP_BOUND, **tabs)
+            dt = time.perf_counter() - t
+            assert res.status == 0
+            mv = max(1, res.stats["moves"])
+            bpm = (32.0 * res.stats["sectors"] + res.stats["out_bytes"]) / mv
+            row["bytes_per_move_source"] = "oracle sector model (32-byte sectors) on the CPU sample"
+            row["cpu_oracle"] = {"steps_per_s": round(res.stats["moves"] / dt, 1), "cores": 1,
+                                 "sample": f"first {walks_cpu} walks, {res.stats['moves']} moves, {dt:.2f}s"}
+            row["attempts_per_move"] = round(res.stats["attempts"] / mv, 4) if s != trw.SAMPLER_ITS else None
+        achieved = moves * bpm / (ms / 1000.0) / 1e9
+        row["roofline"] = {"bound": "hbm", "bytes_per_move": round(bpm, 2), "achieved": round(achieved, 1),
+                           "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                           "peak_kind": f"{peak_kind} copy bandwidth"}
+        out[name] = row
+        log(f"sampler {name}: {row}")
+    G.free()
+    return out
+
+
 def serve_trace(g, n_requests, rate, seed=6):
     """The serving mix (an open-loop Poisson trace): 90% single-source PPR with
     n log-uniform in [1e3, 1e5] (endpoints), 5% weighted DeepWalk and 5%
@@ -770,6 +836,7 @@ def run_ours(args, wl):
     per_algo = None
     serve = None
     replay = None
+    sweep = None
     gather = measure_gather_ceiling(trw, g) if rank == 0 else None
     if rank == 0 and not args.no_extras:
         # every algorithm on this graph: with the label index and neighbour
@@ -784,6 +851,7 @@ def run_ours(args, wl):
         per_algo = measure_per_algo(trw, torch, G, g, flush, sp, G_paper)
         del G_paper
         if G.has_weights:
+            sweep = measure_sampler_sweep(trw, torch, g, flush, sp, gather)
             serve = measure_serve(trw, torch, G, g, n_requests=args.serve_requests)
 
     if rank != 0:
@@ -816,6 +884,7 @@ def run_ours(args, wl):
         "plan_replay": replay,
         "roofline": roof,
         "per_algo": per_algo,
+        "sampler_sweep": sweep,
         "serve": serve,
         "gather_ceiling": gather,
         "cpu_baseline": cpu,

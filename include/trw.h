@@ -46,7 +46,7 @@ typedef enum {
   TRW_PENDING = 1,              /* serve: request still running */
   TRW_ERR_INVALID = -1,         /* bad argument; nothing was written */
   TRW_ERR_OOM = -2,             /* device or host allocation failed */
-  TRW_ERR_NOT_PREPARED = -3,    /* weighted walk before trw_prepare(TRW_PREP_ALIAS) */
+  TRW_ERR_NOT_PREPARED = -3,    /* weighted walk before trw_prepare of its sampler's table */
   TRW_ERR_CUDA = -4,            /* a CUDA runtime call failed */
   TRW_ERR_TIMEOUT = -5,         /* a bounded wait ran out */
   TRW_ERR_REJECT_CAP = -6,      /* a rejection step exceeded TRW_REJECT_CAP trials */
@@ -77,6 +77,28 @@ typedef enum {
 #define TRW_OUT_PATHS 0u        /* out_paths[i * (max_len + 1) + k] = Q[k] */
 #define TRW_OUT_ENDPOINTS 1u    /* out_paths[i] = the last vertex of walk i */
 
+/* Sampling method of TRW_DEEPWALK_WEIGHTED (Section 2.3); the other
+ * algorithms take TRW_SAMPLER_DEFAULT.  All four draw from the same law
+ * over the integer weights W_e = round-half-even(w_e * 2^16), within the
+ * fixed-point rounding of each method's thresholds.
+ *   DEFAULT  ALIAS over the tables of TRW_PREP_ALIAS: one record per move.
+ *   ITS      static ITS over the prefix sums of TRW_PREP_ITS: x uniform in
+ *            [0, p'_{d-1}), then the smallest i with x < p'_i (binary search).
+ *   REJ      rejection against p*_v = max W_e of the row (TRW_PREP_REJ):
+ *            darts (x, y) with x uniform in [0, d_v) until y < W_x / p*_v,
+ *            the 32-bit word y tested against floor(W_x * 2^32 / p*_v).
+ *   OREJ     rejection against the caller's bound P = round-half-even(
+ *            max_weight * 2^16); no preparation.  P should be >= every W_e:
+ *            a larger W_e is accepted like W_e = P.  A row whose weights are
+ *            all zero is a dead end for ALIAS, ITS and REJ; under O-REJ it
+ *            exhausts the trial cap (TRW_ERR_REJECT_CAP).
+ * Draw a of step s of walk i is Philox block (i, s, a, 0); REJ and O-REJ
+ * take as many draws as darts. */
+#define TRW_SAMPLER_DEFAULT 0
+#define TRW_SAMPLER_ITS 1
+#define TRW_SAMPLER_REJ 2
+#define TRW_SAMPLER_OREJ 3
+
 #define TRW_MAX_SCHEMA 16       /* longest MetaPath schema */
 #define TRW_REJECT_CAP 65536    /* rejection trials per step before TRW_ERR_REJECT_CAP */
 
@@ -89,12 +111,13 @@ typedef struct {
   int32_t schema_len;           /* 1 .. TRW_MAX_SCHEMA for MetaPath, ignored otherwise */
   uint32_t out_mode;            /* TRW_OUT_PATHS or TRW_OUT_ENDPOINTS */
   int32_t walks_per_source;     /* >= 1; walk i starts at sources[i / walks_per_source] */
-  int32_t reserved;
+  int32_t sampler;              /* TRW_SAMPLER_*: weighted DeepWalk's sampling method */
   int64_t walk_offset;          /* index of walk 0 in the Philox counter (for sharding a batch) */
+  double max_weight;            /* TRW_SAMPLER_OREJ: MaxWeight, the caller's bound on w_e, finite and > 0 */
 } trw_params;
 
 /* Fills *p with defaults: ppr_stop 0.2, p = q = 1, no schema, paths,
- * one walk per source, offset 0. */
+ * one walk per source, offset 0, the default sampler. */
 void trw_params_default(trw_params* p);
 
 #define TRW_LOAD_CHECK 1u        /* validate col ids and strictly increasing rows on the device */
@@ -108,7 +131,7 @@ void trw_params_default(trw_params* p);
  *   col         host, int32[ne], destination of each edge, in [0, nv).
  *               Node2Vec's IsNeighbor needs every row sorted ascending without
  *               duplicates (checked under TRW_LOAD_CHECK, else assumed).
- *   weights     host, fp32[ne] edge weights (finite, >= 0) or NULL.
+ *   weights     host, fp32[ne] edge weights (finite, >= 0, checked on the device) or NULL.
  *   labels      host, uint8[ne] edge labels or NULL.
  *   flags       TRW_LOAD_CHECK or 0.
  *   out         receives the handle.
@@ -126,6 +149,8 @@ void trw_graph_free(trw_graph* g);
 #define TRW_PREP_NEIGHBOR_HASH 4u /* build the neighbour hash for Node2Vec's IsNeighbor */
 #define TRW_NEIGHBOR_HASH_MIN_DEGREE 8
 #define TRW_PREP_ROW_RECORDS 8u   /* build row records for NAIVE moves and O-REJ candidates */
+#define TRW_PREP_ITS 16u          /* build ITS prefix sums for TRW_SAMPLER_ITS */
+#define TRW_PREP_REJ 32u          /* build REJ bounds p*_v for TRW_SAMPLER_REJ */
 
 /*
  * Preprocessing for static walks (Algorithm 3): for every vertex v, apply the
@@ -158,12 +183,19 @@ void trw_graph_free(trw_graph* g);
  *
  * TRW_PREP_ROW_RECORDS (not in the paper, whose NAIVE move reads the row of
  * the current vertex and then one edge of it, Section 2.3): a 16-byte record
- * per edge slot {destination, its row offset, its degree, 0}, so that a NAIVE
- * move (DeepWalk, PPR) or an O-REJ candidate (Node2Vec) reads one record and
- * the next step needs no row-offset lookup: one dependent random read per
- * move instead of two.  16 bytes of device memory per edge; every walk is
- * identical with and without them.  Preparing records that exist already
- * does nothing.
+ * per edge slot {destination, its row offset, its degree, W_e (the integer
+ * weight, 0 without weights)}, so that a NAIVE move (DeepWalk, PPR), an
+ * O-REJ candidate (Node2Vec), a REJ or O-REJ dart or an ITS pick reads one
+ * record and the next step needs no row-offset lookup: one dependent random
+ * read per move instead of two.  16 bytes of device memory per edge; every
+ * walk is identical with and without them.  Preparing records that exist
+ * already does nothing.
+ *
+ * TRW_PREP_ITS and TRW_PREP_REJ: Algorithm 3 with the ITS and REJ
+ * initialisations of Section 2.3, for the samplers of the same names: the
+ * inclusive prefix sums of every row's integer weights (uint64, 8 bytes of
+ * device memory per edge) and p*_v, every row's largest integer weight
+ * (4 bytes per vertex).  Preparing a table that exists already does nothing.
  *
  * Runs on the device; synchronous.  Errors: TRW_ERR_INVALID (no weights, or
  * no labels, loaded for the requested table; a label too large for the
@@ -188,7 +220,9 @@ trw_status trw_prepare(trw_graph* g, uint32_t what);
  * through device staging; a large batch walks in slices whose copy-out
  * overlaps the next slice's walk.
  * Errors: TRW_ERR_INVALID (a source out of range, max_len < 0, a missing
- * weight/label array, p or q <= 0, ppr_stop outside [0, 1], bad schema),
+ * weight/label array, p or q <= 0, ppr_stop outside [0, 1], bad schema, a
+ * sampler other than the default for an algorithm other than weighted
+ * DeepWalk, an O-REJ max_weight that is not finite or quantises to 0),
  * TRW_ERR_NOT_PREPARED, TRW_ERR_REJECT_CAP, TRW_ERR_OOM, TRW_ERR_CUDA.
  */
 trw_status trw_walk(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
@@ -341,6 +375,12 @@ int64_t trw_graph_device_bytes(const trw_graph* g);
  * H (probability threshold; 0xFFFFFFFF marks a one-element bucket),
  * first/second destination vertex (-1, -1 for a dead vertex).  For tests. */
 trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int32_t* second);
+
+/* Copy the ITS prefix sums (host uint64[ne]) and/or the REJ bounds (host
+ * uint32[nv]) to host buffers; a NULL buffer is skipped.  For tests.
+ * Errors: TRW_ERR_INVALID (NULL graph), TRW_ERR_NOT_PREPARED (a requested
+ * table was not built), TRW_ERR_CUDA. */
+trw_status trw_debug_sampler_tables(const trw_graph* g, uint64_t* cdf, uint32_t* pmax);
 
 /*
  * Copy of the MetaPath label index (tests): *stride receives the words per

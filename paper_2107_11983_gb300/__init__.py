@@ -28,7 +28,11 @@ PREP_LABEL_INDEX = 2
 LABEL_INDEX_MAX_LABELS = 30
 PREP_NEIGHBOR_HASH = 4
 PREP_ROW_RECORDS = 8
-PREP_ALL = PREP_ALIAS | PREP_LABEL_INDEX | PREP_NEIGHBOR_HASH | PREP_ROW_RECORDS
+PREP_ITS = 16
+PREP_REJ = 32
+PREP_ALL = PREP_ALIAS | PREP_LABEL_INDEX | PREP_NEIGHBOR_HASH | PREP_ROW_RECORDS | PREP_ITS | PREP_REJ
+# Sampling method of weighted DeepWalk (Section 2.3): DEFAULT is ALIAS.
+SAMPLER_DEFAULT, SAMPLER_ITS, SAMPLER_REJ, SAMPLER_OREJ = 0, 1, 2, 3
 MAX_SCHEMA = 16
 MAX_BATCH = 64
 
@@ -49,7 +53,8 @@ class TRWError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("ppr_stop", ctypes.c_double), ("n2v_p", ctypes.c_double), ("n2v_q", ctypes.c_double),
                 ("schema", ctypes.c_void_p), ("schema_len", ctypes.c_int32), ("out_mode", ctypes.c_uint32),
-                ("walks_per_source", ctypes.c_int32), ("reserved", ctypes.c_int32), ("walk_offset", ctypes.c_int64)]
+                ("walks_per_source", ctypes.c_int32), ("sampler", ctypes.c_int32), ("walk_offset", ctypes.c_int64),
+                ("max_weight", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -105,6 +110,7 @@ _SIGS = {
     "trw_graph_device_bytes": (ctypes.c_int64, [_VP]),
     "trw_debug_alias": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "trw_debug_label_index": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "trw_debug_sampler_tables": (ctypes.c_int, [_VP, _VP, _VP]),
     "trw_debug_is_neighbor": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP]),
     "trw_debug_philox": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, _VP]),
     "trw_serve_config_default": (None, [_VP]),
@@ -202,8 +208,10 @@ def _stream_arg(stream, *arrays) -> int:
 
 
 def _params(algo: int, ppr_stop: float, n2v_p: float, n2v_q: float, schema, walks_per_source: int,
-            endpoints: bool, walk_offset: int):
+            endpoints: bool, walk_offset: int, sampler: int = SAMPLER_DEFAULT, max_weight: float = 0.0):
     p = _Params()
+    p.sampler = sampler
+    p.max_weight = max_weight
     p.ppr_stop = ppr_stop
     p.n2v_p = n2v_p
     p.n2v_q = n2v_q
@@ -233,6 +241,9 @@ class Graph:
         cl = _as_host(col, np.int32)
         w = None if weights is None else _as_host(weights, np.float32)
         lab = None if labels is None else _as_host(labels, np.uint8)
+        for name, a in (("weights", w), ("labels", lab)):
+            if a is not None and a.shape != cl.shape:
+                raise ValueError(f"{name} has {a.shape[0]} entries for {cl.shape[0]} edges")
         h = ctypes.c_void_p(0)
         st = lib.trw_graph_load(rp.shape[0] - 1, cl.shape[0], rp.ctypes.data, cl.ctypes.data,
                                 0 if w is None else w.ctypes.data, 0 if lab is None else lab.ctypes.data,
@@ -266,7 +277,8 @@ class Graph:
     def prepare(self, what: int = PREP_ALIAS):
         """trw_prepare: PREP_ALIAS (weighted DeepWalk tables), PREP_LABEL_INDEX
         (MetaPath label index), PREP_NEIGHBOR_HASH (Node2Vec IsNeighbor) and/or
-        PREP_ROW_RECORDS (one read per NAIVE move or O-REJ candidate)."""
+        PREP_ROW_RECORDS (one read per NAIVE move or O-REJ candidate), PREP_ITS and
+        PREP_REJ (the tables of weighted DeepWalk's ITS and REJ samplers)."""
         _check(load_library().trw_prepare(self._h, what), "trw_prepare")
 
     def device_bytes(self) -> int:
@@ -276,12 +288,14 @@ class Graph:
     def walk(self, algo: int, sources, max_len: int, seed: int, *, ppr_stop: float = 0.2, n2v_p: float = 1.0,
              n2v_q: float = 1.0, schema=None, walks_per_source: int = 1, endpoints: bool = False,
              walk_offset: int = 0, kernel: int = KERNEL_AUTO, out_paths=None, out_lengths=None, stream=None,
-             sync: bool = True) -> WalkOutput:
+             sync: bool = True, sampler: int = SAMPLER_DEFAULT, max_weight: float = 0.0) -> WalkOutput:
         """trw_walk_ex.  Outputs follow the sources: numpy for host sources, CUDA
-        tensors for CUDA sources, unless out_paths / out_lengths are given."""
+        tensors for CUDA sources, unless out_paths / out_lengths are given.
+        sampler / max_weight choose weighted DeepWalk's sampling method."""
         lib = load_library()
         algo = ALGOS.get(algo, algo) if isinstance(algo, str) else algo
-        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset)
+        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset, sampler,
+                          max_weight)
         if _is_torch(sources):
             src = sources if sources.dtype == _torch().int32 else sources.to(_torch().int32)
             src = src.contiguous()
@@ -328,7 +342,8 @@ class Graph:
             wps = r.get("walks_per_source", 1)
             ep = r.get("endpoints", False)
             p, k = _params(algo, r.get("ppr_stop", 0.2), r.get("n2v_p", 1.0), r.get("n2v_q", 1.0), r.get("schema"),
-                           wps, ep, r.get("walk_offset", 0))
+                           wps, ep, r.get("walk_offset", 0), r.get("sampler", SAMPLER_DEFAULT),
+                           r.get("max_weight", 0.0))
             keep.append(k)
             src = r["sources"]
             if not _is_cuda(src):
@@ -374,7 +389,8 @@ class Graph:
 
     def autotune(self, algo: int, max_len: int = 10, **kw) -> dict:
         p, keep = _params(algo, kw.get("ppr_stop", 0.2), kw.get("n2v_p", 1.0), kw.get("n2v_q", 1.0),
-                          kw.get("schema"), 1, kw.get("endpoints", False), 0)
+                          kw.get("schema"), 1, kw.get("endpoints", False), 0, kw.get("sampler", SAMPLER_DEFAULT),
+                          kw.get("max_weight", 0.0))
         t = Tuning()
         _check(load_library().trw_autotune(self._h, algo, ctypes.byref(p), max_len, ctypes.byref(t)), "trw_autotune")
         return t.as_dict()
@@ -404,6 +420,15 @@ class Graph:
         _check(lib.trw_debug_label_index(self._h, ctypes.byref(st), v.ctypes.data, e.ctypes.data),
                "trw_debug_label_index")
         return st.value, v, e
+
+    def debug_sampler_tables(self, its: bool = True, rej: bool = True):
+        """(ITS prefix sums uint64[ne] or None, REJ bounds uint32[nv] or None) from the device."""
+        cdf = np.empty(self.ne, dtype=np.uint64) if its else None
+        pm = np.empty(self.nv, dtype=np.uint32) if rej else None
+        _check(load_library().trw_debug_sampler_tables(self._h, None if cdf is None else cdf.ctypes.data,
+                                                        None if pm is None else pm.ctypes.data),
+               "trw_debug_sampler_tables")
+        return cdf, pm
 
     def debug_is_neighbor(self, u, v) -> np.ndarray:
         """IsNeighbor(v[i], u[i]) as the walk kernels evaluate it (bool array)."""
@@ -494,10 +519,12 @@ class Server:
 
     def submit(self, algo: int, sources, max_len: int, seed: int, out_paths, out_lengths, *, ppr_stop: float = 0.2,
                n2v_p: float = 1.0, n2v_q: float = 1.0, schema=None, walks_per_source: int = 1,
-               endpoints: bool = False, walk_offset: int = 0) -> int:
+               endpoints: bool = False, walk_offset: int = 0, sampler: int = SAMPLER_DEFAULT,
+               max_weight: float = 0.0) -> int:
         """Queue a request; raises TRWError(ERR_BUSY) when it cannot be admitted now."""
         lib = load_library()
-        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset)
+        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset, sampler,
+                          max_weight)
         src = sources if _is_torch(sources) else np.ascontiguousarray(sources, dtype=np.int32)
         if any(_is_cuda(x) for x in (src, out_paths, out_lengths)):
             # the server runs on its own streams: work queued on the caller's

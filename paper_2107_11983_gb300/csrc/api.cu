@@ -105,6 +105,8 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->lerec);
   cudaFree(g->nh_slots);
   cudaFree(g->rrec);
+  cudaFree(g->its_cdf);
+  cudaFree(g->rej_pmax);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);
@@ -226,6 +228,15 @@ extern "C" trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_
     graph_release(g);
     return trw_fail(TRW_ERR_INVALID, "a column id is outside [0, nv)");
   }
+  if (g->weights) {
+    LOAD_CUDA(launch_check_weights(ne, g->weights, g->ctrl, g->stream), "check weights");
+    LOAD_CUDA(cudaStreamSynchronize(g->stream), "check weights");
+    LOAD_CUDA(cudaMemcpy(&c, g->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost), "read ctrl");
+    if (c.err != 0) {
+      graph_release(g);
+      return trw_fail(TRW_ERR_INVALID, "an edge weight is negative or not finite");
+    }
+  }
   g->sorted = unsorted == 0;
   g->tuning.block_threads = 256;
   g->tuning.blocks_per_sm = 0;
@@ -250,6 +261,9 @@ DevGraph trw_dev_graph(const trw_graph* g) {
   d.col = g->col;
   d.alias = g->alias;
   d.labels = g->labels;
+  d.weights = g->weights;
+  d.cdf = g->its_cdf;
+  d.pmax = g->rej_pmax;
   d.rrec = g->rrec;
   d.lidx.vrec = g->lvrec;
   d.lidx.erec = g->lerec;
@@ -360,7 +374,7 @@ static trw_status prepare_row_records(trw_graph* g) {
   const size_t bytes = sizeof(int4) * (size_t)g->ne;
   trw_status st = alloc_dev((void**)&rec, bytes, "row records");
   if (st != TRW_OK) return st;
-  cudaError_t e = launch_row_records(g->ne, g->row_ptr, g->col, rec, g->stream);
+  cudaError_t e = launch_row_records(g->ne, g->row_ptr, g->col, g->weights, rec, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) {
     cudaFree(rec);
@@ -371,12 +385,48 @@ static trw_status prepare_row_records(trw_graph* g) {
   return TRW_OK;
 }
 
+// ITS prefix sums and REJ bounds (Algorithm 3 with the ITS and REJ
+// initialisations of Section 2.3), built together in one pass over the weights.
+static trw_status prepare_sampler_tables(trw_graph* g, bool its, bool rej) {
+  if (its && g->its_cdf) its = false;
+  if (rej && g->rej_pmax) rej = false;
+  if (!its && !rej) return TRW_OK;
+  unsigned long long* cdf = nullptr;
+  uint32_t* pmax = nullptr;
+  const size_t cbytes = sizeof(unsigned long long) * (size_t)g->ne, pbytes = sizeof(uint32_t) * (size_t)g->nv;
+  trw_status st = TRW_OK;
+  if (its) st = alloc_dev((void**)&cdf, cbytes, "ITS prefix sums");
+  if (st == TRW_OK && rej) st = alloc_dev((void**)&pmax, pbytes, "REJ bounds");
+  if (st == TRW_OK) {
+    cudaError_t e = launch_sampler_tables((int32_t)g->nv, g->row_ptr, g->weights, cdf, pmax, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) st = trw_cuda_fail(e, "prepare ITS / REJ tables");
+  }
+  if (st != TRW_OK) {
+    cudaFree(cdf);
+    cudaFree(pmax);
+    return st;
+  }
+  if (cdf) {
+    g->its_cdf = cdf;
+    g->device_bytes += (int64_t)cbytes;
+  }
+  if (pmax) {
+    g->rej_pmax = pmax;
+    g->device_bytes += (int64_t)pbytes;
+  }
+  return TRW_OK;
+}
+
 extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
-  if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX | TRW_PREP_NEIGHBOR_HASH | TRW_PREP_ROW_RECORDS))
+  if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX | TRW_PREP_NEIGHBOR_HASH | TRW_PREP_ROW_RECORDS | TRW_PREP_ITS |
+               TRW_PREP_REJ))
     return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
   std::lock_guard<std::mutex> lk(g->mu);
   if ((what & TRW_PREP_ALIAS) && !g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
+  if ((what & (TRW_PREP_ITS | TRW_PREP_REJ)) && !g->weights)
+    return trw_fail(TRW_ERR_INVALID, "ITS and REJ preparation need edge weights");
   if ((what & TRW_PREP_LABEL_INDEX) && !g->labels) return trw_fail(TRW_ERR_INVALID, "the label index needs edge labels");
   if (what & TRW_PREP_ALIAS) {
     trw_status st = prepare_alias(g);
@@ -388,6 +438,10 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   }
   if (what & TRW_PREP_NEIGHBOR_HASH) {
     trw_status st = prepare_neighbor_hash(g);
+    if (st != TRW_OK) return st;
+  }
+  if (what & (TRW_PREP_ITS | TRW_PREP_REJ)) {
+    trw_status st = prepare_sampler_tables(g, (what & TRW_PREP_ITS) != 0, (what & TRW_PREP_REJ) != 0);
     if (st != TRW_OK) return st;
   }
   if (what & TRW_PREP_ROW_RECORDS) return prepare_row_records(g);
@@ -447,9 +501,35 @@ trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pi
       else sp->schema_hi |= (uint64_t)p.schema[i] << (8 * (i - 8));
     }
   }
+  if (p.sampler != TRW_SAMPLER_DEFAULT && algo != TRW_DEEPWALK_WEIGHTED)
+    return trw_fail(TRW_ERR_INVALID, "a sampler can be chosen for weighted DeepWalk only");
   if (algo == TRW_DEEPWALK_WEIGHTED) {
     if (!g->weights) return trw_fail(TRW_ERR_INVALID, "weighted walks need edge weights");
-    if (!g->prepared_alias) return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_ALIAS) first");
+    switch (p.sampler) {
+      case TRW_SAMPLER_DEFAULT:
+        if (!g->prepared_alias) return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_ALIAS) first");
+        break;
+      case TRW_SAMPLER_ITS:
+        if (!g->its_cdf) return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_ITS) first");
+        sp->algo = DW_ITS;
+        break;
+      case TRW_SAMPLER_REJ:
+        if (!g->rej_pmax) return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_REJ) first");
+        sp->algo = DW_REJ;
+        break;
+      case TRW_SAMPLER_OREJ: {
+        // the bound P = round-half-even(MaxWeight * 2^16), clamped like a weight
+        if (!std::isfinite(p.max_weight) || !(p.max_weight > 0.0))
+          return trw_fail(TRW_ERR_INVALID, "O-REJ needs a finite max_weight > 0");
+        double t = std::rint(p.max_weight * 65536.0);
+        if (t > 4294967295.0) t = 4294967295.0;
+        if (t < 1.0) return trw_fail(TRW_ERR_INVALID, "max_weight %g quantises to 0", p.max_weight);
+        sp->T_stop = (uint64_t)t;  // the bound rides in the PPR-only threshold
+        sp->algo = DW_OREJ;
+        break;
+      }
+      default: return trw_fail(TRW_ERR_INVALID, "unknown sampler %d", (int)p.sampler);
+    }
   }
   return TRW_OK;
 }
@@ -813,6 +893,16 @@ extern "C" trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* 
     first[i] = (int32_t)rec[(size_t)i].a.y;
     second[i] = (int32_t)rec[(size_t)i].a.z;
   }
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_debug_sampler_tables(const trw_graph* g, uint64_t* cdf, uint32_t* pmax) {
+  if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if ((cdf && !g->its_cdf) || (pmax && !g->rej_pmax)) return trw_fail(TRW_ERR_NOT_PREPARED, "table not prepared");
+  if (cdf && g->ne > 0)
+    CUDA_TRY(cudaMemcpy(cdf, g->its_cdf, sizeof(uint64_t) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy ITS sums");
+  if (pmax && g->nv > 0)
+    CUDA_TRY(cudaMemcpy(pmax, g->rej_pmax, sizeof(uint32_t) * (size_t)g->nv, cudaMemcpyDeviceToHost), "copy REJ bounds");
   return TRW_OK;
 }
 

@@ -512,11 +512,47 @@ __global__ void label_gather_kernel(int64_t ne, int32_t stride, const int32_t* _
 // ---------------------------------------------------------------- row records
 
 __global__ void row_records_kernel(int64_t ne, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                   int4* __restrict__ rec) {
+                                   const float* __restrict__ weights, int4* __restrict__ rec) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = col[e];
     const int32_t o = row_ptr[c];
-    rec[e] = make_int4(c, o, row_ptr[c + 1] - o, 0);
+    const uint32_t w = weights ? weight_fixed(weights[e]) : 0u;
+    rec[e] = make_int4(c, o, row_ptr[c + 1] - o, (int32_t)w);
+  }
+}
+
+// ITS and REJ initialisation (Section 2.3) for static weighted walks, one
+// warp per row: the inclusive prefix sums P' of the row's integer weights
+// (32 at a time: a warp scan plus the running total) and p*_v, the largest
+// integer weight.  Either output may be null.
+__global__ void sampler_tables_kernel(int32_t nv, const int32_t* __restrict__ row_ptr,
+                                      const float* __restrict__ weights, unsigned long long* __restrict__ cdf,
+                                      uint32_t* __restrict__ pmax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
+    const int32_t lo = row_ptr[v], hi = row_ptr[v + 1];
+    unsigned long long run = 0;
+    uint32_t mx = 0;
+    for (int32_t base = lo; base < hi; base += 32) {
+      const int32_t e = base + lane;
+      const uint32_t w = e < hi ? weight_fixed(weights[e]) : 0u;
+      mx = max(mx, w);
+      if (cdf) {
+        unsigned long long incl = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (e < hi) cdf[e] = run + incl;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    if (pmax) {
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) pmax[v] = mx;
+    }
   }
 }
 
@@ -538,6 +574,16 @@ __global__ void check_graph_kernel(int32_t nv, const int32_t* __restrict__ row_p
     }
     if (bad_order) atomicExch(unsorted, 1);
   }
+}
+
+// Every weight finite and non-negative.
+__global__ void check_weights_kernel(int64_t ne, const float* __restrict__ w, Ctrl* ctrl) {
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    const float x = w[e];
+    bad |= !(x >= 0.0f) || isinf(x);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(&ctrl->err, 0, kErrInvalid);
 }
 
 // Rows of kBigRow edges or more, collected on the device and sorted by
@@ -660,11 +706,21 @@ cudaError_t launch_prepare_labels(int32_t nv, int64_t ne, const int32_t* row_ptr
   return e;
 }
 
-cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, int4* rec, cudaStream_t st) {
+cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, const float* weights, int4* rec,
+                               cudaStream_t st) {
   if (ne <= 0) return cudaSuccess;
   int64_t blocks = (ne + 255) / 256;
   if (blocks > 65535) blocks = 65535;
-  row_records_kernel<<<(unsigned)blocks, 256, 0, st>>>(ne, row_ptr, col, rec);
+  row_records_kernel<<<(unsigned)blocks, 256, 0, st>>>(ne, row_ptr, col, weights, rec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sampler_tables(int32_t nv, const int32_t* row_ptr, const float* weights, unsigned long long* cdf,
+                                  uint32_t* pmax, cudaStream_t st) {
+  if (nv <= 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)nv * 32 + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  sampler_tables_kernel<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, weights, cdf, pmax);
   return cudaGetLastError();
 }
 
@@ -674,6 +730,14 @@ cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t
   int64_t blocks = ((int64_t)nv + 255) / 256;
   if (blocks > 65535) blocks = 65535;
   check_graph_kernel<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, col, ctrl, d_unsorted);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_weights(int64_t ne, const float* weights, Ctrl* ctrl, cudaStream_t st) {
+  if (ne <= 0) return cudaSuccess;
+  int64_t blocks = (ne + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  check_weights_kernel<<<(unsigned)blocks, 256, 0, st>>>(ne, weights, ctrl);
   return cudaGetLastError();
 }
 

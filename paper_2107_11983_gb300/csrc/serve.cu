@@ -331,7 +331,9 @@ __device__ __forceinline__ int spec_check(const WalkSpec& sp, unsigned long long
                                           unsigned long long published) {
   if (ck >= published) return 1;
   if (!(cb < ce) || (int64_t)ce > sp.nwalks) return 2;
-  if (sp.algo < 0 || sp.algo > 4 || sp.wps < 1 || sp.max_len < 0 || (sp.algo == METAPATH && sp.schema_len < 1)) return 3;
+  if (sp.algo < 0 || sp.algo > DW_OREJ || sp.algo == MIXED || sp.wps < 1 || sp.max_len < 0 ||
+      (sp.algo == METAPATH && sp.schema_len < 1) || (sp.algo == DW_OREJ && sp.T_stop == 0))
+    return 3;
   const uintptr_t ptrs = reinterpret_cast<uintptr_t>(sp.sources) | reinterpret_cast<uintptr_t>(sp.out_paths) |
                          reinterpret_cast<uintptr_t>(sp.out_lengths);
   if (!sp.sources || !sp.out_paths || !sp.out_lengths || (ptrs & 3)) return 4;

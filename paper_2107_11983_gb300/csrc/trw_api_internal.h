@@ -26,6 +26,8 @@ struct trw_graph {
   int32_t lstride = 0;
   int32_t lnl = 0;                   // labels in the index (largest label + 1)
   int4* rrec = nullptr;              // row records (trw_prepare(ROW_RECORDS))
+  unsigned long long* its_cdf = nullptr;  // ITS prefix sums (trw_prepare(ITS)): ne
+  uint32_t* rej_pmax = nullptr;      // REJ bounds p*_v (trw_prepare(REJ)): nv
   int32_t* nh_slots = nullptr;       // neighbour hash (trw_prepare(NEIGHBOR_HASH)): 2 ne int32
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags

@@ -8,7 +8,14 @@
 
 namespace trw {
 
-enum Algo : int { DEEPWALK = 0, DEEPWALK_WEIGHTED = 1, PPR = 2, NODE2VEC = 3, METAPATH = 4, MIXED = 5 };
+// Device algorithm ids: the public ones, the mixed-batch dispatcher, and
+// weighted DeepWalk under the other samplers of Section 2.3.
+enum Algo : int {
+  DEEPWALK = 0, DEEPWALK_WEIGHTED = 1, PPR = 2, NODE2VEC = 3, METAPATH = 4, MIXED = 5,
+  DW_ITS = 6,    // weighted DeepWalk, static ITS over the stored prefix sums
+  DW_REJ = 7,    // weighted DeepWalk, REJ with the stored per-vertex bound p*_v
+  DW_OREJ = 8    // weighted DeepWalk, O-REJ with the caller's bound
+};
 
 constexpr int kMaxSchema = 16;
 constexpr uint32_t kRejectCap = 65536;
@@ -80,7 +87,10 @@ struct DevGraph {
   const int32_t* __restrict__ col;       // [ne], rows sorted ascending when sorted != 0
   const AliasRec* __restrict__ alias;    // [ne] after ALIAS preparation, or null
   const uint8_t* __restrict__ labels;    // [ne + 16] (padded for word loads), or null
-  const int4* __restrict__ rrec;         // [ne] row records {dst, row_ptr[dst], deg(dst), 0}, or null
+  const float* __restrict__ weights;     // [ne] edge weights, or null
+  const unsigned long long* __restrict__ cdf;  // [ne] ITS: inclusive prefix sums of the row's integer weights, or null
+  const uint32_t* __restrict__ pmax;     // [nv] REJ: largest integer weight of the row (0: none positive), or null
+  const int4* __restrict__ rrec;         // [ne] row records {dst, row_ptr[dst], deg(dst), W_e}, or null
   LabelIndex lidx;
   NeighborHash nh;
   int32_t nv;
@@ -97,7 +107,7 @@ struct WalkSpec {
   uint32_t key0, key1;        // Philox key (seed)
   uint32_t walk_offset;       // Philox counter word 0 of walk 0
   uint32_t schema_len;
-  uint64_t T_stop;            // PPR stop threshold
+  uint64_t T_stop;            // PPR stop threshold; DW_OREJ: the caller's bound P on the integer weights (>= 1)
   uint64_t T_ret, T_nb, T_far;// Node2Vec O-REJ thresholds (Eq. 1 over p*)
   uint64_t T_lo, T_hi;        // min / max of T_nb, T_far (skip IsNeighbor outside [T_lo, T_hi))
   const int32_t* sources;
@@ -149,6 +159,20 @@ __device__ __forceinline__ uint4 draw_block(const WalkSpec& sp, uint32_t w, uint
 __device__ __forceinline__ uint32_t below(uint4 B, uint32_t n) {
   const unsigned long long r64 = ((unsigned long long)B.y << 32) | B.x;
   return (uint32_t)__umul64hi(r64, (unsigned long long)n);
+}
+
+// Uniform integer in [0, n) for a 64-bit n: high 64 bits of r64 * n.
+__device__ __forceinline__ unsigned long long below64(uint4 B, unsigned long long n) {
+  const unsigned long long r64 = ((unsigned long long)B.y << 32) | B.x;
+  return __umul64hi(r64, n);
+}
+
+// Integer weight of a finite non-negative fp32 weight: round-half-even(w * 2^16),
+// clamped to 2^32 - 1.  w * 2^16 is exact in fp32 (a power-of-two scale), and
+// an fp32 value below 2^32 is at most 2^32 - 256, so the clamp is one compare.
+__device__ __forceinline__ uint32_t weight_fixed(float w) {
+  const float t = w * 65536.0f;
+  return t >= 4294967296.0f ? 0xffffffffu : __float2uint_rn(t);
 }
 
 // Read-only loads through the non-coherent path.

@@ -48,7 +48,11 @@ cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr,
                                  int32_t min_degree, int32_t* slots, cudaStream_t st);
 
 // Row records {col[e], row_ptr[col[e]], deg(col[e]), 0} of every edge slot.
-cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, int4* rec, cudaStream_t st);
+cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, const float* weights, int4* rec,
+                               cudaStream_t st);
+cudaError_t launch_sampler_tables(int32_t nv, const int32_t* row_ptr, const float* weights, unsigned long long* cdf,
+                                  uint32_t* pmax, cudaStream_t st);
+cudaError_t launch_check_weights(int64_t ne, const float* weights, Ctrl* ctrl, cudaStream_t st);
 
 // Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl,

@@ -225,6 +225,9 @@ int persistent_blocks_per_sm(int algo, int block_threads, bool coop) {
     case METAPATH:
       return coop ? blocks_per_sm_of(walk_persistent<METAPATH, true>, block_threads)
                   : blocks_per_sm_of(walk_persistent<METAPATH, false>, block_threads);
+    case DW_ITS: return blocks_per_sm_of(walk_persistent<DW_ITS, false>, block_threads);
+    case DW_REJ: return blocks_per_sm_of(walk_persistent<DW_REJ, false>, block_threads);
+    case DW_OREJ: return blocks_per_sm_of(walk_persistent<DW_OREJ, false>, block_threads);
     default:
       return coop ? blocks_per_sm_of(walk_persistent<MIXED, true>, block_threads)
                   : blocks_per_sm_of(walk_persistent<MIXED, false>, block_threads);
@@ -250,6 +253,9 @@ cudaError_t launch_walk_plain(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl,
     case PPR: walk_plain<PPR><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
     case NODE2VEC: walk_plain<NODE2VEC><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
     case METAPATH: walk_plain<METAPATH><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case DW_ITS: walk_plain<DW_ITS><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case DW_REJ: walk_plain<DW_REJ><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case DW_OREJ: walk_plain<DW_OREJ><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -281,6 +287,9 @@ cudaError_t launch_walk_persistent(const DevGraph& g, const WalkSpec& sp, Ctrl* 
       if (cv) TRW_LAUNCH(METAPATH, true);
       else TRW_LAUNCH(METAPATH, false);
       break;
+    case DW_ITS: TRW_LAUNCH(DW_ITS, false); break;
+    case DW_REJ: TRW_LAUNCH(DW_REJ, false); break;
+    case DW_OREJ: TRW_LAUNCH(DW_OREJ, false); break;
     default: return cudaErrorInvalidValue;
   }
 #undef TRW_LAUNCH

@@ -251,6 +251,67 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     if (j < 0) return kBroken;                                 // count and select disagree: internal error
     next = ldg(g.col + W.off + j);
     return kMoved;
+  } else if (A == DW_ITS) {
+    // Static ITS generation from the stored P' of the row: x uniform in
+    // [0, p'_{d-1}), then the smallest i with x < p'_i, by a lower-bound
+    // search over the first d - 1 sums (p'_{d-1} > x bounds the answer).
+    if (CHECK && !g.cdf) return kBroken;
+    const unsigned long long* P = g.cdf + W.off;
+    const unsigned long long S = __ldg(P + W.d - 1);
+    if (S == 0ull) return kStop;                               // no positive weight
+    const unsigned long long x = below64(B, S);
+    int32_t lo = 0, n = W.d - 1;
+    while (n > 0) {
+      const int32_t half = n >> 1;
+      if (__ldg(P + lo + half) <= x) {
+        lo += half + 1;
+        n -= half + 1;
+      } else {
+        n = half;
+      }
+    }
+    const int64_t e = (int64_t)W.off + lo;
+    if (g.rrec) {
+      const int4 r = __ldg(g.rrec + e);
+      next = r.x;
+      W.nxo = r.y;
+      W.nxd = r.z;
+      W.nxv = true;
+    } else {
+      next = ldg(g.col + e);
+    }
+    return kMoved;
+  } else if (A == DW_REJ || A == DW_OREJ) {
+    // REJ / O-REJ: dart (x, y), x uniform in [0, d_v); it hits when
+    // y < floor(W_x * 2^32 / p*), i.e. when (y + 1) * p* <= W_x * 2^32.
+    // p* is the row's stored bound (REJ) or the caller's (O-REJ, in T_stop).
+    if (CHECK && !g.rrec && !g.weights) return kBroken;
+    unsigned long long ps = sp.T_stop;
+    if (A == DW_REJ && sp.algo != DW_OREJ) {
+      if (CHECK && ((uint32_t)W.cur >= (uint32_t)g.nv || !g.pmax)) return kBroken;
+      ps = __ldg(g.pmax + W.cur);
+      if (ps == 0ull) return kStop;                            // no positive weight
+    }
+    const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
+    int4 rr;
+    uint32_t wx;
+    if (g.rrec) {
+      rr = __ldg(g.rrec + e);
+      wx = (uint32_t)rr.w;
+    } else {
+      rr.x = ldg(g.col + e);
+      wx = weight_fixed(__ldg(g.weights + e));
+    }
+    if (((unsigned long long)B.z + 1ull) * ps <= ((unsigned long long)wx << 32)) {
+      next = rr.x;
+      if (g.rrec) {
+        W.nxo = rr.y;
+        W.nxd = rr.z;
+        W.nxv = true;
+      }
+      return kMoved;
+    }
+    return (W.att + 1 >= kRejectCap) ? kFail : kRetry;
   } else {  // NODE2VEC, O-REJ
     const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
     int4 rr = make_int4(0, 0, 0, 0);
@@ -504,6 +565,9 @@ __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& 
       case PPR: return step_serial<PPR, CHECK>(g, sp, W, next);
       case NODE2VEC: return step_serial<NODE2VEC, CHECK>(g, sp, W, next);
       case METAPATH: return step_serial<METAPATH, CHECK>(g, sp, W, next);
+      case DW_ITS: return step_serial<DW_ITS, CHECK>(g, sp, W, next);
+      case DW_REJ:
+      case DW_OREJ: return step_serial<DW_REJ, CHECK>(g, sp, W, next);
       default: return kBroken;
     }
   }
@@ -522,6 +586,9 @@ __device__ __forceinline__ int step_begin_dispatch(const DevGraph& g, const Walk
       case PPR: return step_begin<PPR, CHECK>(g, sp, W, next, p, coop);
       case NODE2VEC: return step_begin<NODE2VEC, CHECK>(g, sp, W, next, p, coop);
       case METAPATH: return step_begin<METAPATH, CHECK>(g, sp, W, next, p, coop);
+      case DW_ITS: return step_begin<DW_ITS, CHECK>(g, sp, W, next, p, coop);
+      case DW_REJ:  // one instance serves both (fewer registers in the mixed kernels)
+      case DW_OREJ: return step_begin<DW_REJ, CHECK>(g, sp, W, next, p, coop);
       default: return kBroken;
     }
   }

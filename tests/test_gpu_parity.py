@@ -243,12 +243,16 @@ def test_invalid_arguments_write_nothing(small):
         trw.Graph(np.array([0, 2, 1], np.int64), np.array([1, 0], np.int32))
 
 
-def test_negative_weight_refused():
+def test_bad_weight_refused_at_load():
     g = synth.from_edges(3, [(0, 1), (1, 2), (2, 0)])
-    G = trw.Graph(g.row_ptr, g.col, np.array([1.0, -2.0, 1.0], np.float32))
-    with pytest.raises(trw.TRWError) as e:
-        G.prepare()
-    assert e.value.status == -1
+    for bad in (-2.0, float("nan"), float("inf"), -0.0001):
+        with pytest.raises(trw.TRWError) as e:
+            trw.Graph(g.row_ptr, g.col, np.array([1.0, bad, 1.0], np.float32))
+        assert e.value.status == -1
+    with pytest.raises(ValueError):
+        trw.Graph(g.row_ptr, g.col, np.array([1.0, 1.0], np.float32))
+    G = trw.Graph(g.row_ptr, g.col, np.array([1.0, 0.0, 1e30], np.float32))  # zero and huge weights are valid
+    G.prepare(trw.PREP_ALL & ~trw.PREP_LABEL_INDEX)
 
 
 def test_mixed_batch_one_launch(small):
