@@ -448,8 +448,12 @@ def measure_sampler_sweep(trw, torch, g, flush, sp, gather, walks_cpu=20000):
     L = 80
     peak, peak_kind = measured_peak_hbm()
     out = {}
+    # the paper's ITS (binary search over P') runs before the guided records
+    # exist, REJ and O-REJ once on the paper's tables and once with row records
     for name, s, flag in (("alias", trw.SAMPLER_DEFAULT, trw.PREP_ALIAS), ("its", trw.SAMPLER_ITS, trw.PREP_ITS),
-                          ("rej", trw.SAMPLER_REJ, trw.PREP_REJ), ("orej", trw.SAMPLER_OREJ, 0)):
+                          ("its_guided", trw.SAMPLER_ITS, trw.PREP_ITS_GUIDE), ("rej", trw.SAMPLER_REJ, trw.PREP_REJ),
+                          ("orej", trw.SAMPLER_OREJ, 0), ("rej_records", trw.SAMPLER_REJ, trw.PREP_ROW_RECORDS),
+                          ("orej_records", trw.SAMPLER_OREJ, 0)):
         row = {}
         b0 = G.device_bytes()
         torch.cuda.synchronize()
@@ -469,6 +473,17 @@ def measure_sampler_sweep(trw, torch, g, flush, sp, gather, walks_cpu=20000):
         if name == "alias":
             bpm = SECTOR + 4
             row["bytes_per_move_source"] = "closed form: one 32-byte record and the path entry"
+        elif name == "its_guided":
+            bpm = 2 * SECTOR + 4
+            row["bytes_per_move_source"] = ("closed form, lower bound: the cell's 32-byte record, the answer's "
+                                            "record and the path entry (walks identical to its)")
+        elif name.endswith("_records"):
+            base = out[name[:-len("_records")]]
+            row["attempts_per_move"] = base["attempts_per_move"]
+            bpm = SECTOR * base["attempts_per_move"] + (SECTOR if s == trw.SAMPLER_REJ else 0) + 4
+            row["bytes_per_move_source"] = ("closed form: one 16-byte row record (one sector) per dart, the "
+                                            "bound p*_v's sector (REJ) and the path entry; trials from the CPU "
+                                            "sample (walks identical without records)")
         else:
             # the oracle on the first walks of the batch (same walk indices)
             tabs = {"its": oracle.prepare_its(g.row_ptr, g.weights)} if s == trw.SAMPLER_ITS else (

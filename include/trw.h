@@ -151,6 +151,7 @@ void trw_graph_free(trw_graph* g);
 #define TRW_PREP_ROW_RECORDS 8u   /* build row records for NAIVE moves and O-REJ candidates */
 #define TRW_PREP_ITS 16u          /* build ITS prefix sums for TRW_SAMPLER_ITS */
 #define TRW_PREP_REJ 32u          /* build REJ bounds p*_v for TRW_SAMPLER_REJ */
+#define TRW_PREP_ITS_GUIDE 64u    /* build guided ITS records for TRW_SAMPLER_ITS */
 
 /*
  * Preprocessing for static walks (Algorithm 3): for every vertex v, apply the
@@ -196,6 +197,15 @@ void trw_graph_free(trw_graph* g);
  * inclusive prefix sums of every row's integer weights (uint64, 8 bytes of
  * device memory per edge) and p*_v, every row's largest integer weight
  * (4 bytes per vertex).  Preparing a table that exists already does nothing.
+ *
+ * TRW_PREP_ITS_GUIDE (not in the paper, whose ITS generation is a binary
+ * search over P', Section 2.3): a 32-byte record per edge slot with the
+ * edge's ITS bound in draw space, its destination and the destination's row,
+ * and the guide entries of Chen and Asau's guide table (one cell per edge, in
+ * draw space), which bound the answer to a few candidates.  An ITS move then
+ * reads the cell's record and usually one more instead of log2(d) prefix
+ * sums and the edge.  The walks are those of TRW_PREP_ITS exactly; when both
+ * exist the records are used.
  *
  * Runs on the device; synchronous.  Errors: TRW_ERR_INVALID (no weights, or
  * no labels, loaded for the requested table; a label too large for the
@@ -375,6 +385,12 @@ int64_t trw_graph_device_bytes(const trw_graph* g);
  * H (probability threshold; 0xFFFFFFFF marks a one-element bucket),
  * first/second destination vertex (-1, -1 for a dead vertex).  For tests. */
 trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int32_t* second);
+
+/* Copy the guided ITS records to host memory, 8 uint32 words per edge slot:
+ * {U low, U high, destination, its row offset, its degree, first candidate of
+ * the cell, last candidate of the cell, 0}.  For tests.  Errors:
+ * TRW_ERR_INVALID (NULL argument), TRW_ERR_NOT_PREPARED, TRW_ERR_CUDA. */
+trw_status trw_debug_its_records(const trw_graph* g, uint32_t* words);
 
 /* Copy the ITS prefix sums (host uint64[ne]) and/or the REJ bounds (host
  * uint32[nv]) to host buffers; a NULL buffer is skipped.  For tests.

@@ -30,7 +30,9 @@ PREP_NEIGHBOR_HASH = 4
 PREP_ROW_RECORDS = 8
 PREP_ITS = 16
 PREP_REJ = 32
-PREP_ALL = PREP_ALIAS | PREP_LABEL_INDEX | PREP_NEIGHBOR_HASH | PREP_ROW_RECORDS | PREP_ITS | PREP_REJ
+PREP_ITS_GUIDE = 64
+PREP_ALL = (PREP_ALIAS | PREP_LABEL_INDEX | PREP_NEIGHBOR_HASH | PREP_ROW_RECORDS | PREP_ITS | PREP_REJ |
+            PREP_ITS_GUIDE)
 # Sampling method of weighted DeepWalk (Section 2.3): DEFAULT is ALIAS.
 SAMPLER_DEFAULT, SAMPLER_ITS, SAMPLER_REJ, SAMPLER_OREJ = 0, 1, 2, 3
 MAX_SCHEMA = 16
@@ -111,6 +113,7 @@ _SIGS = {
     "trw_debug_alias": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "trw_debug_label_index": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "trw_debug_sampler_tables": (ctypes.c_int, [_VP, _VP, _VP]),
+    "trw_debug_its_records": (ctypes.c_int, [_VP, _VP]),
     "trw_debug_is_neighbor": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP]),
     "trw_debug_philox": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, _VP]),
     "trw_serve_config_default": (None, [_VP]),
@@ -278,7 +281,8 @@ class Graph:
         """trw_prepare: PREP_ALIAS (weighted DeepWalk tables), PREP_LABEL_INDEX
         (MetaPath label index), PREP_NEIGHBOR_HASH (Node2Vec IsNeighbor) and/or
         PREP_ROW_RECORDS (one read per NAIVE move or O-REJ candidate), PREP_ITS and
-        PREP_REJ (the tables of weighted DeepWalk's ITS and REJ samplers)."""
+        PREP_REJ (the tables of weighted DeepWalk's ITS and REJ samplers) and
+        PREP_ITS_GUIDE (guided ITS records: the same ITS walks in about two reads a move)."""
         _check(load_library().trw_prepare(self._h, what), "trw_prepare")
 
     def device_bytes(self) -> int:
@@ -429,6 +433,13 @@ class Graph:
                                                         None if pm is None else pm.ctypes.data),
                "trw_debug_sampler_tables")
         return cdf, pm
+
+    def debug_its_records(self) -> np.ndarray:
+        """Guided ITS records as uint32 [ne, 8]: U low/high, destination, its row
+        offset and degree, the cell's first and last candidates, 0."""
+        out = np.empty((self.ne, 8), dtype=np.uint32)
+        _check(load_library().trw_debug_its_records(self._h, out.ctypes.data), "trw_debug_its_records")
+        return out
 
     def debug_is_neighbor(self, u, v) -> np.ndarray:
         """IsNeighbor(v[i], u[i]) as the walk kernels evaluate it (bool array)."""

@@ -107,6 +107,7 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->rrec);
   cudaFree(g->its_cdf);
   cudaFree(g->rej_pmax);
+  cudaFree(g->its_rec);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);
@@ -264,6 +265,7 @@ DevGraph trw_dev_graph(const trw_graph* g) {
   d.weights = g->weights;
   d.cdf = g->its_cdf;
   d.pmax = g->rej_pmax;
+  d.its_rec = g->its_rec;
   d.rrec = g->rrec;
   d.lidx.vrec = g->lvrec;
   d.lidx.erec = g->lerec;
@@ -418,14 +420,31 @@ static trw_status prepare_sampler_tables(trw_graph* g, bool its, bool rej) {
   return TRW_OK;
 }
 
+static trw_status prepare_its_records(trw_graph* g) {
+  if (g->its_rec) return TRW_OK;
+  ItsRec* rec = nullptr;
+  const size_t bytes = sizeof(ItsRec) * (size_t)g->ne;
+  trw_status st = alloc_dev((void**)&rec, bytes, "guided ITS records");
+  if (st != TRW_OK) return st;
+  cudaError_t e = launch_its_records((int32_t)g->nv, g->row_ptr, g->col, g->weights, rec, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    cudaFree(rec);
+    return trw_cuda_fail(e, "prepare guided ITS records");
+  }
+  g->its_rec = rec;
+  g->device_bytes += (int64_t)bytes;
+  return TRW_OK;
+}
+
 extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
   if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX | TRW_PREP_NEIGHBOR_HASH | TRW_PREP_ROW_RECORDS | TRW_PREP_ITS |
-               TRW_PREP_REJ))
+               TRW_PREP_REJ | TRW_PREP_ITS_GUIDE))
     return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
   std::lock_guard<std::mutex> lk(g->mu);
   if ((what & TRW_PREP_ALIAS) && !g->weights) return trw_fail(TRW_ERR_INVALID, "ALIAS preparation needs edge weights");
-  if ((what & (TRW_PREP_ITS | TRW_PREP_REJ)) && !g->weights)
+  if ((what & (TRW_PREP_ITS | TRW_PREP_REJ | TRW_PREP_ITS_GUIDE)) && !g->weights)
     return trw_fail(TRW_ERR_INVALID, "ITS and REJ preparation need edge weights");
   if ((what & TRW_PREP_LABEL_INDEX) && !g->labels) return trw_fail(TRW_ERR_INVALID, "the label index needs edge labels");
   if (what & TRW_PREP_ALIAS) {
@@ -442,6 +461,10 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   }
   if (what & (TRW_PREP_ITS | TRW_PREP_REJ)) {
     trw_status st = prepare_sampler_tables(g, (what & TRW_PREP_ITS) != 0, (what & TRW_PREP_REJ) != 0);
+    if (st != TRW_OK) return st;
+  }
+  if (what & TRW_PREP_ITS_GUIDE) {
+    trw_status st = prepare_its_records(g);
     if (st != TRW_OK) return st;
   }
   if (what & TRW_PREP_ROW_RECORDS) return prepare_row_records(g);
@@ -510,7 +533,8 @@ trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pi
         if (!g->prepared_alias) return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_ALIAS) first");
         break;
       case TRW_SAMPLER_ITS:
-        if (!g->its_cdf) return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_ITS) first");
+        if (!g->its_cdf && !g->its_rec)
+          return trw_fail(TRW_ERR_NOT_PREPARED, "call trw_prepare(TRW_PREP_ITS or TRW_PREP_ITS_GUIDE) first");
         sp->algo = DW_ITS;
         break;
       case TRW_SAMPLER_REJ:
@@ -903,6 +927,14 @@ extern "C" trw_status trw_debug_sampler_tables(const trw_graph* g, uint64_t* cdf
     CUDA_TRY(cudaMemcpy(cdf, g->its_cdf, sizeof(uint64_t) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy ITS sums");
   if (pmax && g->nv > 0)
     CUDA_TRY(cudaMemcpy(pmax, g->rej_pmax, sizeof(uint32_t) * (size_t)g->nv, cudaMemcpyDeviceToHost), "copy REJ bounds");
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_debug_its_records(const trw_graph* g, uint32_t* words) {
+  if (!g || !words) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (!g->its_rec) return trw_fail(TRW_ERR_NOT_PREPARED, "no guided ITS records");
+  if (g->ne > 0)
+    CUDA_TRY(cudaMemcpy(words, g->its_rec, sizeof(ItsRec) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy ITS records");
   return TRW_OK;
 }
 

@@ -715,6 +715,77 @@ cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t
   return cudaGetLastError();
 }
 
+// Guided ITS records (ItsRec), one warp per row.  Pass 1: the row's prefix
+// sums P'_j by warp scans, with each edge's destination and its row.  Pass 2:
+// U_j = floor((P'_j * 2^64 - 1) / S) in place (0 where P'_j = 0).  Pass 3: the
+// guide.  Cell k holds the draws r with floor(r * d / 2^64) = k, and its first
+// candidate is the answer at its smallest draw (at least 1); the answer at r
+// is the smallest j with r <= U_j, so edge j is the first candidate exactly of
+// the cells from the one after U_{j-1}'s cell to U_j's cell (from cell 0 for
+// the first positive edge): each edge writes its own cells, O(d) per row.  The
+// last candidate of cell k is the first of cell k + 1 (d - 1 for the last).
+__global__ void its_records_kernel(int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                   const float* __restrict__ weights, ItsRec* __restrict__ rec) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t* words = reinterpret_cast<uint32_t*>(rec);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
+    const int32_t lo = row_ptr[v], hi = row_ptr[v + 1];
+    const int32_t d = hi - lo;
+    unsigned long long run = 0;
+    for (int32_t base = lo; base < hi; base += 32) {
+      const int32_t e = base + lane;
+      const uint32_t w = e < hi ? weight_fixed(weights[e]) : 0u;
+      unsigned long long incl = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (e < hi) {
+        const unsigned long long P = run + incl;
+        const int32_t c = col[e];
+        const int32_t co = row_ptr[c];
+        rec[e].a = make_uint4((uint32_t)P, (uint32_t)(P >> 32), (uint32_t)c, (uint32_t)co);
+        rec[e].b = make_uint4((uint32_t)(row_ptr[c + 1] - co), 0xffffffffu, 0xffffffffu, 0u);
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    const unsigned long long S = run;
+    if (S == 0) continue;  // no positive weight: every first candidate stays -1
+    __syncwarp();
+    for (int32_t e = lo + lane; e < hi; e += 32) {
+      const unsigned long long P = ((unsigned long long)rec[e].a.y << 32) | rec[e].a.x;
+      const unsigned long long U =
+          P == 0 ? 0ull : (unsigned long long)((((unsigned __int128)P << 64) - 1u) / (unsigned __int128)S);
+      rec[e].a.x = (uint32_t)U;
+      rec[e].a.y = (uint32_t)(U >> 32);
+    }
+    __syncwarp();
+    for (int32_t j = lane; j < d; j += 32) {
+      const unsigned long long U = ((unsigned long long)rec[lo + j].a.y << 32) | rec[lo + j].a.x;
+      if (U == 0) continue;  // zero prefix: never an answer
+      const unsigned long long Up = j == 0 ? 0ull : ((unsigned long long)rec[lo + j - 1].a.y << 32) | rec[lo + j - 1].a.x;
+      const int64_t k0 = Up == 0 ? 0 : (int64_t)__umul64hi(Up, (unsigned long long)d) + 1;
+      const int64_t k1 = (int64_t)__umul64hi(U, (unsigned long long)d);
+      for (int64_t k = k0; k <= k1; ++k) {
+        words[8 * (int64_t)(lo + k) + 5] = (uint32_t)j;               // b.y of cell k
+        if (k >= 1) words[8 * (int64_t)(lo + k - 1) + 6] = (uint32_t)j;  // b.z of cell k - 1
+      }
+    }
+    if (lane == 0) words[8 * (int64_t)(hi - 1) + 6] = (uint32_t)(d - 1);
+  }
+}
+
+cudaError_t launch_its_records(int32_t nv, const int32_t* row_ptr, const int32_t* col, const float* weights,
+                               ItsRec* rec, cudaStream_t st) {
+  if (nv <= 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)nv * 32 + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  its_records_kernel<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, col, weights, rec);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sampler_tables(int32_t nv, const int32_t* row_ptr, const float* weights, unsigned long long* cdf,
                                   uint32_t* pmax, cudaStream_t st) {
   if (nv <= 0) return cudaSuccess;

@@ -28,6 +28,7 @@ struct trw_graph {
   int4* rrec = nullptr;              // row records (trw_prepare(ROW_RECORDS))
   unsigned long long* its_cdf = nullptr;  // ITS prefix sums (trw_prepare(ITS)): ne
   uint32_t* rej_pmax = nullptr;      // REJ bounds p*_v (trw_prepare(REJ)): nv
+  trw::ItsRec* its_rec = nullptr;    // guided ITS records (trw_prepare(ITS_GUIDE)): ne
   int32_t* nh_slots = nullptr;       // neighbour hash (trw_prepare(NEIGHBOR_HASH)): 2 ne int32
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags

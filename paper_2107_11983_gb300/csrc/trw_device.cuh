@@ -36,6 +36,23 @@ struct __align__(32) AliasRec {
   uint4 b;
 };
 
+// Guided ITS records (an optional preparation; walks are identical with and
+// without it).  ITS picks the smallest i with x < p'_i, x = floor(r64 * S / 2^64)
+// and S = p'_{d-1}; since x < p'_i exactly when max(r64, 1) <= U_i with
+//   U_i = floor((p'_i * 2^64 - 1) / S) for p'_i > 0, and U_i = 0 for p'_i = 0,
+// the search runs on r64 itself and needs no S.  The draw's cell
+// k = floor(r64 * d / 2^64) (one of d equal cells of the 64-bit draw space)
+// bounds the answer: it lies between the answers at the smallest draws of
+// cells k and k + 1, the guide entries of cell k (Chen and Asau's guide
+// table, 1974).  One 32-byte record per edge slot j of a row:
+//   a = {U_j low, U_j high, dst_j, row offset of dst_j}
+//   b = {degree of dst_j, first candidate of cell j, last candidate of cell j, 0}
+// A row without positive weight has first candidate -1 in every record.
+struct __align__(32) ItsRec {
+  uint4 a;
+  uint4 b;
+};
+
 // MetaPath label index (an optional preparation; walks are identical with
 // and without it).  Each row is stably partitioned by label, so the group of
 // label l in row v, [g(v, l), g(v, l + 1)), lists the edges labelled l in CSR
@@ -90,6 +107,7 @@ struct DevGraph {
   const float* __restrict__ weights;     // [ne] edge weights, or null
   const unsigned long long* __restrict__ cdf;  // [ne] ITS: inclusive prefix sums of the row's integer weights, or null
   const uint32_t* __restrict__ pmax;     // [nv] REJ: largest integer weight of the row (0: none positive), or null
+  const ItsRec* __restrict__ its_rec;    // [ne] guided ITS records, or null
   const int4* __restrict__ rrec;         // [ne] row records {dst, row_ptr[dst], deg(dst), W_e}, or null
   LabelIndex lidx;
   NeighborHash nh;

@@ -52,6 +52,8 @@ cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t
                                cudaStream_t st);
 cudaError_t launch_sampler_tables(int32_t nv, const int32_t* row_ptr, const float* weights, unsigned long long* cdf,
                                   uint32_t* pmax, cudaStream_t st);
+cudaError_t launch_its_records(int32_t nv, const int32_t* row_ptr, const int32_t* col, const float* weights,
+                               ItsRec* rec, cudaStream_t st);
 cudaError_t launch_check_weights(int64_t ne, const float* weights, Ctrl* ctrl, cudaStream_t st);
 
 // Graph checks: ids in range, rows strictly increasing (sets *sorted_flag to 0 when not).

@@ -251,6 +251,43 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     if (j < 0) return kBroken;                                 // count and select disagree: internal error
     next = ldg(g.col + W.off + j);
     return kMoved;
+  } else if (A == DW_ITS && g.its_rec) {
+    // Guided ITS: the cell's record bounds the answer, usually to one or two
+    // candidates; the answer's record holds the next vertex and its row.
+    const ItsRec* R = g.its_rec + W.off;
+    const unsigned long long r = max(((unsigned long long)B.y << 32) | B.x, 1ull);
+    const uint32_t k = below(B, (uint32_t)W.d);
+    uint4 ja = __ldg(&R[k].a), jb = __ldg(&R[k].b);
+    int32_t a = (int32_t)jb.y;
+    const int32_t hi = (int32_t)jb.z;
+    if (a < 0) return kStop;                                   // no positive weight
+    if (CHECK && (a >= W.d || hi >= W.d || hi < a)) return kBroken;
+    if (a != (int32_t)k) {
+      ja = __ldg(&R[a].a);
+      jb = __ldg(&R[a].b);
+    }
+    if (r > (((unsigned long long)ja.y << 32) | ja.x)) {
+      // smallest j in (a, hi] with r <= U_j; it exists, at hi at the latest
+      int32_t n = hi - a - 1;
+      a += 1;
+      while (n > 0) {
+        const int32_t half = n >> 1;
+        const uint4 m = __ldg(&R[a + half].a);
+        if ((((unsigned long long)m.y << 32) | m.x) < r) {
+          a += half + 1;
+          n -= half + 1;
+        } else {
+          n = half;
+        }
+      }
+      ja = __ldg(&R[a].a);
+      jb = __ldg(&R[a].b);
+    }
+    next = (int32_t)ja.z;
+    W.nxo = (int32_t)ja.w;
+    W.nxd = (int32_t)jb.x;
+    W.nxv = true;
+    return kMoved;
   } else if (A == DW_ITS) {
     // Static ITS generation from the stored P' of the row: x uniform in
     // [0, p'_{d-1}), then the smallest i with x < p'_i, by a lower-bound
@@ -554,6 +591,44 @@ __device__ __forceinline__ void advance(Walker& W, int32_t next) {
   }
 }
 
+
+// Weighted DeepWalk under ITS, REJ or O-REJ in the mixed kernels (batches and
+// the server): one step run out of line, so that these samplers' registers do
+// not weigh on every other algorithm of the dispatcher.  The walker goes in
+// by value; the fields a step may change come back.
+struct SamplerOut {
+  int r;
+  int32_t next, off, d, nxo, nxd;
+  bool nxv;
+};
+
+template <bool CHECK>
+__device__ __noinline__ SamplerOut sampler_step(const DevGraph& g, const WalkSpec& sp, Walker W) {
+  SamplerOut o;
+  Pend p;
+  o.next = -1;
+  o.r = (sp.algo == DW_ITS) ? step_begin<DW_ITS, CHECK>(g, sp, W, o.next, p, Coop{0x7fffffff, 0x7fffffff})
+                            : step_begin<DW_REJ, CHECK>(g, sp, W, o.next, p, Coop{0x7fffffff, 0x7fffffff});
+  o.off = W.off;
+  o.d = W.d;
+  o.nxo = W.nxo;
+  o.nxd = W.nxd;
+  o.nxv = W.nxv;
+  return o;
+}
+
+template <bool CHECK>
+__device__ __forceinline__ int sampler_step_apply(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
+  const SamplerOut o = sampler_step<CHECK>(g, sp, W);
+  W.off = o.off;
+  W.d = o.d;
+  W.nxo = o.nxo;
+  W.nxd = o.nxd;
+  W.nxv = o.nxv;
+  next = o.next;
+  return o.r;
+}
+
 template <int A, bool CHECK = false>
 __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   if constexpr (A != MIXED) {
@@ -565,9 +640,9 @@ __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& 
       case PPR: return step_serial<PPR, CHECK>(g, sp, W, next);
       case NODE2VEC: return step_serial<NODE2VEC, CHECK>(g, sp, W, next);
       case METAPATH: return step_serial<METAPATH, CHECK>(g, sp, W, next);
-      case DW_ITS: return step_serial<DW_ITS, CHECK>(g, sp, W, next);
+      case DW_ITS:
       case DW_REJ:
-      case DW_OREJ: return step_serial<DW_REJ, CHECK>(g, sp, W, next);
+      case DW_OREJ: return sampler_step_apply<CHECK>(g, sp, W, next);
       default: return kBroken;
     }
   }
@@ -586,9 +661,9 @@ __device__ __forceinline__ int step_begin_dispatch(const DevGraph& g, const Walk
       case PPR: return step_begin<PPR, CHECK>(g, sp, W, next, p, coop);
       case NODE2VEC: return step_begin<NODE2VEC, CHECK>(g, sp, W, next, p, coop);
       case METAPATH: return step_begin<METAPATH, CHECK>(g, sp, W, next, p, coop);
-      case DW_ITS: return step_begin<DW_ITS, CHECK>(g, sp, W, next, p, coop);
-      case DW_REJ:  // one instance serves both (fewer registers in the mixed kernels)
-      case DW_OREJ: return step_begin<DW_REJ, CHECK>(g, sp, W, next, p, coop);
+      case DW_ITS:
+      case DW_REJ:
+      case DW_OREJ: p.kind = 0; return sampler_step_apply<CHECK>(g, sp, W, next);
       default: return kBroken;
     }
   }

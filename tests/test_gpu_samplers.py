@@ -50,28 +50,74 @@ def test_tables_match_oracle():
     assert e.value.status == -3
 
 
+def its_records_want(g, cdf):
+    """Guided ITS records recomputed on the host from the oracle's prefix sums:
+    U_j = floor((P'_j 2^64 - 1) / S) (0 where P'_j = 0); the first candidate of
+    cell k is the smallest j with max(ceil(k 2^64 / d), 1) <= U_j, the last
+    one the first of cell k + 1 (d - 1 for the last cell); -1 in a row whose
+    weights are all zero."""
+    M = 1 << 64
+    rows = []
+    for v in range(g.nv):
+        lo, hi = int(g.row_ptr[v]), int(g.row_ptr[v + 1])
+        d = hi - lo
+        if d == 0:
+            continue
+        P = [int(x) for x in cdf[lo:hi]]
+        S = P[-1]
+        U = [0 if p == 0 or S == 0 else ((p << 64) - 1) // S for p in P]
+        Ua = np.array(U, dtype=np.uint64)
+        if S == 0:
+            first = [-1] * d
+            last = [-1] * d
+        else:
+            cells = [max(-(-k * M // d), 1) for k in range(d)]
+            first = [int(np.searchsorted(Ua, np.uint64(c), side="left")) for c in cells]
+            last = first[1:] + [d - 1]
+        for j in range(d):
+            c = int(g.col[lo + j])
+            rows.append([U[j] & 0xFFFFFFFF, U[j] >> 32, c, int(g.row_ptr[c]), int(g.row_ptr[c + 1] - g.row_ptr[c]),
+                         first[j] & 0xFFFFFFFF, last[j] & 0xFFFFFFFF, 0])
+    return np.array(rows, dtype=np.uint64).astype(np.uint32)
+
+
+def test_its_guide_records_match_host():
+    for scale, sym in ((10, True), (11, False)):
+        g = rmat_graph(scale, symmetric=sym)
+        G = trw.Graph(g.row_ptr, g.col, g.weights)
+        G.prepare(trw.PREP_ITS_GUIDE)
+        got = G.debug_its_records()
+        want = its_records_want(g, oracle.prepare_its(g.row_ptr, g.weights))
+        assert np.array_equal(got, want)
+    with pytest.raises(trw.TRWError) as e:
+        trw.Graph(g.row_ptr, g.col, g.weights).debug_its_records()
+    assert e.value.status == -3
+
+
 @pytest.mark.parametrize("records", [False, True], ids=["plain-tables", "records"])
 @pytest.mark.parametrize("kernel", [trw.KERNEL_PLAIN, trw.KERNEL_PERSISTENT], ids=["plain", "persistent"])
 @pytest.mark.parametrize("name", list(SAMPLERS))
 def test_sampler_walks_match_oracle(name, kernel, records):
     g = rmat_graph(12)
-    G = trw.Graph(g.row_ptr, g.col, g.weights)
-    G.prepare(trw.PREP_ITS | trw.PREP_REJ | (trw.PREP_ROW_RECORDS if records else 0))
     src = np.concatenate([synth.vertex_sources(g.nv), synth.sources(1237, g.nv, seed=3)])
     want = oracle_sampled(g, SAMPLERS[name], src, 60, 17, oracle_tables(12))
     assert want.status == 0
-    out = G.walk(trw.DEEPWALK_WEIGHTED, torch.from_numpy(src).cuda(), 60, seed=17, kernel=kernel,
-                 sampler=SAMPLERS[name], max_weight=BOUND)
-    torch.cuda.synchronize()
-    assert_paths_equal(out.paths.cpu().numpy(), out.lengths.cpu().numpy(), want)
-    assert G.last_stats()["moves"] == want.stats["moves"]
+    preps = [trw.PREP_ITS | trw.PREP_REJ] + ([trw.PREP_ITS_GUIDE] if name == "its" else [])
+    for prep in preps:  # ITS: the prefix-sum search, then the guided records alone
+        G = trw.Graph(g.row_ptr, g.col, g.weights)
+        G.prepare(prep | (trw.PREP_ROW_RECORDS if records else 0))
+        out = G.walk(trw.DEEPWALK_WEIGHTED, torch.from_numpy(src).cuda(), 60, seed=17, kernel=kernel,
+                     sampler=SAMPLERS[name], max_weight=BOUND)
+        torch.cuda.synchronize()
+        assert_paths_equal(out.paths.cpu().numpy(), out.lengths.cpu().numpy(), want)
+        assert G.last_stats()["moves"] == want.stats["moves"]
 
 
 @pytest.mark.parametrize("name", list(SAMPLERS))
 def test_sampler_endpoints_offsets_and_host_buffers(name):
     g = rmat_graph(11, symmetric=False)
     G = trw.Graph(g.row_ptr, g.col, g.weights)
-    G.prepare(trw.PREP_ITS | trw.PREP_REJ)
+    G.prepare(trw.PREP_REJ | (trw.PREP_ITS_GUIDE if name == "its" else 0))
     src = synth.sources(700, g.nv, seed=9)
     off = 2 ** 32 - 700 * 3
     want = oracle_sampled(g, SAMPLERS[name], src, 40, 2 ** 64 - 5, oracle_tables(11, False), walks_per_source=3,
@@ -110,13 +156,16 @@ def test_zero_weight_rows_and_extreme_weights():
     G.prepare(trw.PREP_ITS | trw.PREP_REJ | trw.PREP_ROW_RECORDS)
     cdf, pm = G.debug_sampler_tables()
     assert np.array_equal(cdf, tables[0]) and np.array_equal(pm, tables[1])
+    Gg = trw.Graph(g.row_ptr, g.col, g.weights)
+    Gg.prepare(trw.PREP_ITS_GUIDE)
+    assert np.array_equal(Gg.debug_its_records(), its_records_want(g, tables[0]))
     src = np.array([0, 1, 2, 3, 4, 6, 7, 8, 0, 0], np.int32)
-    for name in ("its", "rej"):
+    for name, graph in (("its", G), ("its", Gg), ("rej", G)):
         want = oracle_sampled(g, SAMPLERS[name], src, 25, 6, tables, walks_per_source=300)
         assert want.status == 0
         for kernel in (trw.KERNEL_PLAIN, trw.KERNEL_PERSISTENT):
-            out = G.walk(trw.DEEPWALK_WEIGHTED, src, 25, seed=6, walks_per_source=300, kernel=kernel,
-                         sampler=SAMPLERS[name])
+            out = graph.walk(trw.DEEPWALK_WEIGHTED, src, 25, seed=6, walks_per_source=300, kernel=kernel,
+                             sampler=SAMPLERS[name])
             assert_paths_equal(out.paths, out.lengths, want)
     dead = oracle_sampled(g, trw.SAMPLER_ITS, np.array([5], np.int32), 4, 1, tables)
     assert dead.lengths[0] == 1
@@ -127,10 +176,11 @@ def test_zero_weight_rows_and_extreme_weights():
     assert oracle_sampled(g, trw.SAMPLER_OREJ, np.array([5], np.int32), 4, 1, tables, max_weight=2.0).status == -6
 
 
-def test_mixed_batch_plan_and_server():
+@pytest.mark.parametrize("guide", [False, True], ids=["its-search", "its-guided"])
+def test_mixed_batch_plan_and_server(guide):
     g = rmat_graph(12)
     G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
-    G.prepare(trw.PREP_ALIAS | trw.PREP_ITS | trw.PREP_REJ)
+    G.prepare(trw.PREP_ALIAS | trw.PREP_REJ | (trw.PREP_ITS_GUIDE if guide else trw.PREP_ITS))
     tables = oracle_tables(12)
     reqs = []
     for i, (name, s) in enumerate(SAMPLERS.items()):
@@ -186,13 +236,16 @@ def test_full_size_sampled_parity():
     src = torch.arange(g.nv, dtype=torch.int32, device="cuda")
     pick = np.sort(np.random.default_rng(5).choice(g.nv, 2000, replace=False)).astype(np.int64)
     cdf, pm = oracle_tables(20)
-    for name, s in SAMPLERS.items():
+    runs = list(SAMPLERS.items()) + [("its-guided", trw.SAMPLER_ITS)]
+    for name, s in runs:
+        if name == "its-guided":
+            G.prepare(trw.PREP_ITS_GUIDE)
         out = G.walk(trw.DEEPWALK_WEIGHTED, src, 80, seed=99, sampler=s, max_weight=BOUND,
                      kernel=trw.KERNEL_PERSISTENT)
         torch.cuda.synchronize()
         paths = out.paths.cpu().numpy()[pick]
         lens = out.lengths.cpu().numpy()[pick]
-        for i, v in enumerate(pick[:200] if name != "its" else pick):
+        for i, v in enumerate(pick if name.startswith("its") else pick[:200]):
             w = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, [int(v)], 80, 99, sampler=s,
                             weights=g.weights, its=cdf, pmax=pm, max_weight=BOUND, walk_offset=int(v))
             assert w.status == 0
