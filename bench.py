@@ -410,10 +410,14 @@ def measure_per_algo(trw, torch, G, g, flush, sp, G_paper=None):
         tune_kw = {k: v for k, v in kw.items() if k != "endpoints"}
         row["tuning"] = G.autotune(algo, L, **tune_kw)
         row["autotune_s"] = round(time.time() - t0, 2)
-        for kname, kern in (("persistent", trw.KERNEL_PERSISTENT), ("plain", trw.KERNEL_PLAIN)):
+        for kname, kern in (("persistent", trw.KERNEL_PERSISTENT), ("plain", trw.KERNEL_PLAIN),
+                            ("bsp", trw.KERNEL_BSP)):
             ms, moves = time_walk(trw, torch, G, flush, sp, algo, src, L, 1, kern, **kw)
             row[kname] = {"steps_per_s": round(moves / (ms / 1000.0), 1), "ms": round(ms, 3), "moves": moves}
+            if kern == trw.KERNEL_BSP:
+                row[kname]["launches"] = G.last_stats()["launches"]
         row["speedup"] = round(row["persistent"]["steps_per_s"] / row["plain"]["steps_per_s"], 3)
+        row["speedup_vs_bsp"] = round(row["persistent"]["steps_per_s"] / row["bsp"]["steps_per_s"], 3)
         if G_paper is not None and algo in (trw.NODE2VEC, trw.METAPATH):
             G_paper.autotune(algo, L, **tune_kw)
             ms, moves = time_walk(trw, torch, G_paper, flush, sp, algo, src, L, 1, trw.KERNEL_PERSISTENT, **kw)
@@ -425,6 +429,38 @@ def measure_per_algo(trw, torch, G, g, flush, sp, G_paper=None):
         out[name] = row
         log(f"{name}: {row}")
     G.set_tuning(**base_tuning)
+    return out
+
+
+def measure_query_sweep(trw, torch, G, g, flush, sp, algo, kw):
+    """Throughput against the number of queries (10^2 .. 10^7 uniform random
+    sources, 80 moves) and against the query length (5 .. 160 moves, one query
+    per vertex), for the persistent kernel, the plain one-launch kernel and
+    the step-synchronous baseline (Section 6's sweeps of query count and
+    length; the BSP model of Section 3)."""
+    import synth as sy
+
+    dev = flush.device
+    kernels = (("persistent", trw.KERNEL_PERSISTENT), ("plain", trw.KERNEL_PLAIN), ("bsp", trw.KERNEL_BSP))
+
+    def row_of(src, L):
+        row = {}
+        for kname, kern in kernels:
+            ms, moves = time_walk(trw, torch, G, flush, sp, algo, src, L, 1, kern, **kw)
+            row[kname] = round(moves / (ms / 1000.0), 1)
+            row[kname + "_ms"] = round(ms, 3)
+        row["moves"] = moves
+        return row
+
+    out = {"queries": {}, "length": {}, "unit": UNIT}
+    for n in (100, 1000, 10_000, 100_000, 1_000_000, 10_000_000):
+        src = torch.from_numpy(sy.sources(n, g.nv, seed=5)).to(dev)
+        out["queries"][str(n)] = row_of(src, 80)
+        log(f"queries {n}: {out['queries'][str(n)]}")
+    verts = torch.from_numpy(sy.vertex_sources(g.nv)).to(dev)
+    for L in (5, 10, 20, 40, 80, 160):
+        out["length"][str(L)] = row_of(verts, L)
+        log(f"length {L}: {out['length'][str(L)]}")
     return out
 
 
@@ -852,6 +888,7 @@ def run_ours(args, wl):
     serve = None
     replay = None
     sweep = None
+    queries = None
     gather = measure_gather_ceiling(trw, g) if rank == 0 else None
     if rank == 0 and not args.no_extras:
         # every algorithm on this graph: with the label index and neighbour
@@ -865,6 +902,7 @@ def run_ours(args, wl):
         replay["value"] = round(moves / (replay["graph_replay_ms"] / 1000.0), 1)
         per_algo = measure_per_algo(trw, torch, G, g, flush, sp, G_paper)
         del G_paper
+        queries = measure_query_sweep(trw, torch, G, g, flush, sp, algo, kw)
         if G.has_weights:
             sweep = measure_sampler_sweep(trw, torch, g, flush, sp, gather)
             serve = measure_serve(trw, torch, G, g, n_requests=args.serve_requests)
@@ -900,6 +938,7 @@ def run_ours(args, wl):
         "roofline": roof,
         "per_algo": per_algo,
         "sampler_sweep": sweep,
+        "query_sweep": queries,
         "serve": serve,
         "gather_ceiling": gather,
         "cpu_baseline": cpu,

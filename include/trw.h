@@ -71,7 +71,11 @@ typedef enum {
   TRW_KERNEL_AUTO = 0,          /* the persistent kernel; the plain one for a batch that fits in one
                                    resident wave and needs no warp-cooperative path */
   TRW_KERNEL_PLAIN = 1,         /* baseline: one launch, one thread per walk, no refill */
-  TRW_KERNEL_PERSISTENT = 2     /* persistent kernel, device work queue, refill, staging */
+  TRW_KERNEL_PERSISTENT = 2,    /* persistent kernel, device work queue, refill, staging */
+  TRW_KERNEL_BSP = 3            /* baseline: step-synchronous (the BSP model of KnightKing and C-SAW,
+                                   Section 3): one launch per step over the live walkers, walker state
+                                   in device memory, the live count read back after every launch;
+                                   synchronous calls only */
 } trw_kernel;
 
 #define TRW_OUT_PATHS 0u        /* out_paths[i * (max_len + 1) + k] = Q[k] */
@@ -370,8 +374,8 @@ typedef struct {
   double kernel_ms;             /* device time of the walk kernel (CUDA events) */
   int32_t grid_blocks;          /* launch shape used */
   int32_t block_threads;
-  int32_t kernel;               /* TRW_KERNEL_PLAIN or TRW_KERNEL_PERSISTENT: the kernel that ran */
-  int32_t reserved;
+  int32_t kernel;               /* TRW_KERNEL_PLAIN, _PERSISTENT or _BSP: the kernel that ran */
+  int32_t launches;             /* walk-kernel launches of the call (BSP: one per step, plus one) */
 } trw_stats;
 trw_status trw_last_stats(const trw_graph* g, trw_stats* s);
 

@@ -21,7 +21,7 @@ __all__ = ["TRWError", "Graph", "Server", "load_library", "build", "DEEPWALK", "
            "OUT_ENDPOINTS", "philox_device"]
 
 DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH = 0, 1, 2, 3, 4
-KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT = 0, 1, 2
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT, KERNEL_BSP = 0, 1, 2, 3
 OUT_PATHS, OUT_ENDPOINTS = 0, 1
 PREP_ALIAS = 1
 PREP_LABEL_INDEX = 2
@@ -70,7 +70,7 @@ class Tuning(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("walks", ctypes.c_int64), ("moves", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
                 ("grid_blocks", ctypes.c_int32), ("block_threads", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("launches", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -108,6 +108,9 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->its_cdf);
   cudaFree(g->rej_pmax);
   cudaFree(g->its_rec);
+  cudaFree(g->bsp_walkers[0]);
+  cudaFree(g->bsp_walkers[1]);
+  if (g->bsp_host) cudaFreeHost(g->bsp_host);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);
@@ -651,7 +654,8 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
   CUDA_TRY(cudaEventRecord(g->ev_fork, stream), "event");
   CUDA_TRY(cudaStreamWaitEvent(g->stream2, g->ev_fork, 0), "fork");
   int64_t done_src = 0;
-  for (int64_t i = 0; done_src < n_sources; ++i) {
+  int32_t slices = 0;
+  for (int64_t i = 0; done_src < n_sources; ++i, ++slices) {
     const int b = (int)(i & 1);
     cudaStream_t kst = ks[b];
     const int64_t s0 = done_src, s1 = std::min(n_sources, s0 + src_per);
@@ -683,6 +687,7 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
   g->last.grid_blocks = cfg.grid_blocks;
   g->last.block_threads = cfg.block_threads;
   g->last.kernel = kernel == TRW_KERNEL_PLAIN ? TRW_KERNEL_PLAIN : TRW_KERNEL_PERSISTENT;
+  g->last.launches = slices;
   CUDA_TRY(cudaStreamSynchronize(cs), "copy stream");
   // the second control block's moves and status join the first's
   Ctrl c2;
@@ -697,12 +702,51 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
   return TRW_OK;
 }
 
+// The step-synchronous baseline: one launch per step over the live walkers,
+// the live count read back after each.  Every launch advances or finishes
+// each live walker, so there are at most max_len step launches.
+static trw_status run_bsp(trw_graph* g, const DevGraph& dg, const WalkSpec& sp, cudaStream_t stream) {
+  const size_t bytes = bsp_walker_bytes() * (size_t)sp.nwalks;
+  for (int b = 0; b < 2; ++b) {
+    trw_status st = trw_grow(&g->bsp_walkers[b], &g->bsp_cap[b], bytes);
+    if (st != TRW_OK) return st;
+  }
+  if (!g->bsp_host) CUDA_TRY(cudaMallocHost((void**)&g->bsp_host, sizeof(unsigned long long)), "pinned count");
+  unsigned long long* d_count = reinterpret_cast<unsigned long long*>(static_cast<char*>(g->misc) + 128);
+  CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream), "reset count");
+  CUDA_TRY(launch_bsp_init(dg, sp, g->bsp_walkers[0], d_count, g->ctrl, stream), "BSP init launch");
+  CUDA_TRY(cudaMemcpyAsync(g->bsp_host, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream),
+           "read count");
+  CUDA_TRY(cudaStreamSynchronize(stream), "BSP init");
+  int64_t n = (int64_t)*g->bsp_host;
+  int cur = 0;
+  int32_t steps = 0;
+  while (n > 0) {
+    if (++steps > sp.max_len) return trw_fail(TRW_ERR_INTERNAL, "step-synchronous walk exceeded max_len steps");
+    CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream), "reset count");
+    CUDA_TRY(launch_bsp_step(dg, sp, g->bsp_walkers[cur], n, g->bsp_walkers[1 - cur], d_count, g->ctrl, stream),
+             "BSP step launch");
+    CUDA_TRY(cudaMemcpyAsync(g->bsp_host, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream),
+             "read count");
+    CUDA_TRY(cudaStreamSynchronize(stream), "BSP step");
+    n = (int64_t)*g->bsp_host;
+    cur = 1 - cur;
+  }
+  g->last.launches = steps + 1;
+  g->last.grid_blocks = (int32_t)std::min<int64_t>((sp.nwalks + 255) / 256, INT32_MAX);
+  g->last.block_threads = 256;
+  return TRW_OK;
+}
+
 extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
                                   int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
                                   int32_t* out_lengths, trw_kernel kernel, void* stream_v, int sync) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
-  if (kernel != TRW_KERNEL_AUTO && kernel != TRW_KERNEL_PLAIN && kernel != TRW_KERNEL_PERSISTENT)
+  if (kernel != TRW_KERNEL_AUTO && kernel != TRW_KERNEL_PLAIN && kernel != TRW_KERNEL_PERSISTENT &&
+      kernel != TRW_KERNEL_BSP)
     return trw_fail(TRW_ERR_INVALID, "unknown kernel %d", (int)kernel);
+  if (kernel == TRW_KERNEL_BSP && !sync)
+    return trw_fail(TRW_ERR_INVALID, "the step-synchronous baseline runs synchronously only");
   WalkSpec sp;
   trw_status st = trw_make_spec(g, algo, params, n_sources, max_len, seed, &sp);
   if (st != TRW_OK) return st;
@@ -724,6 +768,7 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
   g->last.walks = nwalks;
   g->last.moves = 0;
   g->last.kernel_ms = 0;
+  g->last.launches = 0;
   g->timed = false;
   if (nwalks == 0) return TRW_OK;
   if (kernel == TRW_KERNEL_AUTO) {
@@ -761,7 +806,7 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
   // device staging buffers and copy each slice out on a second stream while
   // the next slice walks (a double-buffered dump of the paths).
   const int64_t row = sp.endpoints ? 1 : (int64_t)max_len + 1;
-  if (!out_dev && !len_dev && sync && nwalks >= 2 * kSliceWalks)
+  if (!out_dev && !len_dev && sync && nwalks >= 2 * kSliceWalks && kernel != TRW_KERNEL_BSP)
     return walk_sliced(g, sp, kernel, d_src, n_sources, row, out_paths, out_lengths, stream);
   if (!out_dev) {
     st = trw_grow((void**)&g->out_stage, &g->out_cap, sizeof(int32_t) * out_elems);
@@ -781,8 +826,12 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
   else CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, offsetof(Ctrl, err), stream), "reset ctrl");
   if (src_dev) CUDA_TRY(launch_validate_sources(d_src, n_sources, (int32_t)g->nv, g->ctrl, stream), "validate sources");
   CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
-  g->last.kernel = kernel == TRW_KERNEL_PLAIN ? TRW_KERNEL_PLAIN : TRW_KERNEL_PERSISTENT;
-  if (kernel == TRW_KERNEL_PLAIN) {
+  g->last.kernel = kernel;
+  g->last.launches = 1;
+  if (kernel == TRW_KERNEL_BSP) {
+    st = run_bsp(g, dg, sp, stream);
+    if (st != TRW_OK) return st;
+  } else if (kernel == TRW_KERNEL_PLAIN) {
     CUDA_TRY(launch_walk_plain(dg, sp, g->ctrl, stream, 256), "plain walk launch");
     g->last.grid_blocks = (int32_t)((nwalks + 255) / 256);
     g->last.block_threads = 256;
@@ -871,6 +920,7 @@ extern "C" trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw
   CUDA_TRY(cudaEventRecord(g->ev1, stream), "event");
   g->timed = true;
   g->last.kernel = TRW_KERNEL_PERSISTENT;
+  g->last.launches = 1;
   g->last.grid_blocks = cfg.grid_blocks;
   g->last.block_threads = cfg.block_threads;
   if (!sync) return TRW_OK;

@@ -29,6 +29,9 @@ struct trw_graph {
   unsigned long long* its_cdf = nullptr;  // ITS prefix sums (trw_prepare(ITS)): ne
   uint32_t* rej_pmax = nullptr;      // REJ bounds p*_v (trw_prepare(REJ)): nv
   trw::ItsRec* its_rec = nullptr;    // guided ITS records (trw_prepare(ITS_GUIDE)): ne
+  void* bsp_walkers[2] = {nullptr, nullptr};  // step-synchronous baseline: walker lists (grow-only)
+  size_t bsp_cap[2] = {0, 0};
+  unsigned long long* bsp_host = nullptr;     // pinned: the live count read back after each step
   int32_t* nh_slots = nullptr;       // neighbour hash (trw_prepare(NEIGHBOR_HASH)): 2 ne int32
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags

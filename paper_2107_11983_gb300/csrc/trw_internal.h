@@ -21,6 +21,15 @@ struct LaunchCfg {
 // (coop: the variant with the warp-cooperative scan and search).
 int persistent_blocks_per_sm(int algo, int block_threads, bool coop);
 
+// Step-synchronous baseline: bytes of one stored walker, the launch that
+// creates the walkers (all live unless max_len is 0) and one step launch over
+// n live walkers; each appends the walkers still alive to out and counts them
+// in *n_out.
+size_t bsp_walker_bytes();
+cudaError_t launch_bsp_init(const DevGraph& g, const WalkSpec& sp, void* out, unsigned long long* n_out, Ctrl* ctrl,
+                            cudaStream_t st);
+cudaError_t launch_bsp_step(const DevGraph& g, const WalkSpec& sp, const void* in, int64_t n, void* out,
+                            unsigned long long* n_out, Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_validate_sources(const int32_t* src, int64_t n, int32_t nv, Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_walk_plain(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl, cudaStream_t st, int block);
 cudaError_t launch_walk_persistent(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl, cudaStream_t st,

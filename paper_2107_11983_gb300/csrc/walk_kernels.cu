@@ -170,6 +170,95 @@ __global__ void __launch_bounds__(512) walk_persistent(DevGraph g, WalkSpec sp0,
   if (lane == 0 && moves) atomicAdd(&ctrl->moves, moves);
 }
 
+// ------------------------------------------------ step-synchronous baseline
+// The BSP execution of KnightKing and C-SAW: one launch per step moves every
+// live walker by one step (a whole step: the trials of a rejection sampler
+// run inside it), and the walkers still alive are appended to the next
+// step's list.  Walker state lives in device memory between launches; the
+// host reads the live count after every launch.  Same draws, same walks.
+
+struct BspWalker {
+  Walker W;
+  uint32_t walk;  // index within the request
+};
+
+// Finishes a walk: its length (and endpoint) out, its moves counted.
+__device__ __forceinline__ void bsp_finish(const WalkSpec& sp, const Walker& W, uint32_t walk,
+                                           unsigned long long& moves) {
+  if (sp.endpoints) sp.out_paths[walk] = W.cur;
+  sp.out_lengths[walk] = W.s + 1;
+  moves += (unsigned long long)W.s;
+}
+
+// Appends the live lanes' walkers to out with one atomic per warp.
+__device__ __forceinline__ void bsp_append(bool live, const BspWalker& b, BspWalker* __restrict__ out,
+                                           unsigned long long* n_out) {
+  const int lane = threadIdx.x & 31;
+  const unsigned mask = __ballot_sync(kFull, live);
+  if (mask == 0u) return;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(n_out, (unsigned long long)__popc(mask));
+  base = __shfl_sync(kFull, base, leader);
+  if (live) out[base + __popc(mask & ((1u << lane) - 1u))] = b;
+}
+
+__global__ void __launch_bounds__(256) bsp_init(DevGraph g, WalkSpec sp, BspWalker* __restrict__ out,
+                                                unsigned long long* n_out, Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->err != 0) return;  // the call was rejected: write nothing
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool live = false;
+  BspWalker b;
+  unsigned long long moves = 0;
+  if (i < sp.nwalks) {
+    const int32_t src = sp.sources[i / sp.wps];
+    if (src >= 0 && src < g.nv) {
+      walker_init(b.W, sp.walk_offset + (uint32_t)i, src);
+      b.walk = (uint32_t)i;
+      if (!sp.endpoints) sp.out_paths[i * ((int64_t)sp.max_len + 1)] = src;
+      live = sp.max_len > 0;
+      if (!live) bsp_finish(sp, b.W, b.walk, moves);
+    } else {
+      set_err(ctrl, kErrInvalid);
+    }
+  }
+  bsp_append(live, b, out, n_out);
+}
+
+template <int A>
+__global__ void __launch_bounds__(256) bsp_step(DevGraph g, WalkSpec sp, const BspWalker* __restrict__ in, int64_t n,
+                                                BspWalker* __restrict__ out, unsigned long long* n_out, Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->err != 0) return;  // a source was invalid: write nothing more
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool live = false;
+  BspWalker b;
+  unsigned long long moves = 0;
+  if (i < n) {
+    b = in[i];
+    int r;
+    int32_t next;
+    for (;;) {
+      next = -1;
+      r = step_dispatch<A>(g, sp, b.W, next);
+      if (r != kRetry) break;
+      b.W.att += 1;
+    }
+    if (r == kMoved) {
+      advance(b.W, next);
+      if (!sp.endpoints) sp.out_paths[(int64_t)b.walk * ((int64_t)sp.max_len + 1) + b.W.s] = next;
+      live = b.W.s < sp.max_len;
+      if (!live) bsp_finish(sp, b.W, b.walk, moves);
+    } else {
+      if (r == kFail) set_err(ctrl, kErrRejectCap);
+      if (r == kBroken) set_err(ctrl, kErrInternal);
+      bsp_finish(sp, b.W, b.walk, moves);
+    }
+  }
+  bsp_append(live, b, out, n_out);
+  moves = warp_sum(moves);
+  if ((threadIdx.x & 31) == 0 && moves) atomicAdd(&ctrl->moves, moves);
+}
+
 __global__ void validate_sources(const int32_t* __restrict__ src, int64_t n, int32_t nv, Ctrl* ctrl) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = src[i];
@@ -313,6 +402,35 @@ cudaError_t launch_walk_batch(const DevGraph& g, const WalkSpec* d_specs, const 
   else
     walk_persistent<MIXED, false><<<(unsigned)blocks, threads, smem, st>>>(g, dummy, d_specs, d_prefix, nreq, total,
                                                                             ctrl, cfg.chunk, coop);
+  return cudaGetLastError();
+}
+
+size_t bsp_walker_bytes() { return sizeof(BspWalker); }
+
+cudaError_t launch_bsp_init(const DevGraph& g, const WalkSpec& sp, void* out, unsigned long long* n_out, Ctrl* ctrl,
+                            cudaStream_t st) {
+  if (sp.nwalks <= 0) return cudaSuccess;
+  bsp_init<<<(unsigned)((sp.nwalks + 255) / 256), 256, 0, st>>>(g, sp, static_cast<BspWalker*>(out), n_out, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bsp_step(const DevGraph& g, const WalkSpec& sp, const void* in, int64_t n, void* out,
+                            unsigned long long* n_out, Ctrl* ctrl, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  const BspWalker* a = static_cast<const BspWalker*>(in);
+  BspWalker* b = static_cast<BspWalker*>(out);
+  switch (sp.algo) {
+    case DEEPWALK: bsp_step<DEEPWALK><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case DEEPWALK_WEIGHTED: bsp_step<DEEPWALK_WEIGHTED><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case PPR: bsp_step<PPR><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case NODE2VEC: bsp_step<NODE2VEC><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case METAPATH: bsp_step<METAPATH><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case DW_ITS: bsp_step<DW_ITS><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case DW_REJ: bsp_step<DW_REJ><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case DW_OREJ: bsp_step<DW_OREJ><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
