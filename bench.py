@@ -884,6 +884,33 @@ def run_ours(args, wl):
 
     kms = statistics.mean(kern_ms)
 
+    # streaming output: the same batch in slices of 2^20 walks handed to a
+    # consumer (O(slice) memory), and dumped to files on the host's disk
+    stream = None
+    if rank == 0 and not args.no_extras:
+        st_t = []
+        for _ in range(4):  # the first call allocates the pinned slices
+            t = time.perf_counter()
+            G.walk_stream(algo, h_src.numpy(), L, wl["seed"], lambda f, p, ln: None, slice_walks=1 << 20,
+                          walk_offset=walk_offset, **kw)
+            st_t.append(time.perf_counter() - t)
+        st_s = statistics.median(st_t[1:])
+        fdir = tempfile.mkdtemp(prefix="trw_stream_")
+        pf, lf = os.path.join(fdir, "paths.i32"), os.path.join(fdir, "lengths.i32")
+        t = time.perf_counter()
+        G.walk_to_file(algo, h_src.numpy(), L, wl["seed"], pf, lf, walk_offset=walk_offset, **kw)
+        file_s = time.perf_counter() - t
+        fbytes = os.path.getsize(pf) + os.path.getsize(lf)
+        os.remove(pf)
+        os.remove(lf)
+        os.rmdir(fdir)
+        stream = {"consumer": {"value": round(moves / st_s, 1), "unit": UNIT, "ms": round(1000 * st_s, 2),
+                               "slice_walks": 1 << 20, "what": "a consumer that reads nothing, per slice"},
+                  "to_file": {"value": round(moves / file_s, 1), "unit": UNIT, "ms": round(1000 * file_s, 2),
+                              "bytes": fbytes, "GB_per_s": round(fbytes / file_s / 1e9, 3),
+                              "what": "compact paths and lengths written to a temporary directory"}}
+        log(f"stream: {stream}")
+
     per_algo = None
     serve = None
     replay = None
@@ -937,6 +964,7 @@ def run_ours(args, wl):
         "plan_replay": replay,
         "roofline": roof,
         "per_algo": per_algo,
+        "stream_output": stream,
         "sampler_sweep": sweep,
         "query_sweep": queries,
         "serve": serve,

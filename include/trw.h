@@ -52,7 +52,9 @@ typedef enum {
   TRW_ERR_REJECT_CAP = -6,      /* a rejection step exceeded TRW_REJECT_CAP trials */
   TRW_ERR_BUSY = -7,            /* serve: no capacity to admit the request now */
   TRW_ERR_NOT_FOUND = -8,       /* serve: unknown request id */
-  TRW_ERR_INTERNAL = -9         /* a device-side consistency check failed */
+  TRW_ERR_INTERNAL = -9,        /* a device-side consistency check failed */
+  TRW_ERR_STOPPED = -10,        /* stream: the consumer asked to stop */
+  TRW_ERR_IO = -11              /* stream to files: a file could not be opened or written */
 } trw_status;
 
 /* Walk algorithms of Section 2.2 and the sampler each uses (Section 4.3's
@@ -260,6 +262,43 @@ trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params* params, co
 /* Wait for the stream (NULL: the graph's) and return, then clear, the status
  * that kernels launched with sync = 0 left on the device. */
 trw_status trw_sync(trw_graph* g, void* stream);
+
+/*
+ * Streaming output (the paper's double-buffered dump of the walk paths,
+ * Appendix "Input and output"): trw_walk's batch in source-aligned slices of
+ * about slice_walks walks, each handed to fn on the calling thread as soon as
+ * it is on the host.  Slice i walks into device staging buffer i % 2 while the
+ * copy engine moves slice i - 1 into pinned host buffer (i - 1) % 2 and fn
+ * consumes slice i - 2's: device and host memory stay O(slice) whatever the
+ * batch size.
+ *   fn(user, first_walk, n_walks, paths, lengths)
+ *       paths    host, int32[n_walks * (max_len + 1)] (TRW_OUT_PATHS, rows
+ *                padded as in trw_walk) or int32[n_walks] (TRW_OUT_ENDPOINTS);
+ *       lengths  host, int32[n_walks];
+ *       both valid only during the call.  Walk first_walk + k of the batch is
+ *       row k.  Return 0 to continue, anything else to stop.
+ *   slice_walks  walks per slice (rounded down to whole sources, at least one
+ *                source).
+ * Every slice is checked before fn sees it.  Synchronous; the other arguments
+ * as trw_walk.  Errors: those of trw_walk, TRW_ERR_STOPPED (fn returned
+ * non-zero; the slices before were delivered).
+ */
+typedef int (*trw_stream_fn)(void* user, int64_t first_walk, int64_t n_walks, const int32_t* paths,
+                             const int32_t* lengths);
+trw_status trw_walk_stream(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
+                           int64_t n_sources, int32_t max_len, uint64_t seed, int64_t slice_walks, trw_stream_fn fn,
+                           void* user);
+
+/*
+ * trw_walk_stream into two files, written on the calling thread while the
+ * GPU walks the next slice: paths_file receives the vertices of walk 0, then
+ * of walk 1, ... (lengths[i] int32 each, no padding; one int32 per walk with
+ * TRW_OUT_ENDPOINTS) and lengths_file the int32 lengths, both in the host's
+ * byte order.  Errors: those of trw_walk, TRW_ERR_IO.
+ */
+trw_status trw_walk_to_file(trw_graph* g, trw_algo algo, const trw_params* params, const int32_t* sources,
+                            int64_t n_sources, int32_t max_len, uint64_t seed, const char* paths_file,
+                            const char* lengths_file);
 
 /*
  * Random-gather ceiling (measurement aid, no counterpart in the paper): the

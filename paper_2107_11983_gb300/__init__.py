@@ -39,6 +39,9 @@ MAX_SCHEMA = 16
 MAX_BATCH = 64
 
 OK, PENDING = 0, 1
+ERR_STOPPED, ERR_IO = -10, -11
+_STREAM_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                              ctypes.c_void_p)
 STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "ERR_INVALID", -2: "ERR_OOM", -3: "ERR_NOT_PREPARED", -4: "ERR_CUDA",
                 -5: "ERR_TIMEOUT", -6: "ERR_REJECT_CAP", -7: "ERR_BUSY", -8: "ERR_NOT_FOUND", -9: "ERR_INTERNAL"}
 
@@ -125,6 +128,10 @@ _SIGS = {
     "trw_serve_trace": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP]),
     "trw_serve_drain": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "trw_serve_destroy": (None, [_VP]),
+    "trw_walk_stream": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                       ctypes.c_int64, _VP, _VP]),
+    "trw_walk_to_file": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.c_char_p, ctypes.c_char_p]),
     "trw_gather_ceiling": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "trw_last_error": (ctypes.c_char_p, []),
 }
@@ -319,6 +326,62 @@ class Graph:
                              1 if sync else 0)
         _check(st, "trw_walk")
         return WalkOutput(out_paths, out_lengths)
+
+    def walk_stream(self, algo: int, sources, max_len: int, seed: int, consumer, *, slice_walks: int = 1 << 20,
+                    ppr_stop: float = 0.2, n2v_p: float = 1.0, n2v_q: float = 1.0, schema=None,
+                    walks_per_source: int = 1, endpoints: bool = False, walk_offset: int = 0,
+                    sampler: int = SAMPLER_DEFAULT, max_weight: float = 0.0) -> int:
+        """trw_walk_stream: consumer(first_walk, paths, lengths) receives each slice
+        as numpy views of pinned host memory, valid during the call only (paths
+        [n, max_len + 1], or [n] with endpoints); a true return value stops the
+        stream (TRWError ERR_STOPPED).  Returns the moves of the batch."""
+        lib = load_library()
+        algo = ALGOS.get(algo, algo) if isinstance(algo, str) else algo
+        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset, sampler,
+                          max_weight)
+        src = sources if _is_cuda(sources) else np.ascontiguousarray(_as_host(sources, np.int32))
+        if _is_cuda(src):
+            src = src.to(_torch().int32).contiguous()
+            _torch().cuda.current_stream().synchronize()
+        row = 1 if endpoints else max_len + 1
+        raised = []
+
+        def cb(_user, first, n, paths, lengths):
+            try:
+                pa = np.ctypeslib.as_array(ctypes.cast(paths, ctypes.POINTER(ctypes.c_int32)), shape=(n * row,))
+                la = np.ctypeslib.as_array(ctypes.cast(lengths, ctypes.POINTER(ctypes.c_int32)), shape=(n,))
+                stop = consumer(int(first), pa if endpoints else pa.reshape(n, row), la)
+                return 1 if stop else 0
+            except BaseException as e:  # re-raised after the call
+                raised.append(e)
+                return 1
+
+        fn = _STREAM_FN(cb)
+        st = lib.trw_walk_stream(self._h, algo, ctypes.byref(p), _ptr(src), int(src.shape[0]), max_len,
+                                 seed & ((1 << 64) - 1), slice_walks, fn, None)
+        if raised:
+            raise raised[0]
+        _check(st, "trw_walk_stream")
+        return int(self.last_stats()["moves"])
+
+    def walk_to_file(self, algo: int, sources, max_len: int, seed: int, paths_file: str, lengths_file: str, *,
+                     ppr_stop: float = 0.2, n2v_p: float = 1.0, n2v_q: float = 1.0, schema=None,
+                     walks_per_source: int = 1, endpoints: bool = False, walk_offset: int = 0,
+                     sampler: int = SAMPLER_DEFAULT, max_weight: float = 0.0) -> int:
+        """trw_walk_to_file: the vertices of every walk, walk after walk, to
+        paths_file and the int32 lengths to lengths_file.  Returns the moves."""
+        lib = load_library()
+        algo = ALGOS.get(algo, algo) if isinstance(algo, str) else algo
+        p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset, sampler,
+                          max_weight)
+        src = sources if _is_cuda(sources) else np.ascontiguousarray(_as_host(sources, np.int32))
+        if _is_cuda(src):
+            src = src.to(_torch().int32).contiguous()
+            _torch().cuda.current_stream().synchronize()
+        _check(lib.trw_walk_to_file(self._h, algo, ctypes.byref(p), _ptr(src), int(src.shape[0]), max_len,
+                                    seed & ((1 << 64) - 1), os.fsencode(paths_file), os.fsencode(lengths_file)),
+               "trw_walk_to_file")
+        return int(self.last_stats()["moves"])
 
     def sync(self, stream=None):
         """Wait for the stream (default: torch's current stream) and collect the device status."""

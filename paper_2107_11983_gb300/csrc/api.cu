@@ -111,6 +111,7 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->bsp_walkers[0]);
   cudaFree(g->bsp_walkers[1]);
   if (g->bsp_host) cudaFreeHost(g->bsp_host);
+  trw_free_stream_buffers(g);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);

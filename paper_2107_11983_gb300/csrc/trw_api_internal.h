@@ -32,6 +32,11 @@ struct trw_graph {
   void* bsp_walkers[2] = {nullptr, nullptr};  // step-synchronous baseline: walker lists (grow-only)
   size_t bsp_cap[2] = {0, 0};
   unsigned long long* bsp_host = nullptr;     // pinned: the live count read back after each step
+  int32_t* pin_paths[2] = {nullptr, nullptr}; // streaming output: pinned host slices (grow-only)
+  size_t pin_paths_cap[2] = {0, 0};
+  int32_t* pin_lens[2] = {nullptr, nullptr};
+  size_t pin_lens_cap[2] = {0, 0};
+  trw::Ctrl* pin_ctrl = nullptr;              // pinned copies of the two slices' control blocks
   int32_t* nh_slots = nullptr;       // neighbour hash (trw_prepare(NEIGHBOR_HASH)): 2 ne int32
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags
@@ -59,6 +64,7 @@ struct trw_graph {
 };
 
 trw_status trw_fail(trw_status st, const char* fmt, ...);
+void trw_free_stream_buffers(trw_graph* g);
 
 // Every id of src[0..n) in [0, nv) (branch-free, so the loop vectorises).
 inline bool trw_sources_in_range(const int32_t* src, int64_t n, int64_t nv) {
