@@ -23,12 +23,12 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH = 0, 1, 2, 3, 4
+DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH, NODE2VEC_WEIGHTED = 0, 1, 2, 3, 4, 5
 OK, ERR_INVALID, ERR_OOM, ERR_REJECT_CAP = 0, -1, -2, -6
 # Sampling methods of weighted DeepWalk (Section 2.3); DEFAULT is ALIAS.
 SAMPLER_DEFAULT, SAMPLER_ITS, SAMPLER_REJ, SAMPLER_OREJ = 0, 1, 2, 3
 ALGO_NAMES = {DEEPWALK: "deepwalk", DEEPWALK_WEIGHTED: "deepwalk_weighted", PPR: "ppr",
-              NODE2VEC: "node2vec", METAPATH: "metapath"}
+              NODE2VEC: "node2vec", METAPATH: "metapath", NODE2VEC_WEIGHTED: "node2vec_weighted"}
 
 
 def build(force: bool = False) -> str:

@@ -28,6 +28,14 @@
  *     matching edge ends the walk.
  *   - Rejection accepts when y < p_x, strictly (Section 2.3, REJ).
  *   - Node2Vec's IsNeighbor(c, u) means c is an out-neighbour of u.
+ *   - Weighted Node2Vec multiplies Eq. 1 by the edge weight (Section 2.2).
+ *     Its O-REJ dart hits when two independent words pass: y = B2 the class
+ *     threshold of Eq. 1 (as unweighted Node2Vec) and z = B3 the weight
+ *     threshold floor(W_x * 2^32 / P), so a candidate is taken with
+ *     probability proportional to T_class * floor(W_x * 2^32 / P).  P is the
+ *     caller's bound on the weights (quantised like a weight), or p*_v of the
+ *     REJ table when the caller gives none.  With every weight equal to P the
+ *     walk is unweighted Node2Vec's.
  *   - The alias table is built by Vose's method on integer weights, with
  *     first-in first-out work lists (the paper leaves the construction open).
  *   - Weighted DeepWalk may also sample by ITS, REJ or O-REJ (Section 2.3),
@@ -45,7 +53,8 @@
 #include <string.h>
 #include <math.h>
 
-enum { ORC_DEEPWALK = 0, ORC_DEEPWALK_WEIGHTED = 1, ORC_PPR = 2, ORC_NODE2VEC = 3, ORC_METAPATH = 4 };
+enum { ORC_DEEPWALK = 0, ORC_DEEPWALK_WEIGHTED = 1, ORC_PPR = 2, ORC_NODE2VEC = 3, ORC_METAPATH = 4,
+       ORC_NODE2VEC_WEIGHTED = 5 };
 enum { ORC_OK = 0, ORC_ERR_INVALID = -1, ORC_ERR_OOM = -2, ORC_ERR_REJECT_CAP = -6 };
 /* Sampling method of weighted DeepWalk (the other walks take 0). */
 enum { ORC_SAMPLER_DEFAULT = 0, ORC_SAMPLER_ITS = 1, ORC_SAMPLER_REJ = 2, ORC_SAMPLER_OREJ = 3 };
@@ -260,7 +269,7 @@ typedef struct {
   int32_t endpoints_only;     /* 1: out_paths holds one vertex (the end) per walk */
   int64_t walk_offset;        /* index of the first walk in the Philox counter */
   int32_t sampler;            /* weighted DeepWalk: ORC_SAMPLER_* (0 = ALIAS); 0 for the others */
-  double max_weight;          /* O-REJ: the user's bound on the edge weights (MaxWeight) */
+  double max_weight;          /* O-REJ, weighted Node2Vec: the caller's bound on the edge weights (MaxWeight) */
 } orc_params;
 
 typedef struct {
@@ -326,7 +335,7 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
   /* Node2Vec (Eq. 1): weight 1/a on the return edge, 1 at distance 1, 1/b at
    * distance 2; O-REJ bound p* = max{1, 1/a, 1/b} (Section 2.3, Section 4.2). */
   double w_ret = 0, w_nb = 0, w_far = 0, pstar = 1;
-  if (p->algo == ORC_NODE2VEC) {
+  if (p->algo == ORC_NODE2VEC || p->algo == ORC_NODE2VEC_WEIGHTED) {
     if (!(p->n2v_p > 0) || !(p->n2v_q > 0)) return ORC_ERR_INVALID;
     w_ret = 1.0 / p->n2v_p;
     w_nb = 1.0;
@@ -349,6 +358,17 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
   /* O-REJ's bound P: round-half-even(MaxWeight * 2^16), clamped to 2^32 - 1
    * like a weight; it must be at least 1. */
   uint64_t P_user = 0;
+  if (p->algo == ORC_NODE2VEC_WEIGHTED) {
+    if (!g->weights) return ORC_ERR_INVALID;
+    if (p->max_weight == 0.0 && !g->pmax) return ORC_ERR_INVALID;
+    if (p->max_weight != 0.0) {
+      if (!isfinite(p->max_weight) || !(p->max_weight > 0)) return ORC_ERR_INVALID;
+      double t = rint(p->max_weight * 65536.0);
+      if (t > 4294967295.0) t = 4294967295.0;
+      if (t < 1.0) return ORC_ERR_INVALID;
+      P_user = (uint64_t)t;
+    }
+  }
   if (p->algo == ORC_DEEPWALK_WEIGHTED && p->sampler == ORC_SAMPLER_OREJ) {
     if (!isfinite(p->max_weight) || !(p->max_weight > 0)) return ORC_ERR_INVALID;
     double t = rint(p->max_weight * 65536.0);
@@ -453,8 +473,15 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
         }
         next = g->col[off + lo];
         if (sec) sec_touch(sec, SEC_COL, (off + lo) * 4);
-      } else if (p->algo == ORC_NODE2VEC) {
-        /* O-REJ: throw darts (x, y) until y < p_x. */
+      } else if (p->algo == ORC_NODE2VEC || p->algo == ORC_NODE2VEC_WEIGHTED) {
+        /* O-REJ: throw darts (x, y) until y < p_x.  Weighted: the dart must
+         * also pass the weight word, z < W_x / P. */
+        uint64_t P = P_user;
+        if (p->algo == ORC_NODE2VEC_WEIGHTED && P == 0) {
+          P = g->pmax[cur];
+          if (sec) sec_touch(sec, SEC_PMAX, (int64_t)cur * 4);
+          if (P == 0) { if (st) st->stop_dead++; break; }
+        }
         int accepted = 0;
         for (uint32_t a = 0; a < ORC_REJECT_CAP; ++a) {
           if (a > 0) draw_block(seed, w, (uint32_t)s, a, B);
@@ -462,6 +489,11 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
           const int64_t x = (int64_t)uniform_below(B, (uint64_t)d);
           const int32_t c = g->col[off + x];
           if (sec) sec_touch(sec, SEC_COL, (off + x) * 4);
+          if (p->algo == ORC_NODE2VEC_WEIGHTED) {
+            const uint32_t Wx = (uint32_t)orc_quantize_weight(g->weights[off + x]);
+            if (sec) sec_touch(sec, SEC_WEIGHT, (off + x) * 4);
+            if (!((uint64_t)B[3] < orc_rej_threshold(Wx, P))) continue;
+          }
           uint64_t T;
           if (s == 0) {
             T = 4294967296ULL; /* Weight = MaxWeight on the first step */

@@ -619,6 +619,93 @@ def pin_zero_weights(lib=None):
     assert res.status == oracle.ERR_REJECT_CAP
 
 
+# ------------------------------------------------ weighted Node2Vec (Section 2.2)
+
+def node2vec_weighted_step_law(g, path, p_ret, q_io, bound):
+    """Eq. 1 times the edge weight, in the fixed point of its O-REJ dart: a
+    candidate c passes the class word with T_class(c) / 2^32 and the weight
+    word with floor(W_c 2^32 / P) / 2^32; P = bound(v) (p*_v or the caller's)."""
+    v = path[-1]
+    nb = nbrs(g, v)
+    if not nb:
+        return {}
+    P = bound(v)
+    wt = {c: min(TWO32, (int(round(DIR_WEIGHTS[(v, c)] * 65536)) << 32) // P) for c in nb}
+    if len(path) == 1:
+        t = {c: TWO32 for c in nb}
+    else:
+        u = path[-2]
+        w_ret, w_nb, w_far = 1.0 / p_ret, 1.0, 1.0 / q_io
+        pstar = max(w_ret, w_nb, w_far)
+        T = {k: (Fraction(x / pstar) * TWO32).__floor__() for k, x in (("r", w_ret), ("n", w_nb), ("f", w_far))}
+        nu = set(nbrs(g, u))
+        t = {c: T["r"] if c == u else (T["n"] if c in nu else T["f"]) for c in nb}
+    tot = sum(t[c] * wt[c] for c in nb)
+    return {c: t[c] * wt[c] / tot for c in nb}
+
+
+def pin_law_node2vec_weighted(lib=None):
+    """Three-move path laws of weighted Node2Vec with the REJ bound p*_v and
+    with a caller's bound, by chi-square against the exact product law."""
+    g = dir_graph()
+    pm = oracle.prepare_rej(g.row_ptr, g.weights, lib=lib)
+    for (pp, qq, seed, mw) in [(0.5, 2.0, 23, 0.0), (2.0, 0.5, 24, 12.0)]:
+        res = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC_WEIGHTED, [0], 3, seed=seed, walks_per_source=N_LAW,
+                          n2v_p=pp, n2v_q=qq, weights=g.weights, pmax=pm, max_weight=mw, lib=lib)
+        assert res.status == 0
+        bound = (lambda v: int(pm[v])) if mw == 0.0 else (lambda v: int(round(mw * 65536)))
+        law = enumerate_paths(0, 3, lambda path: node2vec_weighted_step_law(g, path, pp, qq, bound))
+        p = chi2_pvalue(path_counts(res), law, N_LAW)
+        assert p > 1e-3, (pp, qq, mw, p)
+
+
+def pin_node2vec_weighted_first_move(lib=None):
+    """The first move of every weighted Node2Vec walk, and its trials, from the
+    dart sequence recomputed in Python: x from words 0-1, the weight word 3
+    tested as (z + 1) * P <= W_x * 2^32 (the class passes at the source)."""
+    g = small_rmat()
+    pm = oracle.prepare_rej(g.row_ptr, g.weights, lib=lib)
+    src = synth.vertex_sources(g.nv)[:300]
+    seed = 5
+    Wq = _wq(g.weights)
+    res = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC_WEIGHTED, src, 1, seed, n2v_p=0.5, n2v_q=2.0,
+                      weights=g.weights, pmax=pm, lib=lib)
+    assert res.status == 0
+    trials = 0
+    for i, v in enumerate(src):
+        lo, hi = int(g.row_ptr[v]), int(g.row_ptr[v + 1])
+        if hi == lo:
+            continue
+        d = hi - lo
+        ps = int(Wq[lo:hi].max())
+        for a in range(65536):
+            B = oracle.philox4x32_10([i, 0, a, 0], [seed, 0])
+            x = (_r64(B) * d) >> 64
+            if (int(B[3]) + 1) * ps <= int(Wq[lo + x]) * TWO32:
+                break
+        trials += a + 1
+        assert res.paths[i, 1] == g.col[lo + x], i
+    assert res.stats["attempts"] == trials
+
+
+def pin_node2vec_weighted_reductions(lib=None):
+    """Every weight equal to the bound: unweighted Node2Vec's walks, bit for bit
+    (the weight word always passes); with p = q = 1 and equal weights, the
+    trials per move are d P / sum(W) = 1."""
+    g = small_rmat()
+    src = synth.vertex_sources(g.nv)
+    w3 = np.full(g.ne, 3.0, dtype=np.float32)
+    base = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src, 15, seed=8, n2v_p=0.5, n2v_q=2.0, lib=lib)
+    for kw in ({"max_weight": 3.0}, {"pmax": oracle.prepare_rej(g.row_ptr, w3, lib=lib)}):
+        res = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC_WEIGHTED, src, 15, seed=8, n2v_p=0.5, n2v_q=2.0,
+                          weights=w3, lib=lib, **kw)
+        assert res.status == 0 and np.array_equal(res.lengths, base.lengths)
+        mask = np.arange(16)[None, :] < base.lengths[:, None]
+        assert np.array_equal(res.paths[mask], base.paths[mask]), kw
+        assert res.stats["attempts"] == base.stats["attempts"]
+
+
 ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
             pin_law_metapath, pin_ppr, pin_rejection_trials, pin_reductions, pin_invariants, pin_sharding, pin_rej_threshold, pin_its_first_move,
-            pin_rej_first_move, pin_law_samplers, pin_rej_trials_closed_form, pin_zero_weights]
+            pin_rej_first_move, pin_law_samplers, pin_rej_trials_closed_form, pin_zero_weights,
+            pin_law_node2vec_weighted, pin_node2vec_weighted_first_move, pin_node2vec_weighted_reductions]

@@ -41,7 +41,17 @@ MUTANTS = [
      "return (((uint64_t)W << 32) + pstar - 1) / pstar;"),
     ("rej: dart reuses the first draw", "if (a > 0) draw_block(seed, w, (uint32_t)s, a, B);\n          if (st) st->attempts++;\n          const int64_t x = (int64_t)uniform_below(B, (uint64_t)d);\n          const uint32_t Wx",
      "if (a > 0) draw_block(seed, w, (uint32_t)s, a > 1 ? a - 1 : a, B);\n          if (st) st->attempts++;\n          const int64_t x = (int64_t)uniform_below(B, (uint64_t)d);\n          const uint32_t Wx"),
-    ("o-rej: bound truncated", "double t = rint(p->max_weight * 65536.0);", "double t = floor(p->max_weight * 65536.0 / 2);"),
+    ("o-rej: bound truncated", "return ORC_ERR_INVALID;\n    double t = rint(p->max_weight * 65536.0);",
+     "return ORC_ERR_INVALID;\n    double t = floor(p->max_weight * 65536.0 / 2);"),
+    ("weighted node2vec: caller's bound truncated", "return ORC_ERR_INVALID;\n      double t = rint(p->max_weight * 65536.0);",
+     "return ORC_ERR_INVALID;\n      double t = floor(p->max_weight * 65536.0 / 2);"),
+    ("weighted node2vec: weight word shares the class word",
+     "if (!((uint64_t)B[3] < orc_rej_threshold(Wx, P))) continue;",
+     "if (!((uint64_t)B[2] < orc_rej_threshold(Wx, P))) continue;"),
+    ("weighted node2vec: bound of the previous vertex", "          P = g->pmax[cur];\n          if (sec) sec_touch(sec, SEC_PMAX, (int64_t)cur * 4);",
+     "          P = g->pmax[s > 0 ? path[s - 1] : cur];\n          if (sec) sec_touch(sec, SEC_PMAX, (int64_t)cur * 4);"),
+    ("weighted node2vec: weight test only after the source", "if (p->algo == ORC_NODE2VEC_WEIGHTED) {\n            const uint32_t Wx",
+     "if (p->algo == ORC_NODE2VEC_WEIGHTED && s > 0) {\n            const uint32_t Wx"),
     ("zero row: not a dead end for REJ", "if (pstar == 0) { if (st) st->stop_dead++; break; }",
      "if (pstar == 0) pstar = 1;"),
 ]
