@@ -400,6 +400,8 @@ def measure_per_algo(trw, torch, G, g, flush, sp, G_paper=None):
     }
     if G.has_weights:
         cases["deepwalk_weighted"] = (trw.DEEPWALK_WEIGHTED, verts, 80, {})
+        cases["node2vec_weighted"] = (trw.NODE2VEC_WEIGHTED, verts, 80,
+                                      {"n2v_p": 0.5, "n2v_q": 2.0, "max_weight": SWEEP_BOUND})
     if G.has_labels:
         cases["metapath"] = (trw.METAPATH, verts, 80, {"schema": schema})
     out = {}
@@ -418,7 +420,7 @@ def measure_per_algo(trw, torch, G, g, flush, sp, G_paper=None):
                 row[kname]["launches"] = G.last_stats()["launches"]
         row["speedup"] = round(row["persistent"]["steps_per_s"] / row["plain"]["steps_per_s"], 3)
         row["speedup_vs_bsp"] = round(row["persistent"]["steps_per_s"] / row["bsp"]["steps_per_s"], 3)
-        if G_paper is not None and algo in (trw.NODE2VEC, trw.METAPATH):
+        if G_paper is not None and algo in (trw.NODE2VEC, trw.METAPATH):  # the unweighted paper graph
             G_paper.autotune(algo, L, **tune_kw)
             ms, moves = time_walk(trw, torch, G_paper, flush, sp, algo, src, L, 1, trw.KERNEL_PERSISTENT, **kw)
             row["paper_path"] = {"what": "binary search" if algo == trw.NODE2VEC else "label scan",

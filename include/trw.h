@@ -65,7 +65,11 @@ typedef enum {
   TRW_DEEPWALK_WEIGHTED = 1,    /* static biased by w_e, ALIAS sampling */
   TRW_PPR = 2,                  /* unbiased with a stop coin per step, NAIVE */
   TRW_NODE2VEC = 3,             /* dynamic second order (Eq. 1), O-REJ */
-  TRW_METAPATH = 4              /* dynamic label filter, ITS */
+  TRW_METAPATH = 4,             /* dynamic label filter, ITS */
+  TRW_NODE2VEC_WEIGHTED = 5     /* Node2Vec with Eq. 1 multiplied by w_e (Section 2.2), O-REJ: a dart
+                                   passes the class threshold (word 2) and the weight threshold
+                                   floor(W_x * 2^32 / P) (word 3); P = the caller's max_weight
+                                   quantised, or the row's p*_v (TRW_PREP_REJ) when max_weight is 0 */
 } trw_algo;
 
 /* Kernel choice for trw_walk_ex. */
@@ -119,7 +123,8 @@ typedef struct {
   int32_t walks_per_source;     /* >= 1; walk i starts at sources[i / walks_per_source] */
   int32_t sampler;              /* TRW_SAMPLER_*: weighted DeepWalk's sampling method */
   int64_t walk_offset;          /* index of walk 0 in the Philox counter (for sharding a batch) */
-  double max_weight;            /* TRW_SAMPLER_OREJ: MaxWeight, the caller's bound on w_e, finite and > 0 */
+  double max_weight;            /* TRW_SAMPLER_OREJ and TRW_NODE2VEC_WEIGHTED: MaxWeight, the caller's
+                                   bound on w_e, finite and > 0 (weighted Node2Vec: 0 = the REJ bounds) */
 } trw_params;
 
 /* Fills *p with defaults: ppr_stop 0.2, p = q = 1, no schema, paths,

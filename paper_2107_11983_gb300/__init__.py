@@ -20,7 +20,7 @@ __all__ = ["TRWError", "Graph", "Server", "load_library", "build", "DEEPWALK", "
            "NODE2VEC", "METAPATH", "KERNEL_AUTO", "KERNEL_PLAIN", "KERNEL_PERSISTENT", "OUT_PATHS",
            "OUT_ENDPOINTS", "philox_device"]
 
-DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH = 0, 1, 2, 3, 4
+DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH, NODE2VEC_WEIGHTED = 0, 1, 2, 3, 4, 5
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT, KERNEL_BSP = 0, 1, 2, 3
 OUT_PATHS, OUT_ENDPOINTS = 0, 1
 PREP_ALIAS = 1
@@ -46,7 +46,7 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "ERR_INVALID", -2: "ERR_OOM", -3: "ER
                 -5: "ERR_TIMEOUT", -6: "ERR_REJECT_CAP", -7: "ERR_BUSY", -8: "ERR_NOT_FOUND", -9: "ERR_INTERNAL"}
 
 ALGOS = {"deepwalk": DEEPWALK, "deepwalk_weighted": DEEPWALK_WEIGHTED, "ppr": PPR, "node2vec": NODE2VEC,
-         "metapath": METAPATH}
+         "metapath": METAPATH, "node2vec_weighted": NODE2VEC_WEIGHTED}
 
 
 class TRWError(RuntimeError):

@@ -483,7 +483,8 @@ trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pi
   if (pin) p = *pin;
   else trw_params_default(&p);
   std::memset(sp, 0, sizeof(*sp));
-  if ((int)algo < TRW_DEEPWALK || (int)algo > TRW_METAPATH) return trw_fail(TRW_ERR_INVALID, "unknown algorithm %d", (int)algo);
+  if ((int)algo < TRW_DEEPWALK || (int)algo > TRW_NODE2VEC_WEIGHTED)
+    return trw_fail(TRW_ERR_INVALID, "unknown algorithm %d", (int)algo);
   if (max_len < 0) return trw_fail(TRW_ERR_INVALID, "max_len < 0");
   if (n_sources < 0) return trw_fail(TRW_ERR_INVALID, "n_sources < 0");
   if (p.walks_per_source < 1) return trw_fail(TRW_ERR_INVALID, "walks_per_source < 1");
@@ -505,7 +506,7 @@ trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pi
     if (!(p.ppr_stop >= 0.0 && p.ppr_stop <= 1.0)) return trw_fail(TRW_ERR_INVALID, "ppr_stop outside [0, 1]");
     sp->T_stop = threshold_of(p.ppr_stop);
   }
-  if (algo == TRW_NODE2VEC) {
+  if (algo == TRW_NODE2VEC || algo == TRW_NODE2VEC_WEIGHTED) {
     if (!(p.n2v_p > 0.0) || !(p.n2v_q > 0.0) || !std::isfinite(p.n2v_p) || !std::isfinite(p.n2v_q))
       return trw_fail(TRW_ERR_INVALID, "node2vec p and q must be finite and > 0");
     if (!g->sorted) return trw_fail(TRW_ERR_INVALID, "node2vec needs sorted adjacency rows");
@@ -517,6 +518,23 @@ trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pi
     sp->T_far = threshold_of(w_far / pstar);
     sp->T_lo = std::min(sp->T_nb, sp->T_far);
     sp->T_hi = std::max(sp->T_nb, sp->T_far);
+  }
+  if (algo == TRW_NODE2VEC_WEIGHTED) {
+    // Eq. 1 times w_e: the weight word's bound is the caller's max_weight,
+    // quantised like a weight, or the row's p*_v when max_weight is 0
+    if (!g->weights) return trw_fail(TRW_ERR_INVALID, "weighted node2vec needs edge weights");
+    if (p.max_weight == 0.0) {
+      if (!g->rej_pmax)
+        return trw_fail(TRW_ERR_NOT_PREPARED, "weighted node2vec without max_weight needs trw_prepare(TRW_PREP_REJ)");
+    } else {
+      if (!std::isfinite(p.max_weight) || !(p.max_weight > 0.0))
+        return trw_fail(TRW_ERR_INVALID, "max_weight must be finite and > 0 (or 0 for the REJ bounds)");
+      double t = std::rint(p.max_weight * 65536.0);
+      if (t > 4294967295.0) t = 4294967295.0;
+      if (t < 1.0) return trw_fail(TRW_ERR_INVALID, "max_weight %g quantises to 0", p.max_weight);
+      sp->T_stop = (uint64_t)t;
+    }
+    sp->algo = N2V_W;
   }
   if (algo == TRW_METAPATH) {
     if (!g->labels) return trw_fail(TRW_ERR_INVALID, "metapath needs edge labels");
@@ -567,7 +585,7 @@ LaunchCfg trw_launch_cfg(const trw_graph* g, int algo) {
   c.block_threads = g->tuning.block_threads;
   int bps = g->tuning.blocks_per_sm;
   const bool coop = algo == MIXED || (algo == METAPATH && !g->lerec && g->tuning.coop_degree < 0x7fffffff) ||
-                    (algo == NODE2VEC && !g->nh_slots && g->tuning.search_degree < 0x7fffffff);
+                    (is_n2v(algo) && !g->nh_slots && g->tuning.search_degree < 0x7fffffff);
   const int occ = persistent_blocks_per_sm(algo, c.block_threads, coop);
   if (bps <= 0 || bps > occ) bps = occ;
   c.grid_blocks = g->num_sms * bps;
@@ -779,7 +797,7 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
     // per step.
     const LaunchCfg cfg = trw_launch_cfg(g, sp.algo);
     const bool coop = (sp.algo == METAPATH && cfg.coop_degree < 0x7fffffff) ||
-                      (sp.algo == NODE2VEC && cfg.search_degree < 0x7fffffff);
+                      (is_n2v(sp.algo) && cfg.search_degree < 0x7fffffff);
     kernel = !coop && nwalks <= (int64_t)cfg.grid_blocks * cfg.block_threads ? TRW_KERNEL_PLAIN : TRW_KERNEL_PERSISTENT;
   }
 

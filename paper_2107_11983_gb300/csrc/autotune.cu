@@ -93,7 +93,7 @@ extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params
     const int chunk_c[] = {8, 32, 128};
     std::vector<int> deg_c;
     if (algo == TRW_METAPATH && !g->lerec) deg_c = {64, 256, 1024, kOff};
-    else if (algo == TRW_NODE2VEC && !g->nh_slots) deg_c = {64, 1024, kOff};
+    else if ((algo == TRW_NODE2VEC || algo == TRW_NODE2VEC_WEIGHTED) && !g->nh_slots) deg_c = {64, 1024, kOff};
     else deg_c = {kOff};
     for (int threads : threads_c) {
       for (int cd : deg_c) {
@@ -109,7 +109,7 @@ extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params
             cfg.grid_blocks = g->num_sms * bps;
             cfg.chunk = chunk;
             cfg.coop_degree = algo == TRW_METAPATH ? cd : g->tuning.coop_degree;
-            cfg.search_degree = algo == TRW_NODE2VEC ? cd : g->tuning.search_degree;
+            cfg.search_degree = (algo == TRW_NODE2VEC || algo == TRW_NODE2VEC_WEIGHTED) ? cd : g->tuning.search_degree;
             float t[4] = {0.f, 0.f, 0.f, 0.f};
             for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) e = timed(cfg, &t[rep]);  // rep 0 warms up
             if (e != cudaSuccess) break;

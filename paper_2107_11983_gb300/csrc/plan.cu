@@ -104,7 +104,7 @@ static cudaError_t capture(trw_plan* p) {
     // cooperation, else the persistent one
     const WalkSpec& s0 = h_specs[0];
     const bool coop = (s0.algo == METAPATH && p->cfg.coop_degree < 0x7fffffff) ||
-                      (s0.algo == NODE2VEC && p->cfg.search_degree < 0x7fffffff);
+                      (is_n2v(s0.algo) && p->cfg.search_degree < 0x7fffffff);
     const bool one_wave = !coop && s0.nwalks <= (int64_t)p->cfg.grid_blocks * p->cfg.block_threads;
     if (e == cudaSuccess) e = launch_validate_sources(s0.sources, p->n_src0, p->dg.nv, p->ctrl, p->cap);
     if (e == cudaSuccess && s0.nwalks > 0)

@@ -331,7 +331,7 @@ __device__ __forceinline__ int spec_check(const WalkSpec& sp, unsigned long long
                                           unsigned long long published) {
   if (ck >= published) return 1;
   if (!(cb < ce) || (int64_t)ce > sp.nwalks) return 2;
-  if (sp.algo < 0 || sp.algo > DW_OREJ || sp.algo == MIXED || sp.wps < 1 || sp.max_len < 0 ||
+  if (sp.algo < 0 || sp.algo > N2V_W || sp.algo == MIXED || sp.wps < 1 || sp.max_len < 0 ||
       (sp.algo == METAPATH && sp.schema_len < 1) || (sp.algo == DW_OREJ && sp.T_stop == 0))
     return 3;
   const uintptr_t ptrs = reinterpret_cast<uintptr_t>(sp.sources) | reinterpret_cast<uintptr_t>(sp.out_paths) |

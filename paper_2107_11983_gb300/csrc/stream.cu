@@ -115,7 +115,7 @@ extern "C" trw_status trw_walk_stream(trw_graph* g, trw_algo algo, const trw_par
   const DevGraph dg = trw_dev_graph(g);
   const LaunchCfg cfg = trw_launch_cfg(g, sp.algo);
   const bool coop = (sp.algo == METAPATH && cfg.coop_degree < 0x7fffffff) ||
-                    (sp.algo == NODE2VEC && cfg.search_degree < 0x7fffffff);
+                    (is_n2v(sp.algo) && cfg.search_degree < 0x7fffffff);
   Ctrl* kc[2] = {g->ctrl, g->ctrl2};
   const int64_t nslices = (n_sources + src_per - 1) / src_per;
   int64_t moves = 0;

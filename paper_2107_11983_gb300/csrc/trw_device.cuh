@@ -14,8 +14,12 @@ enum Algo : int {
   DEEPWALK = 0, DEEPWALK_WEIGHTED = 1, PPR = 2, NODE2VEC = 3, METAPATH = 4, MIXED = 5,
   DW_ITS = 6,    // weighted DeepWalk, static ITS over the stored prefix sums
   DW_REJ = 7,    // weighted DeepWalk, REJ with the stored per-vertex bound p*_v
-  DW_OREJ = 8    // weighted DeepWalk, O-REJ with the caller's bound
+  DW_OREJ = 8,   // weighted DeepWalk, O-REJ with the caller's bound
+  N2V_W = 9      // weighted Node2Vec: O-REJ darts pass Eq. 1's class word and a weight word
 };
+
+// Node2Vec, unweighted or weighted (the same second-order step).
+__host__ __device__ constexpr bool is_n2v(int a) { return a == NODE2VEC || a == N2V_W; }
 
 constexpr int kMaxSchema = 16;
 constexpr uint32_t kRejectCap = 65536;
@@ -125,7 +129,8 @@ struct WalkSpec {
   uint32_t key0, key1;        // Philox key (seed)
   uint32_t walk_offset;       // Philox counter word 0 of walk 0
   uint32_t schema_len;
-  uint64_t T_stop;            // PPR stop threshold; DW_OREJ: the caller's bound P on the integer weights (>= 1)
+  uint64_t T_stop;            // PPR stop threshold; DW_OREJ, N2V_W: the caller's bound P on the integer
+                              // weights (>= 1; N2V_W: 0 for the row's p*_v)
   uint64_t T_ret, T_nb, T_far;// Node2Vec O-REJ thresholds (Eq. 1 over p*)
   uint64_t T_lo, T_hi;        // min / max of T_nb, T_far (skip IsNeighbor outside [T_lo, T_hi))
   const int32_t* sources;

@@ -297,7 +297,7 @@ namespace {
 bool wants_coop(int algo, const LaunchCfg& cfg) {
   if (algo == MIXED) return true;
   if (algo == METAPATH) return cfg.coop_degree < 0x7fffffff;
-  if (algo == NODE2VEC) return cfg.search_degree < 0x7fffffff;
+  if (is_n2v(algo)) return cfg.search_degree < 0x7fffffff;
   return false;
 }
 
@@ -317,6 +317,9 @@ int persistent_blocks_per_sm(int algo, int block_threads, bool coop) {
     case DW_ITS: return blocks_per_sm_of(walk_persistent<DW_ITS, false>, block_threads);
     case DW_REJ: return blocks_per_sm_of(walk_persistent<DW_REJ, false>, block_threads);
     case DW_OREJ: return blocks_per_sm_of(walk_persistent<DW_OREJ, false>, block_threads);
+    case N2V_W:
+      return coop ? blocks_per_sm_of(walk_persistent<N2V_W, true>, block_threads)
+                  : blocks_per_sm_of(walk_persistent<N2V_W, false>, block_threads);
     default:
       return coop ? blocks_per_sm_of(walk_persistent<MIXED, true>, block_threads)
                   : blocks_per_sm_of(walk_persistent<MIXED, false>, block_threads);
@@ -345,6 +348,7 @@ cudaError_t launch_walk_plain(const DevGraph& g, const WalkSpec& sp, Ctrl* ctrl,
     case DW_ITS: walk_plain<DW_ITS><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
     case DW_REJ: walk_plain<DW_REJ><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
     case DW_OREJ: walk_plain<DW_OREJ><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
+    case N2V_W: walk_plain<N2V_W><<<(unsigned)blocks, threads, 0, st>>>(g, sp, ctrl); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -379,6 +383,10 @@ cudaError_t launch_walk_persistent(const DevGraph& g, const WalkSpec& sp, Ctrl* 
     case DW_ITS: TRW_LAUNCH(DW_ITS, false); break;
     case DW_REJ: TRW_LAUNCH(DW_REJ, false); break;
     case DW_OREJ: TRW_LAUNCH(DW_OREJ, false); break;
+    case N2V_W:
+      if (cv) TRW_LAUNCH(N2V_W, true);
+      else TRW_LAUNCH(N2V_W, false);
+      break;
     default: return cudaErrorInvalidValue;
   }
 #undef TRW_LAUNCH
@@ -429,6 +437,7 @@ cudaError_t launch_bsp_step(const DevGraph& g, const WalkSpec& sp, const void* i
     case DW_ITS: bsp_step<DW_ITS><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
     case DW_REJ: bsp_step<DW_REJ><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
     case DW_OREJ: bsp_step<DW_OREJ><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
+    case N2V_W: bsp_step<N2V_W><<<blocks, 256, 0, st>>>(g, sp, a, n, b, n_out, ctrl); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

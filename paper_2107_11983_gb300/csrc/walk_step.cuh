@@ -349,11 +349,28 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
       return kMoved;
     }
     return (W.att + 1 >= kRejectCap) ? kFail : kRetry;
-  } else {  // NODE2VEC, O-REJ
+  } else {  // NODE2VEC, N2V_W: O-REJ
+    unsigned long long P = 0;
+    if (A == N2V_W) {
+      // the weight bound: the caller's, else the row's p*_v
+      P = sp.T_stop;
+      if (P == 0ull) {
+        if (CHECK && ((uint32_t)W.cur >= (uint32_t)g.nv || !g.pmax)) return kBroken;
+        P = __ldg(g.pmax + W.cur);
+        if (P == 0ull) return kStop;                           // no positive weight
+      }
+      if (CHECK && !g.rrec && !g.weights) return kBroken;
+    }
     const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
     int4 rr = make_int4(0, 0, 0, 0);
     if (g.rrec) rr = __ldg(g.rrec + e);
     const int32_t c = g.rrec ? rr.x : ldg(g.col + e);
+    if (A == N2V_W) {
+      // weight word: (z + 1) * P <= W_x * 2^32, i.e. z < floor(W_x * 2^32 / P)
+      const uint32_t wx = g.rrec ? (uint32_t)rr.w : weight_fixed(__ldg(g.weights + e));
+      if (((unsigned long long)B.w + 1ull) * P > ((unsigned long long)wx << 32))
+        return (W.att + 1 >= kRejectCap) ? kFail : kRetry;
+    }
     bool accept;
     if (W.s == 0) accept = true;                               // Weight = MaxWeight on the first step
     else if (c == W.prev) accept = (uint64_t)B.z < sp.T_ret;
@@ -592,8 +609,8 @@ __device__ __forceinline__ void advance(Walker& W, int32_t next) {
 }
 
 
-// Weighted DeepWalk under ITS, REJ or O-REJ in the mixed kernels (batches and
-// the server): one step run out of line, so that these samplers' registers do
+// Weighted DeepWalk under ITS, REJ or O-REJ, and weighted Node2Vec, in the
+// mixed kernels (batches and the server): one step run out of line, so that these samplers' registers do
 // not weigh on every other algorithm of the dispatcher.  The walker goes in
 // by value; the fields a step may change come back.
 struct SamplerOut {
@@ -607,8 +624,10 @@ __device__ __noinline__ SamplerOut sampler_step(const DevGraph& g, const WalkSpe
   SamplerOut o;
   Pend p;
   o.next = -1;
-  o.r = (sp.algo == DW_ITS) ? step_begin<DW_ITS, CHECK>(g, sp, W, o.next, p, Coop{0x7fffffff, 0x7fffffff})
-                            : step_begin<DW_REJ, CHECK>(g, sp, W, o.next, p, Coop{0x7fffffff, 0x7fffffff});
+  const Coop none{0x7fffffff, 0x7fffffff};
+  o.r = sp.algo == DW_ITS  ? step_begin<DW_ITS, CHECK>(g, sp, W, o.next, p, none)
+        : sp.algo == N2V_W ? step_begin<N2V_W, CHECK>(g, sp, W, o.next, p, none)
+                           : step_begin<DW_REJ, CHECK>(g, sp, W, o.next, p, none);
   o.off = W.off;
   o.d = W.d;
   o.nxo = W.nxo;
@@ -642,7 +661,8 @@ __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& 
       case METAPATH: return step_serial<METAPATH, CHECK>(g, sp, W, next);
       case DW_ITS:
       case DW_REJ:
-      case DW_OREJ: return sampler_step_apply<CHECK>(g, sp, W, next);
+      case DW_OREJ:
+      case N2V_W: return sampler_step_apply<CHECK>(g, sp, W, next);
       default: return kBroken;
     }
   }
@@ -663,7 +683,8 @@ __device__ __forceinline__ int step_begin_dispatch(const DevGraph& g, const Walk
       case METAPATH: return step_begin<METAPATH, CHECK>(g, sp, W, next, p, coop);
       case DW_ITS:
       case DW_REJ:
-      case DW_OREJ: p.kind = 0; return sampler_step_apply<CHECK>(g, sp, W, next);
+      case DW_OREJ:
+      case N2V_W: p.kind = 0; return sampler_step_apply<CHECK>(g, sp, W, next);
       default: return kBroken;
     }
   }
