@@ -60,6 +60,12 @@ class _Stats(ctypes.Structure):
                 ("sectors", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("checks", ctypes.c_int64)]
 
 
+_WEIGHT_FN = ctypes.CFUNCTYPE(ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int64)
+_UPDATE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int64)
+
+
 def _bind(path: str):
     """Load a compiled oracle library and declare its signatures."""
     lib = ctypes.CDLL(path)
@@ -79,6 +85,10 @@ def _bind(path: str):
     lib.orc_prepare_rej.restype = ctypes.c_int
     lib.orc_rej_threshold.argtypes = [ctypes.c_uint32, ctypes.c_uint64]
     lib.orc_rej_threshold.restype = ctypes.c_uint64
+    lib.orc_walk_custom.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int32, ctypes.c_uint32, _WEIGHT_FN, _UPDATE_FN,
+                                    vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                    ctypes.c_int64, vp, vp, ctypes.POINTER(_Stats)]
+    lib.orc_walk_custom.restype = ctypes.c_int
     lib.orc_walk.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Params), vp, ctypes.c_int64,
                              ctypes.c_int32, ctypes.c_uint64, vp, vp, ctypes.POINTER(_Stats)]
     lib.orc_walk.restype = ctypes.c_int
@@ -258,3 +268,32 @@ def walk(row_ptr, col, algo: int, sources, max_len: int, seed: int, *, alias: Op
                       paths.ctypes.data, lengths.ctypes.data, ctypes.byref(st))
     stats = {name: getattr(st, name) for name, _ in _Stats._fields_}
     return WalkResult(paths, lengths, stats, rc)
+
+
+NAIVE_SAMPLER, OREJ_SAMPLER = 0, 1
+
+
+def walk_custom(row_ptr, col, sources, max_len: int, seed: int, *, sampler: int, weight=None, max_weight: int = 0,
+                update=None, walks_per_source: int = 1, walk_offset: int = 0, lib=None) -> WalkResult:
+    """A walk given by user functions (Section 4.3): sampler NAIVE_SAMPLER or
+    OREJ_SAMPLER; weight(walk, length, cur, prev, dst, edge) -> int and
+    max_weight (O-REJ, fixed point); update(walk, length, cur, prev, dst, edge)
+    -> bool, called after each move with the query moved (true ends the walk)."""
+    lib = lib or _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    sources = np.ascontiguousarray(sources, dtype=np.int32)
+    g = _Graph()
+    g.nv = row_ptr.shape[0] - 1
+    g.row_ptr = row_ptr.ctypes.data
+    g.col = col.ctypes.data
+    wfn = _WEIGHT_FN((lambda u, *a: int(weight(*a))) if weight else 0)
+    ufn = _UPDATE_FN((lambda u, *a: 1 if update(*a) else 0) if update else 0)
+    nwalks = sources.shape[0] * walks_per_source
+    paths = np.full((nwalks, max_len + 1), -1, dtype=np.int32)
+    lengths = np.zeros(nwalks, dtype=np.int32)
+    st = _Stats()
+    rc = lib.orc_walk_custom(ctypes.byref(g), sampler, max_weight, wfn, ufn, None, sources.ctypes.data,
+                             sources.shape[0], walks_per_source, max_len, seed, walk_offset, paths.ctypes.data,
+                             lengths.ctypes.data, ctypes.byref(st))
+    return WalkResult(paths, lengths, {name: getattr(st, name) for name, _ in _Stats._fields_}, rc)

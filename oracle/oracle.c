@@ -535,3 +535,62 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
   free(sec);
   return rc;
 }
+
+/* ------------------------------------------------------- user-defined walks */
+
+/*
+ * A walk given by user functions (Section 4.3, "APIs"): the sampling method
+ * (0 NAIVE, 1 O-REJ), Weight and MaxWeight as fixed-point integers, and
+ * Update, called after each move with the query already moved; a non-zero
+ * return ends the walk.  Draws as every other walk: block (walk, step,
+ * attempt, 0); NAIVE takes E_cur[x]; an O-REJ dart hits when the 32-bit word
+ * B2 is below floor(Weight * 2^32 / MaxWeight) (2^32 once Weight >= MaxWeight).
+ * A walk also ends after max_len moves and at a vertex without out-edges.
+ */
+typedef uint32_t (*orc_weight_fn)(void* user, int64_t walk, int32_t length, int32_t cur, int32_t prev, int32_t dst,
+                                  int64_t edge);
+typedef int (*orc_update_fn)(void* user, int64_t walk, int32_t length, int32_t cur, int32_t prev, int32_t dst,
+                             int64_t edge);
+
+int orc_walk_custom(const orc_graph* g, int32_t sampler, uint32_t max_weight, orc_weight_fn weight,
+                    orc_update_fn update, void* user, const int32_t* sources, int64_t n_sources,
+                    int32_t walks_per_source, int32_t max_len, uint64_t seed, int64_t walk_offset,
+                    int32_t* out_paths, int32_t* out_lengths, orc_stats* st) {
+  if (max_len < 0 || walks_per_source < 1 || n_sources < 0 || walk_offset < 0) return ORC_ERR_INVALID;
+  if (sampler != 0 && sampler != 1) return ORC_ERR_INVALID;
+  if (sampler == 1 && (max_weight == 0 || !weight)) return ORC_ERR_INVALID;
+  const int64_t nwalks = n_sources * walks_per_source;
+  if (walk_offset + nwalks > 4294967296LL) return ORC_ERR_INVALID;
+  const int64_t row = (int64_t)max_len + 1;
+  for (int64_t i = 0; i < nwalks; ++i) {
+    const uint64_t w = (uint64_t)(walk_offset + i);
+    int32_t cur = sources[i / walks_per_source], prev = -1;
+    if (cur < 0 || cur >= g->nv) return ORC_ERR_INVALID;
+    int32_t s = 0;
+    out_paths[i * row] = cur;
+    while (s < max_len) {
+      const int64_t off = g->row_ptr[cur], d = g->row_ptr[cur + 1] - off;
+      if (d == 0) { if (st) st->stop_dead++; break; }
+      int64_t x = -1;
+      for (uint32_t a = 0; a < ORC_REJECT_CAP; ++a) {
+        uint32_t B[4];
+        draw_block(seed, w, (uint32_t)s, a, B);
+        if (st && sampler == 1) st->attempts++;
+        const int64_t c = (int64_t)uniform_below(B, (uint64_t)d);
+        if (sampler == 0) { x = c; break; }
+        const uint32_t W = weight(user, (int64_t)w, s, cur, prev, g->col[off + c], off + c);
+        if ((uint64_t)B[2] < orc_rej_threshold(W, max_weight)) { x = c; break; }
+      }
+      if (x < 0) return ORC_ERR_REJECT_CAP;
+      const int32_t dst = g->col[off + x];
+      prev = cur;
+      cur = dst;
+      ++s;
+      out_paths[i * row + s] = cur;
+      if (st) st->moves++;
+      if (update && update(user, (int64_t)w, s, cur, prev, dst, off + x)) break;
+    }
+    out_lengths[i] = s + 1;
+  }
+  return ORC_OK;
+}

@@ -705,7 +705,88 @@ def pin_node2vec_weighted_reductions(lib=None):
         assert res.stats["attempts"] == base.stats["attempts"]
 
 
+# ---------------------------------------------- user-defined walks (Section 4.3)
+
+def pin_custom_walk_reductions(lib=None):
+    """User functions that restate a built-in walk give its walks bit for bit:
+    NAIVE with no Update (DeepWalk), an Update that stops after 7 moves
+    (DeepWalk truncated), O-REJ with Eq. 1's weights in fixed point 4 / 2 / 1
+    over MaxWeight 4 (Node2Vec a = 0.5, b = 2), O-REJ with the integer edge
+    weights over the quantised bound (weighted DeepWalk under O-REJ)."""
+    g = small_rmat()
+    src = synth.vertex_sources(g.nv)
+    L = 12
+
+    def same(res, base, what, L=L):
+        assert res.status == 0 and base.status == 0, what
+        assert np.array_equal(res.lengths, base.lengths), what
+        mask = np.arange(L + 1)[None, :] < base.lengths[:, None]
+        assert np.array_equal(res.paths[:, :L + 1][mask], base.paths[mask]), what
+
+    dw = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK, src, L, seed=4, lib=lib)
+    same(oracle.walk_custom(g.row_ptr, g.col, src, L, 4, sampler=oracle.NAIVE_SAMPLER, lib=lib), dw, "naive")
+    dw7 = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK, src, 7, seed=4, lib=lib)
+    res = oracle.walk_custom(g.row_ptr, g.col, src, L, 4, sampler=oracle.NAIVE_SAMPLER,
+                             update=lambda w, ln, cur, prev, dst, e: ln == 7, lib=lib)
+    same(res, dw7, "update at 7", L=7)
+    adj = [set(nbrs(g, v)) for v in range(g.nv)]
+
+    def n2v_weight(w, ln, cur, prev, dst, e):
+        if ln == 0:
+            return 4
+        return 4 if dst == prev else (2 if dst in adj[prev] else 1)
+
+    n2v = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src, L, seed=6, n2v_p=0.5, n2v_q=2.0, lib=lib)
+    same(oracle.walk_custom(g.row_ptr, g.col, src, L, 6, sampler=oracle.OREJ_SAMPLER, weight=n2v_weight,
+                            max_weight=4, lib=lib), n2v, "node2vec")
+    Wq = _wq(g.weights)
+    orej = oracle.walk(g.row_ptr, g.col, oracle.DEEPWALK_WEIGHTED, src, L, seed=8, sampler=oracle.SAMPLER_OREJ,
+                       weights=g.weights, max_weight=100.0, lib=lib)
+    same(oracle.walk_custom(g.row_ptr, g.col, src, L, 8, sampler=oracle.OREJ_SAMPLER,
+                            weight=lambda w, ln, cur, prev, dst, e: int(Wq[e]), max_weight=100 * 65536, lib=lib),
+         orej, "weighted o-rej")
+
+
+def pin_custom_walk_update(lib=None):
+    """Update sees the moved query and ends the walk exactly at the first
+    vertex it accepts; the Weight law of O-REJ by chi-square (a weight of
+    both endpoints, 1 + 3 ((cur + 2 dst) mod 3) over MaxWeight 7, on the
+    directed graph)."""
+    g = small_rmat()
+    src = synth.vertex_sources(g.nv)
+    seen = []
+
+    def upd(w, ln, cur, prev, dst, e):
+        seen.append((ln, cur, dst))
+        return cur % 5 == 0
+
+    res = oracle.walk_custom(g.row_ptr, g.col, src, 30, 2, sampler=oracle.NAIVE_SAMPLER, update=upd, lib=lib)
+    assert res.status == 0 and all(cur == dst for _, cur, dst in seen)
+    for row, ln in zip(res.paths, res.lengths):
+        path = [int(x) for x in row[:ln]]
+        stops = [k for k in range(1, len(path)) if path[k] % 5 == 0]
+        if stops:
+            assert len(path) - 1 == stops[0]
+        else:
+            assert len(path) == 31 or not nbrs(g, path[-1])
+    gd = dir_graph()
+    res = oracle.walk_custom(gd.row_ptr, gd.col, [0], 2, 3, sampler=oracle.OREJ_SAMPLER,
+                             weight=lambda w, ln, cur, prev, dst, e: 1 + 3 * ((cur + 2 * dst) % 3), max_weight=7,
+                             walks_per_source=N_LAW, lib=lib)
+    assert res.status == 0
+
+    def law(path):
+        v = path[-1]
+        nb = nbrs(gd, v)
+        t = {c: 1 + 3 * ((v + 2 * c) % 3) for c in nb}
+        return {c: t[c] / sum(t.values()) for c in nb}
+
+    p = chi2_pvalue(path_counts(res), enumerate_paths(0, 2, law), N_LAW)
+    assert p > 1e-3, p
+
+
 ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
             pin_law_metapath, pin_ppr, pin_rejection_trials, pin_reductions, pin_invariants, pin_sharding, pin_rej_threshold, pin_its_first_move,
             pin_rej_first_move, pin_law_samplers, pin_rej_trials_closed_form, pin_zero_weights,
-            pin_law_node2vec_weighted, pin_node2vec_weighted_first_move, pin_node2vec_weighted_reductions]
+            pin_law_node2vec_weighted, pin_node2vec_weighted_first_move, pin_node2vec_weighted_reductions,
+            pin_custom_walk_reductions, pin_custom_walk_update]

@@ -52,6 +52,12 @@ MUTANTS = [
      "          P = g->pmax[s > 0 ? path[s - 1] : cur];\n          if (sec) sec_touch(sec, SEC_PMAX, (int64_t)cur * 4);"),
     ("weighted node2vec: weight test only after the source", "if (p->algo == ORC_NODE2VEC_WEIGHTED) {\n            const uint32_t Wx",
      "if (p->algo == ORC_NODE2VEC_WEIGHTED && s > 0) {\n            const uint32_t Wx"),
+    ("custom: update sees the query before the move", "if (update && update(user, (int64_t)w, s, cur, prev, dst, off + x)) break;",
+     "if (update && update(user, (int64_t)w, s - 1, prev, prev, dst, off + x)) break;"),
+    ("custom: o-rej dart on word 3", "if ((uint64_t)B[2] < orc_rej_threshold(W, max_weight)) { x = c; break; }",
+     "if ((uint64_t)B[3] < orc_rej_threshold(W, max_weight)) { x = c; break; }"),
+    ("custom: weight sees the previous vertex as cur", "const uint32_t W = weight(user, (int64_t)w, s, cur, prev, g->col[off + c], off + c);",
+     "const uint32_t W = weight(user, (int64_t)w, s, prev, prev, g->col[off + c], off + c);"),
     ("zero row: not a dead end for REJ", "if (pstar == 0) { if (st) st->stop_dead++; break; }",
      "if (pstar == 0) pstar = 1;"),
 ]
