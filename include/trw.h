@@ -154,6 +154,22 @@ trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_ptr, const 
 /* Release every device buffer of the graph.  NULL is ignored. */
 void trw_graph_free(trw_graph* g);
 
+/* The device arrays of a loaded graph, for user-defined walks
+ * (trw_custom.cuh): device pointers owned by the graph, valid until
+ * trw_graph_free; the caller must not write through them. */
+typedef struct {
+  const int32_t* row_ptr;       /* [nv + 1] int32 offsets */
+  const int32_t* col;           /* [ne] */
+  const float* weights;         /* [ne] or NULL */
+  const uint8_t* labels;        /* [ne] or NULL */
+  int64_t nv, ne;
+  int32_t sorted;               /* 1: every row strictly increasing */
+  int32_t device;               /* CUDA device of the arrays */
+} trw_graph_view;
+
+/* Fills *out.  Errors: TRW_ERR_INVALID (NULL argument). */
+trw_status trw_graph_get_view(const trw_graph* g, trw_graph_view* out);
+
 #define TRW_PREP_ALIAS 1u        /* build the ALIAS tables for TRW_DEEPWALK_WEIGHTED */
 #define TRW_PREP_LABEL_INDEX 2u  /* build the MetaPath label index (labelled graphs) */
 #define TRW_LABEL_INDEX_MAX_LABELS 30

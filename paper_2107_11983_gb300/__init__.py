@@ -110,6 +110,7 @@ _SIGS = {
     "trw_set_tuning": (ctypes.c_int, [_VP, _VP]),
     "trw_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int32, _VP]),
     "trw_last_stats": (ctypes.c_int, [_VP, _VP]),
+    "trw_graph_get_view": (ctypes.c_int, [_VP, _VP]),
     "trw_graph_nv": (ctypes.c_int64, [_VP]),
     "trw_graph_ne": (ctypes.c_int64, [_VP]),
     "trw_graph_device_bytes": (ctypes.c_int64, [_VP]),

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtrw.so")
-HEADERS = [os.path.join(ROOT, "include", "trw.h")]
+HEADERS = [os.path.join(ROOT, "include", "trw.h"), os.path.join(ROOT, "include", "trw_draws.cuh")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "--expt-relaxed-constexpr"] + ARCH

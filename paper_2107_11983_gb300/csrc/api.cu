@@ -256,6 +256,19 @@ extern "C" trw_status trw_graph_load(int64_t nv, int64_t ne, const int64_t* row_
 #undef LOAD_CUDA
 }
 
+extern "C" trw_status trw_graph_get_view(const trw_graph* g, trw_graph_view* out) {
+  if (!g || !out) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  out->row_ptr = g->row_ptr;
+  out->col = g->col;
+  out->weights = g->weights;
+  out->labels = g->labels;
+  out->nv = g->nv;
+  out->ne = g->ne;
+  out->sorted = g->sorted ? 1 : 0;
+  out->device = g->device;
+  return TRW_OK;
+}
+
 extern "C" int64_t trw_graph_nv(const trw_graph* g) { return g ? g->nv : -1; }
 extern "C" int64_t trw_graph_ne(const trw_graph* g) { return g ? g->ne : -1; }
 extern "C" int64_t trw_graph_device_bytes(const trw_graph* g) { return g ? g->device_bytes : -1; }

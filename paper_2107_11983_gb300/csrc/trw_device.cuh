@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/trw_draws.cuh"
+
 namespace trw {
 
 // Device algorithm ids: the public ones, the mixed-batch dispatcher, and
@@ -155,22 +157,12 @@ struct Ctrl {
   int pad;
 };
 
-// ------------------------------------------------------------- Philox4x32-10
-// Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy as 1, 2, 3"
-// (SC 2011): ten rounds of two 32x32->64 multiplies with a word swap and a
-// round key; the key advances by the Weyl constants after every round.
+// -------------------------------------------------------------------- draws
+// Philox4x32-10 and the uniform-integer rule, as every walk defines them
+// (include/trw_draws.cuh, shared with user-defined walks).
+
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return c;
+  return trw_draws::philox4x32_10(c, k0, k1);
 }
 
 // Draw `draw` of step `step` of walk `w`.
@@ -178,17 +170,8 @@ __device__ __forceinline__ uint4 draw_block(const WalkSpec& sp, uint32_t w, uint
   return philox10(make_uint4(w, step, draw, 0u), sp.key0, sp.key1);
 }
 
-// Uniform integer in [0, n): high 64 bits of r64 * n, r64 = (B.y:B.x).
-__device__ __forceinline__ uint32_t below(uint4 B, uint32_t n) {
-  const unsigned long long r64 = ((unsigned long long)B.y << 32) | B.x;
-  return (uint32_t)__umul64hi(r64, (unsigned long long)n);
-}
-
-// Uniform integer in [0, n) for a 64-bit n: high 64 bits of r64 * n.
-__device__ __forceinline__ unsigned long long below64(uint4 B, unsigned long long n) {
-  const unsigned long long r64 = ((unsigned long long)B.y << 32) | B.x;
-  return __umul64hi(r64, n);
-}
+using trw_draws::below;
+using trw_draws::below64;
 
 // Integer weight of a finite non-negative fp32 weight: round-half-even(w * 2^16),
 // clamped to 2^32 - 1.  w * 2^16 is exact in fp32 (a power-of-two scale), and
