@@ -102,12 +102,35 @@ def build_graph(wl):
     return g
 
 
+# Weighted DeepWalk's samplers (--sampler): the library's sampler id and the
+# table each prepares (its_guided: the guided ITS records).
+SAMPLER_IDS = {"alias": 0, "its": 1, "its_guided": 1, "rej": 2, "orej": 3}
+SAMPLER_PREP = {"its": 16, "its_guided": 64, "rej": 32}
+
+
 def walk_kwargs(wl):
     kw = {}
     for k in ("n2v_p", "n2v_q", "ppr_stop"):
         if k in wl:
             kw[k] = wl[k]
+    if wl.get("sampler", "alias") != "alias":
+        kw["sampler"] = SAMPLER_IDS[wl["sampler"]]
+        kw["max_weight"] = SWEEP_BOUND
     return kw
+
+
+def oracle_tables(g, wl):
+    """The oracle's own tables for the workload's sampler (none for ALIAS)."""
+    import oracle
+
+    name = wl.get("sampler", "alias")
+    if name in ("its", "its_guided"):
+        return {"its": oracle.prepare_its(g.row_ptr, g.weights)}
+    if name == "rej":
+        return {"pmax": oracle.prepare_rej(g.row_ptr, g.weights), "weights": g.weights}
+    if name == "orej":
+        return {"weights": g.weights}
+    return {}
 
 
 class ClockSampler:
@@ -235,7 +258,8 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
             "node2vec": oracle.NODE2VEC, "metapath": oracle.METAPATH}[wl["algo"]]
     alias = None
     t = time.time()
-    if algo == oracle.DEEPWALK_WEIGHTED:
+    tabs = oracle_tables(g, wl)
+    if algo == oracle.DEEPWALK_WEIGHTED and not tabs:
         alias = oracle.prepare_alias(g.row_ptr, g.weights)
     prep = time.time() - t
     src = synth.vertex_sources(g.nv)
@@ -247,7 +271,7 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
         m = min(n, src.shape[0] - pos)
         t = time.perf_counter()
         res = oracle.walk(g.row_ptr, g.col, algo, src[pos:pos + m], wl["max_len"], wl["seed"], alias=alias,
-                          labels=g.labels, walk_offset=pos, schema=wl.get("schema"), **walk_kwargs(wl))
+                          labels=g.labels, walk_offset=pos, schema=wl.get("schema"), **walk_kwargs(wl), **tabs)
         dt = time.perf_counter() - t
         assert res.status == 0
         done_moves += res.stats["moves"]
@@ -264,13 +288,14 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
     cores = host_cores()
     per = max(1, walks // 2)
     n_all = min(src.shape[0], per * cores)
-    mv_all, dt_all = oracle_parallel(g, algo, src, 0, n_all, wl["max_len"], wl["seed"], alias, walk_kwargs(wl), cores)
+    mv_all, dt_all = oracle_parallel(g, algo, src, 0, n_all, wl["max_len"], wl["seed"], alias,
+                                     dict(walk_kwargs(wl), **tabs), cores)
     all_cores = {"value": mv_all / dt_all, "unit": UNIT, "cores": cores, "kind": "oracle",
                  "sample": f"first {n_all} walks ({mv_all} moves) in {cores} contiguous ranges on {cores} threads, "
                            f"{dt_all:.1f}s"}
     return {"value": done_moves / done_s, "unit": UNIT, "cores": 1, "kind": "oracle", "all_cores": all_cores,
             "sample": f"first {walks} of {src.shape[0]} walks ({done_moves} moves) of the workload, "
-                      f"single-threaded oracle, {done_s:.1f}s walking after {prep:.1f}s of alias preparation",
+                      f"single-threaded oracle, {done_s:.1f}s walking after {prep:.1f}s of table preparation",
             "model_bytes_per_move": (32.0 * sectors + out_bytes) / max(1, done_moves),
             # Node2Vec with the neighbour hash: the row pair of cur, one col sector per
             # attempt, one bucket sector per IsNeighbor that decides an attempt
@@ -325,9 +350,13 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False
     against the measured HBM copy bandwidth; plus the fraction of the
     random-gather ceiling."""
     peak, peak_kind = measured_peak_hbm()
-    bpm = BYTES_PER_MOVE.get(wl["algo"])
+    sampler = wl.get("sampler", "alias")
+    bpm = BYTES_PER_MOVE.get(wl["algo"]) if sampler == "alias" else None
     source = "closed form (32-byte sectors of the device layout)"
     per_walk = BYTES_PER_WALK.get(wl["algo"], BYTES_PER_WALK_BASE)
+    if sampler == "its_guided":
+        bpm = 2 * SECTOR + 4
+        source = "closed form, lower bound: the draw cell's 32-byte record, the answer's record, the path entry"
     if records and wl["algo"] in ("deepwalk", "ppr"):
         # one 16-byte row record (one sector) per move; the source's row pair once per walk
         bpm = SECTOR + 4
@@ -783,7 +812,9 @@ def run_ours(args, wl):
     if algo == trw.DEEPWALK_WEIGHTED:
         torch.cuda.synchronize()
         t = time.time()
-        G.prepare()
+        G.prepare(SAMPLER_PREP.get(wl.get("sampler", "alias"), trw.PREP_ALIAS))
+        if wl.get("sampler", "alias") != "alias":
+            G.prepare(trw.PREP_ALIAS)  # the serving and per-algorithm extras walk ALIAS
         prep_ms = 1000 * (time.time() - t)
     tables = tables_of(wl, args)
     tables_ms = None
@@ -952,7 +983,9 @@ def run_ours(args, wl):
                    "parallelism": f"walk shards x{ws}, graph replicated",
                    "l2": "256 MiB buffer written between timed steps (outside the events)",
                    "tuning": G.tuning(),
-                   "prepared_tables": table_names(tables) + (["alias"] if algo == trw.DEEPWALK_WEIGHTED else [])},
+                   "sampler": wl.get("sampler", "alias") if algo == trw.DEEPWALK_WEIGHTED else None,
+                   "prepared_tables": table_names(tables) + (["alias"] if algo == trw.DEEPWALK_WEIGHTED else []) +
+                   ([wl["sampler"]] if wl.get("sampler", "alias") not in ("alias", "orej") else [])},
         "kernel_ms_per_step": round(kms, 4),
         "wall_s": round(wall, 3),
         "plain_launch": {"value": round(plain_value, 1), "unit": UNIT, "ms": round(statistics.median(plain_ms), 4),
@@ -1240,6 +1273,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-algorithm lines and the gather ceiling")
     ap.add_argument("--scale", type=int, default=0, help="override the R-MAT scale (smaller profiling cases)")
+    ap.add_argument("--sampler", default="alias", choices=sorted(SAMPLER_IDS),
+                    help="weighted DeepWalk's sampler for the timed walk (c2; Section 2.3)")
     ap.add_argument("--paper-paths", action="store_true",
                     help="no optional device tables: MetaPath label scans, Node2Vec binary searches, NAIVE moves "
                          "through the row offsets (the paper's method as written; walks are identical)")
@@ -1251,6 +1286,11 @@ def main():
         log("warm-up raised to 3 steps")
         args.warmup = 3
     wl = dict(WORKLOADS[args.config])
+    if args.sampler != "alias":
+        if wl.get("algo") != "deepwalk_weighted" or wl.get("kind"):
+            ap.error("--sampler applies to the weighted DeepWalk workload")
+        wl["sampler"] = args.sampler
+        wl["name"] = wl["name"].replace("-alias-", f"-{args.sampler.replace('_', '-')}-")
     if args.scale:
         wl["name"] = wl["name"].rsplit("-s", 1)[0] + f"-s{args.scale}"
         wl["scale"] = args.scale

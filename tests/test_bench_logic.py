@@ -91,3 +91,17 @@ def test_oracle_deciding_checks():
     # dart falls in [2^30, 2^31), a quarter of the non-return attempts after the first step
     frac = st["checks"] / (st["attempts"] - len(src))
     assert 0.15 < frac < 0.26
+
+
+def test_sampler_workloads(bench):
+    import paper_2107_11983_gb300 as trw
+    wl = dict(bench.WORKLOADS["c2"], sampler="its_guided")
+    kw = bench.walk_kwargs(wl)
+    assert kw == {"sampler": trw.SAMPLER_ITS, "max_weight": bench.SWEEP_BOUND}
+    assert bench.SAMPLER_PREP == {"its": trw.PREP_ITS, "its_guided": trw.PREP_ITS_GUIDE, "rej": trw.PREP_REJ}
+    r = bench.roofline(wl, 1000, 10, 1.0, None, None, 1.0)
+    assert r["bytes_per_move"] == 68  # the cell's record, the answer's record, the path entry
+    assert bench.roofline(dict(wl, sampler="rej"), 1000, 10, 1.0, None, None, 1.0) is None  # needs the oracle model
+    cpu = {"model_bytes_per_move": 100.0}
+    assert bench.roofline(dict(wl, sampler="rej"), 1000, 10, 1.0, cpu, None, 1.0)["bytes_per_move"] == 100.0
+    assert bench.walk_kwargs(bench.WORKLOADS["c2"]) == {}
