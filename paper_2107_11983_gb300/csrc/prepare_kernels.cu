@@ -556,23 +556,22 @@ __global__ void sampler_tables_kernel(int32_t nv, const int32_t* __restrict__ ro
   }
 }
 
-// Every id in [0, nv); flags a row that is not strictly increasing.
+// Every id in [0, nv); flags a row that is not strictly increasing.  One warp
+// per row, so that a hub row does not hold a single thread for its length.
 __global__ void check_graph_kernel(int32_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                    Ctrl* ctrl, int* unsorted) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {
     const int32_t lo = row_ptr[v], hi = row_ptr[v + 1];
-    int32_t last = -1;
-    bool bad_order = false;
-    for (int32_t e = lo; e < hi; ++e) {
+    bool bad_id = false, bad_order = false;
+    for (int32_t e = lo + lane; e < hi; e += 32) {
       const int32_t c = col[e];
-      if (c < 0 || c >= nv) {
-        atomicCAS(&ctrl->err, 0, kErrInvalid);
-        break;
-      }
-      if (c <= last) bad_order = true;
-      last = c;
+      bad_id |= c < 0 || c >= nv;
+      if (e > lo) bad_order |= col[e - 1] >= c;
     }
-    if (bad_order) atomicExch(unsorted, 1);
+    if (__any_sync(0xffffffffu, bad_id) && lane == 0) atomicCAS(&ctrl->err, 0, kErrInvalid);
+    if (__any_sync(0xffffffffu, bad_order) && lane == 0) atomicExch(unsorted, 1);
   }
 }
 
@@ -798,7 +797,7 @@ cudaError_t launch_sampler_tables(int32_t nv, const int32_t* row_ptr, const floa
 cudaError_t launch_check_graph(int32_t nv, const int32_t* row_ptr, const int32_t* col, Ctrl* ctrl, int* d_unsorted,
                                cudaStream_t st) {
   if (nv <= 0) return cudaSuccess;
-  int64_t blocks = ((int64_t)nv + 255) / 256;
+  int64_t blocks = ((int64_t)nv * 32 + 255) / 256;
   if (blocks > 65535) blocks = 65535;
   check_graph_kernel<<<(unsigned)blocks, 256, 0, st>>>(nv, row_ptr, col, ctrl, d_unsorted);
   return cudaGetLastError();

@@ -119,6 +119,7 @@ extern "C" trw_status trw_walk_stream(trw_graph* g, trw_algo algo, const trw_par
   Ctrl* kc[2] = {g->ctrl, g->ctrl2};
   const int64_t nslices = (n_sources + src_per - 1) / src_per;
   int64_t moves = 0;
+  trw_kernel kernel = TRW_KERNEL_PERSISTENT;  // of the last slice
   CUDA_TRY(cudaEventRecord(g->ev0, stream), "event");
   for (int64_t i = 0; i <= nslices; ++i) {
     if (i < nslices) {
@@ -133,10 +134,13 @@ extern "C" trw_status trw_walk_stream(trw_graph* g, trw_algo algo, const trw_par
       // device buffer b is free once slice i - 2 was copied out
       if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(stream, g->ev_copied[b], 0), "wait for a drained buffer");
       CUDA_TRY(cudaMemsetAsync(kc[b], 0, sizeof(Ctrl), stream), "reset ctrl");
-      if (!coop && sl.nwalks <= (int64_t)cfg.grid_blocks * cfg.block_threads)
+      if (!coop && sl.nwalks <= (int64_t)cfg.grid_blocks * cfg.block_threads) {
         CUDA_TRY(launch_walk_plain(dg, sl, kc[b], stream, 256), "plain walk launch");
-      else
+        kernel = TRW_KERNEL_PLAIN;
+      } else {
         CUDA_TRY(launch_walk_persistent(dg, sl, kc[b], stream, cfg), "persistent walk launch");
+        kernel = TRW_KERNEL_PERSISTENT;
+      }
       CUDA_TRY(cudaEventRecord(g->ev_walked[b], stream), "event");
       // host buffer b is free: slice i - 2 was consumed in the previous iteration
       CUDA_TRY(cudaStreamWaitEvent(cs, g->ev_walked[b], 0), "wait for a walked slice");
@@ -181,7 +185,7 @@ extern "C" trw_status trw_walk_stream(trw_graph* g, trw_algo algo, const trw_par
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) g->last.kernel_ms = ms;
   g->last.moves = moves;
-  g->last.kernel = TRW_KERNEL_AUTO;
+  g->last.kernel = kernel;
   g->last.launches = (int32_t)std::min<int64_t>(nslices, INT32_MAX);
   g->last.grid_blocks = cfg.grid_blocks;
   g->last.block_threads = cfg.block_threads;
