@@ -82,6 +82,19 @@ def test_stream_endpoints_and_files(graph, tmp_path):
     assert np.array_equal(np.fromfile(pf, dtype=np.int32), ends.paths)
 
 
+def test_stream_tiny_slices(graph):
+    # slice_walks below walks_per_source: one source per slice
+    g, G = graph
+    src = synth.sources(40, g.nv, seed=12)
+    algo, L, kw = CASES["node2vec"]
+    want = oracle_of(g, algo, src, L, 4, kw, walks_per_source=5)
+    firsts, got_l = [], []
+    G.walk_stream(algo, src, L, 4, lambda f, p, ln: (firsts.append(f), got_l.append(ln.copy())) and None,
+                  slice_walks=2, walks_per_source=5, **kw)
+    assert firsts == list(range(0, 200, 5))
+    assert np.array_equal(np.concatenate(got_l), want.lengths)
+
+
 def test_stream_stop_errors_and_exceptions(graph, tmp_path):
     g, G = graph
     src = synth.sources(4000, g.nv, seed=6)
