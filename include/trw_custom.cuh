@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) custom_walk(Graph g, typename W::Params p
 // Runs n_sources * walks_per_source walks of type W (walk i starts at
 // sources[i / walks_per_source]) into device buffers paths [nwalks *
 // (max_len + 1)] and lengths [nwalks], on stream (NULL: the legacy default
-// stream), and waits.  *moves (may be NULL) receives the moves made.
+// stream) of the current device, which must be the graph's, and waits.  *moves (may be NULL) receives the moves made.
 // Errors: TRW_ERR_INVALID (arguments, a source outside [0, nv): the outputs
 // are then unspecified), TRW_ERR_REJECT_CAP, TRW_ERR_OOM, TRW_ERR_CUDA.
 template <class W>
@@ -210,6 +210,8 @@ trw_status walk(const trw_graph* graph, const typename W::Params& prm, const int
   trw_status st = trw_graph_get_view(graph, &v);
   if (st != TRW_OK) return st;
   if (n_sources < 0 || walks_per_source < 1 || max_len < 0) return TRW_ERR_INVALID;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != v.device) return TRW_ERR_INVALID;  // not the graph's device
   const int64_t nwalks = n_sources * (int64_t)walks_per_source;
   if ((int64_t)walk_offset + nwalks > 4294967296LL) return TRW_ERR_INVALID;
   if (moves) *moves = 0;
