@@ -199,8 +199,9 @@ __global__ void __launch_bounds__(256) custom_walk(Graph g, typename W::Params p
 // Runs n_sources * walks_per_source walks of type W (walk i starts at
 // sources[i / walks_per_source]) into device buffers paths [nwalks *
 // (max_len + 1)] and lengths [nwalks], on stream (NULL: the legacy default
-// stream) of the current device, which must be the graph's, and waits.  *moves (may be NULL) receives the moves made.
-// Errors: TRW_ERR_INVALID (arguments, a source outside [0, nv): the outputs
+// stream) of the current device, which must be the graph's, and waits.
+// *moves (may be NULL) receives the moves made.  Errors: TRW_ERR_INVALID
+// (arguments, another current device, a source outside [0, nv): the outputs
 // are then unspecified), TRW_ERR_REJECT_CAP, TRW_ERR_OOM, TRW_ERR_CUDA.
 template <class W>
 trw_status walk(const trw_graph* graph, const typename W::Params& prm, const int32_t* sources, int64_t n_sources,
