@@ -39,6 +39,7 @@ namespace {
 
 constexpr uint32_t kQueueCap = 1u << 16;
 constexpr int kMaxActive = 64;        // requests the dispatcher interleaves
+constexpr int kPollSkip = 3;          // iterations a walking warp waits after an empty queue poll
 
 struct Chunk {
   unsigned long long k;   // request number
@@ -405,6 +406,10 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
   int ent = 0;                        // this lane's slot
   unsigned long long my_k = ~0ull;    // this lane's request
   unsigned long long moves_acc = 0;
+  // After an empty poll of the queue while some lanes still walk, the warp
+  // skips its next polls for a few iterations: a poll is a round trip to L2
+  // that would otherwise precede every step of the warp's remaining walks.
+  int poll_wait = 0;
 
   for (;;) {
     unsigned idle = __ballot_sync(0xffffffffu, !active);
@@ -420,6 +425,10 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
     while (idle != 0u) {
       if (wlo >= whi) {
         if (!pend) {
+          if (poll_wait > 0 && idle != 0xffffffffu) {
+            --poll_wait;
+            break;
+          }
           unsigned long long ck = 0;
           uint32_t cb = 0, ce = 0;
           int got = 0;
@@ -448,7 +457,10 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
             }
           }
           got = __shfl_sync(0xffffffffu, got, 0);
-          if (!got) break;
+          if (!got) {
+            poll_wait = idle != 0xffffffffu ? kPollSkip : 0;
+            break;
+          }
           ck = __shfl_sync(0xffffffffu, ck, 0);
           cb = __shfl_sync(0xffffffffu, cb, 0);
           ce = __shfl_sync(0xffffffffu, ce, 0);
