@@ -29,6 +29,12 @@ def _requests(g):
         dict(algo=trw.DEEPWALK_WEIGHTED, sources=synth.sources(777, g.nv, seed=5), max_len=40, seed=23),
         dict(algo=trw.NODE2VEC, sources=synth.sources(555, g.nv, seed=6), max_len=30, seed=24, n2v_p=0.5, n2v_q=2.0),
         dict(algo=trw.DEEPWALK, sources=synth.sources(3, g.nv, seed=7), max_len=80, seed=25, walks_per_source=100),
+        dict(algo=trw.DEEPWALK_WEIGHTED, sources=synth.sources(900, g.nv, seed=8), max_len=30, seed=26,
+             sampler=trw.SAMPLER_ITS),
+        dict(algo=trw.DEEPWALK_WEIGHTED, sources=synth.sources(900, g.nv, seed=9), max_len=30, seed=27,
+             sampler=trw.SAMPLER_OREJ, max_weight=100.0),
+        dict(algo=trw.NODE2VEC_WEIGHTED, sources=synth.sources(600, g.nv, seed=10), max_len=30, seed=28, n2v_p=0.5,
+             n2v_q=2.0, max_weight=100.0),
     ]
 
 
@@ -49,7 +55,7 @@ def _call_noalloc(G, reqs):
         wps = r.get("walks_per_source", 1)
         ep = r.get("endpoints", False)
         p, k = trw._params(r["algo"], r.get("ppr_stop", 0.2), r.get("n2v_p", 1.0), r.get("n2v_q", 1.0),
-                           r.get("schema"), wps, ep, 0)
+                           r.get("schema"), wps, ep, 0, r.get("sampler", trw.SAMPLER_DEFAULT), r.get("max_weight", 0.0))
         src = torch.from_numpy(np.ascontiguousarray(r["sources"], np.int32)).cuda()
         cnt = src.shape[0] * wps
         op = torch.full((cnt,) if ep else (cnt, r["max_len"] + 1), -1, dtype=torch.int32, device="cuda")
@@ -79,7 +85,7 @@ def _same(a_paths, a_lens, b_paths, b_lens):
 def test_noalloc_batch_matches_batch_twice():
     g = rmat_graph(12)
     G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
-    G.prepare()
+    G.prepare(trw.PREP_ALIAS | trw.PREP_ITS)
     reqs = _requests(g)
     want = G.walk_batch(reqs)
     torch.cuda.synchronize()
