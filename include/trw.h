@@ -508,7 +508,8 @@ trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg, trw_serve
  * Submit a request (same meaning as trw_walk; out_paths and out_lengths must be
  * DEVICE buffers that stay valid until poll returns TRW_OK or an error, and
  * that no other stream still writes when submit is called: the server runs
- * on its own streams and does not order itself after the caller's).
+ * on its own streams and orders itself after the caller's only through
+ * trw_serve_order_after).
  * sources may be host or device; every source is checked at submit
  * (TRW_ERR_INVALID for one outside [0, nv): nothing queued or written).  Host
  * sources are copied into the server's pool before submit returns; device
@@ -520,6 +521,16 @@ trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg, trw_serve
 trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* params, const int32_t* sources,
                             int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
                             int32_t* out_lengths, uint64_t* req_id);
+
+/*
+ * Orders the server after a caller's stream without blocking the host: the
+ * requests submitted after this call become visible to the device (and
+ * their device sources are read for the range check) only once the work
+ * queued on stream before this call has finished -- e.g. the allocation or
+ * fill of a request's buffers.  stream is a cudaStream_t ((void*)1 names the
+ * legacy default stream).  Errors: TRW_ERR_INVALID (NULL), TRW_ERR_CUDA.
+ */
+trw_status trw_serve_order_after(trw_server* s, void* stream);
 
 /* TRW_OK when request req_id has finished (its slot is released), TRW_PENDING
  * while it runs, TRW_ERR_NOT_FOUND for an unknown or already collected id,

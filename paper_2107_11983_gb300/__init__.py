@@ -124,6 +124,7 @@ _SIGS = {
     "trw_serve_create": (ctypes.c_int, [_VP, _VP, _VP]),
     "trw_serve_submit": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32,
                                         ctypes.c_uint64, _VP, _VP, _VP]),
+    "trw_serve_order_after": (ctypes.c_int, [_VP, _VP]),
     "trw_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "trw_serve_reap": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
     "trw_serve_trace": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP]),
@@ -603,8 +604,10 @@ class Server:
         src = sources if _is_torch(sources) else np.ascontiguousarray(sources, dtype=np.int32)
         if any(_is_cuda(x) for x in (src, out_paths, out_lengths)):
             # the server runs on its own streams: work queued on the caller's
-            # stream for these buffers (allocation, fills) must finish first
-            _torch().cuda.current_stream().synchronize()
+            # stream for these buffers (allocation, fills) must finish before
+            # the request becomes visible -- ordered on the device, not waited for
+            _check(lib.trw_serve_order_after(self._h, _torch().cuda.current_stream().cuda_stream or 1),
+                   "trw_serve_order_after")
         rid = ctypes.c_uint64(0)
         st = lib.trw_serve_submit(self._h, algo, ctypes.byref(p), _ptr(src), int(src.shape[0]), max_len,
                                   seed & ((1 << 64) - 1), _ptr(out_paths), _ptr(out_lengths), ctypes.byref(rid))

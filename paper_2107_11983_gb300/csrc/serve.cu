@@ -653,6 +653,7 @@ struct trw_server {
   int R = 0;
   cudaStream_t stream = nullptr;       // the resident kernel
   cudaStream_t copy_stream = nullptr;  // descriptor uploads
+  cudaEvent_t ev_after = nullptr;      // trw_serve_order_after: the caller's stream, recorded
   ServeState* state = nullptr;
   Chunk* queue = nullptr;
   SlotRec* slots = nullptr;
@@ -695,6 +696,7 @@ static void server_release(trw_server* s) {
   if (!s) return;
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  if (s->ev_after) cudaEventDestroy(s->ev_after);
   cudaFree(s->state);
   cudaFree(s->queue);
   cudaFree(s->slots);
@@ -736,6 +738,7 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   const int R = s->R;
   SV_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking), "stream");
   SV_TRY(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "stream");
+  SV_TRY(cudaEventCreateWithFlags(&s->ev_after, cudaEventDisableTiming), "event");
   SV_TRY(cudaMalloc(&s->state, sizeof(ServeState)), "serve state");
   SV_TRY(cudaMemset(s->state, 0, sizeof(ServeState)), "serve state");
   SV_TRY(cudaMalloc(&s->queue, sizeof(Chunk) * kQueueCap), "chunk queue");
@@ -820,6 +823,15 @@ static cudaError_t launch_if_idle(trw_server* s) {
 // Collect finished requests at the front of the ring (frees their slots and source ranges).
 static void retire_front(trw_server* s) {
   while (s->oldest < s->next_k && s->collected[s->oldest % s->R]) ++s->oldest;
+}
+
+extern "C" trw_status trw_serve_order_after(trw_server* s, void* stream) {
+  if (!s || !stream) return trw_fail(TRW_ERR_INVALID, "NULL server or stream");
+  std::lock_guard<std::mutex> lk(s->mu);
+  cudaError_t e = cudaEventRecord(s->ev_after, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, s->ev_after, 0);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "serve order after");
+  return TRW_OK;
 }
 
 extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* params, const int32_t* sources,
