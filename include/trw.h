@@ -297,7 +297,8 @@ trw_status trw_sync(trw_graph* g, void* stream);
  *                padded as in trw_walk) or int32[n_walks] (TRW_OUT_ENDPOINTS);
  *       lengths  host, int32[n_walks];
  *       both valid only during the call.  Walk first_walk + k of the batch is
- *       row k.  Return 0 to continue, anything else to stop.
+ *       row k.  Return 0 to continue, anything else to stop.  fn runs with
+ *       the graph locked: it must not call the library on the same graph.
  *   slice_walks  walks per slice (rounded down to whole sources, at least one
  *                source).
  * Every slice is checked before fn sees it.  Synchronous; the other arguments

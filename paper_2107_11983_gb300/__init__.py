@@ -336,7 +336,8 @@ class Graph:
         """trw_walk_stream: consumer(first_walk, paths, lengths) receives each slice
         as numpy views of pinned host memory, valid during the call only (paths
         [n, max_len + 1], or [n] with endpoints); a true return value stops the
-        stream (TRWError ERR_STOPPED).  Returns the moves of the batch."""
+        stream (TRWError ERR_STOPPED).  The consumer must not walk this graph
+        (the graph is locked while it runs).  Returns the moves of the batch."""
         lib = load_library()
         algo = ALGOS.get(algo, algo) if isinstance(algo, str) else algo
         p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset, sampler,
