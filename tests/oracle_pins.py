@@ -430,19 +430,28 @@ def pin_invariants(lib=None):
 
 def pin_sharding(lib=None):
     """A walk depends only on (seed, walk index): splitting the batch with
-    walk_offset reproduces the whole batch."""
+    walk_offset reproduces the whole batch (Node2Vec, weighted Node2Vec and
+    weighted DeepWalk under ITS, REJ and O-REJ)."""
     g = small_rmat()
     src = synth.vertex_sources(g.nv)
-    full = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src, 12, seed=9, n2v_p=0.5, n2v_q=2.0, lib=lib)
-    a = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src[:300], 12, seed=9, n2v_p=0.5, n2v_q=2.0, lib=lib)
-    b = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src[300:], 12, seed=9, n2v_p=0.5, n2v_q=2.0,
-                    walk_offset=300, lib=lib)
-    assert np.array_equal(np.concatenate([a.lengths, b.lengths]), full.lengths)
-    for i in range(g.nv):
-        part = a if i < 300 else b
-        j = i if i < 300 else i - 300
-        ln = full.lengths[i]
-        assert np.array_equal(part.paths[j, :ln], full.paths[i, :ln])
+    tabs = {"weights": g.weights, "its": oracle.prepare_its(g.row_ptr, g.weights, lib=lib),
+            "pmax": oracle.prepare_rej(g.row_ptr, g.weights, lib=lib)}
+    cases = [(oracle.NODE2VEC, {"n2v_p": 0.5, "n2v_q": 2.0}),
+             (oracle.NODE2VEC_WEIGHTED, dict(tabs, n2v_p=2.0, n2v_q=0.5)),
+             (oracle.DEEPWALK_WEIGHTED, dict(tabs, sampler=oracle.SAMPLER_ITS)),
+             (oracle.DEEPWALK_WEIGHTED, dict(tabs, sampler=oracle.SAMPLER_REJ)),
+             (oracle.DEEPWALK_WEIGHTED, dict(tabs, sampler=oracle.SAMPLER_OREJ, max_weight=100.0))]
+    for algo, kw in cases:
+        full = oracle.walk(g.row_ptr, g.col, algo, src, 12, seed=9, lib=lib, **kw)
+        a = oracle.walk(g.row_ptr, g.col, algo, src[:300], 12, seed=9, lib=lib, **kw)
+        b = oracle.walk(g.row_ptr, g.col, algo, src[300:], 12, seed=9, walk_offset=300, lib=lib, **kw)
+        assert full.status == a.status == b.status == 0
+        assert np.array_equal(np.concatenate([a.lengths, b.lengths]), full.lengths), algo
+        for i in range(g.nv):
+            part = a if i < 300 else b
+            j = i if i < 300 else i - 300
+            ln = full.lengths[i]
+            assert np.array_equal(part.paths[j, :ln], full.paths[i, :ln]), (algo, i)
 
 
 # ------------------------------------------- ITS, REJ and O-REJ (Section 2.3)
