@@ -666,7 +666,11 @@ static trw_status walk_sliced(trw_graph* g, WalkSpec sp, trw_kernel kernel, cons
                               int64_t row, int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream) {
   const int64_t wps = (int64_t)sp.wps;
   const int64_t nwalks = sp.nwalks;
-  int64_t nslices = nwalks / kSliceWalks;
+  // Slices of 2^18 walks, 2 to 16 of them: more slices shorten the copy-out
+  // tail that no walk overlaps (weighted DeepWalk s22: 8 -> 16 slices,
+  // 9.24 -> 8.85 ms), but past 16 the slices' own walk tails cost more
+  // (Node2Vec s24: 32 slices, 82 -> 87 ms).
+  int64_t nslices = nwalks / (kSliceWalks / 2);
   if (nslices < 2) nslices = 2;
   if (nslices > 16) nslices = 16;
   const int64_t src_per = (n_sources + nslices - 1) / nslices;
