@@ -921,6 +921,23 @@ def run_ours(args, wl):
     e2e_value = moves * ws / e2e_s
     assert int((h_len.to(torch.int64) - 1).sum().item()) == moves
 
+    # the same end to end with compact output (TRW_OUT_COMPACT): the walks'
+    # vertices one after the other, no padding crosses the host link
+    h_flat = h_paths.view(-1).numpy()
+    G.walk(algo, h_src.numpy(), L, wl["seed"], out_paths=h_flat, out_lengths=h_len.numpy(), walk_offset=walk_offset,
+           compact=True, **kw)
+    cmp_t = []
+    for i in range(max(3, min(args.steps, 5))):
+        t = time.perf_counter()
+        G.walk(algo, h_src.numpy(), L, wl["seed"], out_paths=h_flat, out_lengths=h_len.numpy(),
+               walk_offset=walk_offset, compact=True, **kw)
+        cmp_t.append(time.perf_counter() - t)
+    cmp_s = statistics.median(cmp_t)
+    assert int((h_len.to(torch.int64) - 1).sum().item()) == moves
+    e2e_compact = {"value": round(moves / cmp_s, 1), "unit": UNIT, "h2d_bytes_per_step": int(n * 4),
+                   "d2h_bytes_per_step": int((moves + n) * 4 + n * 4), "ms": round(1000 * cmp_s, 3),
+                   "what": "trw_walk with TRW_OUT_COMPACT: host sources in, the walks' vertices out without padding"}
+
     kms = statistics.mean(kern_ms)
 
     # streaming output: the same batch in slices of 2^20 walks handed to a
@@ -1001,6 +1018,7 @@ def run_ours(args, wl):
                        "autotune_s": round(tune_s, 2)},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(n * 4),
                 "d2h_bytes_per_step": int(n * (L + 1) * 4 + n * 4), "ms": round(1000 * e2e_s, 3)},
+        "e2e_compact": e2e_compact,
         "gpu_launches": 2 * args.steps,
         "plan_replay": replay,
         "roofline": roof,

@@ -86,6 +86,10 @@ typedef enum {
 
 #define TRW_OUT_PATHS 0u        /* out_paths[i * (max_len + 1) + k] = Q[k] */
 #define TRW_OUT_ENDPOINTS 1u    /* out_paths[i] = the last vertex of walk i */
+#define TRW_OUT_COMPACT 2u      /* trw_walk / trw_walk_ex only: the vertices of walk 0, then of walk 1, ...
+                                   with no padding (out_paths[o_i + k] = Q_i[k], o_i the sum of the
+                                   lengths of walks 0 .. i-1); out_paths needs room for the sum of the
+                                   lengths, at most nwalks * (max_len + 1) */
 
 /* Sampling method of TRW_DEEPWALK_WEIGHTED (Section 2.3); the other
  * algorithms take TRW_SAMPLER_DEFAULT.  All four draw from the same law

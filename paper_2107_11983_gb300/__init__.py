@@ -22,7 +22,7 @@ __all__ = ["TRWError", "Graph", "Server", "load_library", "build", "DEEPWALK", "
 
 DEEPWALK, DEEPWALK_WEIGHTED, PPR, NODE2VEC, METAPATH, NODE2VEC_WEIGHTED = 0, 1, 2, 3, 4, 5
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_PERSISTENT, KERNEL_BSP = 0, 1, 2, 3
-OUT_PATHS, OUT_ENDPOINTS = 0, 1
+OUT_PATHS, OUT_ENDPOINTS, OUT_COMPACT = 0, 1, 2
 PREP_ALIAS = 1
 PREP_LABEL_INDEX = 2
 LABEL_INDEX_MAX_LABELS = 30
@@ -301,14 +301,19 @@ class Graph:
     def walk(self, algo: int, sources, max_len: int, seed: int, *, ppr_stop: float = 0.2, n2v_p: float = 1.0,
              n2v_q: float = 1.0, schema=None, walks_per_source: int = 1, endpoints: bool = False,
              walk_offset: int = 0, kernel: int = KERNEL_AUTO, out_paths=None, out_lengths=None, stream=None,
-             sync: bool = True, sampler: int = SAMPLER_DEFAULT, max_weight: float = 0.0) -> WalkOutput:
+             sync: bool = True, sampler: int = SAMPLER_DEFAULT, max_weight: float = 0.0,
+             compact: bool = False) -> WalkOutput:
         """trw_walk_ex.  Outputs follow the sources: numpy for host sources, CUDA
         tensors for CUDA sources, unless out_paths / out_lengths are given.
-        sampler / max_weight choose weighted DeepWalk's sampling method."""
+        sampler / max_weight choose weighted DeepWalk's sampling method.
+        compact: TRW_OUT_COMPACT, paths is the walks' vertices one after the
+        other (trimmed to the sum of the lengths when the call allocates it)."""
         lib = load_library()
         algo = ALGOS.get(algo, algo) if isinstance(algo, str) else algo
         p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset, sampler,
                           max_weight)
+        if compact:
+            p.out_mode = OUT_COMPACT
         if _is_torch(sources):
             src = sources if sources.dtype == _torch().int32 else sources.to(_torch().int32)
             src = src.contiguous()
@@ -316,7 +321,8 @@ class Graph:
             src = np.ascontiguousarray(sources, dtype=np.int32)
         n = int(src.shape[0])
         nwalks = n * walks_per_source
-        shape = (nwalks,) if endpoints else (nwalks, max_len + 1)
+        shape = (nwalks,) if endpoints else ((nwalks * (max_len + 1),) if compact else (nwalks, max_len + 1))
+        trim = compact and out_paths is None
         if out_paths is None:
             out_paths = (_torch().empty(shape, dtype=_torch().int32, device=src.device) if _is_cuda(src)
                          else np.empty(shape, dtype=np.int32))
@@ -327,6 +333,9 @@ class Graph:
                              _ptr(out_paths), _ptr(out_lengths), kernel, _stream_arg(stream, src, out_paths, out_lengths),
                              1 if sync else 0)
         _check(st, "trw_walk")
+        if trim and sync:
+            total = int(out_lengths.sum().item()) if _is_torch(out_lengths) else int(out_lengths.sum())
+            out_paths = out_paths[:total]
         return WalkOutput(out_paths, out_lengths)
 
     def walk_stream(self, algo: int, sources, max_len: int, seed: int, consumer, *, slice_walks: int = 1 << 20,

@@ -112,6 +112,9 @@ static void graph_release(trw_graph* g) {
   cudaFree(g->bsp_walkers[1]);
   if (g->bsp_host) cudaFreeHost(g->bsp_host);
   trw_free_stream_buffers(g);
+  cudaFree(g->cmp_stage);
+  cudaFree(g->cmp_scratch);
+  if (g->cmp_host) cudaFreeHost(g->cmp_host);
   cudaFree(g->ctrl);
   cudaFree(g->src_stage);
   cudaFree(g->out_stage);
@@ -491,7 +494,7 @@ extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
 // --------------------------------------------------------------------- walk
 
 trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pin, int64_t n_sources,
-                         int32_t max_len, uint64_t seed, WalkSpec* sp) {
+                         int32_t max_len, uint64_t seed, WalkSpec* sp, bool allow_compact) {
   trw_params p;
   if (pin) p = *pin;
   else trw_params_default(&p);
@@ -501,7 +504,9 @@ trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* pi
   if (max_len < 0) return trw_fail(TRW_ERR_INVALID, "max_len < 0");
   if (n_sources < 0) return trw_fail(TRW_ERR_INVALID, "n_sources < 0");
   if (p.walks_per_source < 1) return trw_fail(TRW_ERR_INVALID, "walks_per_source < 1");
-  if (p.out_mode != TRW_OUT_PATHS && p.out_mode != TRW_OUT_ENDPOINTS) return trw_fail(TRW_ERR_INVALID, "bad out_mode");
+  if (p.out_mode != TRW_OUT_PATHS && p.out_mode != TRW_OUT_ENDPOINTS && !(allow_compact && p.out_mode == TRW_OUT_COMPACT))
+    return trw_fail(TRW_ERR_INVALID, p.out_mode == TRW_OUT_COMPACT ? "compact output is for trw_walk and trw_walk_ex only"
+                                                                  : "bad out_mode");
   if (p.walk_offset < 0) return trw_fail(TRW_ERR_INVALID, "walk_offset < 0");
   const int64_t nwalks = n_sources * (int64_t)p.walks_per_source;
   if (n_sources > 0 && nwalks / n_sources != p.walks_per_source) return trw_fail(TRW_ERR_INVALID, "walk count overflows");
@@ -783,8 +788,11 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
     return trw_fail(TRW_ERR_INVALID, "unknown kernel %d", (int)kernel);
   if (kernel == TRW_KERNEL_BSP && !sync)
     return trw_fail(TRW_ERR_INVALID, "the step-synchronous baseline runs synchronously only");
+  const bool compact = params && params->out_mode == TRW_OUT_COMPACT;
+  if (compact && (!sync || kernel == TRW_KERNEL_BSP))
+    return trw_fail(TRW_ERR_INVALID, "compact output runs synchronously, in the plain or persistent kernel");
   WalkSpec sp;
-  trw_status st = trw_make_spec(g, algo, params, n_sources, max_len, seed, &sp);
+  trw_status st = trw_make_spec(g, algo, params, n_sources, max_len, seed, &sp, true);
   if (st != TRW_OK) return st;
   if (n_sources > 0 && (!sources || !out_paths || !out_lengths)) return trw_fail(TRW_ERR_INVALID, "NULL buffer");
   std::lock_guard<std::mutex> lk(g->mu);
@@ -828,9 +836,10 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
              "copy sources");
     d_src = g->src_stage;
   }
-  // Device sources with host outputs: check them before anything is copied out
-  // (an invalid batch must leave the caller's buffers untouched).
-  if (src_dev && (!out_dev || !len_dev)) {
+  // Device sources with host outputs (or compact output): check them before
+  // anything is copied out (an invalid batch must leave the caller's buffers
+  // untouched).
+  if (src_dev && (!out_dev || !len_dev || compact)) {
     CUDA_TRY(cudaMemsetAsync(g->ctrl, 0, sizeof(Ctrl), stream), "reset ctrl");
     CUDA_TRY(launch_validate_sources(d_src, n_sources, (int32_t)g->nv, g->ctrl, stream), "validate sources");
     Ctrl c;
@@ -842,6 +851,18 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
   // device staging buffers and copy each slice out on a second stream while
   // the next slice walks (a double-buffered dump of the paths).
   const int64_t row = sp.endpoints ? 1 : (int64_t)max_len + 1;
+  if (compact) {
+    Ctrl c2{};
+    st = trw_walk_compact(g, sp, kernel, d_src, n_sources, out_paths, out_lengths, stream, &c2);
+    if (st != TRW_OK) return st;
+    const trw_status rs = collect_status(g, stream);
+    g->last.moves += (int64_t)c2.moves;
+    if (rs != TRW_OK) return rs;
+    if (c2.err == kErrRejectCap) return trw_fail(TRW_ERR_REJECT_CAP, "a rejection step exceeded %d trials", TRW_REJECT_CAP);
+    if (c2.err == kErrInvalid) return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
+    if (c2.err != 0) return trw_fail(TRW_ERR_INTERNAL, "device status %d", c2.err);
+    return TRW_OK;
+  }
   if (!out_dev && !len_dev && sync && nwalks >= 2 * kSliceWalks && kernel != TRW_KERNEL_BSP)
     return walk_sliced(g, sp, kernel, d_src, n_sources, row, out_paths, out_lengths, stream);
   if (!out_dev) {

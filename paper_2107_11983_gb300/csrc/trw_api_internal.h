@@ -37,6 +37,11 @@ struct trw_graph {
   int32_t* pin_lens[2] = {nullptr, nullptr};
   size_t pin_lens_cap[2] = {0, 0};
   trw::Ctrl* pin_ctrl = nullptr;              // pinned copies of the two slices' control blocks
+  int32_t* cmp_stage = nullptr;               // compact output: compacted slices (grow-only)
+  size_t cmp_cap = 0;
+  int64_t* cmp_scratch = nullptr;             // their scan offsets, block sums and totals
+  size_t cmp_scratch_cap = 0;
+  int64_t* cmp_host = nullptr;                // pinned: the two slices' totals
   int32_t* nh_slots = nullptr;       // neighbour hash (trw_prepare(NEIGHBOR_HASH)): 2 ne int32
   trw::Ctrl* ctrl = nullptr;         // per-call control block
   void* misc = nullptr;              // 256 bytes of flags
@@ -76,7 +81,13 @@ trw_status trw_cuda_fail(cudaError_t e, const char* what);
 bool trw_is_device_ptr(const void* p);
 trw_status trw_grow(void** p, size_t* cap, size_t need);
 trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* p, int64_t n_sources, int32_t max_len,
-                         uint64_t seed, trw::WalkSpec* sp);
+                         uint64_t seed, trw::WalkSpec* sp, bool allow_compact = false);
+// The walk of trw_walk_ex with TRW_OUT_COMPACT (sources on the device and
+// checked; outputs host or device).  The status and moves of the slices that
+// ran on the graph's second stream come back in *second.
+trw_status trw_walk_compact(trw_graph* g, trw::WalkSpec sp, trw_kernel kernel, const int32_t* d_src,
+                            int64_t n_sources, int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream,
+                            trw::Ctrl* second);
 trw::LaunchCfg trw_launch_cfg(const trw_graph* g, int algo);
 trw::LaunchCfg trw_launch_cfg_batch(const trw_graph* g, const trw::WalkSpec* specs, int n);
 trw::DevGraph trw_dev_graph(const trw_graph* g);
