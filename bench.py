@@ -316,7 +316,8 @@ def run_reference(args, wl):
     g = build_graph(wl)
     algo = {"deepwalk": oracle.DEEPWALK, "deepwalk_weighted": oracle.DEEPWALK_WEIGHTED,
             "node2vec": oracle.NODE2VEC}[wl["algo"]]
-    alias = oracle.prepare_alias(g.row_ptr, g.weights) if algo == oracle.DEEPWALK_WEIGHTED else None
+    tabs = oracle_tables(g, wl)
+    alias = oracle.prepare_alias(g.row_ptr, g.weights) if algo == oracle.DEEPWALK_WEIGHTED and not tabs else None
     src = synth.vertex_sources(g.nv)
     cores = host_cores()
     per_step = 20000 * cores  # 20,000 walks per core per step
@@ -324,7 +325,7 @@ def run_reference(args, wl):
     for i in range(args.warmup + args.steps):
         lo = (i * per_step) % max(1, src.shape[0] - per_step)
         mv, dt = oracle_parallel(g, algo, src, lo, min(per_step, src.shape[0]), wl["max_len"], wl["seed"], alias,
-                                 walk_kwargs(wl), cores)
+                                 dict(walk_kwargs(wl), **tabs), cores)
         if i >= args.warmup:
             times.append(dt)
             moves.append(mv)
