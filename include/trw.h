@@ -97,7 +97,8 @@ typedef enum {
  * fixed-point rounding of each method's thresholds.
  *   DEFAULT  ALIAS over the tables of TRW_PREP_ALIAS: one record per move.
  *   ITS      static ITS over the prefix sums of TRW_PREP_ITS: x uniform in
- *            [0, p'_{d-1}), then the smallest i with x < p'_i (binary search).
+ *            [0, p'_{d-1}), then the smallest i with x < p'_i (binary search;
+ *            with TRW_PREP_ITS_GUIDE the same answer through guided records).
  *   REJ      rejection against p*_v = max W_e of the row (TRW_PREP_REJ):
  *            darts (x, y) with x uniform in [0, d_v) until y < W_x / p*_v,
  *            the 32-bit word y tested against floor(W_x * 2^32 / p*_v).
@@ -123,7 +124,7 @@ typedef struct {
   double n2v_q;                 /* Node2Vec in-out parameter (the paper's b): weight 1/q at distance 2, > 0 */
   const uint8_t* schema;        /* MetaPath schema H (host memory), step s uses H[s mod schema_len] */
   int32_t schema_len;           /* 1 .. TRW_MAX_SCHEMA for MetaPath, ignored otherwise */
-  uint32_t out_mode;            /* TRW_OUT_PATHS or TRW_OUT_ENDPOINTS */
+  uint32_t out_mode;            /* TRW_OUT_PATHS, TRW_OUT_ENDPOINTS or (trw_walk / trw_walk_ex) TRW_OUT_COMPACT */
   int32_t walks_per_source;     /* >= 1; walk i starts at sources[i / walks_per_source] */
   int32_t sampler;              /* TRW_SAMPLER_*: weighted DeepWalk's sampling method */
   int64_t walk_offset;          /* index of walk 0 in the Philox counter (for sharding a batch) */
