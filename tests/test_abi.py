@@ -1,8 +1,13 @@
 """The C-ABI library builds, loads and exports every function include/trw.h
-declares (CPU only: no compute calls)."""
+declares, and a plain C99 program compiles and links against it (CPU only: no
+compute calls)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
+
+import pytest
 
 import paper_2107_11983_gb300 as trw
 from paper_2107_11983_gb300 import _build
@@ -32,3 +37,29 @@ def test_binding_declares_the_same_functions():
 def test_binding_loads_without_gpu():
     lib = trw.load_library()
     assert lib.trw_last_error() is not None
+
+
+def test_plain_c_consumer(tmp_path):
+    """tests/abi_consumer.c: strict C99 against trw.h, linked with libtrw.so;
+    argument errors, NULL handles and per-thread error messages need no GPU."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib = _build.build()
+    src = os.path.join(ROOT, "tests", "abi_consumer.c")
+    inc = os.path.join(ROOT, "include")
+    exe = str(tmp_path / "abi_consumer")
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-pthread", "-I", inc, src, lib,
+           "-Wl,-rpath," + os.path.dirname(lib), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    gxx = shutil.which("g++")
+    if gxx is not None:  # the same program is valid C++ (the header's extern "C" guard)
+        r = subprocess.run([gxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-x", "c++", "-fsyntax-only",
+                            "-I", inc, src], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    load = int(re.search(r"load=(-?\d+)", r.stdout).group(1))
+    import torch
+    assert load == (0 if torch.cuda.is_available() else -4), r.stdout  # TRW_OK, or TRW_ERR_CUDA without a GPU
