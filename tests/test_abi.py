@@ -63,3 +63,29 @@ def test_plain_c_consumer(tmp_path):
     load = int(re.search(r"load=(-?\d+)", r.stdout).group(1))
     import torch
     assert load == (0 if torch.cuda.is_available() else -4), r.stdout  # TRW_OK, or TRW_ERR_CUDA without a GPU
+
+
+def test_no_fallback_without_gpu():
+    """The product path has no CPU fallback: without a GPU, loading a graph
+    fails with TRW_ERR_CUDA, importing the package pulls in nothing from
+    oracle/, and no package source imports or includes it."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    import numpy as np
+    rp = np.array([0, 2, 4, 6], np.int64)
+    col = np.array([1, 2, 0, 2, 0, 1], np.int32)
+    with pytest.raises(trw.TRWError) as e:
+        trw.Graph(rp, col)
+    assert e.value.status == -4
+    code = ("import sys, paper_2107_11983_gb300, paper_2107_11983_gb300.shard; "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "assert not bad, bad")
+    r = subprocess.run([os.sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    pkg = os.path.join(ROOT, "paper_2107_11983_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b|#include\s+\"oracle", text, re.M), f
