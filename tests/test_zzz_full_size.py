@@ -2,10 +2,10 @@
 configuration bench.py times: the same synthetic graphs, tables, autotuning
 and kernel choice, every walk of the batch on the GPU, and a sample of walks
 recomputed one by one by the oracle (walk_offset = the walk's index) and
-compared vertex for vertex: C1 DeepWalk on R-MAT s14, C2 weighted DeepWalk on
-s22, C3 Node2Vec on s24 with the neighbour hash and row records, and C4's
-mixed batch (1M PPR + one MetaPath walk per vertex) on s23 with the label
-index."""
+compared vertex for vertex: DeepWalk on R-MAT s14, weighted DeepWalk (ALIAS)
+on s22, Node2Vec on s24 with the neighbour hash and row records, and the
+mixed batch (1M PPR endpoints + one MetaPath walk per vertex) on s23 with the
+label index."""
 import argparse
 import importlib.util
 import os
