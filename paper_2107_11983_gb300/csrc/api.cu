@@ -40,12 +40,6 @@ trw_status trw_cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" const char* trw_last_error(void) { return t_last_error.c_str(); }
 
-#define CUDA_TRY(call, what)                      \
-  do {                                            \
-    cudaError_t e__ = (call);                     \
-    if (e__ != cudaSuccess) return trw_cuda_fail(e__, what); \
-  } while (0)
-
 // ------------------------------------------------------------ small helpers
 
 bool trw_is_device_ptr(const void* p) {

@@ -15,12 +15,6 @@
 
 using namespace trw;
 
-#define CUDA_TRY(call, what)                                 \
-  do {                                                       \
-    cudaError_t e__ = (call);                                \
-    if (e__ != cudaSuccess) return trw_cuda_fail(e__, what); \
-  } while (0)
-
 namespace {
 
 constexpr int kScanBlock = 1024;  // lengths per scan block

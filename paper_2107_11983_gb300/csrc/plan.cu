@@ -18,12 +18,6 @@
 
 using namespace trw;
 
-#define CUDA_TRY(call, what)                                 \
-  do {                                                       \
-    cudaError_t e__ = (call);                                \
-    if (e__ != cudaSuccess) return trw_cuda_fail(e__, what); \
-  } while (0)
-
 struct trw_plan {
   trw_graph* g = nullptr;
   int32_t nreq = 0;

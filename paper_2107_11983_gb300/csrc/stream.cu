@@ -16,12 +16,6 @@
 
 using namespace trw;
 
-#define CUDA_TRY(call, what)                                 \
-  do {                                                       \
-    cudaError_t e__ = (call);                                \
-    if (e__ != cudaSuccess) return trw_cuda_fail(e__, what); \
-  } while (0)
-
 namespace {
 
 trw_status grow_pinned(void** p, size_t* cap, size_t need) {

@@ -78,13 +78,20 @@ inline bool trw_sources_in_range(const int32_t* src, int64_t n, int64_t nv) {
   return bad == 0;
 }
 trw_status trw_cuda_fail(cudaError_t e, const char* what);
+// Returns TRW_ERR_CUDA from the enclosing function, with `what` and CUDA's
+// message in trw_last_error(), when the runtime call fails.
+#define CUDA_TRY(call, what)                                 \
+  do {                                                       \
+    cudaError_t e__ = (call);                                \
+    if (e__ != cudaSuccess) return trw_cuda_fail(e__, what); \
+  } while (0)
 bool trw_is_device_ptr(const void* p);
 trw_status trw_grow(void** p, size_t* cap, size_t need);
 trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* p, int64_t n_sources, int32_t max_len,
                          uint64_t seed, trw::WalkSpec* sp, bool allow_compact = false);
 // The walk of trw_walk_ex with TRW_OUT_COMPACT (sources on the device and
-// checked; outputs host or device).  The status and moves of the slices that
-// ran on the graph's second stream come back in *second.
+// checked; outputs host or device).  Every slice runs on `stream` and reports
+// into the graph's control block; *second comes back zeroed.
 trw_status trw_walk_compact(trw_graph* g, trw::WalkSpec sp, trw_kernel kernel, const int32_t* d_src,
                             int64_t n_sources, int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream,
                             trw::Ctrl* second);
