@@ -841,22 +841,17 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
     CUDA_TRY(cudaStreamSynchronize(stream), "validate sources");
     if (c.err != 0) return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
   }
+  // Compact output: sliced, each slice compacted on the device and copied out
+  // at its running offset.
+  if (compact) {
+    st = trw_walk_compact(g, sp, kernel, d_src, n_sources, out_paths, out_lengths, stream);
+    if (st != TRW_OK) return st;
+    return collect_status(g, stream);
+  }
   // Host outputs of a large batch: walk it in source-aligned slices into two
   // device staging buffers and copy each slice out on a second stream while
   // the next slice walks (a double-buffered dump of the paths).
   const int64_t row = sp.endpoints ? 1 : (int64_t)max_len + 1;
-  if (compact) {
-    Ctrl c2{};
-    st = trw_walk_compact(g, sp, kernel, d_src, n_sources, out_paths, out_lengths, stream, &c2);
-    if (st != TRW_OK) return st;
-    const trw_status rs = collect_status(g, stream);
-    g->last.moves += (int64_t)c2.moves;
-    if (rs != TRW_OK) return rs;
-    if (c2.err == kErrRejectCap) return trw_fail(TRW_ERR_REJECT_CAP, "a rejection step exceeded %d trials", TRW_REJECT_CAP);
-    if (c2.err == kErrInvalid) return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
-    if (c2.err != 0) return trw_fail(TRW_ERR_INTERNAL, "device status %d", c2.err);
-    return TRW_OK;
-  }
   if (!out_dev && !len_dev && sync && nwalks >= 2 * kSliceWalks && kernel != TRW_KERNEL_BSP)
     return walk_sliced(g, sp, kernel, d_src, n_sources, row, out_paths, out_lengths, stream);
   if (!out_dev) {

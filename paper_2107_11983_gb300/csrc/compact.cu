@@ -105,11 +105,10 @@ __global__ void compact_rows(const int32_t* __restrict__ padded, const int32_t* 
 }  // namespace
 
 trw_status trw_walk_compact(trw_graph* g, WalkSpec sp, trw_kernel kernel, const int32_t* d_src, int64_t n_sources,
-                            int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream, Ctrl* second) {
+                            int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream) {
   const int64_t wps = (int64_t)sp.wps;
   const int64_t nwalks = sp.nwalks;
   const int32_t row = sp.max_len + 1;
-  *second = Ctrl{};
   // Slices of about 2^18 walks, at most 16, on one compute stream: each
   // slice's walk and compaction run in order while the copy engine drains
   // the previous slice.  (Two compute streams, as the padded output uses,

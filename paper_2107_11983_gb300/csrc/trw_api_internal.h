@@ -91,10 +91,9 @@ trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* p,
                          uint64_t seed, trw::WalkSpec* sp, bool allow_compact = false);
 // The walk of trw_walk_ex with TRW_OUT_COMPACT (sources on the device and
 // checked; outputs host or device).  Every slice runs on `stream` and reports
-// into the graph's control block; *second comes back zeroed.
+// its moves and status into the graph's control block.
 trw_status trw_walk_compact(trw_graph* g, trw::WalkSpec sp, trw_kernel kernel, const int32_t* d_src,
-                            int64_t n_sources, int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream,
-                            trw::Ctrl* second);
+                            int64_t n_sources, int32_t* out_paths, int32_t* out_lengths, cudaStream_t stream);
 trw::LaunchCfg trw_launch_cfg(const trw_graph* g, int algo);
 trw::LaunchCfg trw_launch_cfg_batch(const trw_graph* g, const trw::WalkSpec* specs, int n);
 trw::DevGraph trw_dev_graph(const trw_graph* g);
