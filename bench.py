@@ -320,11 +320,11 @@ def run_reference(args, wl):
     alias = oracle.prepare_alias(g.row_ptr, g.weights) if algo == oracle.DEEPWALK_WEIGHTED and not tabs else None
     src = synth.vertex_sources(g.nv)
     cores = host_cores()
-    per_step = 20000 * cores  # 20,000 walks per core per step
+    per_step = min(20000 * cores, src.shape[0])  # 20,000 walks per core per step, at most the batch
     times, moves = [], []
     for i in range(args.warmup + args.steps):
         lo = (i * per_step) % max(1, src.shape[0] - per_step)
-        mv, dt = oracle_parallel(g, algo, src, lo, min(per_step, src.shape[0]), wl["max_len"], wl["seed"], alias,
+        mv, dt = oracle_parallel(g, algo, src, lo, per_step, wl["max_len"], wl["seed"], alias,
                                  dict(walk_kwargs(wl), **tabs), cores)
         if i >= args.warmup:
             times.append(dt)

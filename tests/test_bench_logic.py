@@ -105,3 +105,33 @@ def test_sampler_workloads(bench):
     cpu = {"model_bytes_per_move": 100.0}
     assert bench.roofline(dict(wl, sampler="rej"), 1000, 10, 1.0, cpu, None, 1.0)["bytes_per_move"] == 100.0
     assert bench.walk_kwargs(bench.WORKLOADS["c2"]) == {}
+
+
+@pytest.mark.parametrize("config", ["c1", "c4"])
+def test_reference_arm_line(config):
+    """bench.py --impl reference: one JSON line with the contract's keys, the
+    oracle timed on the host cores over a sample no larger than the batch; a
+    workload it does not walk gives the one-line unavailable form."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", config,
+                        "--steps", "2", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    if config == "c4":
+        assert set(d) == {"impl", "unavailable"}
+        return
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["metric"] == "walk steps/sec" and d["unit"] == "steps/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["value"] > 0
+    assert d["config"]["workload"] == "deepwalk-rmat-s14"
+    assert d["config"]["walks_per_step"] == 1 << 14  # the whole batch: smaller than the per-core sample
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert str(1 << 14) in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
