@@ -47,6 +47,13 @@
  *     clamped to 2^32 when W_x >= p*.  A row whose weights are all zero is a
  *     dead end for ITS and REJ (their initialisation sees it); O-REJ cannot
  *     see it and runs into the trial cap.
+ *
+ * Pins: tests/oracle_pins.py holds every function here to something other
+ * than itself: Philox known-answer vectors, closed forms of the fixed-point
+ * conventions, exact rational laws of the alias tables, chi-square tests of
+ * path laws against brute force on tiny graphs, the PPR chain's linear solve,
+ * closed-form rejection trial counts, and reductions to NAIVE.  No function
+ * is unpinned.
  */
 #include <stdint.h>
 #include <stdlib.h>
