@@ -89,3 +89,29 @@ def test_no_fallback_without_gpu():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b|#include\s+\"oracle", text, re.M), f
+
+
+def test_readme_c_example(tmp_path):
+    """The README's C quick start compiles as strict C99, links against
+    libtrw.so and runs: it walks on a GPU, and without one it reports the
+    CUDA error through trw_last_error() and exits 1."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    text = open(os.path.join(ROOT, "README.md")).read()
+    m = re.search(r"## Quick start \(C\)\s*```c\n(.*?)```", text, re.S)
+    assert m, "README has no C quick start"
+    src = tmp_path / "example.c"
+    src.write_text(m.group(1))
+    lib = _build.build()
+    exe = str(tmp_path / "example")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                        os.path.join(ROOT, "include"), str(src), lib, "-Wl,-rpath," + os.path.dirname(lib), "-o", exe],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    import torch
+    if torch.cuda.is_available():
+        assert r.returncode == 0 and r.stdout.startswith("walk 0: "), r.stdout + r.stderr
+    else:
+        assert r.returncode == 1 and r.stderr.startswith("trw: ") and "cudaGetDevice" in r.stderr, r.stderr
