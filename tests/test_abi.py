@@ -115,3 +115,39 @@ def test_readme_c_example(tmp_path):
         assert r.returncode == 0 and r.stdout.startswith("walk 0: "), r.stdout + r.stderr
     else:
         assert r.returncode == 1 and r.stderr.startswith("trw: ") and "cudaGetDevice" in r.stderr, r.stderr
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the size, field offsets and field
+    sizes of their C counterparts in trw.h (compiled and measured by gcc)."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"trw_params": trw._Params, "trw_tuning": trw.Tuning, "trw_stats": trw.Stats,
+               "trw_serve_config": trw.ServeConfig}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "trw.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu %zu\\n", offsetof({cname}, {f}), sizeof((({cname}*)0)->{f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    seen = 0
+    for ln in out:
+        parts = ln.split()
+        if not parts:
+            continue
+        py = structs[parts[0]]
+        if parts[1] == "sizeof":
+            assert ctypes.sizeof(py) == int(parts[2]), ln
+        else:
+            fd = getattr(py, parts[1])
+            assert (fd.offset, fd.size) == (int(parts[2]), int(parts[3])), ln
+        seen += 1
+    assert seen == sum(len(py._fields_) + 1 for py in structs.values())
