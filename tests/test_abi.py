@@ -151,3 +151,38 @@ def test_struct_layouts_match_header(tmp_path):
             assert (fd.offset, fd.size) == (int(parts[2]), int(parts[3])), ln
         seen += 1
     assert seen == sum(len(py._fields_) + 1 for py in structs.values())
+
+
+def _c_kind(t: str) -> str:
+    t = " ".join(t.split())
+    if "*" in t or t.startswith("trw_stream_fn"):
+        return "ptr"
+    base = t.replace("const ", "").split()[0]
+    return {"int64_t": "i64", "int32_t": "i32", "int": "i32", "trw_algo": "i32", "trw_kernel": "i32",
+            "trw_status": "i32", "uint32_t": "u32", "uint64_t": "u64", "double": "f64", "void": "void"}[base]
+
+
+def _ctypes_kind(c) -> str:
+    if c is None:
+        return "void"
+    if c in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(c, (ctypes._Pointer, ctypes._CFuncPtr)):
+        return "ptr"
+    if c is ctypes.c_double:
+        return "f64"
+    return ("i" if c(-1).value < 0 else "u") + str(8 * ctypes.sizeof(c))
+
+
+def test_binding_signatures_match_header():
+    """Every ctypes signature has the header prototype's return kind and the
+    same number, order, width and signedness of arguments (a mismatch would
+    pass garbage through the ABI without any error)."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "trw.h")).read(), flags=re.S)
+    protos = re.findall(r"([A-Za-z_][A-Za-z_0-9 \*]*?)\b(trw_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text, re.S)
+    assert sorted(name for _, name, _ in protos) == declared_functions()
+    for ret, name, args in protos:
+        args = " ".join(args.split())
+        want_args = [] if args in ("void", "") else [
+            _c_kind(re.sub(r"\b[A-Za-z_0-9]+$", "", a.strip())) for a in args.split(",")]
+        pr, pa = trw._SIGS[name]
+        assert _ctypes_kind(pr) == _c_kind(ret), name
+        assert [_ctypes_kind(a) for a in pa] == want_args, name
