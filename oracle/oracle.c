@@ -52,8 +52,9 @@
  * than itself: Philox known-answer vectors, closed forms of the fixed-point
  * conventions, exact rational laws of the alias tables, chi-square tests of
  * path laws against brute force on tiny graphs, the PPR chain's linear solve,
- * closed-form rejection trial counts, and reductions to NAIVE.  No function
- * is unpinned.
+ * closed-form rejection trial counts, reductions to NAIVE, and hand counts
+ * of the statistics' sector model (the distinct 32-byte sectors a move reads
+ * in the device layout) on tiny graphs.  No function is unpinned.
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -13,6 +13,9 @@ paper or the mathematics fixes:
   * the PPR end-vertex law by a linear solve of the absorbing chain, and the
     geometric length law (mean 5 vertices at stop 0.2, Section 6.2);
   * the O-REJ expected number of trials d * p* / sum(p) (Section 2.3);
+  * the sector model of the statistics (distinct 32-byte sectors a move
+    reads in the device layout, and the output bytes) against hand counts
+    on tiny graphs;
   * special cases that must reduce exactly to NAIVE sampling;
   * weighted DeepWalk under ITS, REJ and O-REJ: the first move of every walk
     recomputed independently (numpy prefix sums and searchsorted for ITS,
@@ -466,6 +469,101 @@ def _r64(B):
     return int(B[0]) | (int(B[1]) << 32)
 
 
+# ------------------------------------------------------------- sector model
+# The oracle's statistics count, per move, the distinct 32-byte sectors the
+# device layout reads (4-byte row offsets and vertex ids, 16-byte packed alias
+# records, 8-byte ITS prefix sums, 4-byte REJ bounds and weights, 1-byte
+# labels), and the bytes of path output.  The counts below are worked out by
+# hand on graphs built so that the count does not depend on which neighbour a
+# draw picks; each comment gives the byte ranges.
+
+def _cycle(nv=10):
+    return synth.from_edges(nv, [(v, (v + 1) % nv) for v in range(nv)], symmetric=False)
+
+
+def pin_sector_model(lib=None):
+    """stats.sectors and stats.out_bytes against hand counts (the per-step
+    access chains of Section 2.3's samplers on the device layout)."""
+    g = _cycle()
+    src = np.arange(10, dtype=np.int32)
+    ones = np.ones(g.ne, dtype=np.float32)
+
+    def run(algo, L, **kw):
+        res = oracle.walk(g.row_ptr, g.col, algo, src, L, seed=11, lib=lib, **kw)
+        assert res.status == 0
+        return res.stats
+
+    # Cycle v -> v+1: every move reads the row pair of v (bytes 4v..4v+7: one
+    # sector, two for v = 7, whose pair straddles byte 32) and one more
+    # sector per array the sampler reads (a row of one edge).
+    st = run(oracle.DEEPWALK, 1)
+    assert (st["moves"], st["sectors"], st["out_bytes"]) == (10, 21, 80), st
+    # Three moves from each vertex: 30 moves, and vertex 7 starts a move of
+    # the walks from 5, 6 and 7.  Paths of 4 vertices: 10 * 16 bytes.
+    st = run(oracle.DEEPWALK, 3)
+    assert (st["moves"], st["sectors"], st["out_bytes"]) == (30, 63, 160), st
+    st = run(oracle.PPR, 3, ppr_stop=0.0, endpoints_only=True)
+    assert (st["moves"], st["sectors"], st["out_bytes"]) == (30, 63, 40), st
+    # ALIAS: the row pair and one packed record (its destination inside).
+    al = oracle.prepare_alias(g.row_ptr, ones, lib=lib)
+    st = run(oracle.DEEPWALK_WEIGHTED, 1, alias=al)
+    assert (st["moves"], st["sectors"]) == (10, 21), st
+    # ITS on a one-edge row: the row pair, P'_{d-1}, the picked id.
+    st = run(oracle.DEEPWALK_WEIGHTED, 1, sampler=oracle.SAMPLER_ITS, its=oracle.prepare_its(g.row_ptr, ones, lib=lib))
+    assert (st["moves"], st["sectors"]) == (10, 31), st
+    # REJ: the row pair, p*_v, then the dart's weight and id (a dart on the
+    # row's largest weight always hits).
+    st = run(oracle.DEEPWALK_WEIGHTED, 1, sampler=oracle.SAMPLER_REJ, weights=ones,
+             pmax=oracle.prepare_rej(g.row_ptr, ones, lib=lib))
+    assert (st["moves"], st["attempts"], st["sectors"]) == (10, 10, 41), st
+    # O-REJ: as REJ without p*_v (the caller's bound).
+    st = run(oracle.DEEPWALK_WEIGHTED, 1, sampler=oracle.SAMPLER_OREJ, weights=ones, max_weight=1.0)
+    assert (st["moves"], st["attempts"], st["sectors"]) == (10, 10, 31), st
+
+    # ITS binary search: 0 -> 1..16, all weight on the edge at index 12.
+    # P' = 0 (indices 0..11), then W.  Probes: P'_15 (byte 120), then the
+    # lower-bound search over [0, 15): 7 (byte 56), 11 (88), 13 (104),
+    # 12 (96): sectors 1, 2, 3.  The id at index 12 is at byte 48 (sector 1)
+    # and the row pair of 0 in sector 0: 5 sectors a move.
+    gs = synth.from_edges(17, [(0, c) for c in range(1, 17)], symmetric=False)
+    w = np.zeros(16, dtype=np.float32)
+    w[12] = 1.0
+    res = oracle.walk(gs.row_ptr, gs.col, oracle.DEEPWALK_WEIGHTED, [0], 1, seed=5, walks_per_source=6,
+                      sampler=oracle.SAMPLER_ITS, its=oracle.prepare_its(gs.row_ptr, w, lib=lib), lib=lib)
+    assert res.status == 0 and np.all(res.paths[:, 1] == 13)
+    assert (res.stats["moves"], res.stats["sectors"]) == (6, 30), res.stats
+
+    # MetaPath: vertex 0 has 31 edges, so vertex 1's two edges sit at
+    # indices 31 and 32: its labels span bytes 31..32 (sectors 0 and 1), its
+    # ids bytes 124..131 (one sector either way), its row pair bytes 4..11.
+    # Vertex 0: labels bytes 0..30, one sector.
+    gm = synth.from_edges(33, [(0, c) for c in range(2, 33)] + [(1, 2), (1, 3)], symmetric=False)
+    lab = np.zeros(gm.ne, dtype=np.uint8)
+    for s0, per in ((1, 4), (0, 3)):
+        res = oracle.walk(gm.row_ptr, gm.col, oracle.METAPATH, [s0], 1, seed=5, walks_per_source=4, labels=lab,
+                          schema=[0], lib=lib)
+        assert res.status == 0
+        assert (res.stats["moves"], res.stats["sectors"]) == (4, 4 * per), (s0, res.stats)
+
+    # Node2Vec IsNeighbor: N(0) = {1, 3, 4, 5, 6, 8..18} (16 ids, bytes
+    # 0..63), vertices 1, 3, 4, 5, 6 each lead only to 2, and 2 is not in
+    # N(0).  First move from 0: row pair (sector 0) and one id: 2 sectors.
+    # Second move from v in {1, 3, 4, 5, 6} (vertices 8..18 are dead ends):
+    # every dart draws 2 (ids at indices 16..21, sector 2); IsNeighbor(2, 0)
+    # reads 0's row pair (sector 0, as v's) and probes indices 8, 4, 2, 1, 0
+    # (sectors 1 and 0): 4 sectors, however many darts the step throws.
+    n0 = [1, 3, 4, 5, 6] + list(range(8, 19))
+    gn = synth.from_edges(19, [(0, c) for c in n0] + [(v, 2) for v in (1, 3, 4, 5, 6)] + [(2, 0)], symmetric=False)
+    n = 2000
+    res = oracle.walk(gn.row_ptr, gn.col, oracle.NODE2VEC, [0], 2, seed=9, walks_per_source=n, n2v_p=0.5,
+                      n2v_q=2.0, lib=lib)
+    assert res.status == 0
+    second = res.stats["moves"] - n
+    assert 0 < second < n
+    assert res.stats["attempts"] > res.stats["moves"]  # some darts were rejected
+    assert res.stats["sectors"] == 2 * n + 4 * second, res.stats
+
+
 def pin_rej_threshold(lib=None):
     """T = rej_threshold(W, p*) is the number of 32-bit words y with
     (y + 1) / 2^32 <= W / p*: word T - 1 passes and word T fails."""
@@ -794,7 +892,7 @@ def pin_custom_walk_update(lib=None):
     assert p > 1e-3, p
 
 
-ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
+ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_sector_model, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
             pin_law_metapath, pin_ppr, pin_rejection_trials, pin_reductions, pin_invariants, pin_sharding, pin_rej_threshold, pin_its_first_move,
             pin_rej_first_move, pin_law_samplers, pin_rej_trials_closed_form, pin_zero_weights,
             pin_law_node2vec_weighted, pin_node2vec_weighted_first_move, pin_node2vec_weighted_reductions,

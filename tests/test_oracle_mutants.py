@@ -60,6 +60,19 @@ MUTANTS = [
      "const uint32_t W = weight(user, (int64_t)w, s, prev, prev, g->col[off + c], off + c);"),
     ("zero row: not a dead end for REJ", "if (pstar == 0) { if (st) st->stop_dead++; break; }",
      "if (pstar == 0) pstar = 1;"),
+    ("sectors: IsNeighbor probes not counted", "      sec_touch(sec, SEC_COL, m * 4);\n", "\n"),
+    ("sectors: range bound one byte short", "for (int64_t b = byte_lo & ~31LL; b < byte_hi; b += 32)",
+     "for (int64_t b = byte_lo & ~31LL; b < byte_hi - 1; b += 32)"),
+    ("sectors: range start not rounded to its sector", "for (int64_t b = byte_lo & ~31LL; b < byte_hi; b += 32)",
+     "for (int64_t b = byte_lo; b < byte_hi; b += 32)"),
+    ("sectors: row pair counted as its first offset only",
+     "if (sec) { sec_touch(sec, SEC_ROW, (int64_t)cur * 4); sec_touch(sec, SEC_ROW, (int64_t)(cur + 1) * 4); }",
+     "if (sec) { sec_touch(sec, SEC_ROW, (int64_t)cur * 4); }"),
+    ("sectors: ITS search probes not counted", "          if (sec) sec_touch(sec, SEC_CDF, (off + mid) * 8);\n", "\n"),
+    ("sectors: REJ bound not counted", "          if (sec) sec_touch(sec, SEC_PMAX, (int64_t)cur * 4);\n          if (pstar == 0)",
+     "          if (pstar == 0)"),
+    ("sectors: set cleared once per walk, not per step", "    path[0] = cur;\n    for (;;) {\n      if (sec) sec->n = 0;\n",
+     "    path[0] = cur;\n    if (sec) sec->n = 0;\n    for (;;) {\n"),
 ]
 
 
