@@ -28,6 +28,12 @@
  *    probability t is the threshold floor(t * 2^32) against a 32-bit word.
  *  - Graph sizes: nv < 2^31 and ne < 2^31 (int32 device offsets); walk
  *    indices walk_offset + i < 2^32.
+ *  - A graph lives on the device that was current when it was loaded.  Every
+ *    call that works on a graph (directly, or through a plan or a server)
+ *    returns TRW_ERR_INVALID, before any copy or launch, when another device
+ *    is current.
+ *  - TRW_ERR_OOM reports a device or pinned host allocation that failed; the
+ *    graph (or server) keeps the state it had before the call.
  */
 #ifndef TRW_H
 #define TRW_H
@@ -394,7 +400,12 @@ void trw_plan_destroy(trw_plan* plan);
  * memory, code under an allocator that must see every allocation, or code
  * that must not let cudaMalloc/cudaFree synchronise the device).
  * Same requests, results and errors as trw_walk_batch (device buffers only),
- * on the caller's stream (NULL: the legacy default stream); synchronous.
+ * on the caller's stream (NULL: the legacy default stream).  Synchronous on
+ * that stream: the request table goes up from host memory on it, and the call
+ * returns once the walks are done and their status is read back on it; it
+ * waits for no other stream unless that stream is the legacy default stream,
+ * which orders itself after every blocking stream of the device.  Refused
+ * with TRW_ERR_INVALID when the current device is not the graph's.
  * Its scratch -- control block, request table, prefix sums, about 9 KB -- is a
  * fixed array in device memory that every GPU loading the library holds
  * until the process exits; n_requests above TRW_NOALLOC_MAX_REQUESTS is
@@ -489,6 +500,24 @@ trw_status trw_debug_is_neighbor(const trw_graph* g, const int32_t* u, const int
  * ctr[4*i..4*i+3] and key (key0, key1).  Host buffers.  For tests. */
 trw_status trw_debug_philox(const uint32_t* ctr, int64_t n, uint32_t key0, uint32_t key1, uint32_t* out);
 
+/*
+ * Test hook (the paper has no counterpart): after the next `after`
+ * allocations of device or pinned host memory that the library makes, every
+ * later one fails as if the device were out of memory, until the hook is
+ * reset with a negative `after`.  Calls then return TRW_ERR_OOM and leave the
+ * graph or server as it was.  Process-wide; for failure tests only.
+ */
+void trw_debug_fail_allocs(int64_t after);
+
+/*
+ * Test hook (the paper has no counterpart): the device checks of every call
+ * compare the graph's device with `device` instead of the current device
+ * (negative: the current device again).  It changes no launch: a call either
+ * refuses with TRW_ERR_INVALID or runs on the current device as always.
+ * Process-wide; lets a one-GPU test exercise the wrong-device refusal.
+ */
+void trw_debug_pretend_device(int32_t device);
+
 /* ------------------------------------------------------------- serving */
 
 /* Serving configuration. */
@@ -516,14 +545,20 @@ trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg, trw_serve
  * that no other stream still writes when submit is called: the server runs
  * on its own streams and orders itself after the caller's only through
  * trw_serve_order_after).
- * sources may be host or device; every source is checked at submit
- * (TRW_ERR_INVALID for one outside [0, nv): nothing queued or written).  Host
- * sources are copied into the server's pool before submit returns; device
- * sources are read in place, so they must stay valid and unchanged until the
- * request is reported.  Submit does not wait for the walk kernel.  Returns TRW_ERR_BUSY when admitting it would exceed the
+ * sources may be host or device, and every source is range-checked before any
+ * walk of the request runs.  Host sources, and device sources of requests with
+ * more than TRW_SERVE_DEVICE_CHECK_MAX sources, are checked at submit
+ * (TRW_ERR_INVALID for one outside [0, nv): nothing queued or written).  The
+ * device sources of a smaller request are checked on the device when the
+ * server admits it, which saves submit a copy to the host and a wait: one
+ * outside [0, nv) completes the request with TRW_ERR_INVALID (reported by
+ * poll or reap) and nothing is written.  Host sources are copied into the
+ * server's pool before submit returns; device sources are read in place, so
+ * they must stay valid and unchanged until the request is reported.  Submit does not wait for the walk kernel.  Returns TRW_ERR_BUSY when admitting it would exceed the
  * configured walk, byte or slot limits (nothing is queued), else queues it
  * and writes *req_id.
  */
+#define TRW_SERVE_DEVICE_CHECK_MAX 1024
 trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* params, const int32_t* sources,
                             int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
                             int32_t* out_lengths, uint64_t* req_id);

@@ -120,6 +120,8 @@ _SIGS = {
     "trw_debug_its_records": (ctypes.c_int, [_VP, _VP]),
     "trw_debug_is_neighbor": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP]),
     "trw_debug_philox": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, _VP]),
+    "trw_debug_fail_allocs": (None, [ctypes.c_int64]),
+    "trw_debug_pretend_device": (None, [ctypes.c_int32]),
     "trw_serve_config_default": (None, [_VP]),
     "trw_serve_create": (ctypes.c_int, [_VP, _VP, _VP]),
     "trw_serve_submit": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_int64, ctypes.c_int32,
@@ -400,8 +402,9 @@ class Graph:
         sa = _stream_arg(stream) if stream is not None else (int(_torch().cuda.current_stream().cuda_stream) or 1)
         _check(load_library().trw_sync(self._h, sa), "trw_sync")
 
-    def _batch_args(self, requests: Sequence[dict]):
-        """ctypes arrays of a mixed batch; outputs allocated as CUDA tensors."""
+    def _batch_args(self, requests: Sequence[dict], outputs=None):
+        """ctypes arrays of a mixed batch; outputs allocated as CUDA tensors
+        unless given as (paths, lengths) pairs, one per request."""
         torch = _torch()
         nreq = len(requests)
         if not 1 <= nreq <= MAX_BATCH:
@@ -432,19 +435,25 @@ class Graph:
             n = int(src.shape[0])
             L = int(r["max_len"])
             shape = (n * wps,) if ep else (n * wps, L + 1)
-            op = torch.empty(shape, dtype=torch.int32, device=src.device)
-            ol = torch.empty(n * wps, dtype=torch.int32, device=src.device)
+            if outputs is not None:
+                op, ol = outputs[i]
+                if tuple(op.shape) != shape or tuple(ol.shape) != (n * wps,) or not (_is_cuda(op) and _is_cuda(ol)):
+                    raise ValueError(f"request {i}: outputs must be CUDA tensors of shapes {shape} and {(n * wps,)}")
+            else:
+                op = torch.empty(shape, dtype=torch.int32, device=src.device)
+                ol = torch.empty(n * wps, dtype=torch.int32, device=src.device)
             algos[i], params[i], srcs[i], ns[i], lens[i] = algo, p, src.data_ptr(), n, L
             seeds[i] = int(r["seed"]) & ((1 << 64) - 1)
             outs[i], outl[i] = op.data_ptr(), ol.data_ptr()
             results.append(WalkOutput(op, ol))
         return (nreq, algos, params, srcs, ns, lens, seeds, outs, outl), keep, results
 
-    def walk_batch(self, requests: Sequence[dict], stream=None, sync: bool = True):
+    def walk_batch(self, requests: Sequence[dict], stream=None, sync: bool = True, outputs=None):
         """One persistent launch over a mixed batch.  Each request is a dict with
         algo, sources (CUDA tensor), max_len, seed and optional parameters; outputs
-        are allocated as CUDA tensors and returned as a list of WalkOutput."""
-        args, keep, results = self._batch_args(requests)
+        are allocated as CUDA tensors (or taken from `outputs`, one (paths,
+        lengths) pair per request) and returned as a list of WalkOutput."""
+        args, keep, results = self._batch_args(requests, outputs)
         st = load_library().trw_walk_batch(self._h, *args, _stream_arg(stream, *[k for k in keep if _is_torch(k)]),
                                            1 if sync else 0)
         _check(st, "trw_walk_batch")
@@ -542,6 +551,20 @@ def philox_device(ctr, key0: int, key1: int) -> np.ndarray:
     out = np.empty_like(c)
     _check(load_library().trw_debug_philox(c.ctypes.data, c.shape[0], key0, key1, out.ctypes.data), "philox")
     return out
+
+
+def fail_allocs(after: int) -> None:
+    """Test hook (trw_debug_fail_allocs): after the next `after` device or
+    pinned allocations of the library every later one fails as out of memory;
+    a negative `after` turns the failures off."""
+    load_library().trw_debug_fail_allocs(int(after))
+
+
+def pretend_device(device: int) -> None:
+    """Test hook (trw_debug_pretend_device): the library's device checks
+    compare graphs with `device` instead of the current device (negative:
+    the current device again).  Calls refuse; nothing launches elsewhere."""
+    load_library().trw_debug_pretend_device(int(device))
 
 
 class Plan:

@@ -3,6 +3,7 @@
 // Every step of a walk runs in the kernels of walk_kernels.cu and
 // prepare_kernels.cu; this file never computes a walk on the host.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -35,10 +36,65 @@ trw_status trw_fail(trw_status st, const char* fmt, ...) {
 }
 
 trw_status trw_cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // not sticky: clear it so the next call starts clean
+    return trw_fail(TRW_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
   return trw_fail(TRW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
 extern "C" const char* trw_last_error(void) { return t_last_error.c_str(); }
+
+// ------------------------------------------- allocation gate, device check
+// Two test hooks (declared in trw.h) make failures that a test could not
+// otherwise cause on a healthy one-GPU machine.  Neither can make a call do
+// anything but refuse or fail cleanly: the injected allocation failure is
+// reported as the runtime's own out-of-memory error, and the pretended device
+// only changes what the device check compares.
+
+static std::atomic<long long> g_allocs_before_failure{-1};  // -1: no injected failure
+static std::atomic<int> g_pretend_device{-1};               // -1: the current device
+
+extern "C" void trw_debug_fail_allocs(int64_t after) { g_allocs_before_failure.store(after < 0 ? -1 : after); }
+
+extern "C" void trw_debug_pretend_device(int32_t device) { g_pretend_device.store(device < 0 ? -1 : device); }
+
+// True when the test hook makes this allocation fail: once its count of
+// allocations to let through reaches zero, every later one fails until the
+// hook is reset.
+static bool injected_alloc_failure() {
+  long long n = g_allocs_before_failure.load();
+  while (n > 0 && !g_allocs_before_failure.compare_exchange_weak(n, n - 1)) {
+  }
+  return n == 0;
+}
+
+cudaError_t trw_dev_malloc(void** p, size_t bytes) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t trw_host_alloc(void** p, size_t bytes, unsigned int flags) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaHostAlloc(p, bytes, flags);
+}
+
+trw_status trw_check_device(const trw_graph* g) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return trw_cuda_fail(e, "cudaGetDevice");
+  const int pretend = g_pretend_device.load();
+  if (pretend >= 0) dev = pretend;
+  if (dev != g->device)
+    return trw_fail(TRW_ERR_INVALID, "the current device is %d but the graph lives on device %d", dev, g->device);
+  return TRW_OK;
+}
 
 // ------------------------------------------------------------ small helpers
 
@@ -64,7 +120,7 @@ trw_status trw_grow(void** p, size_t* cap, size_t need) {
   *p = nullptr;
   *cap = 0;
   size_t n = std::max(need, (size_t)4096);
-  cudaError_t e = cudaMalloc(p, n);
+  cudaError_t e = trw_dev_malloc(p, n);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return trw_fail(TRW_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
@@ -134,7 +190,7 @@ static void graph_release(trw_graph* g) {
 extern "C" void trw_graph_free(trw_graph* g) { graph_release(g); }
 
 static trw_status alloc_dev(void** p, size_t bytes, const char* what) {
-  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  cudaError_t e = trw_dev_malloc(p, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -453,6 +509,7 @@ static trw_status prepare_its_records(trw_graph* g) {
 
 extern "C" trw_status trw_prepare(trw_graph* g, uint32_t what) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (what & ~(TRW_PREP_ALIAS | TRW_PREP_LABEL_INDEX | TRW_PREP_NEIGHBOR_HASH | TRW_PREP_ROW_RECORDS | TRW_PREP_ITS |
                TRW_PREP_REJ | TRW_PREP_ITS_GUIDE))
     return trw_fail(TRW_ERR_INVALID, "unknown prepare flags 0x%x", what);
@@ -746,7 +803,8 @@ static trw_status run_bsp(trw_graph* g, const DevGraph& dg, const WalkSpec& sp, 
     trw_status st = trw_grow(&g->bsp_walkers[b], &g->bsp_cap[b], bytes);
     if (st != TRW_OK) return st;
   }
-  if (!g->bsp_host) CUDA_TRY(cudaMallocHost((void**)&g->bsp_host, sizeof(unsigned long long)), "pinned count");
+  if (!g->bsp_host)
+    CUDA_TRY(trw_host_alloc((void**)&g->bsp_host, sizeof(unsigned long long), cudaHostAllocDefault), "pinned count");
   unsigned long long* d_count = reinterpret_cast<unsigned long long*>(static_cast<char*>(g->misc) + 128);
   CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), stream), "reset count");
   CUDA_TRY(launch_bsp_init(dg, sp, g->bsp_walkers[0], d_count, g->ctrl, stream), "BSP init launch");
@@ -777,6 +835,7 @@ extern "C" trw_status trw_walk_ex(trw_graph* g, trw_algo algo, const trw_params*
                                   int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
                                   int32_t* out_lengths, trw_kernel kernel, void* stream_v, int sync) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (kernel != TRW_KERNEL_AUTO && kernel != TRW_KERNEL_PLAIN && kernel != TRW_KERNEL_PERSISTENT &&
       kernel != TRW_KERNEL_BSP)
     return trw_fail(TRW_ERR_INVALID, "unknown kernel %d", (int)kernel);
@@ -907,6 +966,7 @@ extern "C" trw_status trw_walk(trw_graph* g, trw_algo algo, const trw_params* pa
 
 extern "C" trw_status trw_sync(trw_graph* g, void* stream_v) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   std::lock_guard<std::mutex> lk(g->mu);
   return collect_status(g, stream_v ? (cudaStream_t)stream_v : g->stream);
 }
@@ -916,6 +976,7 @@ extern "C" trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw
                                      const uint64_t* seeds, int32_t* const* out_paths, int32_t* const* out_lengths,
                                      void* stream_v, int sync) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (n_requests < 1 || n_requests > TRW_MAX_BATCH)
     return trw_fail(TRW_ERR_INVALID, "n_requests must be in [1, %d]", TRW_MAX_BATCH);
   if (!algos || !sources || !n_sources || !max_lens || !seeds || !out_paths || !out_lengths)
@@ -941,7 +1002,7 @@ extern "C" trw_status trw_walk_batch(trw_graph* g, int32_t n_requests, const trw
   if (!g->batch_specs) {
     trw_status st = alloc_dev((void**)&g->batch_specs, need, "batch table");
     if (st != TRW_OK) return st;
-    CUDA_TRY(cudaMallocHost((void**)&g->batch_host, need), "pinned batch table");
+    CUDA_TRY(trw_host_alloc((void**)&g->batch_host, need, cudaHostAllocDefault), "pinned batch table");
   }
   // The pinned staging copy stays untouched until the previous copy finished.
   CUDA_TRY(cudaStreamSynchronize(stream), "batch table");
@@ -1004,6 +1065,7 @@ extern "C" trw_status trw_last_stats(const trw_graph* g, trw_stats* s) {
 
 extern "C" trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int32_t* second) {
   if (!g || !H || !first || !second) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (!g->prepared_alias) return trw_fail(TRW_ERR_NOT_PREPARED, "no alias tables");
   std::vector<AliasRec> rec((size_t)g->ne);
   if (g->ne > 0)
@@ -1018,6 +1080,7 @@ extern "C" trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* 
 
 extern "C" trw_status trw_debug_sampler_tables(const trw_graph* g, uint64_t* cdf, uint32_t* pmax) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if ((cdf && !g->its_cdf) || (pmax && !g->rej_pmax)) return trw_fail(TRW_ERR_NOT_PREPARED, "table not prepared");
   if (cdf && g->ne > 0)
     CUDA_TRY(cudaMemcpy(cdf, g->its_cdf, sizeof(uint64_t) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy ITS sums");
@@ -1028,6 +1091,7 @@ extern "C" trw_status trw_debug_sampler_tables(const trw_graph* g, uint64_t* cdf
 
 extern "C" trw_status trw_debug_its_records(const trw_graph* g, uint32_t* words) {
   if (!g || !words) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (!g->its_rec) return trw_fail(TRW_ERR_NOT_PREPARED, "no guided ITS records");
   if (g->ne > 0)
     CUDA_TRY(cudaMemcpy(words, g->its_rec, sizeof(ItsRec) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy ITS records");
@@ -1036,6 +1100,7 @@ extern "C" trw_status trw_debug_its_records(const trw_graph* g, uint32_t* words)
 
 extern "C" trw_status trw_debug_label_index(const trw_graph* g, int32_t* stride, int32_t* vrec, int32_t* erec) {
   if (!g || !stride) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   *stride = g->lerec ? g->lstride : 0;
   if (!g->lerec || !vrec || !erec) return TRW_OK;
   const size_t sw = (size_t)g->lstride;
@@ -1049,6 +1114,7 @@ extern "C" trw_status trw_debug_label_index(const trw_graph* g, int32_t* stride,
 extern "C" trw_status trw_debug_is_neighbor(const trw_graph* g, const int32_t* u, const int32_t* v, int64_t n,
                                             uint8_t* out) {
   if (!g || n < 0 || (n > 0 && (!u || !v || !out))) return trw_fail(TRW_ERR_INVALID, "bad arguments");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   for (int64_t i = 0; i < n; ++i)
     if (u[i] < 0 || u[i] >= g->nv) return trw_fail(TRW_ERR_INVALID, "vertex %d out of range", u[i]);
   if (n == 0) return TRW_OK;

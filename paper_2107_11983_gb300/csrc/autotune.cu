@@ -20,6 +20,7 @@ using namespace trw;
 extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params* params, int32_t max_len,
                                    trw_tuning* best_out) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (g->nv == 0) return trw_fail(TRW_ERR_INVALID, "empty graph");
   const int32_t len0 = std::max(1, std::min<int32_t>(max_len, 10));
   const int32_t len_max = std::max(1, std::min<int32_t>(max_len, 80));
@@ -39,9 +40,9 @@ extern "C" trw_status trw_autotune(trw_graph* g, trw_algo algo, const trw_params
   const size_t out_elems = sp.endpoints ? (size_t)n : (size_t)n * ((size_t)len_max + 1);
   int32_t *d_src = nullptr, *d_out = nullptr, *d_len = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaMalloc(&d_src, sizeof(int32_t) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(int32_t) * out_elems);
-  if (e == cudaSuccess) e = cudaMalloc(&d_len, sizeof(int32_t) * (size_t)n);
+  cudaError_t e = trw_dev_malloc((void**)&d_src, sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = trw_dev_malloc((void**)&d_out, sizeof(int32_t) * out_elems);
+  if (e == cudaSuccess) e = trw_dev_malloc((void**)&d_len, sizeof(int32_t) * (size_t)n);
   if (e == cudaSuccess) e = cudaMemcpy(d_src, src.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);

@@ -126,7 +126,7 @@ trw_status trw_walk_compact(trw_graph* g, WalkSpec sp, trw_kernel kernel, const 
     st = trw_grow((void**)&g->cmp_scratch, &g->cmp_scratch_cap,
                   sizeof(int64_t) * (size_t)(2 * (walks_per + nb_per) + 2));
   if (st != TRW_OK) return st;
-  if (!g->cmp_host) CUDA_TRY(cudaMallocHost((void**)&g->cmp_host, 2 * sizeof(int64_t)), "pinned totals");
+  if (!g->cmp_host) CUDA_TRY(trw_host_alloc((void**)&g->cmp_host, 2 * sizeof(int64_t), cudaHostAllocDefault), "pinned totals");
   const DevGraph dg = trw_dev_graph(g);
   const LaunchCfg cfg = trw_launch_cfg(g, sp.algo);
   cudaStream_t cs = g->copy_stream;

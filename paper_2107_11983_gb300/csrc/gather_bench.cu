@@ -68,8 +68,8 @@ cudaError_t run(uint64_t table_bytes, int hops, int chains, double* lps, double*
   T* t = nullptr;
   unsigned long long* sink = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaMalloc(&t, n * RB);
-  if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(unsigned long long));
+  cudaError_t e = trw_dev_malloc((void**)&t, n * RB);
+  if (e == cudaSuccess) e = trw_dev_malloc((void**)&sink, sizeof(unsigned long long));
   if (e == cudaSuccess) fill_table<RB><<<num_sms * 8, 256>>>(t, n), e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);

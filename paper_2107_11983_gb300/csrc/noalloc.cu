@@ -20,6 +20,12 @@
 // clears the control block before its kernels run, and calls that overlap on
 // the GPU (different streams, or host threads that do not serialise) race on
 // it.
+//
+// The call is synchronous on the stream it is given: its request table goes
+// up from host memory on that stream, and it returns once the walks are done
+// and their status is read back on that stream.  It waits for no other
+// stream, unless the stream given is the legacy default stream (NULL), which
+// orders itself after every blocking stream of the device.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -73,6 +79,9 @@ extern "C" trw_status trw_walk_batch_noalloc(const trw_graph* g, int32_t n_reque
                                              const uint64_t* seeds, int32_t* const* out_paths,
                                              int32_t* const* out_lengths, void* stream_v) {
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  // The graph's arrays live on one device: refuse before any launch when
+  // another one is current (its kernels would read another GPU's memory).
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (n_requests < 1 || n_requests > kNoAllocMaxRequests)
     return trw_fail(TRW_ERR_INVALID, "n_requests must be in [1, %d] (the size of the no-alloc request table)",
                     kNoAllocMaxRequests);
@@ -110,12 +119,13 @@ extern "C" trw_status trw_walk_batch_noalloc(const trw_graph* g, int32_t n_reque
     e = cudaMemcpyAsync(d_prefix, prefix, sizeof(int64_t) * ((size_t)n_requests + 1), cudaMemcpyHostToDevice, stream);
   for (int r = 0; r < n_requests && e == cudaSuccess; ++r)
     if (specs[r].nwalks > 0) e = launch_validate_sources(specs[r].sources, n_sources[r], (int32_t)g->nv, ctrl, stream);
-  const LaunchCfg cfg = trw_launch_cfg(g, MIXED);
+  // the launch configuration of trw_walk_batch for the same requests
+  const LaunchCfg cfg = trw_launch_cfg_batch(g, specs, n_requests);
   if (e == cudaSuccess)
     e = launch_walk_batch(trw_dev_graph(g), d_specs, d_prefix, n_requests, prefix[n_requests], ctrl, stream, cfg);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   Ctrl c;
-  if (e == cudaSuccess) e = cudaMemcpy(&c, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return trw_cuda_fail(e, "no-alloc batch walk");
   if (c.err == kErrRejectCap) return trw_fail(TRW_ERR_REJECT_CAP, "a rejection step exceeded %d trials", TRW_REJECT_CAP);
   if (c.err == kErrInvalid) return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");

@@ -126,6 +126,7 @@ extern "C" trw_status trw_plan_create(trw_graph* g, int32_t n_requests, const tr
   if (!out) return trw_fail(TRW_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!g) return trw_fail(TRW_ERR_INVALID, "graph is NULL");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (n_requests < 1 || n_requests > TRW_MAX_BATCH)
     return trw_fail(TRW_ERR_INVALID, "n_requests must be in [1, %d]", TRW_MAX_BATCH);
   if (!algos || !sources || !n_sources || !max_lens || !seeds || !out_paths || !out_lengths)
@@ -150,12 +151,12 @@ extern "C" trw_status trw_plan_create(trw_graph* g, int32_t n_requests, const tr
   p->total = prefix[(size_t)n_requests];
   const size_t spec_bytes = sizeof(WalkSpec) * (size_t)n_requests;
   p->table_bytes = spec_bytes + sizeof(int64_t) * ((size_t)n_requests + 1);
-  PLAN_CUDA(cudaMalloc((void**)&p->d_table, p->table_bytes), "plan table");
-  PLAN_CUDA(cudaMallocHost((void**)&p->h_table, p->table_bytes), "plan table");
+  PLAN_CUDA(trw_dev_malloc((void**)&p->d_table, p->table_bytes), "plan table");
+  PLAN_CUDA(trw_host_alloc((void**)&p->h_table, p->table_bytes, cudaHostAllocDefault), "plan table");
   std::memcpy(p->h_table, specs.data(), spec_bytes);
   std::memcpy(p->h_table + spec_bytes, prefix.data(), sizeof(int64_t) * ((size_t)n_requests + 1));
   PLAN_CUDA(cudaMemcpy(p->d_table, p->h_table, p->table_bytes, cudaMemcpyHostToDevice), "plan table");
-  PLAN_CUDA(cudaMalloc((void**)&p->ctrl, sizeof(Ctrl)), "plan control block");
+  PLAN_CUDA(trw_dev_malloc((void**)&p->ctrl, sizeof(Ctrl)), "plan control block");
   PLAN_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "plan stream");
   PLAN_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming), "plan event");
   {
@@ -171,6 +172,7 @@ extern "C" trw_status trw_plan_create(trw_graph* g, int32_t n_requests, const tr
 
 extern "C" trw_status trw_plan_set_seed(trw_plan* p, int32_t request, uint64_t seed) {
   if (!p) return trw_fail(TRW_ERR_INVALID, "plan is NULL");
+  if (trw_status dc = trw_check_device(p->g); dc != TRW_OK) return dc;
   if (request < 0 || request >= p->nreq) return trw_fail(TRW_ERR_INVALID, "request %d out of range", request);
   // The table is read by the last launch: wait for it before rewriting.
   if (p->launched) CUDA_TRY(cudaEventSynchronize(p->done), "plan wait");
@@ -185,6 +187,7 @@ extern "C" trw_status trw_plan_set_seed(trw_plan* p, int32_t request, uint64_t s
 
 extern "C" trw_status trw_plan_launch(trw_plan* p, void* stream) {
   if (!p) return trw_fail(TRW_ERR_INVALID, "plan is NULL");
+  if (trw_status dc = trw_check_device(p->g); dc != TRW_OK) return dc;
   cudaStream_t st = stream ? (cudaStream_t)stream : p->g->stream;
   CUDA_TRY(cudaGraphLaunch(p->exec, st), "plan launch");
   CUDA_TRY(cudaEventRecord(p->done, st), "plan event");
@@ -194,6 +197,7 @@ extern "C" trw_status trw_plan_launch(trw_plan* p, void* stream) {
 
 extern "C" trw_status trw_plan_sync(trw_plan* p, int64_t* moves) {
   if (!p) return trw_fail(TRW_ERR_INVALID, "plan is NULL");
+  if (trw_status dc = trw_check_device(p->g); dc != TRW_OK) return dc;
   if (p->launched) CUDA_TRY(cudaEventSynchronize(p->done), "plan wait");
   Ctrl c;
   CUDA_TRY(cudaMemcpy(&c, p->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost), "plan status");

@@ -602,9 +602,9 @@ struct BigRows {
 
 cudaError_t collect_big(int32_t nv, int64_t ne, const int32_t* row_ptr, cudaStream_t st, BigRows& br) {
   const size_t max_big = (size_t)(ne / kBigRow) + 1;
-  cudaError_t e = cudaMalloc(&br.keys, sizeof(unsigned long long) * max_big);
-  if (e == cudaSuccess) e = cudaMalloc(&br.list, sizeof(int32_t) * max_big);
-  if (e == cudaSuccess) e = cudaMalloc(&br.counters, sizeof(unsigned int) * 4);
+  cudaError_t e = trw_dev_malloc((void**)&br.keys, sizeof(unsigned long long) * max_big);
+  if (e == cudaSuccess) e = trw_dev_malloc((void**)&br.list, sizeof(int32_t) * max_big);
+  if (e == cudaSuccess) e = trw_dev_malloc((void**)&br.counters, sizeof(unsigned int) * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(br.counters, 0, sizeof(unsigned int) * 4, st);
   int64_t blocks = ((int64_t)nv + 255) / 256;
   if (blocks > 65535) blocks = 65535;
@@ -660,7 +660,7 @@ cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr,
                                  int32_t min_degree, int32_t* slots, cudaStream_t st) {
   if (nv <= 0 || ne <= 0) return cudaSuccess;
   unsigned int* d_probe = nullptr;
-  cudaError_t e = cudaMalloc(&d_probe, sizeof(unsigned int));
+  cudaError_t e = trw_dev_malloc((void**)&d_probe, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemsetAsync(d_probe, 0, sizeof(unsigned int), st);
   BigRows br;
   if (e == cudaSuccess) e = collect_big(nv, ne, row_ptr, st, br);

@@ -14,8 +14,10 @@
 //     (field by field, past L1, so a reused table entry is never read stale),
 //     runs the walks with the same step code as the batch kernels and refills
 //     a lane as soon as its walk ends, from the newest request it holds;
-//   - when the last walk of a request ends, the lane that finished it fences
-//     and writes the request's done flag to host-mapped memory.
+//   - a warp counts the walks it finished per request and adds the count to
+//     the request's completion word when it holds no more of its walks; the
+//     add that completes the request writes its status and done flag, in one
+//     word, to host-mapped memory.
 // Every wait is bounded: with no work for idle_timeout_us the kernel exits,
 // and the host relaunches it when work is pending (submit, poll, drain).
 // Queue and dispatcher state live in device memory, so nothing is lost
@@ -39,7 +41,15 @@ namespace {
 
 constexpr uint32_t kQueueCap = 1u << 16;
 constexpr int kMaxActive = 64;        // requests the dispatcher interleaves
-constexpr int kPollSkip = 3;          // iterations a walking warp waits after an empty queue poll
+constexpr int kPollSkip = 3;          // refills a walking warp skips after its first empty queue poll
+constexpr int kPollSkipMax = 24;      // ... doubling after each further empty poll, up to this many
+constexpr int64_t kDeviceCheckMax = TRW_SERVE_DEVICE_CHECK_MAX;  // device sources the dispatcher checks
+// A request's completion word (SlotRec::finished): finished walks in the low
+// 48 bits, one bit per error kind above them.  Recording an error and adding
+// a warp's count are atomics on the same word, so the add that completes the
+// request also returns every error recorded before it.
+constexpr unsigned long long kCountMask = (1ull << 48) - 1;
+constexpr int kErrBitRejectCap = 56, kErrBitInternal = 57;
 
 struct Chunk {
   unsigned long long k;   // request number
@@ -75,10 +85,10 @@ struct ServeState {       // device memory, persists across launches
 // Everything the device keeps per request slot, uploaded at submit in one copy.
 struct SlotRec {
   WalkSpec spec;                  // the request
-  unsigned long long finished;    // walks finished (zero at submit)
+  unsigned long long finished;    // completion word: walks finished, error bits (zero at submit)
   uint32_t cw;                    // walks per chunk
-  int err;                        // first error of the request (zero at submit)
   uint32_t exp_moves;             // expected moves per walk (the dispatcher's work estimate)
+  uint32_t check_n;               // device sources the dispatcher range-checks at admission (0: none)
   uint32_t pad;
   unsigned long long t_admit;     // device clock (ns): the dispatcher took the request in
   unsigned long long t_first;     // a worker loaded its descriptor (first walks start)
@@ -95,11 +105,11 @@ struct ServeDev {
   Chunk* queue;                     // [kQueueCap]
   SlotRec* slots;                   // [R]
   volatile ServeHost* host;         // device pointer to host-mapped control
-  volatile unsigned long long* done;// [R] host-mapped: k + 1 once request k finished
-  volatile int* done_err;           // [R] host-mapped: status of request k
+  volatile unsigned long long* done;// [R] host-mapped: (k + 1) << 8 | -status once request k finished
   int R;
   step::Coop coop;                  // rows this long go to the whole warp
   long long idle_ns;
+  int32_t nv;                       // vertices of the graph (the dispatcher's source check)
   unsigned long long depth;         // queued chunks the dispatcher keeps ahead of the workers
 };
 
@@ -134,12 +144,15 @@ struct ActiveSet {
 struct WarpState {
   unsigned long long ticket;      // lane 0: queue ticket held (has_ticket)
   unsigned long long pk;          // popped chunk not yet placed (pend): request
-  long long idle_since;           // last time the warp had a walk to step
+  unsigned long long fin[2];      // walks of key[e] finished here and not yet added to the request's count
+  long long idle_since;           // when the warp ran out of walks (-1: it has some)
   uint32_t wlo, whi;              // unassigned walks of key[cur]
   uint32_t pb, pe;                // popped chunk not yet placed: walk range
   int cur;                        // slot receiving new walks
   int pend;
   int has_ticket;
+  int poll_wait;                  // refills left before the next poll (after an empty one)
+  int empty_polls;                // empty polls in a row while some lanes walk
   int pad;
 };
 
@@ -172,13 +185,36 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
   for (;;) {
     int go = 1;
     unsigned long long P = 0;
-    if (lane == 0) {
-      P = ld_acquire_gpu(&st->published);
-      while (n_act < kMaxActive && disp_next < P) {
-        const int slot = (int)(disp_next % (unsigned long long)sv.R);
-        const unsigned long long n = (unsigned long long)__ldcg(&sv.slots[slot].spec.nwalks);
+    if (lane == 0) P = ld_acquire_gpu(&st->published);
+    // Admission, one request at a time.  A small request with device sources
+    // has its sources range-checked here by the whole warp; one out of range
+    // completes the request with the invalid-argument status, and no walk runs.
+    for (;;) {
+      int adm = 0, slot = 0;
+      unsigned long long n = 0, src = 0;
+      uint32_t chk = 0;
+      if (lane == 0 && n_act < kMaxActive && disp_next < P) {
+        adm = 1;
+        slot = (int)(disp_next % (unsigned long long)sv.R);
+        n = (unsigned long long)__ldcg(&sv.slots[slot].spec.nwalks);
+        chk = __ldcg(&sv.slots[slot].check_n);
+        src = __ldcg(reinterpret_cast<const unsigned long long*>(&sv.slots[slot].spec.sources));
         sv.slots[slot].t_admit = (unsigned long long)now_ns();
-        if (n > 0) {
+      }
+      if (!__shfl_sync(0xffffffffu, adm, 0)) break;
+      chk = __shfl_sync(0xffffffffu, chk, 0);
+      uint32_t bad = 0;
+      if (chk) {
+        const int32_t* s_ptr = reinterpret_cast<const int32_t*>(__shfl_sync(0xffffffffu, src, 0));
+        for (uint32_t i = (uint32_t)lane; i < chk; i += 32) bad |= (uint32_t)__ldcg(s_ptr + i) >= (uint32_t)sv.nv;
+        bad = __any_sync(0xffffffffu, bad != 0u) ? 1u : 0u;
+      }
+      if (lane == 0) {
+        if (bad) {
+          sv.slots[slot].t_first = sv.slots[slot].t_done = (unsigned long long)now_ns();
+          __threadfence_system();
+          sv.done[slot] = ((disp_next + 1) << 8) | (unsigned long long)(-kErrInvalid);
+        } else if (n > 0) {
           act->k[n_act] = disp_next;
           act->pos[n_act] = 0;
           act->n[n_act] = n;
@@ -302,28 +338,19 @@ __device__ __forceinline__ T ldcg_as(const T* p) {
   return r;
 }
 
-// Field-by-field copy of a slot's descriptor into shared memory.
+// The warp copies a slot's descriptor into shared memory: one 8-byte word per
+// lane, loaded past L1 (the slot table is rewritten between requests), so the
+// copy costs one round trip to L2.  Every lane calls it; the copy is complete
+// for every lane when it returns.
 __device__ __forceinline__ void load_spec(const WalkSpec* src, WalkSpec* dst) {
-  dst->algo = ldcg_as(&src->algo);
-  dst->max_len = ldcg_as(&src->max_len);
-  dst->wps = ldcg_as(&src->wps);
-  dst->endpoints = ldcg_as(&src->endpoints);
-  dst->key0 = ldcg_as(&src->key0);
-  dst->key1 = ldcg_as(&src->key1);
-  dst->walk_offset = ldcg_as(&src->walk_offset);
-  dst->schema_len = ldcg_as(&src->schema_len);
-  dst->T_stop = ldcg_as(&src->T_stop);
-  dst->T_ret = ldcg_as(&src->T_ret);
-  dst->T_nb = ldcg_as(&src->T_nb);
-  dst->T_far = ldcg_as(&src->T_far);
-  dst->T_lo = ldcg_as(&src->T_lo);
-  dst->T_hi = ldcg_as(&src->T_hi);
-  dst->sources = ldcg_as(&src->sources);
-  dst->out_paths = ldcg_as(&src->out_paths);
-  dst->out_lengths = ldcg_as(&src->out_lengths);
-  dst->nwalks = ldcg_as(&src->nwalks);
-  dst->schema_lo = ldcg_as(&src->schema_lo);
-  dst->schema_hi = ldcg_as(&src->schema_hi);
+  static_assert(sizeof(WalkSpec) % 8 == 0 && sizeof(WalkSpec) / 8 <= 32, "one 8-byte word per lane");
+  const int lane = threadIdx.x & 31;
+  if (lane < (int)(sizeof(WalkSpec) / 8)) {
+    const unsigned long long v = __ldcg(reinterpret_cast<const unsigned long long*>(src) + lane);
+    const unsigned sh = (unsigned)__cvta_generic_to_shared(reinterpret_cast<unsigned long long*>(dst) + lane);
+    asm volatile("st.shared.u64 [%0], %1;" ::"r"(sh), "l"(v) : "memory");
+  }
+  __syncwarp();
 }
 
 // Usable descriptor for chunk [cb, ce) of request ck?  0 if so, else the
@@ -351,12 +378,51 @@ __device__ __forceinline__ void record_bad(const ServeDev& sv, int bad, unsigned
   }
 }
 
+// Status of a completed request from the error bits of its completion word
+// (a request that met several kinds of error reports the internal one).
+__device__ __forceinline__ unsigned long long status_byte(unsigned long long word) {
+  if ((word >> kErrBitInternal) & 1ull) return (unsigned long long)(-kErrInternal);
+  if ((word >> kErrBitRejectCap) & 1ull) return (unsigned long long)(-kErrRejectCap);
+  return 0ull;
+}
+
+// Adds a warp's finished walks of slot e to the request's count and, when
+// they were the request's last, publishes the request's status and done flag
+// in one host-mapped word.  Every lane calls it: each lane's fence orders the
+// outputs of its walks (all of them, this iteration's and earlier ones)
+// before the count.
+__device__ __forceinline__ void flush_finished(const ServeDev& sv, int e, const WalkSpec* spec,
+                                               const unsigned long long* key, WarpState* wsp) {
+  __threadfence();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long cnt = wsp->fin[e];
+    wsp->fin[e] = 0;
+    const unsigned long long k = key[e];
+    const int slot = (int)(k % (unsigned long long)sv.R);
+    const unsigned long long old = atomicAdd(&sv.slots[slot].finished, cnt);
+    if ((old & kCountMask) + cnt == (unsigned long long)spec[e].nwalks) {
+      sv.slots[slot].t_done = (unsigned long long)now_ns();
+      __threadfence_system();
+      sv.done[slot] = ((k + 1) << 8) | status_byte(old);
+    }
+  }
+  __syncwarp();
+}
+
 // Worker warps hold up to two requests in two descriptor slots: the current
 // slot, which new walks come from, and the other, whose walks may still be
 // running.  Idle lanes therefore start walks of a new request at once; a chunk
-// of a third request waits until the other slot has drained.  Every lane keeps
-// the number of its own request and checks it against its slot before using
-// the slot (a mismatch is recorded and the walk ends without a write).
+// of a third request waits until the other slot has drained.  A slot takes a
+// new request only when none of its lanes is running and its finished walks
+// have been counted.
+//
+// The step itself is the batch kernels' (the descriptor comes from shared
+// memory instead of a kernel argument).  Finished walks are counted per warp
+// and slot, and added to the request's count only when the warp holds no more
+// walks of that request: one atomic per warp and request instead of one per
+// finishing iteration, which for a large request would all land on the same
+// address.
 // COOP compiles in the warp-cooperative MetaPath scan and Node2Vec search
 // (needed only when a graph without the label index or neighbour hash is
 // tuned to use them); without it the kernel fits four blocks per SM.
@@ -384,11 +450,14 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
     WarpState w0;
     w0.ticket = 0;
     w0.pk = 0;
-    w0.idle_since = now_ns();
+    w0.fin[0] = w0.fin[1] = 0;
+    w0.idle_since = -1;
     w0.wlo = w0.whi = w0.pb = w0.pe = 0;
     w0.cur = 0;
     w0.pend = 0;
     w0.has_ticket = 0;
+    w0.poll_wait = 0;
+    w0.empty_polls = 0;
     w0.pad = 0;
     *wsp = w0;
   }
@@ -402,33 +471,63 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
   step::Walker W;
   step::walker_init(W, 0u, 0);
   bool active = false;
-  int64_t walk = 0;
+  uint32_t walk = 0;                  // this lane's walk within its request (walk ids are 32-bit)
   int ent = 0;                        // this lane's slot
-  unsigned long long my_k = ~0ull;    // this lane's request
   unsigned long long moves_acc = 0;
-  // After an empty poll of the queue while some lanes still walk, the warp
-  // skips its next polls for a few iterations: a poll is a round trip to L2
-  // that would otherwise precede every step of the warp's remaining walks.
-  int poll_wait = 0;
+  unsigned act_mask = 0;              // lanes with a walk (warp-uniform)
 
   for (;;) {
-    unsigned idle = __ballot_sync(0xffffffffu, !active);
-    if (idle != 0u) {
-    // the warp's bookkeeping, loaded for this refill and stored back below
+    if (act_mask != 0xffffffffu) {
+    unsigned idle = ~act_mask;
     int cur = wsp->cur;
     uint32_t wlo = wsp->wlo, whi = wsp->whi;
+    if (wlo < whi) {
+      // Fast path: idle lanes take walks left in the current chunk.
+      const int take = (int)min((uint32_t)__popc(idle), whi - wlo);
+      const int rank = __popc(idle & lt_mask);
+      if (((idle >> lane) & 1u) && rank < take) {
+        const WalkSpec& sp = spec[cur];
+        ent = cur;
+        walk = wlo + (uint32_t)rank;
+        const int32_t src = __ldcg(sp.sources + walk / sp.wps);
+        step::walker_init(W, sp.walk_offset + walk, src);
+        if (!sp.endpoints) {
+          st.gpos = (int64_t)walk * ((int64_t)sp.max_len + 1);
+          st.lo = (int)(st.gpos & 7);
+          step::stage_put(st, sp.out_paths, src, (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0);
+        }
+        active = true;
+      }
+      wlo += (uint32_t)take;
+      idle = __ballot_sync(0xffffffffu, !active);
+      act_mask = ~idle;
+      __syncwarp();
+      if (lane == 0) wsp->wlo = wlo;
+      __syncwarp();
+    }
+    // A partly busy warp that is waiting out its poll backoff only counts down.
+    const bool skip_poll = idle != 0u && idle != 0xffffffffu && wsp->poll_wait > 0 && wsp->pend == 0;
+    if (skip_poll) {
+      __syncwarp();
+      if (lane == 0) wsp->poll_wait -= 1;
+      __syncwarp();
+    }
+    if (idle != 0u && !skip_poll) {
+    // the rest of the warp's bookkeeping, loaded for this refill and stored back below
     bool pend = wsp->pend != 0;
     bool has_ticket = wsp->has_ticket != 0;   // lane 0's
     unsigned long long ticket = wsp->ticket;
     unsigned long long pk = wsp->pk;
     uint32_t pb = wsp->pb, pe = wsp->pe;
+    // After an empty poll of the queue while some lanes still walk, the warp
+    // skips its next polls for a few refills: a poll is a round trip to L2
+    // that would otherwise precede every step of the warp's remaining walks.
+    int poll_wait = 0;
+    int empty_polls = wsp->empty_polls;
+    const unsigned was_active = act_mask;
     while (idle != 0u) {
       if (wlo >= whi) {
         if (!pend) {
-          if (poll_wait > 0 && idle != 0xffffffffu) {
-            --poll_wait;
-            break;
-          }
           unsigned long long ck = 0;
           uint32_t cb = 0, ce = 0;
           int got = 0;
@@ -458,9 +557,13 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
           }
           got = __shfl_sync(0xffffffffu, got, 0);
           if (!got) {
-            poll_wait = idle != 0xffffffffu ? kPollSkip : 0;
+            if (idle != 0xffffffffu) {  // lanes still walk: back off before the next poll
+              poll_wait = min(kPollSkip << min(empty_polls, 3), kPollSkipMax);
+              ++empty_polls;
+            }
             break;
           }
+          empty_polls = 0;
           ck = __shfl_sync(0xffffffffu, ck, 0);
           cb = __shfl_sync(0xffffffffu, cb, 0);
           ce = __shfl_sync(0xffffffffu, ce, 0);
@@ -483,14 +586,15 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
           continue;
         }
         // a slot takes a new request only once none of its lanes is running
-        const bool other_busy = __ballot_sync(0xffffffffu, active && ent == other) != 0u;
-        const bool cur_busy = __ballot_sync(0xffffffffu, active && ent == cur) != 0u;
+        const bool other_busy = (act_mask & __ballot_sync(0xffffffffu, ent == other)) != 0u;
+        const bool cur_busy = (act_mask & __ballot_sync(0xffffffffu, ent == cur)) != 0u;
         const int tgt = !other_busy ? other : (!cur_busy ? cur : -1);
         if (tgt < 0) break;
+        if (wsp->fin[tgt] != 0) flush_finished(sv, tgt, spec, key, wsp);  // counted before it changes hands
         int bad = 0;
+        load_spec(&sv.slots[(int)(pk % (unsigned long long)sv.R)].spec, &spec[tgt]);
         if (lane == 0) {
           atomicCAS(&sv.slots[(int)(pk % (unsigned long long)sv.R)].t_first, 0ull, (unsigned long long)now_ns());
-          load_spec(&sv.slots[(int)(pk % (unsigned long long)sv.R)].spec, &spec[tgt]);
           bad = spec_check(spec[tgt], pk, pb, pe, ld_acquire_gpu(&sv.state->published));
           if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec[tgt].nwalks,
                               reinterpret_cast<uintptr_t>(spec[tgt].out_paths));
@@ -510,12 +614,11 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
       if (((idle >> lane) & 1u) && rank < take) {
         const WalkSpec& sp = spec[cur];
         ent = cur;
-        my_k = key[cur];
-        walk = (int64_t)wlo + rank;
+        walk = wlo + (uint32_t)rank;
         const int32_t src = __ldcg(sp.sources + walk / sp.wps);
-        step::walker_init(W, sp.walk_offset + (uint32_t)walk, src);
+        step::walker_init(W, sp.walk_offset + walk, src);
         if (!sp.endpoints) {
-          st.gpos = walk * ((int64_t)sp.max_len + 1);
+          st.gpos = (int64_t)walk * ((int64_t)sp.max_len + 1);
           st.lo = (int)(st.gpos & 7);
           step::stage_put(st, sp.out_paths, src, (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0);
         }
@@ -523,9 +626,13 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
       }
       wlo += (uint32_t)take;
       idle = __ballot_sync(0xffffffffu, !active);
+      act_mask = ~idle;
     }
     __syncwarp();
     if (lane == 0) {
+      if (act_mask != was_active) wsp->idle_since = -1;  // walks started: the warp is not idle
+      wsp->poll_wait = poll_wait;
+      wsp->empty_polls = empty_polls;
       wsp->cur = cur;
       wsp->wlo = wlo;
       wsp->whi = whi;
@@ -538,38 +645,42 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
     }
     __syncwarp();
     }
+    }
 
-    if (!__any_sync(0xffffffffu, active)) {
-      // Idle: wait for chunks until the dispatcher ends the launch (with an
-      // absolute bound of 1000 idle timeouts should it never do so).
+    if (act_mask == 0u) {
+      // Idle: lane 0 waits until the queue holds the entry of this warp's
+      // ticket (then the warp refills), the dispatcher ends the launch and no
+      // entry waits for this warp, or an absolute bound of 1000 idle timeouts
+      // passes should the dispatcher never end it.  The other lanes wait at the
+      // shuffle: an idle warp takes few issue slots from the warps that walk.
       int go = 1;
       if (lane == 0) {
-        const long long t = now_ns();
-        const unsigned long long tl = ld_acquire_gpu(&sv.state->q_tail);
+        if (wsp->idle_since < 0) wsp->idle_since = now_ns();
+        const long long idle_since = wsp->idle_since;
         const bool has_ticket = wsp->has_ticket != 0;
         const unsigned long long ticket = wsp->ticket;
-        // leave once the dispatcher ended the launch and no entry waits for this warp
-        if (*(volatile int*)&sv.state->exit_now && (!has_ticket || ticket >= tl))
-          go = 0;
-        else if (t - wsp->idle_since > 1000 * sv.idle_ns) go = 0;
-        else {
+        for (;;) {
+          const unsigned long long tl = ld_acquire_gpu(&sv.state->q_tail);
+          if (!has_ticket || ticket < tl) break;  // refill: take a ticket, or read the entry
+          if (*(volatile int*)&sv.state->exit_now) {
+            go = 0;
+            break;
+          }
+          if (now_ns() - idle_since > 1000 * sv.idle_ns) {
+            go = 0;
+            break;
+          }
           // warps whose ticket is near the tail poll often, the rest back off
-          const unsigned long long dist = has_ticket && ticket > tl ? ticket - tl : 0;
+          const unsigned long long dist = ticket - tl;
           __nanosleep(dist < 64 ? 256u : dist < 512 ? 2000u : 8000u);
         }
       }
       if (!__shfl_sync(0xffffffffu, go, 0)) break;
       continue;
     }
-    if (lane == 0) wsp->idle_since = now_ns();
 
+    // ---- one unit of work per active lane (the batch kernels' step)
     bool finishing = false;
-    const bool mine = active && key[ent] == my_k;
-    if (active && !mine) {
-      // the slot no longer holds this lane's request: record, stop, write nothing
-      record_bad(sv, 6, my_k, (unsigned long long)walk, key[ent], (unsigned long long)ent);
-      active = false;
-    }
     const WalkSpec& sp = spec[ent];
     int r = step::kIdle;
     int32_t next = -1;
@@ -577,16 +688,15 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
     pend_work.kind = 0;
     pend_work.res = 0;
     if constexpr (COOP) {
-      if (mine) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend_work, sv.coop);
+      if (active) r = step::step_begin_dispatch<MIXED>(g, sp, W, next, pend_work, sv.coop);
       if (__any_sync(0xffffffffu, r == step::kDefer)) {
         step::warp_resolve(g, r, W, pend_work);
         if (r == step::kDefer) r = step::step_finish(g, sp, W, pend_work, next);
       }
     } else {
-      if (mine) r = step::step_begin_dispatch<MIXED, true>(g, sp, W, next, pend_work, step::Coop{0x7fffffff, 0x7fffffff});
+      if (active) r = step::step_begin_dispatch<MIXED>(g, sp, W, next, pend_work, step::Coop{0x7fffffff, 0x7fffffff});
     }
-    if (mine) {
-      const int slot = (int)(my_k % (unsigned long long)sv.R);
+    if (active) {
       const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
       if (r == step::kMoved) {
         step::advance(W, next);
@@ -594,11 +704,9 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
       } else if (r == step::kRetry) {
         W.att += 1;
       } else {
-        if (r == step::kFail) atomicCAS(&sv.slots[slot].err, 0, kErrRejectCap);
-        if (r == step::kBroken) {
-          atomicCAS(&sv.slots[slot].err, 0, kErrInternal);
-          record_bad(sv, 5, my_k, (unsigned long long)walk, (unsigned long long)(uint32_t)W.cur,
-                     ((unsigned long long)(uint32_t)W.off << 32) | (uint32_t)W.d);
+        if (r == step::kFail || r == step::kBroken) {
+          const int slot = (int)(key[ent] % (unsigned long long)sv.R);
+          atomicOr(&sv.slots[slot].finished, 1ull << (r == step::kFail ? kErrBitRejectCap : kErrBitInternal));
         }
         if (sp.endpoints) __stcs(sp.out_paths + walk, W.cur);
         else step::stage_finish(st, sp.out_paths, aligned);
@@ -608,33 +716,29 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
         active = false;
       }
     }
-    // Completion, per slot: every finishing lane of slot e belongs to key[e].
-    const unsigned fin0 = __ballot_sync(0xffffffffu, finishing && ent == 0);
-    const unsigned fin1 = __ballot_sync(0xffffffffu, finishing && ent == 1);
-    if (fin0 | fin1) {
-      __threadfence();  // outputs of the finishing lanes before their count
-      __syncwarp();
-      if (lane == 0) {
-        for (int e = 0; e < 2; ++e) {
-          const unsigned fin = e == 0 ? fin0 : fin1;
-          if (!fin) continue;
-          const unsigned long long k = key[e];
-          const int slot = (int)(k % (unsigned long long)sv.R);
-          const unsigned long long cnt = (unsigned long long)__popc(fin);
-          const unsigned long long old = atomicAdd(&sv.slots[slot].finished, cnt);
-          if (old + cnt == (unsigned long long)spec[e].nwalks) {
-            sv.slots[slot].t_done = (unsigned long long)now_ns();
-            __threadfence();
-            const int err = atomicAdd(&sv.slots[slot].err, 0);
-            sv.done_err[slot] = err;
-            __threadfence_system();
-            sv.done[slot] = k + 1;
-            __threadfence_system();
-          }
-        }
+    const unsigned fin = __ballot_sync(0xffffffffu, finishing);
+    if (fin) {
+      // Count the finished walks per slot; hand a slot's count to its request
+      // once the warp holds no more of its walks (none running, none left in
+      // the current chunk).
+      act_mask &= ~fin;
+      const unsigned in1 = __ballot_sync(0xffffffffu, ent == 1);
+      const int cur = wsp->cur;
+      const bool left = wsp->wlo < wsp->whi;
+      for (int e = 0; e < 2; ++e) {
+        const unsigned fe = fin & (e ? in1 : ~in1);
+        if (!fe) continue;
+        if (lane == 0) wsp->fin[e] += (unsigned long long)__popc(fe);
+        __syncwarp();
+        const unsigned re = act_mask & (e ? in1 : ~in1);
+        if (re == 0u && !(cur == e && left)) flush_finished(sv, e, spec, key, wsp);
       }
     }
   }
+  // Nothing is left to count at exit (a warp leaves only when idle, after its
+  // last walks' counts were handed over); flushing again is harmless.
+  for (int e = 0; e < 2; ++e)
+    if (wsp->fin[e] != 0) flush_finished(sv, e, spec, key, wsp);
   const unsigned long long mv = step::warp_sum(moves_acc);
   if (lane == 0) {
     if (mv) atomicAdd(&sv.state->moves, mv);
@@ -661,10 +765,8 @@ struct trw_server {
   int64_t src_cap = 0;
   ServeHost* host = nullptr;           // mapped
   unsigned long long* done = nullptr;  // mapped [R]
-  int* done_err = nullptr;             // mapped [R]
   ServeHost* host_dev = nullptr;
   unsigned long long* done_dev = nullptr;
-  int* done_err_dev = nullptr;
   SlotRec* slot_stage = nullptr;       // pinned staging [R]
   unsigned long long* pub_stage = nullptr;  // pinned [R]: the count that publishes request k is pub_stage[k % R]
   int32_t* check_buf = nullptr;        // pinned: host copy of device sources for the range check
@@ -703,7 +805,6 @@ static void server_release(trw_server* s) {
   cudaFree(s->src_pool);
   if (s->host) cudaFreeHost(s->host);
   if (s->done) cudaFreeHost(s->done);
-  if (s->done_err) cudaFreeHost(s->done_err);
   if (s->slot_stage) cudaFreeHost(s->slot_stage);
   if (s->pub_stage) cudaFreeHost(s->pub_stage);
   if (s->check_buf) cudaFreeHost(s->check_buf);
@@ -722,6 +823,7 @@ static void server_release(trw_server* s) {
 extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg_in, trw_server** out) {
   if (!g || !out) return trw_fail(TRW_ERR_INVALID, "NULL argument");
   *out = nullptr;
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   trw_serve_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else trw_serve_config_default(&cfg);
@@ -739,23 +841,20 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   SV_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking), "stream");
   SV_TRY(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "stream");
   SV_TRY(cudaEventCreateWithFlags(&s->ev_after, cudaEventDisableTiming), "event");
-  SV_TRY(cudaMalloc(&s->state, sizeof(ServeState)), "serve state");
+  SV_TRY(trw_dev_malloc((void**)&s->state, sizeof(ServeState)), "serve state");
   SV_TRY(cudaMemset(s->state, 0, sizeof(ServeState)), "serve state");
-  SV_TRY(cudaMalloc(&s->queue, sizeof(Chunk) * kQueueCap), "chunk queue");
-  SV_TRY(cudaMalloc(&s->slots, sizeof(SlotRec) * R), "slot table");
+  SV_TRY(trw_dev_malloc((void**)&s->queue, sizeof(Chunk) * kQueueCap), "chunk queue");
+  SV_TRY(trw_dev_malloc((void**)&s->slots, sizeof(SlotRec) * R), "slot table");
   SV_TRY(cudaMemset(s->slots, 0, sizeof(SlotRec) * R), "slot table");
-  SV_TRY(cudaMalloc(&s->src_pool, sizeof(int32_t) * (size_t)s->src_cap), "source pool");
-  SV_TRY(cudaHostAlloc(&s->host, sizeof(ServeHost), cudaHostAllocMapped), "mapped control");
-  SV_TRY(cudaHostAlloc(&s->done, sizeof(unsigned long long) * R, cudaHostAllocMapped), "mapped flags");
-  SV_TRY(cudaHostAlloc(&s->done_err, sizeof(int) * R, cudaHostAllocMapped), "mapped flags");
-  SV_TRY(cudaHostAlloc(&s->slot_stage, sizeof(SlotRec) * R, cudaHostAllocDefault), "pinned staging");
-  SV_TRY(cudaHostAlloc(&s->pub_stage, sizeof(unsigned long long) * R, cudaHostAllocDefault), "pinned staging");
+  SV_TRY(trw_dev_malloc((void**)&s->src_pool, sizeof(int32_t) * (size_t)s->src_cap), "source pool");
+  SV_TRY(trw_host_alloc((void**)&s->host, sizeof(ServeHost), cudaHostAllocMapped), "mapped control");
+  SV_TRY(trw_host_alloc((void**)&s->done, sizeof(unsigned long long) * R, cudaHostAllocMapped), "mapped flags");
+  SV_TRY(trw_host_alloc((void**)&s->slot_stage, sizeof(SlotRec) * R, cudaHostAllocDefault), "pinned staging");
+  SV_TRY(trw_host_alloc((void**)&s->pub_stage, sizeof(unsigned long long) * R, cudaHostAllocDefault), "pinned staging");
   std::memset((void*)s->host, 0, sizeof(ServeHost));
   std::memset((void*)s->done, 0, sizeof(unsigned long long) * R);
-  std::memset((void*)s->done_err, 0, sizeof(int) * R);
   SV_TRY(cudaHostGetDevicePointer((void**)&s->host_dev, (void*)s->host, 0), "mapped pointer");
   SV_TRY(cudaHostGetDevicePointer((void**)&s->done_dev, (void*)s->done, 0), "mapped pointer");
-  SV_TRY(cudaHostGetDevicePointer((void**)&s->done_err_dev, (void*)s->done_err, 0), "mapped pointer");
   s->req_walks.assign(R, 0);
   s->req_bytes.assign(R, 0);
   s->req_src_pos.assign(R, 0);
@@ -789,10 +888,10 @@ static cudaError_t launch_if_idle(trw_server* s) {
   sv.slots = s->slots;
   sv.host = s->host_dev;
   sv.done = s->done_dev;
-  sv.done_err = s->done_err_dev;
   sv.R = s->R;
   sv.coop = step::Coop{s->g->tuning.coop_degree, s->g->tuning.search_degree};
   sv.idle_ns = (long long)s->cfg.idle_timeout_us * 1000;
+  sv.nv = (int32_t)s->g->nv;
   {
     // enough queued chunks to cover the workers' claims between dispatcher rounds
     const unsigned long long workers = (unsigned long long)s->grid_blocks * (s->block_threads / 32);
@@ -811,8 +910,8 @@ static cudaError_t launch_if_idle(trw_server* s) {
   // the cooperative variant only when the tuning asks for a warp path that no
   // prepared table replaces
   const trw_graph* g = s->g;
-  const bool coop = (g->tuning.coop_degree < 0x7fffffff && !g->lerec) ||
-                    (g->tuning.search_degree < 0x7fffffff && !g->nh_slots);
+  const bool coop = (g->labels && !g->lerec && g->tuning.coop_degree < 0x7fffffff) ||
+                    (!g->nh_slots && g->tuning.search_degree < 0x7fffffff);
   if (coop)
     serve_kernel<true><<<s->grid_blocks_coop, s->block_threads, s->smem, s->stream>>>(trw_dev_graph(g), sv);
   else
@@ -827,6 +926,7 @@ static void retire_front(trw_server* s) {
 
 extern "C" trw_status trw_serve_order_after(trw_server* s, void* stream) {
   if (!s || !stream) return trw_fail(TRW_ERR_INVALID, "NULL server or stream");
+  if (trw_status dc = trw_check_device(s->g); dc != TRW_OK) return dc;
   std::lock_guard<std::mutex> lk(s->mu);
   cudaError_t e = cudaEventRecord(s->ev_after, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, s->ev_after, 0);
@@ -838,6 +938,7 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
                                        int64_t n_sources, int32_t max_len, uint64_t seed, int32_t* out_paths,
                                        int32_t* out_lengths, uint64_t* req_id) {
   if (!s || !req_id) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (trw_status dc = trw_check_device(s->g); dc != TRW_OK) return dc;
   WalkSpec sp;
   trw_status stt = trw_make_spec(s->g, algo, params, n_sources, max_len, seed, &sp);
   if (stt != TRW_OK) return stt;
@@ -877,14 +978,17 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
     }
   }
   if (pos < 0) return trw_fail(TRW_ERR_BUSY, "source pool full");
-  if (src_dev && n_sources > 0) {
+  // Device sources of a small request are range-checked by the dispatcher
+  // when it admits the request; larger ones here, through pinned memory.
+  const bool dev_check = src_dev && n_sources > 0 && n_sources <= kDeviceCheckMax;
+  if (src_dev && n_sources > 0 && !dev_check) {
     // device sources: one copy to pinned memory and a host range check
     // before anything is queued
     if (n_sources > s->check_cap) {
       if (s->check_buf) cudaFreeHost(s->check_buf);
       s->check_buf = nullptr;
       s->check_cap = 0;
-      const cudaError_t ea = cudaHostAlloc(&s->check_buf, sizeof(int32_t) * (size_t)n_sources, cudaHostAllocDefault);
+      const cudaError_t ea = trw_host_alloc((void**)&s->check_buf, sizeof(int32_t) * (size_t)n_sources, cudaHostAllocDefault);
       if (ea != cudaSuccess) return trw_cuda_fail(ea, "serve source check buffer");
       s->check_cap = n_sources;
     }
@@ -914,8 +1018,8 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   rec.spec = sp;
   rec.finished = 0;
   rec.cw = cw;
-  rec.err = 0;
   rec.exp_moves = (uint32_t)std::max(1.0, std::ceil(exp_moves));
+  rec.check_n = dev_check ? (uint32_t)n_sources : 0u;
   rec.pad = 0;
   rec.t_admit = rec.t_first = rec.t_done = 0;
   // Nothing below waits for the device: the sources, the slot record and
@@ -924,7 +1028,6 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   // collected, when their copies have long completed.
   cudaStream_t cs = s->copy_stream;
   s->done[slot] = 0;
-  s->done_err[slot] = 0;
   cudaError_t e = cudaSuccess;
   if (pool_n > 0)
     e = cudaMemcpyAsync(s->src_pool + pos, sources, sizeof(int32_t) * (size_t)pool_n, cudaMemcpyHostToDevice, cs);
@@ -944,7 +1047,7 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   s->src_head = pos + pool_n;
   s->next_k = k + 1;
   if (sp.nwalks == 0) {
-    s->done[slot] = k + 1;  // nothing to run
+    s->done[slot] = (k + 1) << 8;  // nothing to run
   }
   std::atomic_thread_fence(std::memory_order_seq_cst);
   e = launch_if_idle(s);
@@ -970,7 +1073,7 @@ static trw_status poll_locked(trw_server* s, uint64_t k) {
   const int slot = (int)(k % (unsigned long long)s->R);
   if (s->collected[slot]) return trw_fail(TRW_ERR_NOT_FOUND, "request %llu already collected", (unsigned long long)k);
   const unsigned long long d = reinterpret_cast<volatile unsigned long long*>(s->done)[slot];
-  if (d != k + 1) {
+  if ((d >> 8) != k + 1) {
     cudaError_t e = launch_if_idle(s);
     if (e != cudaSuccess) return trw_cuda_fail(e, "serve kernel relaunch");
     if ((++s->polls & 63) == 0) {
@@ -980,7 +1083,7 @@ static trw_status poll_locked(trw_server* s, uint64_t k) {
     return TRW_PENDING;
   }
   std::atomic_thread_fence(std::memory_order_acquire);
-  const int err = reinterpret_cast<volatile int*>(s->done_err)[slot];
+  const int err = -(int)(d & 0xffu);
   s->collected[slot] = 1;
   s->inflight_walks -= s->req_walks[slot];
   s->inflight_bytes -= s->req_bytes[slot];
@@ -993,12 +1096,14 @@ static trw_status poll_locked(trw_server* s, uint64_t k) {
 
 extern "C" trw_status trw_serve_poll(trw_server* s, uint64_t req_id) {
   if (!s) return trw_fail(TRW_ERR_INVALID, "NULL server");
+  if (trw_status dc = trw_check_device(s->g); dc != TRW_OK) return dc;
   std::lock_guard<std::mutex> lk(s->mu);
   return poll_locked(s, req_id);
 }
 
 extern "C" trw_status trw_serve_reap(trw_server* s, uint64_t* ids, int32_t* statuses, int32_t max, int32_t* n_out) {
   if (!s || !n_out || max < 0 || (max > 0 && (!ids || !statuses))) return trw_fail(TRW_ERR_INVALID, "bad arguments");
+  if (trw_status dc = trw_check_device(s->g); dc != TRW_OK) return dc;
   *n_out = 0;
   std::lock_guard<std::mutex> lk(s->mu);
   int32_t n = 0;
@@ -1007,12 +1112,12 @@ extern "C" trw_status trw_serve_reap(trw_server* s, uint64_t* ids, int32_t* stat
     const int slot = (int)(k % (unsigned long long)s->R);
     if (s->collected[slot]) continue;
     const unsigned long long d = reinterpret_cast<volatile unsigned long long*>(s->done)[slot];
-    if (d != k + 1) {
+    if ((d >> 8) != k + 1) {
       pending = true;
       continue;
     }
     std::atomic_thread_fence(std::memory_order_acquire);
-    const int err = reinterpret_cast<volatile int*>(s->done_err)[slot];
+    const int err = -(int)(d & 0xffu);
     s->collected[slot] = 1;
     s->inflight_walks -= s->req_walks[slot];
     s->inflight_bytes -= s->req_bytes[slot];
@@ -1035,6 +1140,7 @@ extern "C" trw_status trw_serve_reap(trw_server* s, uint64_t* ids, int32_t* stat
 
 extern "C" trw_status trw_serve_trace(trw_server* s, uint64_t req_id, uint64_t* t_ns) {
   if (!s || !t_ns) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (trw_status dc = trw_check_device(s->g); dc != TRW_OK) return dc;
   std::lock_guard<std::mutex> lk(s->mu);
   if (req_id >= s->next_k || req_id + (unsigned long long)s->R < s->next_k)
     return trw_fail(TRW_ERR_NOT_FOUND, "request %llu is not in the slot table", (unsigned long long)req_id);
@@ -1049,6 +1155,7 @@ extern "C" trw_status trw_serve_trace(trw_server* s, uint64_t req_id, uint64_t* 
 
 extern "C" trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms) {
   if (!s) return trw_fail(TRW_ERR_INVALID, "NULL server");
+  if (trw_status dc = trw_check_device(s->g); dc != TRW_OK) return dc;
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     {
@@ -1058,7 +1165,7 @@ extern "C" trw_status trw_serve_drain(trw_server* s, int32_t timeout_ms) {
         const int slot = (int)(k % (unsigned long long)s->R);
         if (s->collected[slot]) continue;
         const unsigned long long d = reinterpret_cast<volatile unsigned long long*>(s->done)[slot];
-        if (d != k + 1) pending = true;
+        if ((d >> 8) != k + 1) pending = true;
       }
       if (!pending) return check_state(s);
       cudaError_t e = launch_if_idle(s);

@@ -24,7 +24,7 @@ trw_status grow_pinned(void** p, size_t* cap, size_t need) {
   *p = nullptr;
   *cap = 0;
   const size_t bytes = std::max<size_t>(need, 64);
-  if (cudaMallocHost(p, bytes) != cudaSuccess) {
+  if (trw_host_alloc(p, bytes, cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return trw_fail(TRW_ERR_OOM, "pinned host allocation of %zu bytes failed", bytes);
@@ -57,6 +57,7 @@ extern "C" trw_status trw_walk_stream(trw_graph* g, trw_algo algo, const trw_par
                                       int64_t n_sources, int32_t max_len, uint64_t seed, int64_t slice_walks,
                                       trw_stream_fn fn, void* user) {
   if (!g || !fn) return trw_fail(TRW_ERR_INVALID, "NULL graph or consumer");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   if (slice_walks < 1) return trw_fail(TRW_ERR_INVALID, "slice_walks must be >= 1");
   WalkSpec sp;
   trw_status st = trw_make_spec(g, algo, params, n_sources, max_len, seed, &sp);
@@ -230,6 +231,7 @@ extern "C" trw_status trw_walk_to_file(trw_graph* g, trw_algo algo, const trw_pa
                                        int64_t n_sources, int32_t max_len, uint64_t seed, const char* paths_file,
                                        const char* lengths_file) {
   if (!g || !paths_file || !lengths_file) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
   WalkSpec sp;
   trw_status st = trw_make_spec(g, algo, params, n_sources, max_len, seed, &sp);
   if (st != TRW_OK) return st;

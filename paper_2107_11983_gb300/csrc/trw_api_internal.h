@@ -86,6 +86,8 @@ trw_status trw_cuda_fail(cudaError_t e, const char* what);
     if (e__ != cudaSuccess) return trw_cuda_fail(e__, what); \
   } while (0)
 bool trw_is_device_ptr(const void* p);
+// TRW_ERR_INVALID unless the current device is the one the graph was loaded on.
+trw_status trw_check_device(const trw_graph* g);
 trw_status trw_grow(void** p, size_t* cap, size_t need);
 trw_status trw_make_spec(const trw_graph* g, trw_algo algo, const trw_params* p, int64_t n_sources, int32_t max_len,
                          uint64_t seed, trw::WalkSpec* sp, bool allow_compact = false);

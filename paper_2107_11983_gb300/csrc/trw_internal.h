@@ -75,3 +75,8 @@ cudaError_t launch_debug_philox(const uint32_t* d_ctr, int64_t n, uint32_t k0, u
                                 cudaStream_t st);
 
 }  // namespace trw
+
+// Every device and pinned host allocation of the library goes through these
+// two (the allocation-failure test hook of trw.h sits here).
+cudaError_t trw_dev_malloc(void** p, size_t bytes);
+cudaError_t trw_host_alloc(void** p, size_t bytes, unsigned int flags);

@@ -219,6 +219,44 @@ def test_serve_device_source_check_and_reap(served, server_factory):
     assert e.value.status == -8
 
 
+def test_serve_small_device_sources_checked_on_device(served, server_factory):
+    """A small request's device sources are range-checked when the server
+    admits it: one out of range completes that request with ERR_INVALID at
+    reap, writes nothing, and the requests around it match the oracle."""
+    g, G = served
+    S = server_factory(G, max_requests=32)
+    rng = np.random.default_rng(21)
+    reqs = [make_request(g, i, rng) for i in range(8)]
+    bad_src = torch.from_numpy(synth.sources(500, g.nv, seed=78)).cuda()
+    bad_src[321] = g.nv + 5
+    neg_src = torch.from_numpy(synth.sources(3, g.nv, seed=79)).cuda()
+    neg_src[2] = -1
+    live, bad_ids = {}, {}
+    for i, r in enumerate(reqs):
+        rid, op, ol = submit(S, dict(r, sources=torch.from_numpy(r["sources"]).cuda()))
+        live[rid] = (r, op, ol)
+        if i in (2, 5):
+            src = bad_src if i == 2 else neg_src
+            n = int(src.shape[0])
+            bop = torch.full((n, 41), -1, dtype=torch.int32, device="cuda")
+            bol = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+            bad_ids[S.submit(trw.DEEPWALK, src, 40, 3, bop, bol)] = (bop, bol)
+    statuses = {}
+    t = time.time()
+    while len(statuses) < len(live) + len(bad_ids):
+        for rid, st in S.reap():
+            statuses[rid] = st
+        assert time.time() - t < 60, "requests did not finish"
+        time.sleep(0.0005)
+    torch.cuda.synchronize()
+    for rid, (bop, bol) in bad_ids.items():
+        assert statuses[rid] == -1
+        assert bool((bol == -1).all()) and bool((bop == -1).all())
+    for rid, (r, op, ol) in live.items():
+        assert statuses[rid] == 0
+        check(g, r, op, ol)
+
+
 def test_serve_trace_timeline(served, server_factory):
     """Every served request carries a device timeline: admitted, started and
     finished, in that order."""

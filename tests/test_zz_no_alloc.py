@@ -1,19 +1,25 @@
-"""The no-allocation batch walk (GPU only), for callers that must not
-allocate device memory during a call -- e.g. while their own memory pool
-owns the free device memory, or where cudaMalloc/cudaFree would synchronise
-the device.  It calls trw_walk_batch_noalloc through the C ABI and checks its
-paths and lengths against trw_walk_batch, bit for bit (the tolerance of every
-walk test here), on two calls in a row that share the library's fixed
-scratch array.  Collected last so that a failure here leaves every other
-test already run."""
+"""The no-allocation batch walk (GPU only).
+
+trw_walk_batch_noalloc is for callers that must not allocate device memory
+during a call: code that runs while the caller's own memory pool owns the
+free device memory, code under an allocator that must see every allocation,
+or a path where cudaMalloc/cudaFree would synchronise the device.  These tests
+call it through the C ABI and check, on two calls in a row that share the
+library's fixed scratch array, its paths and lengths against the oracle and
+against trw_walk_batch, bit for bit (the tolerance of every walk test here);
+that a call leaves the device's free memory unchanged and still succeeds when
+every allocation the library makes is forced to fail; and the NULL stream.
+Collected last but one (the full-size file is slower) so that a failure here
+leaves every other test already run."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2107_11983_gb300 as trw
 import synth
-from gpu_common import rmat_graph
+from gpu_common import assert_paths_equal, oracle_alias, rmat_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -38,8 +44,9 @@ def _requests(g):
     ]
 
 
-def _call_noalloc(G, reqs):
-    """Marshal the requests and call the C entry point directly."""
+def _call_noalloc(G, reqs, stream="torch"):
+    """Marshal the requests and call the C entry point directly (stream: the
+    current torch stream, or None for the NULL stream)."""
     lib = trw.load_library()
     n = len(reqs)
     algos = (ctypes.c_int * n)()
@@ -66,11 +73,43 @@ def _call_noalloc(G, reqs):
         outs[i], outl[i] = op.data_ptr(), ol.data_ptr()
         results.append((op, ol))
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream().cuda_stream or 1
-    st = lib.trw_walk_batch_noalloc(G.handle, n, algos, params, srcs, ns, lens, seeds, outs, outl, stream)
+    st_arg = (torch.cuda.current_stream().cuda_stream or 1) if stream == "torch" else None
+    free0 = torch.cuda.mem_get_info()[0]
+    st = lib.trw_walk_batch_noalloc(G.handle, n, algos, params, srcs, ns, lens, seeds, outs, outl, st_arg)
+    free1 = torch.cuda.mem_get_info()[0]
     assert st == 0, lib.trw_last_error()
     torch.cuda.synchronize()
-    return results
+    return results, free0 - free1
+
+
+def _oracle_results(g, reqs):
+    """The oracle's walks of every request (walk i of a request keyed on i)."""
+    its = oracle.prepare_its(g.row_ptr, g.weights)
+    pmax = oracle.prepare_rej(g.row_ptr, g.weights)
+    out = []
+    for r in reqs:
+        algo = {trw.DEEPWALK: oracle.DEEPWALK, trw.DEEPWALK_WEIGHTED: oracle.DEEPWALK_WEIGHTED, trw.PPR: oracle.PPR,
+                trw.NODE2VEC: oracle.NODE2VEC, trw.METAPATH: oracle.METAPATH,
+                trw.NODE2VEC_WEIGHTED: oracle.NODE2VEC_WEIGHTED}[r["algo"]]
+        sampler = r.get("sampler", trw.SAMPLER_DEFAULT)
+        kw = dict(walks_per_source=r.get("walks_per_source", 1), endpoints_only=r.get("endpoints", False),
+                  ppr_stop=r.get("ppr_stop", 0.0), n2v_p=r.get("n2v_p", 1.0), n2v_q=r.get("n2v_q", 1.0),
+                  max_weight=r.get("max_weight", 0.0))
+        if algo == oracle.METAPATH:
+            kw.update(labels=g.labels, schema=r["schema"])
+        if algo == oracle.DEEPWALK_WEIGHTED:
+            if sampler == trw.SAMPLER_DEFAULT:
+                kw["alias"] = oracle_alias(12)
+            elif sampler == trw.SAMPLER_ITS:
+                kw.update(sampler=oracle.SAMPLER_ITS, its=its)
+            else:
+                kw.update(sampler=oracle.SAMPLER_OREJ, weights=g.weights)
+        if algo == oracle.NODE2VEC_WEIGHTED:
+            kw.update(weights=g.weights, pmax=pmax)
+        res = oracle.walk(g.row_ptr, g.col, algo, r["sources"], r["max_len"], r["seed"], **kw)
+        assert res.status == 0, (r["algo"], res.status)
+        out.append(res)
+    return out
 
 
 def _same(a_paths, a_lens, b_paths, b_lens):
@@ -82,17 +121,53 @@ def _same(a_paths, a_lens, b_paths, b_lens):
         assert torch.equal(a_paths[mask], b_paths[mask])
 
 
-def test_noalloc_batch_matches_batch_twice():
+def _graph():
     g = rmat_graph(12)
     G = trw.Graph(g.row_ptr, g.col, g.weights, g.labels)
     G.prepare(trw.PREP_ALIAS | trw.PREP_ITS)
+    return g, G
+
+
+def test_noalloc_batch_matches_oracle_and_batch_twice():
+    g, G = _graph()
     reqs = _requests(g)
-    want = G.walk_batch(reqs)
+    want = _oracle_results(g, reqs)
+    batch = G.walk_batch(reqs)
     torch.cuda.synchronize()
     for _ in range(2):  # the second call reuses the scratch the first one left behind
-        got = _call_noalloc(G, reqs)
-        for (op, ol), w in zip(got, want):
-            _same(w.paths, w.lengths, op, ol)
+        got, _ = _call_noalloc(G, reqs)
+        for (op, ol), w, b, r in zip(got, want, batch, reqs):
+            assert_paths_equal(op.cpu().numpy(), ol.cpu().numpy(), w, endpoints=r.get("endpoints", False))
+            _same(b.paths, b.lengths, op, ol)
+
+
+def test_noalloc_allocates_nothing():
+    g, G = _graph()
+    reqs = _requests(g)
+    want = _oracle_results(g, reqs)
+    _call_noalloc(G, reqs)  # the first call on the device may load the module and look up the scratch
+    got, used = _call_noalloc(G, reqs)
+    assert used == 0, f"the device's free memory fell by {used} bytes during the call"
+    # every allocation the library makes now fails as out of memory; this
+    # entry point makes none, so it still walks
+    trw.fail_allocs(0)
+    try:
+        got, used = _call_noalloc(G, reqs)
+    finally:
+        trw.fail_allocs(-1)
+    assert used == 0
+    for (op, ol), w, r in zip(got, want, reqs):
+        assert_paths_equal(op.cpu().numpy(), ol.cpu().numpy(), w, endpoints=r.get("endpoints", False))
+
+
+def test_noalloc_null_stream():
+    g, G = _graph()
+    reqs = _requests(g)
+    want = _oracle_results(g, reqs)
+    for _ in range(2):
+        got, _ = _call_noalloc(G, reqs, stream=None)
+        for (op, ol), w, r in zip(got, want, reqs):
+            assert_paths_equal(op.cpu().numpy(), ol.cpu().numpy(), w, endpoints=r.get("endpoints", False))
 
 
 def test_noalloc_refuses_oversized_batch():
