@@ -703,6 +703,34 @@ def measure_serve(trw, torch, G, g, n_requests=10000, rate=2000.0):
     out["saturating"] = {"steps_per_s": round(moves / wall, 1), "wall_s": round(wall, 3), "moves": moves}
     lat, wall, moves = run_plain(False)
     out["plain_fifo_saturating"] = {"steps_per_s": round(moves / wall, 1), "wall_s": round(wall, 3), "moves": moves}
+    # the batch kernel on the same requests: mixed batches of up to 64
+    # requests in the trace's order, one launch each, back to back on one
+    # stream (outputs allocated before the timed launches)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream or 1
+    breqs = [dict(r, sources=srcs[i]) for i, r in enumerate(reqs[:n_sat])]
+    outs = [_out_buffers(torch, r, dev) for r in reqs[:n_sat]]
+
+    def batch_pass():
+        for k0 in range(0, n_sat, 64):
+            G.walk_batch(breqs[k0:k0 + 64], stream=sp, sync=False, outputs=outs[k0:k0 + 64])
+
+    batch_pass()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    batch_pass()
+    b.record(stream)
+    torch.cuda.synchronize()
+    bms = a.elapsed_time(b)
+    bmoves = int(sum(int((ol.to(torch.int64) - 1).sum().item()) for _, ol in outs))
+    assert bmoves == moves, (bmoves, moves)
+    out["batch_same_requests"] = {"steps_per_s": round(moves / (bms / 1000.0), 1), "ms": round(bms, 3),
+                                  "launches": (n_sat + 63) // 64,
+                                  "what": "trw_walk_batch over the saturating requests, 64 per launch, one stream"}
+    out["saturating_over_batch"] = round(out["saturating"]["steps_per_s"] /
+                                         out["batch_same_requests"]["steps_per_s"], 3)
+    del outs
     out["saturating_speedup_vs_plain"] = round(out["saturating"]["steps_per_s"] /
                                                out["plain_fifo_saturating"]["steps_per_s"], 3)
     out["p99_speedup_vs_plain"] = round(out["plain_fifo"]["p99_ms"] / out["served"]["p99_ms"], 3)
@@ -995,7 +1023,7 @@ def run_ours(args, wl):
         if ws > 1:
             dist.destroy_process_group()
         return
-    cpu = cpu_baseline(g, wl) if ws == 1 and not args.no_cpu_baseline else None
+    cpu = cpu_baseline(g, wl, seconds=args.cpu_seconds) if ws == 1 and not args.no_cpu_baseline else None
     roof = roofline(wl, moves, n, kms, cpu, gather, value / ws, hashed=hashed,
                     records=bool(tables & TABLE_FLAGS["row_records"]), kernel=kernel_ran)
     line = {
@@ -1032,9 +1060,50 @@ def run_ours(args, wl):
         "cpu_baseline": cpu,
         "clocks": clk,
     }
+    if ws == 1 and args.config == "c2" and not args.no_configs:
+        line["configs"] = run_config_block(args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# The other workloads, measured after the headline by the default run: each
+# in a process of its own (its graph leaves the device before the next one is
+# built), condensed into the headline line's "configs".
+CONFIG_BLOCK = ("c1", "c3", "c4", "c5")
+SUMMARY_KEYS = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "kernel_ms_per_step", "config",
+                "plain_launch", "roofline", "gather_ceiling", "e2e", "clocks", "value_kind", "serve",
+                "batch_largest_graph", "preprocess")
+
+
+def run_config_block(args) -> dict:
+    out = {}
+    steps = max(3, min(args.steps, 10))
+    for c in CONFIG_BLOCK:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--config", c, "--steps", str(steps), "--warmup", "3",
+               "--no-configs", "--no-extras", "--cpu-seconds", "4"]
+        if c == "c5":
+            cmd += ["--serve-requests", str(args.serve_requests), "--no-cpu-baseline"]
+        t = time.time()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=1200)
+        except subprocess.TimeoutExpired:
+            out[c] = {"error": "timed out after 1200 s"}
+            continue
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            out[c] = {"error": f"exit {r.returncode}", "stderr_tail": r.stderr[-600:]}
+            log(f"config {c} failed: {r.stderr[-2000:]}")
+            continue
+        full = json.loads(lines[-1])
+        summ = {k: full[k] for k in SUMMARY_KEYS if k in full}
+        if summ.get("gather_ceiling"):
+            summ["gather_ceiling"] = {k: summ["gather_ceiling"][k] for k in ("loads_per_s", "table_bytes")}
+        summ["command"] = " ".join(["python"] + cmd[1:])
+        summ["wall_s"] = round(time.time() - t, 1)
+        out[c] = summ
+        log(f"config {c}: {json.dumps(summ)[:800]}")
+    return out
 
 
 def _common_line(args, wl, value, ms_per_step, cfg_extra):
@@ -1145,14 +1214,14 @@ def run_mixed(args, wl):
                 "ms": round(statistics.median(sms), 3), "tuning": Gs.tuning(),
                 "speedup_index": round(statistics.median(sms) / statistics.mean(ms), 2)}
         del Gs
-    gather = measure_gather_ceiling(trw, g) if not args.no_extras else None
+    gather = measure_gather_ceiling(trw, g)
     cpu = None
     if not args.no_cpu_baseline:
         # the oracle on a sample of both requests, in proportion to their walks
         t0 = time.perf_counter()
         mv, sec, ob, walks = 0, 0, 0, 0
         step = 0
-        while time.perf_counter() - t0 < 12.0:
+        while time.perf_counter() - t0 < args.cpu_seconds:
             lo = step * 20000
             res = oracle.walk(g.row_ptr, g.col, oracle.METAPATH, mp_src_h[lo:lo + 20000], 80, 1, labels=g.labels,
                               schema=schema, walk_offset=lo)
@@ -1240,9 +1309,9 @@ def run_serve(args, wl):
         f"{G.device_bytes() / 1e9:.1f} GB on the device")
     if not args.no_autotune:
         G.autotune(trw.DEEPWALK_WEIGHTED, 80)
-    # batch walk on the largest graph: 16,777,216 uniform sources x 80 moves
-    n = 1 << 24
-    src = torch.from_numpy(synth.sources(n, g.nv, seed=1)).to(dev)
+    # batch walk on the largest graph: one weighted DeepWalk walk of 80 moves per vertex
+    src = torch.from_numpy(synth.vertex_sources(g.nv)).to(dev)
+    n = int(src.shape[0])
     out_p = torch.empty((n, 81), dtype=torch.int32, device=dev)
     out_l = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -1274,7 +1343,7 @@ def run_serve(args, wl):
         "trace": f"{args.serve_requests} requests, Poisson 2000/s", "tuning": G.tuning()})
     line["value_kind"] = "saturating served steps/s (every request queued at once)"
     line["serve"] = serve
-    line["batch_largest_graph"] = {"workload": "weighted DeepWalk, 16,777,216 uniform sources x 80 moves",
+    line["batch_largest_graph"] = {"workload": f"weighted DeepWalk, one walk per vertex ({n}) x 80 moves",
                                    "steps_per_s": round(batch_value, 1), "kernel_ms": round(kms_m, 3), "moves": moves}
     line["preprocess"] = {"graph_load_s": round(load_s, 2), "alias_prepare_s": round(prep_s, 2),
                           "tables_s": round(tables_s, 2), "prepared_tables": table_names(tables) + ["alias"]}
@@ -1305,6 +1374,9 @@ def main():
                          "through the row offsets (the paper's method as written; walks are identical)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tuning (profiling runs: the first launches are then the timed ones)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="the default run only: skip the other workloads' lines (configs)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="single-threaded oracle time of the CPU baseline")
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests in the open-loop serving trace (the saturating runs queue the first 3000)")
     args = ap.parse_args()
