@@ -738,6 +738,65 @@ def measure_serve(trw, torch, G, g, n_requests=10000, rate=2000.0):
     return out
 
 
+def measure_serve_alone(trw, torch, G, g, idle_timeout_us=2000, reps=3):
+    """One large request of each long-walk class, served alone, against the
+    batch kernel on the same request: weighted DeepWalk (2^20 walks) and
+    Node2Vec (2^19 walks), 80 moves, uniform sources.  Served time is the
+    device timeline of the request (first walk started to last walk done),
+    batch time the kernel's CUDA events."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cases = {"deepwalk_weighted": (trw.DEEPWALK_WEIGHTED, 1 << 20, {}),
+             "node2vec": (trw.NODE2VEC, 1 << 19, {"n2v_p": 0.5, "n2v_q": 2.0})}
+    out = {}
+    S = trw.Server(G, idle_timeout_us=idle_timeout_us)
+    try:
+        for name, (algo, n, kw) in cases.items():
+            src = torch.from_numpy(synth.sources(n, g.nv, seed=31)).to(dev)
+            op = torch.empty((n, 81), dtype=torch.int32, device=dev)
+            ol = torch.empty(n, dtype=torch.int32, device=dev)
+            bms = []
+            for _ in range(reps + 1):
+                G.walk(algo, src, 80, 7, out_paths=op, out_lengths=ol, kernel=trw.KERNEL_PERSISTENT, **kw)
+                bms.append(G.last_stats()["kernel_ms"])
+            moves = int((ol.to(torch.int64) - 1).sum().item())
+            sms = []
+            for _ in range(reps + 1):
+                torch.cuda.synchronize()
+                rid = S.submit(algo, src, 80, 7, op, ol, **kw)
+                S.drain(600000)
+                tr = S.trace(rid)
+                sms.append((tr["done_ns"] - tr["first_ns"]) / 1e6)
+            assert int((ol.to(torch.int64) - 1).sum().item()) == moves
+            b, sv = statistics.median(bms[1:] or bms), statistics.median(sms[1:] or sms)
+            out[name] = {"walks": n, "moves": moves, "batch_ms": round(b, 3), "served_ms": round(sv, 3),
+                         "batch_steps_per_s": round(moves / b * 1e3, 1), "served_steps_per_s": round(moves / sv * 1e3, 1),
+                         "served_over_batch": round(b / sv, 3)}
+    finally:
+        S.close()
+    log(f"serve alone: {out}")
+    return out
+
+
+def run_serve_alone(args, wl):
+    """Profiling case of the serving kernel (--serve-alone): the graph of the
+    workload, its tables, and measure_serve_alone's two requests (each its own
+    serve_kernel launch; the idle timeout is short so that a launch ends soon
+    after its request)."""
+    import torch
+
+    import paper_2107_11983_gb300 as trw
+
+    g = build_graph(wl)
+    G = trw.Graph(g.row_ptr, g.col, g.weights, None)
+    G.prepare()
+    tables = tables_of(wl, args)
+    if tables:
+        G.prepare(tables)
+    line = {"workload": wl["name"], "graph": g.name, "nv": g.nv, "ne": g.ne,
+            "serve_alone": measure_serve_alone(trw, torch, G, g, idle_timeout_us=50, reps=0)}
+    print(json.dumps(line), flush=True)
+
+
 def serve_cpu_baseline(g, seconds: float = 12.0):
     """The oracle on a bounded sample of the serving trace: the PPR and
     Node2Vec requests in arrival order, at most 2000 walks of each, until about
@@ -1337,6 +1396,7 @@ def run_serve(args, wl):
     del out_p, out_l
     torch.cuda.empty_cache()
     serve = measure_serve(trw, torch, G, g, n_requests=args.serve_requests, rate=2000.0)
+    serve["alone"] = measure_serve_alone(trw, torch, G, g)
     value = serve["saturating"]["steps_per_s"]
     line = _common_line(args, wl, value, 0.0, {
         "graph": f"rmat-s{wl['scale']}-ef16-directed", "nv": g.nv, "ne": g.ne, "device_bytes": G.device_bytes(),
@@ -1374,6 +1434,8 @@ def main():
                          "through the row offsets (the paper's method as written; walks are identical)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tuning (profiling runs: the first launches are then the timed ones)")
+    ap.add_argument("--serve-alone", action="store_true",
+                    help="serving-kernel profiling case: one weighted DeepWalk and one Node2Vec request served alone")
     ap.add_argument("--no-configs", action="store_true",
                     help="the default run only: skip the other workloads' lines (configs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="single-threaded oracle time of the CPU baseline")
@@ -1396,6 +1458,8 @@ def main():
         run_reference(args, wl)
     elif wl.get("kind") == "mixed":
         run_mixed(args, wl)
+    elif wl.get("kind") == "serve" and args.serve_alone:
+        run_serve_alone(args, wl)
     elif wl.get("kind") == "serve":
         run_serve(args, wl)
     else:

@@ -41,8 +41,8 @@ namespace {
 
 constexpr uint32_t kQueueCap = 1u << 16;
 constexpr int kMaxActive = 64;        // requests the dispatcher interleaves
-constexpr int kPollSkip = 3;          // refills a walking warp skips after its first empty queue poll
-constexpr int kPollSkipMax = 24;      // ... doubling after each further empty poll, up to this many
+constexpr int kPollSkip = 6;          // refills a walking warp skips after its first empty queue poll
+constexpr int kPollSkipMax = 48;      // ... doubling after each further empty poll, up to this many
 constexpr int64_t kDeviceCheckMax = TRW_SERVE_DEVICE_CHECK_MAX;  // device sources the dispatcher checks
 // A request's completion word (SlotRec::finished): finished walks in the low
 // 48 bits, one bit per error kind above them.  Recording an error and adding
@@ -534,12 +534,17 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
           if (lane == 0) {
             // A ticket (fetch-and-add on the queue head, which always succeeds)
             // names the next entry this warp reads once the tail passes it.
+            // A warp with lanes still walking takes one only for an entry that
+            // is already there and unclaimed: a ticket binds its entry to this
+            // warp, and a warp that polls now and then would hold the entry up
+            // while idle warps wait.
             ServeState* s = sv.state;
-            if (!has_ticket) {
+            const unsigned long long tl = ld_acquire_gpu(&s->q_tail);
+            if (!has_ticket && (idle == 0xffffffffu || *(volatile unsigned long long*)&s->q_head < tl)) {
               ticket = atomicAdd(&s->q_head, 1ull);
               has_ticket = true;
             }
-            if (ticket < ld_acquire_gpu(&s->q_tail)) {
+            if (has_ticket && ticket < tl) {
               const Chunk* c = &sv.queue[ticket % kQueueCap];
               ck = ldcg_as(&c->k);
               cb = ldcg_as(&c->begin);
@@ -557,7 +562,9 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
           }
           got = __shfl_sync(0xffffffffu, got, 0);
           if (!got) {
-            if (idle != 0xffffffffu) {  // lanes still walk: back off before the next poll
+            // Lanes still walk and no entry is bound to this warp: back off
+            // before the next poll.  A warp holding a ticket polls every refill.
+            if (idle != 0xffffffffu && !__shfl_sync(0xffffffffu, has_ticket ? 1 : 0, 0)) {
               poll_wait = min(kPollSkip << min(empty_polls, 3), kPollSkipMax);
               ++empty_polls;
             }
@@ -694,7 +701,23 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
         if (r == step::kDefer) r = step::step_finish(g, sp, W, pend_work, next);
       }
     } else {
-      if (active) r = step::step_begin_dispatch<MIXED>(g, sp, W, next, pend_work, step::Coop{0x7fffffff, 0x7fffffff});
+      // The warp's walking lanes share one algorithm when they all run walks
+      // of one slot, or both slots hold requests of the same algorithm; the
+      // warp then runs that algorithm's step (the batch kernel's), else each
+      // lane's request picks it.
+      const unsigned in1 = __ballot_sync(0xffffffffu, ent == 1);
+      const int a0 = spec[0].algo, a1 = spec[1].algo;
+      const int walgo = (act_mask & in1) == 0u ? a0 : (act_mask & ~in1) == 0u ? a1 : a0 == a1 ? a0 : -1;
+      const step::Coop none{0x7fffffff, 0x7fffffff};
+      if (active) {
+        switch (walgo) {
+          case DEEPWALK: r = step::step_begin<DEEPWALK>(g, sp, W, next, pend_work, none); break;
+          case DEEPWALK_WEIGHTED: r = step::step_begin<DEEPWALK_WEIGHTED>(g, sp, W, next, pend_work, none); break;
+          case PPR: r = step::step_begin<PPR>(g, sp, W, next, pend_work, none); break;
+          case NODE2VEC: r = step::step_begin<NODE2VEC>(g, sp, W, next, pend_work, none); break;
+          default: r = step::step_begin_dispatch<MIXED>(g, sp, W, next, pend_work, none); break;
+        }
+      }
     }
     if (active) {
       const bool aligned = (reinterpret_cast<uintptr_t>(sp.out_paths) & 31) == 0;
