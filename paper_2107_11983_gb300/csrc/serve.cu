@@ -40,6 +40,8 @@ using namespace trw;
 namespace {
 
 constexpr uint32_t kQueueCap = 1u << 16;
+constexpr int kServeThreads = 256;    // threads per block of the serving kernel
+constexpr int kServeWarps = kServeThreads / 32;
 constexpr int kMaxActive = 64;        // requests the dispatcher interleaves
 constexpr int kPollSkip = 6;          // refills a walking warp skips after its first empty queue poll
 constexpr int kPollSkipMax = 48;      // ... doubling after each further empty poll, up to this many
@@ -113,6 +115,18 @@ struct ServeDev {
   unsigned long long depth;         // queued chunks the dispatcher keeps ahead of the workers
 };
 
+// Polling uses relaxed loads: an acquire invalidates the SM's L1 cache, and
+// warps that poll often would take the L1 hits of the warps that walk (the
+// second half of an alias record, for one).  A poll that finds work takes
+// the acquire as a fence before reading what it found.
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -185,7 +199,10 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
   for (;;) {
     int go = 1;
     unsigned long long P = 0;
-    if (lane == 0) P = ld_acquire_gpu(&st->published);
+    if (lane == 0) {
+      P = ld_relaxed_gpu(&st->published);
+      if (P > disp_next) fence_acquire_gpu();  // the new requests' slot records after their count
+    }
     // Admission, one request at a time.  A small request with device sources
     // has its sources range-checked here by the whole warp; one out of range
     // completes the request with the invalid-argument status, and no walk runs.
@@ -427,18 +444,21 @@ __device__ __forceinline__ void flush_finished(const ServeDev& sv, int e, const 
 // (needed only when a graph without the label index or neighbour hash is
 // tuned to use them); without it the kernel fits four blocks per SM.
 template <bool COOP>
-__global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, ServeDev sv) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kServeThreads, COOP ? 3 : 4) serve_kernel(DevGraph g, ServeDev sv) {
+  // Static shared memory (the block size is fixed): the compiler addresses it
+  // directly, with no generic pointers held in registers.
+  __shared__ WalkSpec s_spec[kServeWarps][2];          // the warp's two descriptor slots
+  __shared__ unsigned long long s_key[kServeWarps][2];  // their request numbers
+  __shared__ __align__(16) int32_t s_stage[kServeThreads * 8];
+  __shared__ ActiveSet s_act;                            // the dispatcher's (block 0)
+  __shared__ __align__(16) WarpState s_ws[kServeWarps];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  WalkSpec* spec = reinterpret_cast<WalkSpec*>(smem_raw) + 2 * wid;
-  unsigned long long* key =
-      reinterpret_cast<unsigned long long*>(smem_raw + sizeof(WalkSpec) * 2 * nwarps) + 2 * wid;
-  int32_t* stage_mem = reinterpret_cast<int32_t*>(smem_raw + (sizeof(WalkSpec) + 8) * 2 * nwarps);
-  ActiveSet* act =
-      reinterpret_cast<ActiveSet*>(smem_raw + (sizeof(WalkSpec) + 8) * 2 * nwarps + (size_t)blockDim.x * 32);
-  WarpState* wsp = reinterpret_cast<WarpState*>(reinterpret_cast<unsigned char*>(act) + sizeof(ActiveSet)) + wid;
+  WalkSpec* spec = s_spec[wid];
+  unsigned long long* key = s_key[wid];
+  int32_t* stage_mem = s_stage;
+  ActiveSet* act = &s_act;
+  WarpState* wsp = &s_ws[wid];
 
   if (blockIdx.x == 0 && wid == 0) {
     dispatcher(sv, act);
@@ -539,12 +559,13 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
             // warp, and a warp that polls now and then would hold the entry up
             // while idle warps wait.
             ServeState* s = sv.state;
-            const unsigned long long tl = ld_acquire_gpu(&s->q_tail);
+            const unsigned long long tl = ld_relaxed_gpu(&s->q_tail);
             if (!has_ticket && (idle == 0xffffffffu || *(volatile unsigned long long*)&s->q_head < tl)) {
               ticket = atomicAdd(&s->q_head, 1ull);
               has_ticket = true;
             }
             if (has_ticket && ticket < tl) {
+              fence_acquire_gpu();  // the entry after the tail that covers it
               const Chunk* c = &sv.queue[ticket % kQueueCap];
               ck = ldcg_as(&c->k);
               cb = ldcg_as(&c->begin);
@@ -602,7 +623,7 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
         load_spec(&sv.slots[(int)(pk % (unsigned long long)sv.R)].spec, &spec[tgt]);
         if (lane == 0) {
           atomicCAS(&sv.slots[(int)(pk % (unsigned long long)sv.R)].t_first, 0ull, (unsigned long long)now_ns());
-          bad = spec_check(spec[tgt], pk, pb, pe, ld_acquire_gpu(&sv.state->published));
+          bad = spec_check(spec[tgt], pk, pb, pe, ld_relaxed_gpu(&sv.state->published));
           if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec[tgt].nwalks,
                               reinterpret_cast<uintptr_t>(spec[tgt].out_paths));
           key[tgt] = bad ? ~0ull : pk;
@@ -667,7 +688,7 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 4) serve_kernel(DevGraph g, Se
         const bool has_ticket = wsp->has_ticket != 0;
         const unsigned long long ticket = wsp->ticket;
         for (;;) {
-          const unsigned long long tl = ld_acquire_gpu(&sv.state->q_tail);
+          const unsigned long long tl = ld_relaxed_gpu(&sv.state->q_tail);
           if (!has_ticket || ticket < tl) break;  // refill: take a ticket, or read the entry
           if (*(volatile int*)&sv.state->exit_now) {
             go = 0;
@@ -883,10 +904,8 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   s->req_src_pos.assign(R, 0);
   s->req_src_n.assign(R, 0);
   s->collected.assign(R, 1);
-  s->block_threads = 256;
-  const int nwarps = s->block_threads / 32;
-  s->smem = (sizeof(WalkSpec) + 8) * 2 * nwarps + (size_t)s->block_threads * 8 * sizeof(int32_t) + sizeof(ActiveSet) +
-            sizeof(WarpState) * nwarps;
+  s->block_threads = kServeThreads;
+  s->smem = 0;  // the kernel's shared memory is static
   int bps = 0, bps_coop = 0;
   SV_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, serve_kernel<false>, s->block_threads, s->smem),
          "occupancy");
