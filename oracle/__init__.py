@@ -57,7 +57,8 @@ class _Params(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("moves", ctypes.c_int64), ("attempts", ctypes.c_int64), ("stop_len", ctypes.c_int64),
                 ("stop_coin", ctypes.c_int64), ("stop_dead", ctypes.c_int64), ("stop_schema", ctypes.c_int64),
-                ("sectors", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("checks", ctypes.c_int64)]
+                ("sectors", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("return_only", ctypes.c_int64)]
 
 
 _WEIGHT_FN = ctypes.CFUNCTYPE(ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,

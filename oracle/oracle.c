@@ -288,6 +288,8 @@ typedef struct {
   int64_t out_bytes;      /* bytes of path output written */
   int64_t checks;         /* Node2Vec: IsNeighbor results that decided an attempt (the dart fell
                              between the neighbour and far thresholds) */
+  int64_t return_only;    /* unweighted Node2Vec: attempts after the first move whose word lies at or
+                             past both non-return thresholds (only a return to prev accepts them) */
 } orc_stats;
 
 /* Sector model of the device layout, used only for the roofline: 4-byte
@@ -494,6 +496,8 @@ int orc_walk(const orc_graph* g, const orc_params* p, const int32_t* sources, in
         for (uint32_t a = 0; a < ORC_REJECT_CAP; ++a) {
           if (a > 0) draw_block(seed, w, (uint32_t)s, a, B);
           if (st) st->attempts++;
+          if (st && p->algo == ORC_NODE2VEC && s > 0 && (uint64_t)B[2] >= (T_nb > T_far ? T_nb : T_far))
+            st->return_only++;
           const int64_t x = (int64_t)uniform_below(B, (uint64_t)d);
           const int32_t c = g->col[off + x];
           if (sec) sec_touch(sec, SEC_COL, (off + x) * 4);

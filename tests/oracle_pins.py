@@ -564,6 +564,32 @@ def pin_sector_model(lib=None):
     assert res.stats["sectors"] == 2 * n + 4 * second, res.stats
 
 
+def pin_return_only_count(lib=None):
+    """stats.return_only (unweighted Node2Vec darts after the first move whose
+    word is at or past both non-return thresholds): zero where no such word
+    exists (p = q = 1, or a non-return class with weight p*, or one move per
+    walk), else a fraction 1 - T_hi / 2^32 of the darts after the first move,
+    T_hi = floor(max(w_nb, w_far) / p* * 2^32)."""
+    g = small_rmat()
+    src = synth.vertex_sources(g.nv)
+
+    def st(L, pp, qq):
+        res = oracle.walk(g.row_ptr, g.col, oracle.NODE2VEC, src, L, seed=7, n2v_p=pp, n2v_q=qq, lib=lib)
+        assert res.status == 0
+        return res.stats
+
+    for pp, qq in ((1.0, 1.0), (2.0, 0.5), (1.0, 0.5)):
+        assert st(30, pp, qq)["return_only"] == 0, (pp, qq)
+    assert st(1, 0.5, 2.0)["return_only"] == 0
+    for pp, qq, frac in ((0.5, 2.0, 0.5), (0.25, 4.0, 0.75)):
+        first = st(1, pp, qq)["attempts"]  # the first move takes one dart (Weight = MaxWeight)
+        s = st(30, pp, qq)
+        later = s["attempts"] - first
+        assert later > 20000
+        got = s["return_only"] / later
+        assert abs(got - frac) < 6 * np.sqrt(frac * (1 - frac) / later), (pp, qq, got, frac)
+
+
 def pin_rej_threshold(lib=None):
     """T = rej_threshold(W, p*) is the number of 32-bit words y with
     (y + 1) / 2^32 <= W / p*: word T - 1 passes and word T fails."""
@@ -892,7 +918,7 @@ def pin_custom_walk_update(lib=None):
     assert p > 1e-3, p
 
 
-ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_sector_model, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
+ALL_PINS = [pin_philox_kat, pin_fixed_point, pin_sector_model, pin_return_only_count, pin_alias_law, pin_law_deepwalk, pin_law_alias, pin_law_node2vec,
             pin_law_metapath, pin_ppr, pin_rejection_trials, pin_reductions, pin_invariants, pin_sharding, pin_rej_threshold, pin_its_first_move,
             pin_rej_first_move, pin_law_samplers, pin_rej_trials_closed_form, pin_zero_weights,
             pin_law_node2vec_weighted, pin_node2vec_weighted_first_move, pin_node2vec_weighted_reductions,

@@ -71,6 +71,10 @@ MUTANTS = [
     ("sectors: ITS search probes not counted", "          if (sec) sec_touch(sec, SEC_CDF, (off + mid) * 8);\n", "\n"),
     ("sectors: REJ bound not counted", "          if (sec) sec_touch(sec, SEC_PMAX, (int64_t)cur * 4);\n          if (pstar == 0)",
      "          if (pstar == 0)"),
+    ("return-only count includes the first move", "if (st && p->algo == ORC_NODE2VEC && s > 0 && (uint64_t)B[2] >=",
+     "if (st && p->algo == ORC_NODE2VEC && s >= 0 && (uint64_t)B[2] >="),
+    ("return-only count against the lower threshold", "(uint64_t)B[2] >= (T_nb > T_far ? T_nb : T_far))",
+     "(uint64_t)B[2] >= (T_nb < T_far ? T_nb : T_far))"),
     ("sectors: set cleared once per walk, not per step", "    path[0] = cur;\n    for (;;) {\n      if (sec) sec->n = 0;\n",
      "    path[0] = cur;\n    if (sec) sec->n = 0;\n    for (;;) {\n"),
 ]
