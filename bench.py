@@ -265,7 +265,7 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
     src = synth.vertex_sources(g.nv)
     n = 2000
     done_moves, done_s, walks = 0, 0.0, 0
-    sectors, out_bytes, attempts, checks = 0, 0, 0, 0
+    sectors, out_bytes, attempts, checks, ret_only = 0, 0, 0, 0, 0
     pos = 0
     while done_s < seconds and pos < src.shape[0]:
         m = min(n, src.shape[0] - pos)
@@ -279,6 +279,7 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
         out_bytes += res.stats["out_bytes"]
         attempts += res.stats["attempts"]
         checks += res.stats["checks"]
+        ret_only += res.stats["return_only"]
         done_s += dt
         walks += m
         pos += m
@@ -300,7 +301,13 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
             # Node2Vec with the neighbour hash: the row pair of cur, one col sector per
             # attempt, one bucket sector per IsNeighbor that decides an attempt
             "model_bytes_per_move_hashed": ROW_PAIR + (SECTOR * (attempts + checks) + out_bytes) / max(1, done_moves),
-            "attempts_per_move": attempts / max(1, done_moves), "checks_per_move": checks / max(1, done_moves)}
+            # with row records as well: a move reads no row-offset pair; a dart
+            # reads its candidate's record unless it is return-only (decided from
+            # prev's position in the row)
+            "model_bytes_per_move_records_hashed": (SECTOR * (attempts - ret_only + checks) + out_bytes) /
+            max(1, done_moves),
+            "attempts_per_move": attempts / max(1, done_moves), "checks_per_move": checks / max(1, done_moves),
+            "return_only_per_move": ret_only / max(1, done_moves)}
 
 
 def run_reference(args, wl):
@@ -363,7 +370,14 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False
         bpm = SECTOR + 4
         per_walk = BYTES_PER_WALK_BASE + ROW_PAIR
         source = "closed form (32-byte sectors of the device layout, row records)"
-    if bpm is None and cpu is not None and hashed:
+    if bpm is None and cpu is not None and hashed and records and wl["algo"] == "node2vec":
+        bpm = cpu["model_bytes_per_move_records_hashed"]
+        per_walk = BYTES_PER_WALK_BASE + ROW_PAIR
+        source = ("one 32-byte row record per dart that reads its candidate (darts past both non-return "
+                  "thresholds are decided from the previous vertex's position) and one sector per deciding "
+                  "IsNeighbor (neighbour hash), plus the path entry; counts from the oracle on the CPU-baseline "
+                  "sample; the source's row once per walk")
+    elif bpm is None and cpu is not None and hashed:
         bpm = cpu["model_bytes_per_move_hashed"]
         source = ("row pair + one 32-byte sector per attempt and per deciding IsNeighbor (neighbour hash), "
                   "counts from the oracle on the CPU-baseline sample")

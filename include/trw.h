@@ -221,14 +221,18 @@ trw_status trw_graph_get_view(const trw_graph* g, trw_graph_view* out);
  * it.  Preparing a hash that exists already does nothing.
  *
  * TRW_PREP_ROW_RECORDS (not in the paper, whose NAIVE move reads the row of
- * the current vertex and then one edge of it, Section 2.3): a 16-byte record
- * per edge slot {destination, its row offset, its degree, W_e (the integer
- * weight, 0 without weights)}, so that a NAIVE move (DeepWalk, PPR), an
- * O-REJ candidate (Node2Vec), a REJ or O-REJ dart or an ITS pick reads one
- * record and the next step needs no row-offset lookup: one dependent random
- * read per move instead of two.  16 bytes of device memory per edge; every
- * walk is identical with and without them.  Preparing records that exist
- * already does nothing.
+ * the current vertex and then one edge of it, Section 2.3): a 32-byte record
+ * per edge slot e = (v -> dst) {destination, its row offset, its degree, W_e
+ * (the integer weight, 0 without weights), the position of v in dst's row
+ * (-1 when dst has no edge back to v, or the rows are not sorted), 0, 0, 0},
+ * so that a NAIVE move (DeepWalk, PPR), an O-REJ candidate (Node2Vec), a REJ
+ * or O-REJ dart or an ITS pick reads one record and the next step needs no
+ * row-offset lookup: one dependent random read per move instead of two.  With
+ * the records, an unweighted Node2Vec dart whose word lies at or past both
+ * non-return thresholds (only a return to the previous vertex can accept it)
+ * is decided from the previous vertex's position in the row, without reading
+ * its candidate.  32 bytes of device memory per edge; every walk is identical
+ * with and without them.  Preparing records that exist already does nothing.
  *
  * TRW_PREP_ITS and TRW_PREP_REJ: Algorithm 3 with the ITS and REJ
  * initialisations of Section 2.3, for the samplers of the same names: the
@@ -472,6 +476,13 @@ trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int3
  * the cell, last candidate of the cell, 0}.  For tests.  Errors:
  * TRW_ERR_INVALID (NULL argument), TRW_ERR_NOT_PREPARED, TRW_ERR_CUDA. */
 trw_status trw_debug_its_records(const trw_graph* g, uint32_t* words);
+
+/* Copy the row records to host memory, 8 int32 words per edge slot e = (v ->
+ * dst): {dst, its row offset, its degree, the integer weight W_e (0 without
+ * weights), the position of v in dst's row (-1: none, or rows not sorted), 0,
+ * 0, 0}.  For tests.  Errors: TRW_ERR_INVALID (NULL argument),
+ * TRW_ERR_NOT_PREPARED, TRW_ERR_CUDA. */
+trw_status trw_debug_row_records(const trw_graph* g, int32_t* words);
 
 /* Copy the ITS prefix sums (host uint64[ne]) and/or the REJ bounds (host
  * uint32[nv]) to host buffers; a NULL buffer is skipped.  For tests.

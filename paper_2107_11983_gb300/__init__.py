@@ -118,6 +118,7 @@ _SIGS = {
     "trw_debug_label_index": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "trw_debug_sampler_tables": (ctypes.c_int, [_VP, _VP, _VP]),
     "trw_debug_its_records": (ctypes.c_int, [_VP, _VP]),
+    "trw_debug_row_records": (ctypes.c_int, [_VP, _VP]),
     "trw_debug_is_neighbor": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP]),
     "trw_debug_philox": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, _VP]),
     "trw_debug_fail_allocs": (None, [ctypes.c_int64]),
@@ -523,6 +524,14 @@ class Graph:
         offset and degree, the cell's first and last candidates, 0."""
         out = np.empty((self.ne, 8), dtype=np.uint32)
         _check(load_library().trw_debug_its_records(self._h, out.ctypes.data), "trw_debug_its_records")
+        return out
+
+    def debug_row_records(self) -> np.ndarray:
+        """Row records as int32 [ne, 8]: destination, its row offset and degree,
+        the integer weight, the position of the source in the destination's
+        row (-1: none), 0, 0, 0."""
+        out = np.empty((self.ne, 8), dtype=np.int32)
+        _check(load_library().trw_debug_row_records(self._h, out.ctypes.data), "trw_debug_row_records")
         return out
 
     def debug_is_neighbor(self, u, v) -> np.ndarray:

@@ -442,11 +442,11 @@ static trw_status prepare_neighbor_hash(trw_graph* g) {
 
 static trw_status prepare_row_records(trw_graph* g) {
   if (g->rrec) return TRW_OK;
-  int4* rec = nullptr;
-  const size_t bytes = sizeof(int4) * (size_t)g->ne;
+  RowRec* rec = nullptr;
+  const size_t bytes = sizeof(RowRec) * (size_t)g->ne;
   trw_status st = alloc_dev((void**)&rec, bytes, "row records");
   if (st != TRW_OK) return st;
-  cudaError_t e = launch_row_records(g->ne, g->row_ptr, g->col, g->weights, rec, g->stream);
+  cudaError_t e = launch_row_records((int32_t)g->nv, g->ne, g->row_ptr, g->col, g->weights, g->sorted, rec, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) {
     cudaFree(rec);
@@ -1086,6 +1086,15 @@ extern "C" trw_status trw_debug_sampler_tables(const trw_graph* g, uint64_t* cdf
     CUDA_TRY(cudaMemcpy(cdf, g->its_cdf, sizeof(uint64_t) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy ITS sums");
   if (pmax && g->nv > 0)
     CUDA_TRY(cudaMemcpy(pmax, g->rej_pmax, sizeof(uint32_t) * (size_t)g->nv, cudaMemcpyDeviceToHost), "copy REJ bounds");
+  return TRW_OK;
+}
+
+extern "C" trw_status trw_debug_row_records(const trw_graph* g, int32_t* words) {
+  if (!g || !words) return trw_fail(TRW_ERR_INVALID, "NULL argument");
+  if (trw_status dc = trw_check_device(g); dc != TRW_OK) return dc;
+  if (!g->rrec) return trw_fail(TRW_ERR_NOT_PREPARED, "no row records");
+  if (g->ne > 0)
+    CUDA_TRY(cudaMemcpy(words, g->rrec, sizeof(RowRec) * (size_t)g->ne, cudaMemcpyDeviceToHost), "copy row records");
   return TRW_OK;
 }
 

@@ -511,13 +511,49 @@ __global__ void label_gather_kernel(int64_t ne, int32_t stride, const int32_t* _
 
 // ---------------------------------------------------------------- row records
 
-__global__ void row_records_kernel(int64_t ne, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                   const float* __restrict__ weights, int4* __restrict__ rec) {
+// One thread per edge e = (v -> c): c's row, the integer weight, and the
+// position of v in c's sorted row (a lower-bound search; -1 when absent or the
+// rows are not sorted).  v is found from e by a search of the row offsets.
+__global__ void row_records_kernel(int32_t nv, int64_t ne, const int32_t* __restrict__ row_ptr,
+                                   const int32_t* __restrict__ col, const float* __restrict__ weights, bool sorted,
+                                   RowRec* __restrict__ rec) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = col[e];
     const int32_t o = row_ptr[c];
+    const int32_t d = row_ptr[c + 1] - o;
     const uint32_t w = weights ? weight_fixed(weights[e]) : 0u;
-    rec[e] = make_int4(c, o, row_ptr[c + 1] - o, (int32_t)w);
+    int32_t rev = -1;
+    if (sorted) {
+      // v: the last row whose offset is <= e
+      int32_t lo = 0, n = nv;
+      while (n > 0) {
+        const int32_t half = n >> 1;
+        if ((int64_t)row_ptr[lo + half + 1] <= e) {
+          lo += half + 1;
+          n -= half + 1;
+        } else {
+          n = half;
+        }
+      }
+      const int32_t v = lo;
+      // lower bound of v in c's row
+      int32_t a = 0;
+      n = d;
+      while (n > 0) {
+        const int32_t half = n >> 1;
+        if (col[o + a + half] < v) {
+          a += half + 1;
+          n -= half + 1;
+        } else {
+          n = half;
+        }
+      }
+      if (a < d && col[o + a] == v) rev = a;
+    }
+    RowRec r;
+    r.a = make_int4(c, o, d, (int32_t)w);
+    r.b = make_int4(rev, 0, 0, 0);
+    rec[e] = r;
   }
 }
 
@@ -705,12 +741,12 @@ cudaError_t launch_prepare_labels(int32_t nv, int64_t ne, const int32_t* row_ptr
   return e;
 }
 
-cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, const float* weights, int4* rec,
-                               cudaStream_t st) {
+cudaError_t launch_row_records(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                               const float* weights, bool sorted, RowRec* rec, cudaStream_t st) {
   if (ne <= 0) return cudaSuccess;
   int64_t blocks = (ne + 255) / 256;
   if (blocks > 65535) blocks = 65535;
-  row_records_kernel<<<(unsigned)blocks, 256, 0, st>>>(ne, row_ptr, col, weights, rec);
+  row_records_kernel<<<(unsigned)blocks, 256, 0, st>>>(nv, ne, row_ptr, col, weights, sorted, rec);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ struct trw_graph {
   int32_t* lerec = nullptr;          // and edge records, lstride words each
   int32_t lstride = 0;
   int32_t lnl = 0;                   // labels in the index (largest label + 1)
-  int4* rrec = nullptr;              // row records (trw_prepare(ROW_RECORDS))
+  trw::RowRec* rrec = nullptr;       // row records (trw_prepare(ROW_RECORDS))
   unsigned long long* its_cdf = nullptr;  // ITS prefix sums (trw_prepare(ITS)): ne
   uint32_t* rej_pmax = nullptr;      // REJ bounds p*_v (trw_prepare(REJ)): nv
   trw::ItsRec* its_rec = nullptr;    // guided ITS records (trw_prepare(ITS_GUIDE)): ne

@@ -42,6 +42,19 @@ struct __align__(32) AliasRec {
   uint4 b;
 };
 
+// Row record of one edge slot e = (v -> dst), one 32-byte sector (an optional
+// preparation; walks are identical with and without it):
+//   a = {dst, row offset of dst, degree of dst, W_e (the integer weight, 0 without weights)}
+//   b = {rev_e, 0, 0, 0}
+// rev_e is the position in dst's row of the edge back to v, -1 when dst has
+// none or the rows are not sorted.  A NAIVE move, an O-REJ candidate or a REJ
+// dart reads a; Node2Vec also reads rev_e, which lets a later step decide a
+// return-only dart without reading its candidate.
+struct __align__(32) RowRec {
+  int4 a;
+  int4 b;
+};
+
 // Guided ITS records (an optional preparation; walks are identical with and
 // without it).  ITS picks the smallest i with x < p'_i, x = floor(r64 * S / 2^64)
 // and S = p'_{d-1}; since x < p'_i exactly when max(r64, 1) <= U_i with
@@ -114,7 +127,7 @@ struct DevGraph {
   const unsigned long long* __restrict__ cdf;  // [ne] ITS: inclusive prefix sums of the row's integer weights, or null
   const uint32_t* __restrict__ pmax;     // [nv] REJ: largest integer weight of the row (0: none positive), or null
   const ItsRec* __restrict__ its_rec;    // [ne] guided ITS records, or null
-  const int4* __restrict__ rrec;         // [ne] row records {dst, row_ptr[dst], deg(dst), W_e}, or null
+  const RowRec* __restrict__ rrec;       // [ne] row records, or null
   LabelIndex lidx;
   NeighborHash nh;
   int32_t nv;

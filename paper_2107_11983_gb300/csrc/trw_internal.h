@@ -57,7 +57,8 @@ cudaError_t launch_neighbor_hash(int32_t nv, int64_t ne, const int32_t* row_ptr,
                                  int32_t min_degree, int32_t* slots, cudaStream_t st);
 
 // Row records {col[e], row_ptr[col[e]], deg(col[e]), 0} of every edge slot.
-cudaError_t launch_row_records(int64_t ne, const int32_t* row_ptr, const int32_t* col, const float* weights, int4* rec,
+cudaError_t launch_row_records(int32_t nv, int64_t ne, const int32_t* row_ptr, const int32_t* col,
+                               const float* weights, bool sorted, RowRec* rec,
                                cudaStream_t st);
 cudaError_t launch_sampler_tables(int32_t nv, const int32_t* row_ptr, const float* weights, unsigned long long* cdf,
                                   uint32_t* pmax, cudaStream_t st);

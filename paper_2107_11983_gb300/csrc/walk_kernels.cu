@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) walk_plain(DevGraph g, WalkSpec sp, Ctrl*
       if (!sp.endpoints) sp.out_paths[base] = src;
       for (;;) {
         int32_t next = -1;
-        const int r = step_dispatch<A>(g, sp, W, next);
+        const int r = step_dispatch<A, false, false>(g, sp, W, next);
         if (r == kMoved) {
           advance(W, next);
           if (!sp.endpoints) sp.out_paths[base + W.s] = next;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) bsp_step(DevGraph g, WalkSpec sp, const B
     int32_t next;
     for (;;) {
       next = -1;
-      r = step_dispatch<A>(g, sp, b.W, next);
+      r = step_dispatch<A, false, false>(g, sp, b.W, next);
       if (r != kRetry) break;
       b.W.att += 1;
     }

@@ -22,6 +22,8 @@ struct Walker {
   int32_t poff, pd; // CSR row of prev
   uint32_t att;     // rejection trial within the step
   int32_t nxo, nxd; // row of the vertex an ALIAS move picked (from its record)
+  int32_t rev;      // Node2Vec: position of prev in cur's row (-1: not in it, -2: unknown)
+  int32_t px;       // Node2Vec: position of cur in prev's row (-2: unknown)
   bool nxv;         // nxo/nxd hold the next vertex's row
   bool rowok;       // off/d already hold cur's row
 };
@@ -34,6 +36,7 @@ __device__ __forceinline__ void walker_init(Walker& W, uint32_t w, int32_t src) 
   W.off = W.d = W.poff = W.pd = 0;
   W.att = 0;
   W.nxo = W.nxd = 0;
+  W.rev = W.px = -2;
   W.nxv = false;
   W.rowok = false;
 }
@@ -151,7 +154,7 @@ __device__ __forceinline__ bool is_neighbor(const DevGraph& g, int32_t prev, int
 // (warp_metapath / warp_neighbor) and step_finish completes the step.
 // CHECK adds range checks of the walker's vertex and of the row it loads
 // before any access through them (kBroken instead of an out-of-range read).
-template <int A, bool CHECK = false>
+template <int A, bool CHECK = false, bool FOLD = true>
 __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next, Pend& p,
                                           Coop coop) {
   p.kind = 0;
@@ -184,7 +187,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     // picked vertex's row for the next step.
     const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
     if (g.rrec) {
-      const int4 r = __ldg(g.rrec + e);
+      const int4 r = __ldg(&g.rrec[e].a);
       next = r.x;
       W.nxo = r.y;
       W.nxd = r.z;
@@ -309,7 +312,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     }
     const int64_t e = (int64_t)W.off + lo;
     if (g.rrec) {
-      const int4 r = __ldg(g.rrec + e);
+      const int4 r = __ldg(&g.rrec[e].a);
       next = r.x;
       W.nxo = r.y;
       W.nxd = r.z;
@@ -333,7 +336,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     int4 rr;
     uint32_t wx;
     if (g.rrec) {
-      rr = __ldg(g.rrec + e);
+      rr = __ldg(&g.rrec[e].a);
       wx = (uint32_t)rr.w;
     } else {
       rr.x = ldg(g.col + e);
@@ -361,28 +364,60 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
       }
       if (CHECK && !g.rrec && !g.weights) return kBroken;
     }
-    const int64_t e = (int64_t)W.off + below(B, (uint32_t)W.d);
+    uint4 Bd = B;  // this dart's block
+    uint32_t x = below(Bd, (uint32_t)W.d);
+    if (A == NODE2VEC && W.s > 0 && W.rev != -2) {
+      // At or past both non-return thresholds only a return to prev can
+      // accept, and prev's position in this row is known (-1: not in it): such
+      // a dart is decided without reading its candidate.  With FOLD, when it is
+      // rejected the next dart is drawn at once, within this unit of work (the
+      // warp-synchronous kernels); without, the unit ends with the retry (the
+      // kernels whose threads run free, where a per-lane loop here splits the
+      // warp).
+      while ((uint64_t)Bd.z >= sp.T_hi) {
+        if ((int32_t)x == W.rev && (uint64_t)Bd.z < sp.T_ret) {
+          next = W.prev;
+          W.nxo = W.poff;
+          W.nxd = W.pd;
+          W.nxv = true;
+          const int32_t t = W.rev;  // back along the edge just walked
+          W.rev = W.px;
+          W.px = t;
+          return kMoved;
+        }
+        if (W.att + 1 >= kRejectCap) return kFail;
+        if (!FOLD) return kRetry;
+        W.att += 1;
+        Bd = draw_block(sp, W.w, (uint32_t)W.s, W.att);
+        x = below(Bd, (uint32_t)W.d);
+      }
+    }
+    const int64_t e = (int64_t)W.off + x;
     int4 rr = make_int4(0, 0, 0, 0);
-    if (g.rrec) rr = __ldg(g.rrec + e);
+    int32_t rrev = -2;
+    if (g.rrec) {
+      rr = __ldg(&g.rrec[e].a);
+      if (A == NODE2VEC) rrev = __ldg(&g.rrec[e].b).x;  // same sector
+    }
     const int32_t c = g.rrec ? rr.x : ldg(g.col + e);
     if (A == N2V_W) {
       // weight word: (z + 1) * P <= W_x * 2^32, i.e. z < floor(W_x * 2^32 / P)
       const uint32_t wx = g.rrec ? (uint32_t)rr.w : weight_fixed(__ldg(g.weights + e));
-      if (((unsigned long long)B.w + 1ull) * P > ((unsigned long long)wx << 32))
+      if (((unsigned long long)Bd.w + 1ull) * P > ((unsigned long long)wx << 32))
         return (W.att + 1 >= kRejectCap) ? kFail : kRetry;
     }
     bool accept;
     if (W.s == 0) accept = true;                               // Weight = MaxWeight on the first step
-    else if (c == W.prev) accept = (uint64_t)B.z < sp.T_ret;
-    else if ((uint64_t)B.z < sp.T_lo) accept = true;
-    else if ((uint64_t)B.z >= sp.T_hi) accept = false;
+    else if (c == W.prev) accept = (uint64_t)Bd.z < sp.T_ret;
+    else if ((uint64_t)Bd.z < sp.T_lo) accept = true;
+    else if ((uint64_t)Bd.z >= sp.T_hi) accept = false;
     else if (W.pd >= coop.search && !g.nh.slots) {
       p.kind = 2;
       p.c = c;
-      p.y = B.z;
+      p.y = Bd.z;
       return kDefer;
     } else {
-      accept = (uint64_t)B.z < (is_neighbor(g, W.prev, W.poff, W.pd, c) ? sp.T_nb : sp.T_far);
+      accept = (uint64_t)Bd.z < (is_neighbor(g, W.prev, W.poff, W.pd, c) ? sp.T_nb : sp.T_far);
     }
     if (accept) {
       next = c;
@@ -390,6 +425,10 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
         W.nxo = rr.y;
         W.nxd = rr.z;
         W.nxv = true;
+        if (A == NODE2VEC) {  // positions for the next step's return-only darts
+          W.rev = rrev;
+          W.px = (int32_t)x;
+        }
       }
       return kMoved;
     }
@@ -398,14 +437,14 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
 }
 
 // The thread-serial step (no warp cooperation).
-template <int A, bool CHECK = false>
+template <int A, bool CHECK = false, bool FOLD = true>
 __device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   Pend p;
-  return step_begin<A, CHECK>(g, sp, W, next, p, Coop{0x7fffffff, 0x7fffffff});
+  return step_begin<A, CHECK, FOLD>(g, sp, W, next, p, Coop{0x7fffffff, 0x7fffffff});
 }
 
 // Completes a deferred step once the warp has filled p.res.
-__device__ __forceinline__ int step_finish(const DevGraph& g, const WalkSpec& sp, const Walker& W, const Pend& p,
+__device__ __forceinline__ int step_finish(const DevGraph& g, const WalkSpec& sp, Walker& W, const Pend& p,
                                            int32_t& next) {
   if (p.kind == 1) {
     if (p.res < 0) return kStop;                               // no edge carries the label
@@ -414,6 +453,7 @@ __device__ __forceinline__ int step_finish(const DevGraph& g, const WalkSpec& sp
   }
   if ((uint64_t)p.y < (p.res ? sp.T_nb : sp.T_far)) {
     next = p.c;
+    W.rev = W.px = -2;  // the candidate's record was not read
     return kMoved;
   }
   return (W.att + 1 >= kRejectCap) ? kFail : kRetry;
@@ -648,17 +688,17 @@ __device__ __forceinline__ int sampler_step_apply(const DevGraph& g, const WalkS
   return o.r;
 }
 
-template <int A, bool CHECK = false>
+template <int A, bool CHECK = false, bool FOLD = true>
 __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   if constexpr (A != MIXED) {
-    return step_serial<A, CHECK>(g, sp, W, next);
+    return step_serial<A, CHECK, FOLD>(g, sp, W, next);
   } else {
     switch (sp.algo) {
-      case DEEPWALK: return step_serial<DEEPWALK, CHECK>(g, sp, W, next);
-      case DEEPWALK_WEIGHTED: return step_serial<DEEPWALK_WEIGHTED, CHECK>(g, sp, W, next);
-      case PPR: return step_serial<PPR, CHECK>(g, sp, W, next);
-      case NODE2VEC: return step_serial<NODE2VEC, CHECK>(g, sp, W, next);
-      case METAPATH: return step_serial<METAPATH, CHECK>(g, sp, W, next);
+      case DEEPWALK: return step_serial<DEEPWALK, CHECK, FOLD>(g, sp, W, next);
+      case DEEPWALK_WEIGHTED: return step_serial<DEEPWALK_WEIGHTED, CHECK, FOLD>(g, sp, W, next);
+      case PPR: return step_serial<PPR, CHECK, FOLD>(g, sp, W, next);
+      case NODE2VEC: return step_serial<NODE2VEC, CHECK, FOLD>(g, sp, W, next);
+      case METAPATH: return step_serial<METAPATH, CHECK, FOLD>(g, sp, W, next);
       case DW_ITS:
       case DW_REJ:
       case DW_OREJ:
