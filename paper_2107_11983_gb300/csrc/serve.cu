@@ -165,9 +165,8 @@ struct WarpState {
   int cur;                        // slot receiving new walks
   int pend;
   int has_ticket;
-  int poll_wait;                  // refills left before the next poll (after an empty one)
   int empty_polls;                // empty polls in a row while some lanes walk
-  int pad;
+  int pad[2];
 };
 
 // Dispatcher: admits published requests into an active set and cuts them into
@@ -476,9 +475,8 @@ __global__ void __launch_bounds__(kServeThreads, COOP ? 3 : 4) serve_kernel(DevG
     w0.cur = 0;
     w0.pend = 0;
     w0.has_ticket = 0;
-    w0.poll_wait = 0;
     w0.empty_polls = 0;
-    w0.pad = 0;
+    w0.pad[0] = w0.pad[1] = 0;
     *wsp = w0;
   }
   __syncwarp();
@@ -495,6 +493,11 @@ __global__ void __launch_bounds__(kServeThreads, COOP ? 3 : 4) serve_kernel(DevG
   int ent = 0;                        // this lane's slot
   unsigned long long moves_acc = 0;
   unsigned act_mask = 0;              // lanes with a walk (warp-uniform)
+  // After an empty poll of the queue while some lanes still walk, the warp
+  // skips its next polls for a few refills (warp-uniform): a poll is a round
+  // trip to L2 that would otherwise precede every step of the warp's
+  // remaining walks.
+  int poll_wait = 0;
 
   for (;;) {
     if (act_mask != 0xffffffffu) {
@@ -526,12 +529,8 @@ __global__ void __launch_bounds__(kServeThreads, COOP ? 3 : 4) serve_kernel(DevG
       __syncwarp();
     }
     // A partly busy warp that is waiting out its poll backoff only counts down.
-    const bool skip_poll = idle != 0u && idle != 0xffffffffu && wsp->poll_wait > 0 && wsp->pend == 0;
-    if (skip_poll) {
-      __syncwarp();
-      if (lane == 0) wsp->poll_wait -= 1;
-      __syncwarp();
-    }
+    const bool skip_poll = idle != 0u && idle != 0xffffffffu && poll_wait > 0 && wsp->pend == 0;
+    if (skip_poll) --poll_wait;
     if (idle != 0u && !skip_poll) {
     // the rest of the warp's bookkeeping, loaded for this refill and stored back below
     bool pend = wsp->pend != 0;
@@ -539,10 +538,7 @@ __global__ void __launch_bounds__(kServeThreads, COOP ? 3 : 4) serve_kernel(DevG
     unsigned long long ticket = wsp->ticket;
     unsigned long long pk = wsp->pk;
     uint32_t pb = wsp->pb, pe = wsp->pe;
-    // After an empty poll of the queue while some lanes still walk, the warp
-    // skips its next polls for a few refills: a poll is a round trip to L2
-    // that would otherwise precede every step of the warp's remaining walks.
-    int poll_wait = 0;
+    poll_wait = 0;
     int empty_polls = wsp->empty_polls;
     const unsigned was_active = act_mask;
     while (idle != 0u) {
@@ -659,7 +655,6 @@ __global__ void __launch_bounds__(kServeThreads, COOP ? 3 : 4) serve_kernel(DevG
     __syncwarp();
     if (lane == 0) {
       if (act_mask != was_active) wsp->idle_since = -1;  // walks started: the warp is not idle
-      wsp->poll_wait = poll_wait;
       wsp->empty_polls = empty_polls;
       wsp->cur = cur;
       wsp->wlo = wlo;
