@@ -301,9 +301,9 @@ def cpu_baseline(g, wl, seconds: float = 12.0):
             # Node2Vec with the neighbour hash: the row pair of cur, one col sector per
             # attempt, one bucket sector per IsNeighbor that decides an attempt
             "model_bytes_per_move_hashed": ROW_PAIR + (SECTOR * (attempts + checks) + out_bytes) / max(1, done_moves),
-            # with row records as well: a move reads no row-offset pair; a dart
-            # reads its candidate's record unless it is return-only (decided from
-            # prev's position in the row)
+            # with row records as well (graph without weights): a move reads no
+            # row-offset pair; a dart reads its candidate's record unless it is
+            # return-only (decided from prev's position in the row)
             "model_bytes_per_move_records_hashed": (SECTOR * (attempts - ret_only + checks) + out_bytes) /
             max(1, done_moves),
             "attempts_per_move": attempts / max(1, done_moves), "checks_per_move": checks / max(1, done_moves),
@@ -373,8 +373,9 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False
     if bpm is None and cpu is not None and hashed and records and wl["algo"] == "node2vec":
         bpm = cpu["model_bytes_per_move_records_hashed"]
         per_walk = BYTES_PER_WALK_BASE + ROW_PAIR
-        source = ("one 32-byte row record per dart that reads its candidate (darts past both non-return "
-                  "thresholds are decided from the previous vertex's position) and one sector per deciding "
+        source = ("one row record (its 32-byte sector) per dart that reads its candidate (on this unweighted "
+                  "graph, darts past both non-return thresholds are decided from the previous vertex's position "
+                  "in the record's aux word) and one sector per deciding "
                   "IsNeighbor (neighbour hash), plus the path entry; counts from the oracle on the CPU-baseline "
                   "sample; the source's row once per walk")
     elif bpm is None and cpu is not None and hashed:

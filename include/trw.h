@@ -477,10 +477,10 @@ trw_status trw_debug_alias(const trw_graph* g, uint32_t* H, int32_t* first, int3
  * TRW_ERR_INVALID (NULL argument), TRW_ERR_NOT_PREPARED, TRW_ERR_CUDA. */
 trw_status trw_debug_its_records(const trw_graph* g, uint32_t* words);
 
-/* Copy the row records to host memory, 8 int32 words per edge slot e = (v ->
- * dst): {dst, its row offset, its degree, the integer weight W_e (0 without
- * weights), the position of v in dst's row (-1: none, or rows not sorted), 0,
- * 0, 0}.  For tests.  Errors: TRW_ERR_INVALID (NULL argument),
+/* Copy the row records to host memory, 4 int32 words per edge slot e = (v ->
+ * dst): {dst, its row offset, its degree, aux}, aux the integer weight W_e on a
+ * weighted graph, else the position of v in dst's row (-1: none, or rows not
+ * sorted).  For tests.  Errors: TRW_ERR_INVALID (NULL argument),
  * TRW_ERR_NOT_PREPARED, TRW_ERR_CUDA. */
 trw_status trw_debug_row_records(const trw_graph* g, int32_t* words);
 

@@ -527,10 +527,10 @@ class Graph:
         return out
 
     def debug_row_records(self) -> np.ndarray:
-        """Row records as int32 [ne, 8]: destination, its row offset and degree,
-        the integer weight, the position of the source in the destination's
-        row (-1: none), 0, 0, 0."""
-        out = np.empty((self.ne, 8), dtype=np.int32)
+        """Row records as int32 [ne, 4]: destination, its row offset and degree,
+        and aux: the integer weight on a weighted graph, else the position of
+        the source in the destination's row (-1: none)."""
+        out = np.empty((self.ne, 4), dtype=np.int32)
         _check(load_library().trw_debug_row_records(self._h, out.ctypes.data), "trw_debug_row_records")
         return out
 

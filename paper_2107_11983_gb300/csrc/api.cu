@@ -337,6 +337,7 @@ DevGraph trw_dev_graph(const trw_graph* g) {
   d.pmax = g->rej_pmax;
   d.its_rec = g->its_rec;
   d.rrec = g->rrec;
+  d.rrec_rev = (g->rrec && !g->weights) ? 1 : 0;
   d.lidx.vrec = g->lvrec;
   d.lidx.erec = g->lerec;
   d.lidx.stride = g->lstride;

@@ -511,9 +511,10 @@ __global__ void label_gather_kernel(int64_t ne, int32_t stride, const int32_t* _
 
 // ---------------------------------------------------------------- row records
 
-// One thread per edge e = (v -> c): c's row, the integer weight, and the
-// position of v in c's sorted row (a lower-bound search; -1 when absent or the
-// rows are not sorted).  v is found from e by a search of the row offsets.
+// One thread per edge e = (v -> c): c's row and the aux word, the integer
+// weight on a weighted graph, else the position of v in c's sorted row (a
+// lower-bound search; -1 when absent or the rows are not sorted), where v is
+// found from e by a search of the row offsets.
 __global__ void row_records_kernel(int32_t nv, int64_t ne, const int32_t* __restrict__ row_ptr,
                                    const int32_t* __restrict__ col, const float* __restrict__ weights, bool sorted,
                                    RowRec* __restrict__ rec) {
@@ -521,9 +522,10 @@ __global__ void row_records_kernel(int32_t nv, int64_t ne, const int32_t* __rest
     const int32_t c = col[e];
     const int32_t o = row_ptr[c];
     const int32_t d = row_ptr[c + 1] - o;
-    const uint32_t w = weights ? weight_fixed(weights[e]) : 0u;
-    int32_t rev = -1;
-    if (sorted) {
+    int32_t aux = -1;
+    if (weights) {
+      aux = (int32_t)weight_fixed(weights[e]);
+    } else if (sorted) {
       // v: the last row whose offset is <= e
       int32_t lo = 0, n = nv;
       while (n > 0) {
@@ -548,11 +550,10 @@ __global__ void row_records_kernel(int32_t nv, int64_t ne, const int32_t* __rest
           n = half;
         }
       }
-      if (a < d && col[o + a] == v) rev = a;
+      if (a < d && col[o + a] == v) aux = a;
     }
     RowRec r;
-    r.a = make_int4(c, o, d, (int32_t)w);
-    r.b = make_int4(rev, 0, 0, 0);
+    r.a = make_int4(c, o, d, aux);
     rec[e] = r;
   }
 }

@@ -42,17 +42,17 @@ struct __align__(32) AliasRec {
   uint4 b;
 };
 
-// Row record of one edge slot e = (v -> dst), one 32-byte sector (an optional
+// Row record of one edge slot e = (v -> dst), 16 bytes (an optional
 // preparation; walks are identical with and without it):
-//   a = {dst, row offset of dst, degree of dst, W_e (the integer weight, 0 without weights)}
-//   b = {rev_e, 0, 0, 0}
-// rev_e is the position in dst's row of the edge back to v, -1 when dst has
-// none or the rows are not sorted.  A NAIVE move, an O-REJ candidate or a REJ
-// dart reads a; Node2Vec also reads rev_e, which lets a later step decide a
-// return-only dart without reading its candidate.
-struct __align__(32) RowRec {
+//   a = {dst, row offset of dst, degree of dst, aux}
+// On a weighted graph aux is W_e, the integer weight, which a REJ dart or a
+// weighted O-REJ candidate reads.  On a graph without weights it is rev_e, the
+// position in dst's row of the edge back to v (-1 when dst has none or the rows
+// are not sorted): Node2Vec keeps it for the next step, where it decides a
+// return-only dart without reading its candidate.  Two records share a 32-byte
+// sector, so neighbouring edge slots of a row cost one DRAM sector.
+struct __align__(16) RowRec {
   int4 a;
-  int4 b;
 };
 
 // Guided ITS records (an optional preparation; walks are identical with and
@@ -132,6 +132,7 @@ struct DevGraph {
   NeighborHash nh;
   int32_t nv;
   int32_t ne;
+  int32_t rrec_rev;                     // 1: the records' aux word is rev_e (no weights), 0: W_e
 };
 
 // One walk request as a kernel sees it.  Thresholds are fixed-point

@@ -154,7 +154,10 @@ __device__ __forceinline__ bool is_neighbor(const DevGraph& g, int32_t prev, int
 // (warp_metapath / warp_neighbor) and step_finish completes the step.
 // CHECK adds range checks of the walker's vertex and of the row it loads
 // before any access through them (kBroken instead of an out-of-range read).
-template <int A, bool CHECK = false, bool FOLD = true>
+// RET lets Node2Vec keep the positions that decide return-only darts; the
+// per-request dispatch of mixed batches leaves it off, which keeps that
+// kernel's code and live state those of the other algorithms.
+template <int A, bool CHECK = false, bool FOLD = true, bool RET = true>
 __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next, Pend& p,
                                           Coop coop) {
   p.kind = 0;
@@ -325,7 +328,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     // REJ / O-REJ: dart (x, y), x uniform in [0, d_v); it hits when
     // y < floor(W_x * 2^32 / p*), i.e. when (y + 1) * p* <= W_x * 2^32.
     // p* is the row's stored bound (REJ) or the caller's (O-REJ, in T_stop).
-    if (CHECK && !g.rrec && !g.weights) return kBroken;
+    if (CHECK && !g.weights) return kBroken;
     unsigned long long ps = sp.T_stop;
     if (A == DW_REJ && sp.algo != DW_OREJ) {
       if (CHECK && ((uint32_t)W.cur >= (uint32_t)g.nv || !g.pmax)) return kBroken;
@@ -362,11 +365,11 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
         P = __ldg(g.pmax + W.cur);
         if (P == 0ull) return kStop;                           // no positive weight
       }
-      if (CHECK && !g.rrec && !g.weights) return kBroken;
+      if (CHECK && !g.weights) return kBroken;
     }
     uint4 Bd = B;  // this dart's block
     uint32_t x = below(Bd, (uint32_t)W.d);
-    if (A == NODE2VEC && W.s > 0 && W.rev != -2) {
+    if (A == NODE2VEC && RET && W.s > 0 && W.rev != -2) {
       // At or past both non-return thresholds only a return to prev can
       // accept, and prev's position in this row is known (-1: not in it): such
       // a dart is decided without reading its candidate.  With FOLD, when it is
@@ -397,7 +400,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     int32_t rrev = -2;
     if (g.rrec) {
       rr = __ldg(&g.rrec[e].a);
-      if (A == NODE2VEC) rrev = __ldg(&g.rrec[e].b).x;  // same sector
+      if (A == NODE2VEC && RET && g.rrec_rev) rrev = rr.w;  // the aux word holds rev_e
     }
     const int32_t c = g.rrec ? rr.x : ldg(g.col + e);
     if (A == N2V_W) {
@@ -425,7 +428,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
         W.nxo = rr.y;
         W.nxd = rr.z;
         W.nxv = true;
-        if (A == NODE2VEC) {  // positions for the next step's return-only darts
+        if (A == NODE2VEC && RET) {  // positions for the next step's return-only darts
           W.rev = rrev;
           W.px = (int32_t)x;
         }
@@ -437,10 +440,10 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
 }
 
 // The thread-serial step (no warp cooperation).
-template <int A, bool CHECK = false, bool FOLD = true>
+template <int A, bool CHECK = false, bool FOLD = true, bool RET = true>
 __device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   Pend p;
-  return step_begin<A, CHECK, FOLD>(g, sp, W, next, p, Coop{0x7fffffff, 0x7fffffff});
+  return step_begin<A, CHECK, FOLD, RET>(g, sp, W, next, p, Coop{0x7fffffff, 0x7fffffff});
 }
 
 // Completes a deferred step once the warp has filled p.res.
@@ -697,7 +700,7 @@ __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& 
       case DEEPWALK: return step_serial<DEEPWALK, CHECK, FOLD>(g, sp, W, next);
       case DEEPWALK_WEIGHTED: return step_serial<DEEPWALK_WEIGHTED, CHECK, FOLD>(g, sp, W, next);
       case PPR: return step_serial<PPR, CHECK, FOLD>(g, sp, W, next);
-      case NODE2VEC: return step_serial<NODE2VEC, CHECK, FOLD>(g, sp, W, next);
+      case NODE2VEC: return step_serial<NODE2VEC, CHECK, FOLD, false>(g, sp, W, next);
       case METAPATH: return step_serial<METAPATH, CHECK, FOLD>(g, sp, W, next);
       case DW_ITS:
       case DW_REJ:
@@ -719,7 +722,7 @@ __device__ __forceinline__ int step_begin_dispatch(const DevGraph& g, const Walk
       case DEEPWALK: return step_begin<DEEPWALK, CHECK>(g, sp, W, next, p, coop);
       case DEEPWALK_WEIGHTED: return step_begin<DEEPWALK_WEIGHTED, CHECK>(g, sp, W, next, p, coop);
       case PPR: return step_begin<PPR, CHECK>(g, sp, W, next, p, coop);
-      case NODE2VEC: return step_begin<NODE2VEC, CHECK>(g, sp, W, next, p, coop);
+      case NODE2VEC: return step_begin<NODE2VEC, CHECK, true, false>(g, sp, W, next, p, coop);
       case METAPATH: return step_begin<METAPATH, CHECK>(g, sp, W, next, p, coop);
       case DW_ITS:
       case DW_REJ:

@@ -1,14 +1,16 @@
-"""Node2Vec's return-only darts (GPU only).  With row records, each record
-carries the position of the edge's source in its destination's row; a
-Node2Vec dart whose word lies at or past both non-return thresholds can only
-be accepted as a return to the previous vertex, so the kernels decide it from
-that position without reading the candidate.  The positions must be exact and
-the walks the oracle's, for parameters that do and do not leave such darts,
-on symmetric and directed graphs (where the edge back may be missing), in
-every kernel and with or without the neighbour hash."""
+"""Node2Vec's return-only darts (GPU only).  With row records on a graph
+without weights, each record's aux word is the position of the edge's source
+in its destination's row; a Node2Vec dart whose word lies at or past both
+non-return thresholds can only be accepted as a return to the previous vertex,
+so the kernels decide it from that position without reading the candidate.
+The positions must be exact and the walks the oracle's, for parameters that do
+and do not leave such darts, on symmetric and directed graphs (where the edge
+back may be missing), in every kernel and with or without the neighbour hash;
+on a weighted graph the aux word is the weight and the walks stay exact."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2107_11983_gb300 as trw
 import synth
 from gpu_common import assert_paths_equal, oracle_walk, rmat_graph
@@ -16,6 +18,13 @@ from gpu_common import assert_paths_equal, oracle_walk, rmat_graph
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+
+def expected_weight_words(weights):
+    """The records' aux word on a weighted graph: the oracle's integer weight,
+    as the int32 with the same bits."""
+    q = np.array([oracle.quantize_weight(float(w)) for w in weights], dtype=np.int64)
+    return q.astype(np.uint32).view(np.int32)
 
 
 def expected_records(g, weights=None):
@@ -43,9 +52,7 @@ def test_row_record_reverse_positions(symmetric):
     assert np.array_equal(rec[:, 0], dst)
     assert np.array_equal(rec[:, 1], off)
     assert np.array_equal(rec[:, 2], deg)
-    assert np.array_equal(rec[:, 3], np.zeros(g.ne))
-    assert np.array_equal(rec[:, 4], rev)
-    assert not rec[:, 5:].any()
+    assert np.array_equal(rec[:, 3], rev)
     if symmetric:
         assert (rev >= 0).all()
     else:
@@ -74,12 +81,12 @@ def test_node2vec_return_only_darts_match_oracle(symmetric, kernel, prep):
 
 def test_node2vec_return_only_darts_in_mixed_batch_and_weighted_graph():
     """Node2Vec beside other algorithms in one launch, on a weighted graph
-    (the records' weight word is set, the position word still read)."""
+    (the records' aux word is the weight: no return positions)."""
     g = rmat_graph(12)
     G = trw.Graph(g.row_ptr, g.col, g.weights, None)
     G.prepare(trw.PREP_ALIAS | trw.PREP_ROW_RECORDS)
     rec = G.debug_row_records()
-    assert (rec[:, 3] > 0).all() and (rec[:, 4] >= 0).all()
+    assert np.array_equal(rec[:, 3], expected_weight_words(g.weights))
     srcs = [synth.sources(3000, g.nv, seed=s) for s in (5, 6, 7)]
     reqs = [dict(algo=trw.NODE2VEC, sources=torch.from_numpy(srcs[0]).cuda(), max_len=40, seed=31, n2v_p=0.5,
                  n2v_q=2.0),

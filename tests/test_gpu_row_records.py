@@ -46,7 +46,7 @@ def test_row_records_identical_walks(symmetric):
     plain = trw.Graph(g.row_ptr, g.col, None, None)
     rec = trw.Graph(g.row_ptr, g.col, None, None)
     rec.prepare(trw.PREP_ROW_RECORDS)
-    assert rec.device_bytes() >= plain.device_bytes() + 32 * g.ne
+    assert rec.device_bytes() >= plain.device_bytes() + 16 * g.ne
     for algo, L, kw in CASES.values():
         a = plain.walk(algo, src, L, seed=5, walks_per_source=2, **kw)
         b = rec.walk(algo, src, L, seed=5, walks_per_source=2, **kw)
