@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import argparse
 import contextlib
+import gc
 import hashlib
 import json
 import math
@@ -710,13 +711,24 @@ def measure_serve(trw, torch, G, g, n_requests=10000, rate=2000.0):
         return {"p50_ms": round(1000 * float(np.percentile(a, 50)), 3), "p99_ms": round(1000 * float(np.percentile(a, 99)), 3),
                 "mean_ms": round(1000 * float(a.mean()), 3)}
 
-    lat, wall, moves = run_server(True)
+    # Python's cycle collector stays off while a trace runs: a full collection
+    # over thousands of live tensors pauses the submitting thread for tens of
+    # milliseconds, which shows up in whichever arm it hits
+    def no_gc(fn, *a):
+        gc.collect()
+        gc.disable()
+        try:
+            return fn(*a)
+        finally:
+            gc.enable()
+
+    lat, wall, moves = no_gc(run_server, True)
     out["served"] = dict(pct(lat), steps_per_s=round(moves / wall, 1), wall_s=round(wall, 3))
-    lat, wall, moves = run_plain()
+    lat, wall, moves = no_gc(run_plain, True)
     out["plain_fifo"] = dict(pct(lat), steps_per_s=round(moves / wall, 1), wall_s=round(wall, 3))
-    lat, wall, moves = run_server(False)
+    lat, wall, moves = no_gc(run_server, False)
     out["saturating"] = {"steps_per_s": round(moves / wall, 1), "wall_s": round(wall, 3), "moves": moves}
-    lat, wall, moves = run_plain(False)
+    lat, wall, moves = no_gc(run_plain, False)
     out["plain_fifo_saturating"] = {"steps_per_s": round(moves / wall, 1), "wall_s": round(wall, 3), "moves": moves}
     # the batch kernel on the same requests: mixed batches of up to 64
     # requests in the trace's order, one launch each, back to back on one

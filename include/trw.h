@@ -580,7 +580,8 @@ trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_params* para
  * their device sources are read for the range check) only once the work
  * queued on stream before this call has finished -- e.g. the allocation or
  * fill of a request's buffers.  stream is a cudaStream_t ((void*)1 names the
- * legacy default stream).  Errors: TRW_ERR_INVALID (NULL), TRW_ERR_CUDA.
+ * legacy default stream).  A stream with no work left orders nothing, and the
+ * next submit publishes at once.  Errors: TRW_ERR_INVALID (NULL), TRW_ERR_CUDA.
  */
 trw_status trw_serve_order_after(trw_server* s, void* stream);
 

@@ -205,6 +205,16 @@ def _as_host(x, dtype):
     return np.ascontiguousarray(x, dtype=dtype)
 
 
+def _current_stream_handle() -> int:
+    """The caller's current CUDA stream as a cudaStream_t (1: the legacy
+    default stream), without building a torch Stream object where torch
+    exposes the raw handle."""
+    torch = _torch()
+    raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+    h = raw(torch.cuda.current_device()) if raw is not None else torch.cuda.current_stream().cuda_stream
+    return h or 1
+
+
 def _is_cuda(x) -> bool:
     return _is_torch(x) and x.is_cuda
 
@@ -218,7 +228,7 @@ def _stream_arg(stream, *arrays) -> int:
             stream = stream.cuda_stream
         return int(stream) or 1
     if any(_is_cuda(a) for a in arrays):
-        return int(_torch().cuda.current_stream().cuda_stream) or 1
+        return _current_stream_handle()
     return 0
 
 
@@ -634,6 +644,7 @@ class Server:
         self._h = h
         self.graph = graph
         self._keep = {}
+        self._reap_bufs = {}
 
     def submit(self, algo: int, sources, max_len: int, seed: int, out_paths, out_lengths, *, ppr_stop: float = 0.2,
                n2v_p: float = 1.0, n2v_q: float = 1.0, schema=None, walks_per_source: int = 1,
@@ -644,12 +655,11 @@ class Server:
         p, keep = _params(algo, ppr_stop, n2v_p, n2v_q, schema, walks_per_source, endpoints, walk_offset, sampler,
                           max_weight)
         src = sources if _is_torch(sources) else np.ascontiguousarray(sources, dtype=np.int32)
-        if any(_is_cuda(x) for x in (src, out_paths, out_lengths)):
+        if _is_cuda(src) or _is_cuda(out_paths) or _is_cuda(out_lengths):
             # the server runs on its own streams: work queued on the caller's
             # stream for these buffers (allocation, fills) must finish before
             # the request becomes visible -- ordered on the device, not waited for
-            _check(lib.trw_serve_order_after(self._h, _torch().cuda.current_stream().cuda_stream or 1),
-                   "trw_serve_order_after")
+            _check(lib.trw_serve_order_after(self._h, _current_stream_handle()), "trw_serve_order_after")
         rid = ctypes.c_uint64(0)
         st = lib.trw_serve_submit(self._h, algo, ctypes.byref(p), _ptr(src), int(src.shape[0]), max_len,
                                   seed & ((1 << 64) - 1), _ptr(out_paths), _ptr(out_lengths), ctypes.byref(rid))
@@ -669,9 +679,11 @@ class Server:
     def reap(self, max_requests: int = 256):
         """Finished requests, oldest first, as (request id, status) pairs (status 0
         is OK, else the request's error status); empty when none has finished."""
-        ids = (ctypes.c_uint64 * max_requests)()
-        sts = (ctypes.c_int32 * max_requests)()
-        n = ctypes.c_int32(0)
+        bufs = self._reap_bufs.get(max_requests)
+        if bufs is None:  # kept per size: a poll loop reaps often
+            bufs = self._reap_bufs[max_requests] = ((ctypes.c_uint64 * max_requests)(),
+                                                    (ctypes.c_int32 * max_requests)(), ctypes.c_int32(0))
+        ids, sts, n = bufs
         _check(load_library().trw_serve_reap(self._h, ids, sts, max_requests, ctypes.byref(n)), "trw_serve_reap")
         out = []
         for i in range(n.value):

@@ -1,14 +1,17 @@
 // Serving loop with continuous batching.
 //
 // Requests (any algorithm, any size) arrive while others run.  The host
-// copies a request's descriptor into a device slot table and publishes it by
-// copying the new request count into a device counter, both on a copy
-// stream (copy engines, no SM: the resident kernel holds every SM), so a
+// writes a request's descriptor into a ring of records in mapped host memory
+// and publishes it by raising the request count: with a store into mapped
+// memory, or, while the request must wait for a caller's stream (or its host
+// sources go up first), with a copy of the count into a device counter on a
+// copy stream (copy engines, no SM: the resident kernel holds every SM).  A
 // submit never waits for the device.  A resident persistent kernel does the
 // rest:
-//   - warp 0 of block 0 is the dispatcher: it reads the published counter
-//     (the only reader of the host ring), cuts each new request into chunks of
-//     walks and pushes them into a device chunk queue;
+//   - warp 0 of block 0 is the dispatcher: it reads the two counts (the only
+//     reader of the host ring), copies each new record into the device slot
+//     table, cuts the request into chunks of walks and pushes them into a
+//     device chunk queue;
 //   - every other warp is a worker: it pops chunks (CAS on the queue head),
 //     copies the request's descriptor into one of its two shared-memory slots
 //     (field by field, past L1, so a reused table entry is never read stale),
@@ -25,6 +28,7 @@
 #include <atomic>
 #include <cmath>
 #include <chrono>
+#include <cstddef>
 #include <cstring>
 #include <cstdint>
 #include <thread>
@@ -68,7 +72,9 @@ struct ServeState {       // device memory, persists across launches
   alignas(128) unsigned long long q_head;      // next queue entry to pop (tickets)
   alignas(128) unsigned long long q_tail;      // entries pushed
   alignas(128) unsigned long long q_consumed;  // entries popped and read
-  alignas(128) unsigned long long published;   // requests 0..published-1 are visible (written by host copies)
+  alignas(128) unsigned long long published;   // requests 0..published-1 are visible: a copy-engine store of the
+                                               // host's count (requests ordered after a caller's stream), raised
+                                               // by the dispatcher to the host-mapped count
   alignas(128) int exit_now;      // set by the dispatcher: the launch is ending (cleared before each launch)
   alignas(128) unsigned long long disp_next;   // dispatcher: next published request to admit
   int n_act;                      // dispatcher: requests with walks not yet queued
@@ -96,16 +102,26 @@ struct SlotRec {
   unsigned long long t_first;     // a worker loaded its descriptor (first walks start)
   unsigned long long t_done;      // its last walk finished
 };
+// The dispatcher copies a record as 16-byte words, one per lane, and reads
+// its own fields from the words it holds.
+constexpr int kRecWords = (int)(sizeof(SlotRec) / 16);
+static_assert(sizeof(SlotRec) % 16 == 0 && kRecWords <= 32, "slot record: whole 16-byte words, one per lane");
+static_assert(offsetof(SlotRec, spec) + offsetof(WalkSpec, sources) == 5 * 16, "sources: word 5, x-y");
+static_assert(offsetof(SlotRec, spec) + offsetof(WalkSpec, nwalks) == 6 * 16 + 8, "nwalks: word 6, z-w");
+static_assert(offsetof(SlotRec, cw) == 8 * 16 + 8 && offsetof(SlotRec, exp_moves) == 8 * 16 + 12, "cw, exp_moves: word 8, z, w");
+static_assert(offsetof(SlotRec, check_n) == 9 * 16 && offsetof(SlotRec, t_admit) == 9 * 16 + 8, "check_n, t_admit: word 9");
 
 struct ServeHost {        // host-mapped pinned memory
   unsigned int stop;              // the host asks the kernel to end
   unsigned int pad;
+  unsigned long long published;   // requests 0..published-1 are visible (host stores; see ServeState::published)
 };
 
 struct ServeDev {
   ServeState* state;
   Chunk* queue;                     // [kQueueCap]
   SlotRec* slots;                   // [R]
+  const SlotRec* stage;             // [R] host-mapped: the records as the host wrote them
   volatile ServeHost* host;         // device pointer to host-mapped control
   volatile unsigned long long* done;// [R] host-mapped: (k + 1) << 8 | -status once request k finished
   int R;
@@ -126,6 +142,17 @@ __device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long
 }
 
 __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_acquire_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+
+// 16 bytes of host-mapped memory, read again on every call.
+__device__ __forceinline__ uint4 ld_volatile_v4(const void* p) {
+  uint4 v;
+  asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
   unsigned long long v;
@@ -199,26 +226,47 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
     int go = 1;
     unsigned long long P = 0;
     if (lane == 0) {
+      // the larger of the two counts; the device count is raised to the host's
+      // (atomically: a copy-engine store may land at the same time) before any
+      // of its requests' chunks are queued, so workers may check against it
       P = ld_relaxed_gpu(&st->published);
-      if (P > disp_next) fence_acquire_gpu();  // the new requests' slot records after their count
+      const unsigned long long H = sv.host->published;
+      if (H > P) {
+        atomicMax(&st->published, H);
+        P = H;
+      }
+      if (P > disp_next) fence_acquire_sys();  // the new requests' records (host memory) after their count
     }
     // Admission, one request at a time.  A small request with device sources
     // has its sources range-checked here by the whole warp; one out of range
     // completes the request with the invalid-argument status, and no walk runs.
     for (;;) {
       int adm = 0, slot = 0;
-      unsigned long long n = 0, src = 0;
-      uint32_t chk = 0;
       if (lane == 0 && n_act < kMaxActive && disp_next < P) {
         adm = 1;
         slot = (int)(disp_next % (unsigned long long)sv.R);
-        n = (unsigned long long)__ldcg(&sv.slots[slot].spec.nwalks);
-        chk = __ldcg(&sv.slots[slot].check_n);
-        src = __ldcg(reinterpret_cast<const unsigned long long*>(&sv.slots[slot].spec.sources));
-        sv.slots[slot].t_admit = (unsigned long long)now_ns();
       }
       if (!__shfl_sync(0xffffffffu, adm, 0)) break;
-      chk = __shfl_sync(0xffffffffu, chk, 0);
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      // The request's record: from the host's staging into the device table,
+      // one 16-byte word per lane, stamped with the admission time.
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      if (lane < kRecWords) {
+        w = ld_volatile_v4(reinterpret_cast<const uint4*>(sv.stage + slot) + lane);
+        if (lane == 9) {
+          const unsigned long long t = (unsigned long long)now_ns();
+          w.z = (uint32_t)t;
+          w.w = (uint32_t)(t >> 32);
+        }
+        __stcg(reinterpret_cast<uint4*>(sv.slots + slot) + lane, w);
+      }
+      const unsigned long long src = ((unsigned long long)__shfl_sync(0xffffffffu, w.y, 5) << 32) |
+                                     __shfl_sync(0xffffffffu, w.x, 5);
+      const unsigned long long n = ((unsigned long long)__shfl_sync(0xffffffffu, w.w, 6) << 32) |
+                                   __shfl_sync(0xffffffffu, w.z, 6);
+      const uint32_t rcw = __shfl_sync(0xffffffffu, w.z, 8);
+      const uint32_t rexp = __shfl_sync(0xffffffffu, w.w, 8);
+      const uint32_t chk = __shfl_sync(0xffffffffu, w.x, 9);
       uint32_t bad = 0;
       if (chk) {
         const int32_t* s_ptr = reinterpret_cast<const int32_t*>(__shfl_sync(0xffffffffu, src, 0));
@@ -234,8 +282,8 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
           act->k[n_act] = disp_next;
           act->pos[n_act] = 0;
           act->n[n_act] = n;
-          act->cw[n_act] = __ldcg(&sv.slots[slot].cw);
-          act->w[n_act] = __ldcg(&sv.slots[slot].exp_moves);
+          act->cw[n_act] = rcw;
+          act->w[n_act] = rexp;
           ++n_act;
         }
         ++disp_next;
@@ -616,10 +664,12 @@ __global__ void __launch_bounds__(kServeThreads, COOP ? 3 : 4) serve_kernel(DevG
         if (tgt < 0) break;
         if (wsp->fin[tgt] != 0) flush_finished(sv, tgt, spec, key, wsp);  // counted before it changes hands
         int bad = 0;
+        // the published count for the self-check, in flight with the descriptor
+        const unsigned long long pub_now = lane == 0 ? ld_relaxed_gpu(&sv.state->published) : 0ull;
         load_spec(&sv.slots[(int)(pk % (unsigned long long)sv.R)].spec, &spec[tgt]);
         if (lane == 0) {
           atomicCAS(&sv.slots[(int)(pk % (unsigned long long)sv.R)].t_first, 0ull, (unsigned long long)now_ns());
-          bad = spec_check(spec[tgt], pk, pb, pe, ld_relaxed_gpu(&sv.state->published));
+          bad = spec_check(spec[tgt], pk, pb, pe, pub_now);
           if (bad) record_bad(sv, bad, pk, ((unsigned long long)pb << 32) | pe, (unsigned long long)spec[tgt].nwalks,
                               reinterpret_cast<uintptr_t>(spec[tgt].out_paths));
           key[tgt] = bad ? ~0ull : pk;
@@ -797,6 +847,9 @@ struct trw_server {
   cudaStream_t stream = nullptr;       // the resident kernel
   cudaStream_t copy_stream = nullptr;  // descriptor uploads
   cudaEvent_t ev_after = nullptr;      // trw_serve_order_after: the caller's stream, recorded
+  bool after_pending = false;          // ev_after recorded and not yet known to be complete
+  cudaEvent_t ev_pub = nullptr;        // after the last copy-engine publication
+  bool ce_pub_pending = false;         // ev_pub recorded and not yet known to be complete
   ServeState* state = nullptr;
   Chunk* queue = nullptr;
   SlotRec* slots = nullptr;
@@ -806,7 +859,8 @@ struct trw_server {
   unsigned long long* done = nullptr;  // mapped [R]
   ServeHost* host_dev = nullptr;
   unsigned long long* done_dev = nullptr;
-  SlotRec* slot_stage = nullptr;       // pinned staging [R]
+  SlotRec* slot_stage = nullptr;       // mapped [R]: the records the dispatcher copies in at admission
+  SlotRec* slot_stage_dev = nullptr;
   unsigned long long* pub_stage = nullptr;  // pinned [R]: the count that publishes request k is pub_stage[k % R]
   int32_t* check_buf = nullptr;        // pinned: host copy of device sources for the range check
   int64_t check_cap = 0;
@@ -838,6 +892,7 @@ static void server_release(trw_server* s) {
   if (s->stream) cudaStreamDestroy(s->stream);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->ev_after) cudaEventDestroy(s->ev_after);
+  if (s->ev_pub) cudaEventDestroy(s->ev_pub);
   cudaFree(s->state);
   cudaFree(s->queue);
   cudaFree(s->slots);
@@ -880,6 +935,7 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   SV_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking), "stream");
   SV_TRY(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "stream");
   SV_TRY(cudaEventCreateWithFlags(&s->ev_after, cudaEventDisableTiming), "event");
+  SV_TRY(cudaEventCreateWithFlags(&s->ev_pub, cudaEventDisableTiming), "event");
   SV_TRY(trw_dev_malloc((void**)&s->state, sizeof(ServeState)), "serve state");
   SV_TRY(cudaMemset(s->state, 0, sizeof(ServeState)), "serve state");
   SV_TRY(trw_dev_malloc((void**)&s->queue, sizeof(Chunk) * kQueueCap), "chunk queue");
@@ -888,12 +944,13 @@ extern "C" trw_status trw_serve_create(trw_graph* g, const trw_serve_config* cfg
   SV_TRY(trw_dev_malloc((void**)&s->src_pool, sizeof(int32_t) * (size_t)s->src_cap), "source pool");
   SV_TRY(trw_host_alloc((void**)&s->host, sizeof(ServeHost), cudaHostAllocMapped), "mapped control");
   SV_TRY(trw_host_alloc((void**)&s->done, sizeof(unsigned long long) * R, cudaHostAllocMapped), "mapped flags");
-  SV_TRY(trw_host_alloc((void**)&s->slot_stage, sizeof(SlotRec) * R, cudaHostAllocDefault), "pinned staging");
+  SV_TRY(trw_host_alloc((void**)&s->slot_stage, sizeof(SlotRec) * R, cudaHostAllocMapped), "mapped records");
   SV_TRY(trw_host_alloc((void**)&s->pub_stage, sizeof(unsigned long long) * R, cudaHostAllocDefault), "pinned staging");
   std::memset((void*)s->host, 0, sizeof(ServeHost));
   std::memset((void*)s->done, 0, sizeof(unsigned long long) * R);
   SV_TRY(cudaHostGetDevicePointer((void**)&s->host_dev, (void*)s->host, 0), "mapped pointer");
   SV_TRY(cudaHostGetDevicePointer((void**)&s->done_dev, (void*)s->done, 0), "mapped pointer");
+  SV_TRY(cudaHostGetDevicePointer((void**)&s->slot_stage_dev, (void*)s->slot_stage, 0), "mapped pointer");
   s->req_walks.assign(R, 0);
   s->req_bytes.assign(R, 0);
   s->req_src_pos.assign(R, 0);
@@ -923,6 +980,7 @@ static cudaError_t launch_if_idle(trw_server* s) {
   sv.state = s->state;
   sv.queue = s->queue;
   sv.slots = s->slots;
+  sv.stage = s->slot_stage_dev;
   sv.host = s->host_dev;
   sv.done = s->done_dev;
   sv.R = s->R;
@@ -965,9 +1023,15 @@ extern "C" trw_status trw_serve_order_after(trw_server* s, void* stream) {
   if (!s || !stream) return trw_fail(TRW_ERR_INVALID, "NULL server or stream");
   if (trw_status dc = trw_check_device(s->g); dc != TRW_OK) return dc;
   std::lock_guard<std::mutex> lk(s->mu);
+  // A stream with nothing left to run orders nothing.  Otherwise the next
+  // submit publishes through the copy stream, behind an event recorded here,
+  // unless the event has completed by then.
+  const cudaError_t q = cudaStreamQuery((cudaStream_t)stream);
+  if (q == cudaSuccess) return TRW_OK;
+  if (q != cudaErrorNotReady) return trw_cuda_fail(q, "serve order after");
   cudaError_t e = cudaEventRecord(s->ev_after, (cudaStream_t)stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, s->ev_after, 0);
   if (e != cudaSuccess) return trw_cuda_fail(e, "serve order after");
+  s->after_pending = true;
   return TRW_OK;
 }
 
@@ -1029,8 +1093,14 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
       if (ea != cudaSuccess) return trw_cuda_fail(ea, "serve source check buffer");
       s->check_cap = n_sources;
     }
-    cudaError_t ec = cudaMemcpyAsync(s->check_buf, sources, sizeof(int32_t) * (size_t)n_sources,
-                                     cudaMemcpyDeviceToHost, s->copy_stream);
+    cudaError_t ec = cudaSuccess;
+    if (s->after_pending) {  // the caller's writes of the sources first
+      ec = cudaStreamWaitEvent(s->copy_stream, s->ev_after, 0);
+      if (ec == cudaSuccess) s->after_pending = false;
+    }
+    if (ec == cudaSuccess)
+      ec = cudaMemcpyAsync(s->check_buf, sources, sizeof(int32_t) * (size_t)n_sources, cudaMemcpyDeviceToHost,
+                           s->copy_stream);
     if (ec == cudaSuccess) ec = cudaStreamSynchronize(s->copy_stream);
     if (ec != cudaSuccess) return trw_cuda_fail(ec, "serve source check");
     if (!trw_sources_in_range(s->check_buf, n_sources, s->g->nv))
@@ -1059,21 +1129,47 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   rec.check_n = dev_check ? (uint32_t)n_sources : 0u;
   rec.pad = 0;
   rec.t_admit = rec.t_first = rec.t_done = 0;
-  // Nothing below waits for the device: the sources, the slot record and
-  // then the new request count go up on the copy stream, in submission
-  // order.  The pinned record and count are not reused before the request is
-  // collected, when their copies have long completed.
+  // Publication waits for nothing.  The record stays in mapped host memory,
+  // where the dispatcher copies it into the device table when it admits the
+  // request; the request count goes either straight into mapped memory or,
+  // while an ordering event or an earlier copy-engine publication is still
+  // pending, or host sources must go up first, through the copy stream in
+  // submission order.  The record is not rewritten before the request is
+  // collected, long after its admission.
   cudaStream_t cs = s->copy_stream;
   s->done[slot] = 0;
   cudaError_t e = cudaSuccess;
-  if (pool_n > 0)
-    e = cudaMemcpyAsync(s->src_pool + pos, sources, sizeof(int32_t) * (size_t)pool_n, cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&s->slots[slot], &rec, sizeof(SlotRec), cudaMemcpyHostToDevice, cs);
-  s->pub_stage[slot] = k + 1;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&s->state->published, &s->pub_stage[slot], sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                        cs);
-  if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit upload");
+  bool direct = pool_n == 0;
+  if (direct && s->after_pending) {
+    const cudaError_t q = cudaEventQuery(s->ev_after);
+    if (q == cudaSuccess) s->after_pending = false;
+    else if (q == cudaErrorNotReady) direct = false;
+    else return trw_cuda_fail(q, "serve order after");
+  }
+  if (direct && s->ce_pub_pending) {
+    const cudaError_t q = cudaEventQuery(s->ev_pub);
+    if (q == cudaSuccess) s->ce_pub_pending = false;
+    else if (q == cudaErrorNotReady) direct = false;
+    else return trw_cuda_fail(q, "serve publication");
+  }
+  if (direct) {
+    __atomic_store_n(&s->host->published, k + 1, __ATOMIC_RELEASE);  // after the record's stores
+  } else {
+    if (s->after_pending) {
+      e = cudaStreamWaitEvent(cs, s->ev_after, 0);
+      if (e == cudaSuccess) s->after_pending = false;
+    }
+    if (e == cudaSuccess && pool_n > 0)
+      e = cudaMemcpyAsync(s->src_pool + pos, sources, sizeof(int32_t) * (size_t)pool_n, cudaMemcpyHostToDevice, cs);
+    s->pub_stage[slot] = k + 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);  // the record before the count
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&s->state->published, &s->pub_stage[slot], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                          cs);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_pub, cs);
+    if (e == cudaSuccess) s->ce_pub_pending = true;
+    if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit upload");
+  }
   s->req_walks[slot] = sp.nwalks;
   s->req_bytes[slot] = out_bytes;
   s->req_src_pos[slot] = pos;

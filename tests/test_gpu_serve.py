@@ -273,3 +273,29 @@ def test_serve_trace_timeline(served, server_factory):
     with pytest.raises(trw.TRWError) as e:
         S.trace(10 ** 6)
     assert e.value.status == -8
+
+
+@pytest.mark.parametrize("n", [300, 3000], ids=["checked-on-device", "checked-on-host"])
+def test_serve_waits_for_the_callers_stream(served, server_factory, n):
+    """A request whose device sources are still being written on the caller's
+    stream (a long-running kernel ahead of the write) runs on the written
+    sources: the submit publishes it only after that stream's work, whether
+    the dispatcher or the host range-checks the sources.  Requests submitted
+    while the stream is idle publish straight away (the other serve tests)."""
+    g, G = served
+    S = server_factory(G)
+    want_src = synth.sources(n, g.nv, seed=77)
+    r = dict(algo=trw.DEEPWALK, sources=want_src, max_len=40, seed=5)
+    src = torch.full((n,), g.nv + 7, dtype=torch.int32, device="cuda")  # out of range until written
+    good = torch.from_numpy(want_src).cuda()
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(50_000_000)  # tens of milliseconds of device time before the write
+        src.copy_(good)
+        op = torch.full((n, 41), -1, dtype=torch.int32, device="cuda")
+        ol = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        assert not stream.query(), "the caller's stream finished before the submit: nothing to order"
+        rid = S.submit(trw.DEEPWALK, src, 40, 5, op, ol)
+    wait(S, rid)
+    check(g, r, op, ol)
