@@ -198,5 +198,13 @@ __device__ __forceinline__ uint32_t weight_fixed(float w) {
 // Read-only loads through the non-coherent path.
 __device__ __forceinline__ int32_t ldg(const int32_t* p) { return __ldg(p); }
 __device__ __forceinline__ uint4 ldg(const uint4* p) { return __ldg(p); }
+// A 32-byte record (32-byte aligned) in one load: one L1 request for its one
+// sector, so its second half never depends on the line staying in L1 after
+// the first half's fill.  Read-only data (non-coherent path).
+__device__ __forceinline__ void ldg32(const void* p, uint4& a, uint4& b) {
+  asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+      : "l"(p));
+}
 
 }  // namespace trw

@@ -203,8 +203,8 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     // ALIAS generation from the stored C_v (no Gather for static walks); the
     // record also carries the picked vertex's row for the next step.
     const AliasRec* rec = g.alias + W.off + below(B, (uint32_t)W.d);
-    const uint4 ra = __ldg(&rec->a);
-    const uint4 rb = __ldg(&rec->b);
+    uint4 ra, rb;
+    ldg32(rec, ra, rb);
     const bool first = B.z < ra.x;
     const int32_t pick = first ? (int32_t)ra.y : (int32_t)ra.z;
     if (pick < 0) return kStop;                                // no positive weight
@@ -225,7 +225,8 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
         lo = hi = 0;
       } else if (g.lidx.stride == 8) {
         const uint4* rp = reinterpret_cast<const uint4*>(g.lidx.erec + e * 8);
-        const uint4 ra = __ldg(rp), rb = __ldg(rp + 1);
+        uint4 ra, rb;
+        ldg32(rp, ra, rb);
         next = (int32_t)ra.x;
         lo = (int32_t)word8(ra, rb, 1 + h2);
         hi = (int32_t)word8(ra, rb, 2 + h2);
