@@ -203,9 +203,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key: str):
-    """DRAM bytes per launch of the kernel from the committed ncu summary, or
-    None when absent or captured from a different kernel source."""
+def ncu_traffic(kernel_key: str, moves: int):
+    """DRAM bytes of this launch from the committed ncu capture of the kernel
+    on the workload (read + write bytes per move of a captured launch, smaller
+    where the full size is too large to capture, times this launch's moves),
+    or None when absent or captured from a different kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -214,7 +216,7 @@ def ncu_traffic(kernel_key: str):
     e = d.get(kernel_key)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("bytes_per_launch")
+    return int(round(e["dram_bytes"] / e["moves"] * moves))
 
 
 # ------------------------------------------------------------------ CPU baseline
@@ -391,7 +393,7 @@ def roofline(wl, moves, walks, kernel_ms, cpu, gather, steps_per_s, hashed=False
     alg_bytes = moves * bpm + walks * per_walk
     achieved = alg_bytes / (kernel_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(f"{kernel}/{wl['name']}"),
+            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(f"{kernel}/{wl['name']}", moves),
             "peak_kind": f"{peak_kind} copy bandwidth", "kernel": kernel,
             "bytes_per_move": round(bpm, 2), "bytes_per_move_source": source,
             "algorithmic_bytes_per_launch": int(alg_bytes)}
@@ -1350,7 +1352,9 @@ def run_mixed(args, wl):
         peak, kind = measured_peak_hbm()
         ach = alg / (kms / 1000.0) / 1e9
         line["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                            "frac": round(ach / peak, 4), "traffic": None, "peak_kind": f"{kind} copy bandwidth",
+                            "frac": round(ach / peak, 4),
+                            "traffic": ncu_traffic(f"walk_persistent<MIXED>/{wl['name']}", moves),
+                            "peak_kind": f"{kind} copy bandwidth",
                             "kernel": "walk_persistent<MIXED>", "bytes_per_move": round(alg / max(1, moves), 2),
                             "bytes_per_move_source": "closed form (32-byte sectors of the device layout, label index)",
                             "algorithmic_bytes_per_launch": int(alg)}
