@@ -90,7 +90,8 @@ struct ServeState {       // device memory, persists across launches
   unsigned long long bad[4];      // what that check saw
 };
 
-// Everything the device keeps per request slot, uploaded at submit in one copy.
+// Everything the device keeps per request slot: the host writes it into mapped
+// memory at submit, the dispatcher copies it into the device table at admission.
 struct SlotRec {
   WalkSpec spec;                  // the request
   unsigned long long finished;    // completion word: walks finished, error bits (zero at submit)
