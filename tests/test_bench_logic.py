@@ -135,3 +135,18 @@ def test_reference_arm_line(config):
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert str(1 << 14) in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_traffic_scales_captured_bytes_per_move(bench, monkeypatch):
+    """The bench's `traffic` is a committed capture's DRAM bytes per move times
+    the moves of the timed launch, and null once the kernel source changed."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    key = "walk_persistent/deepwalk-weighted-alias-rmat-s22"
+    e = rec[key]
+    assert e["source_hash"] == bench.kernel_source_hash(), "traffic.json was captured from another kernel source"
+    assert bench.ncu_traffic(key, e["moves"]) == e["dram_bytes"]
+    assert bench.ncu_traffic(key, 2 * e["moves"]) == 2 * e["dram_bytes"]
+    assert bench.ncu_traffic("walk_persistent/no-such-workload", 1000) is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.ncu_traffic(key, e["moves"]) is None

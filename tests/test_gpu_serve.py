@@ -299,3 +299,38 @@ def test_serve_waits_for_the_callers_stream(served, server_factory, n):
         rid = S.submit(trw.DEEPWALK, src, 40, 5, op, ol)
     wait(S, rid)
     check(g, r, op, ol)
+
+
+def test_serve_mixes_ordered_and_direct_publication(served, server_factory):
+    """Requests published through the copy stream (the caller's stream still
+    busy) and straight into mapped memory (an idle stream) interleave without
+    a request lost, admitted twice or out of order: every result is the
+    oracle's."""
+    g, G = served
+    S = server_factory(G)
+    rng = np.random.default_rng(9)
+    busy = torch.cuda.Stream()
+    idle = torch.cuda.Stream()
+    reqs, out = [], []
+    for i in range(12):
+        n = int(rng.integers(50, 400))
+        src_h = synth.sources(n, g.nv, seed=300 + i)
+        r = dict(algo=trw.DEEPWALK if i % 2 else trw.PPR, sources=src_h, max_len=30, seed=40 + i, ppr_stop=0.2)
+        src = torch.from_numpy(src_h).cuda()
+        op = torch.full((n, 31), -1, dtype=torch.int32, device="cuda")
+        ol = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        if i % 4 == 0:
+            # a request behind device work on its stream: published through the copy stream
+            with torch.cuda.stream(busy):
+                torch.cuda._sleep(5_000_000)
+                rid = S.submit(r["algo"], src, 30, r["seed"], op, ol, ppr_stop=0.2)
+        else:
+            with torch.cuda.stream(idle):
+                rid = S.submit(r["algo"], src, 30, r["seed"], op, ol, ppr_stop=0.2)
+        reqs.append(r)
+        out.append((rid, op, ol))
+    assert [rid for rid, _, _ in out] == list(range(out[0][0], out[0][0] + 12))
+    for r, (rid, op, ol) in zip(reqs, out):
+        wait(S, rid)
+        check(g, r, op, ol)
