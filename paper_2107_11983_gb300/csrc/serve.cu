@@ -849,6 +849,8 @@ struct trw_server {
   cudaStream_t copy_stream = nullptr;  // descriptor uploads
   cudaEvent_t ev_after = nullptr;      // trw_serve_order_after: the caller's stream, recorded
   bool after_pending = false;          // ev_after recorded and not yet known to be complete
+  bool cs_gated = false;               // the copy stream waits for an earlier ordering event: the next
+                                       // request is published behind it
   cudaEvent_t ev_pub = nullptr;        // after the last copy-engine publication
   bool ce_pub_pending = false;         // ev_pub recorded and not yet known to be complete
   ServeState* state = nullptr;
@@ -1030,7 +1032,15 @@ extern "C" trw_status trw_serve_order_after(trw_server* s, void* stream) {
   const cudaError_t q = cudaStreamQuery((cudaStream_t)stream);
   if (q == cudaSuccess) return TRW_OK;
   if (q != cudaErrorNotReady) return trw_cuda_fail(q, "serve order after");
-  cudaError_t e = cudaEventRecord(s->ev_after, (cudaStream_t)stream);
+  cudaError_t e = cudaSuccess;
+  if (s->after_pending) {
+    // an earlier call's event that no submit has consumed: the copy stream
+    // takes it over before the event is recorded again
+    e = cudaStreamWaitEvent(s->copy_stream, s->ev_after, 0);
+    if (e != cudaSuccess) return trw_cuda_fail(e, "serve order after");
+    s->cs_gated = true;
+  }
+  e = cudaEventRecord(s->ev_after, (cudaStream_t)stream);
   if (e != cudaSuccess) return trw_cuda_fail(e, "serve order after");
   s->after_pending = true;
   return TRW_OK;
@@ -1104,6 +1114,7 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
                            s->copy_stream);
     if (ec == cudaSuccess) ec = cudaStreamSynchronize(s->copy_stream);
     if (ec != cudaSuccess) return trw_cuda_fail(ec, "serve source check");
+    s->cs_gated = false;  // every wait on the copy stream has completed
     if (!trw_sources_in_range(s->check_buf, n_sources, s->g->nv))
       return trw_fail(TRW_ERR_INVALID, "a source vertex is outside [0, nv)");
   }
@@ -1140,7 +1151,7 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
   cudaStream_t cs = s->copy_stream;
   s->done[slot] = 0;
   cudaError_t e = cudaSuccess;
-  bool direct = pool_n == 0;
+  bool direct = pool_n == 0 && !s->cs_gated;
   if (direct && s->after_pending) {
     const cudaError_t q = cudaEventQuery(s->ev_after);
     if (q == cudaSuccess) s->after_pending = false;
@@ -1168,7 +1179,10 @@ extern "C" trw_status trw_serve_submit(trw_server* s, trw_algo algo, const trw_p
       e = cudaMemcpyAsync(&s->state->published, &s->pub_stage[slot], sizeof(unsigned long long), cudaMemcpyHostToDevice,
                           cs);
     if (e == cudaSuccess) e = cudaEventRecord(s->ev_pub, cs);
-    if (e == cudaSuccess) s->ce_pub_pending = true;
+    if (e == cudaSuccess) {
+      s->ce_pub_pending = true;
+      s->cs_gated = false;  // this publication follows every wait on the copy stream
+    }
     if (e != cudaSuccess) return trw_cuda_fail(e, "serve submit upload");
   }
   s->req_walks[slot] = sp.nwalks;

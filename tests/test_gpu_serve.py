@@ -334,3 +334,36 @@ def test_serve_mixes_ordered_and_direct_publication(served, server_factory):
     for r, (rid, op, ol) in zip(reqs, out):
         wait(S, rid)
         check(g, r, op, ol)
+
+
+def test_serve_two_ordering_calls_before_a_submit(served, server_factory):
+    """Through the C entry points: ordering after stream A, then after stream
+    B, then one submit.  The request waits for both streams' earlier work,
+    not only the last one's: its sources are written on A behind a long
+    kernel, while B has little to do."""
+    import ctypes
+    g, G = served
+    S = server_factory(G)
+    lib = trw.load_library()
+    n = 200
+    want_src = synth.sources(n, g.nv, seed=88)
+    src = torch.full((n,), g.nv + 3, dtype=torch.int32, device="cuda")  # out of range until written
+    good = torch.from_numpy(want_src).cuda()
+    op = torch.full((n, 31), -1, dtype=torch.int32, device="cuda")
+    ol = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(a):
+        torch.cuda._sleep(50_000_000)
+        src.copy_(good)
+    with torch.cuda.stream(b):
+        torch.cuda._sleep(1_000_000)
+    assert not a.query() and not b.query()
+    assert lib.trw_serve_order_after(S._h, a.cuda_stream) == 0
+    assert lib.trw_serve_order_after(S._h, b.cuda_stream) == 0
+    p, keep = trw._params(trw.DEEPWALK, 0.2, 1.0, 1.0, None, 1, False, 0, trw.SAMPLER_DEFAULT, 0.0)
+    rid = ctypes.c_uint64(0)
+    assert lib.trw_serve_submit(S._h, trw.DEEPWALK, ctypes.byref(p), src.data_ptr(), n, 30, 7, op.data_ptr(),
+                                ol.data_ptr(), ctypes.byref(rid)) == 0
+    wait(S, rid.value)
+    check(g, dict(algo=trw.DEEPWALK, sources=want_src, max_len=30, seed=7), op, ol)
