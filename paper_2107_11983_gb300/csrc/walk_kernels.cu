@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) walk_plain(DevGraph g, WalkSpec sp, Ctrl*
       if (!sp.endpoints) sp.out_paths[base] = src;
       for (;;) {
         int32_t next = -1;
-        const int r = step_dispatch<A, false, false>(g, sp, W, next);
+        const int r = step_dispatch<A, false, 0>(g, sp, W, next);
         if (r == kMoved) {
           advance(W, next);
           if (!sp.endpoints) sp.out_paths[base + W.s] = next;
@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(512) walk_persistent(DevGraph g, WalkSpec sp0,
     Pend pend;
     pend.kind = 0;
     pend.res = 0;
-    if (active) r = step_begin_dispatch<A>(g, sp, W, next, pend, COOP ? coop : Coop{0x7fffffff, 0x7fffffff});
+    if (active)
+      r = step_begin_dispatch<A, false, kFoldDarts>(g, sp, W, next, pend, COOP ? coop : Coop{0x7fffffff, 0x7fffffff});
     if constexpr (COOP) {
       if (__any_sync(kFull, r == kDefer)) {
         warp_resolve(g, r, W, pend);
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(256) bsp_step(DevGraph g, WalkSpec sp, const B
     int32_t next;
     for (;;) {
       next = -1;
-      r = step_dispatch<A, false, false>(g, sp, b.W, next);
+      r = step_dispatch<A, false, 0>(g, sp, b.W, next);
       if (r != kRetry) break;
       b.W.att += 1;
     }

@@ -41,6 +41,14 @@ __device__ __forceinline__ void walker_init(Walker& W, uint32_t w, int32_t src) 
   W.rowok = false;
 }
 
+// FOLD: how many of Node2Vec's return-only darts one unit decides before it
+// yields.  0 for the kernels whose threads run free (a per-lane loop splits
+// the warp); the persistent kernel takes kFoldDarts (its warp runs as many
+// Philox blocks as its busiest lane: more folded darts idle more lanes, fewer
+// cost more units); kFoldAll folds until the dart needs its candidate.
+constexpr int kFoldDarts = 2;
+constexpr int kFoldAll = 1 << 30;
+
 enum StepResult : int { kIdle = -1, kMoved = 0, kStop = 1, kRetry = 2, kFail = 3, kBroken = 4, kDefer = 5 };
 
 // Row lengths from which a lane hands its work to the warp.
@@ -157,7 +165,7 @@ __device__ __forceinline__ bool is_neighbor(const DevGraph& g, int32_t prev, int
 // RET lets Node2Vec keep the positions that decide return-only darts; the
 // per-request dispatch of mixed batches leaves it off, which keeps that
 // kernel's code and live state those of the other algorithms.
-template <int A, bool CHECK = false, bool FOLD = true, bool RET = true>
+template <int A, bool CHECK = false, int FOLD = kFoldAll, bool RET = true>
 __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next, Pend& p,
                                           Coop coop) {
   p.kind = 0;
@@ -373,11 +381,10 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
     if (A == NODE2VEC && RET && W.s > 0 && W.rev != -2) {
       // At or past both non-return thresholds only a return to prev can
       // accept, and prev's position in this row is known (-1: not in it): such
-      // a dart is decided without reading its candidate.  With FOLD, when it is
-      // rejected the next dart is drawn at once, within this unit of work (the
-      // warp-synchronous kernels); without, the unit ends with the retry (the
-      // kernels whose threads run free, where a per-lane loop here splits the
-      // warp).
+      // a dart is decided without reading its candidate.  When it is rejected
+      // the next dart is drawn at once, within this unit of work, up to FOLD
+      // darts; past them the unit ends with the retry.
+      int folds = 0;
       while ((uint64_t)Bd.z >= sp.T_hi) {
         if ((int32_t)x == W.rev && (uint64_t)Bd.z < sp.T_ret) {
           next = W.prev;
@@ -390,7 +397,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
           return kMoved;
         }
         if (W.att + 1 >= kRejectCap) return kFail;
-        if (!FOLD) return kRetry;
+        if (FOLD == 0 || (FOLD < kFoldAll && ++folds >= FOLD)) return kRetry;
         W.att += 1;
         Bd = draw_block(sp, W.w, (uint32_t)W.s, W.att);
         x = below(Bd, (uint32_t)W.d);
@@ -441,7 +448,7 @@ __device__ __forceinline__ int step_begin(const DevGraph& g, const WalkSpec& sp,
 }
 
 // The thread-serial step (no warp cooperation).
-template <int A, bool CHECK = false, bool FOLD = true, bool RET = true>
+template <int A, bool CHECK = false, int FOLD = kFoldAll, bool RET = true>
 __device__ __forceinline__ int step_serial(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   Pend p;
   return step_begin<A, CHECK, FOLD, RET>(g, sp, W, next, p, Coop{0x7fffffff, 0x7fffffff});
@@ -692,7 +699,7 @@ __device__ __forceinline__ int sampler_step_apply(const DevGraph& g, const WalkS
   return o.r;
 }
 
-template <int A, bool CHECK = false, bool FOLD = true>
+template <int A, bool CHECK = false, int FOLD = kFoldAll>
 __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next) {
   if constexpr (A != MIXED) {
     return step_serial<A, CHECK, FOLD>(g, sp, W, next);
@@ -713,17 +720,17 @@ __device__ __forceinline__ int step_dispatch(const DevGraph& g, const WalkSpec& 
 }
 
 // step_begin for a compile-time or per-request algorithm.
-template <int A, bool CHECK = false>
+template <int A, bool CHECK = false, int FOLD = kFoldAll>
 __device__ __forceinline__ int step_begin_dispatch(const DevGraph& g, const WalkSpec& sp, Walker& W, int32_t& next,
                                                    Pend& p, Coop coop) {
   if constexpr (A != MIXED) {
-    return step_begin<A, CHECK>(g, sp, W, next, p, coop);
+    return step_begin<A, CHECK, FOLD>(g, sp, W, next, p, coop);
   } else {
     switch (sp.algo) {
       case DEEPWALK: return step_begin<DEEPWALK, CHECK>(g, sp, W, next, p, coop);
       case DEEPWALK_WEIGHTED: return step_begin<DEEPWALK_WEIGHTED, CHECK>(g, sp, W, next, p, coop);
       case PPR: return step_begin<PPR, CHECK>(g, sp, W, next, p, coop);
-      case NODE2VEC: return step_begin<NODE2VEC, CHECK, true, false>(g, sp, W, next, p, coop);
+      case NODE2VEC: return step_begin<NODE2VEC, CHECK, kFoldAll, false>(g, sp, W, next, p, coop);
       case METAPATH: return step_begin<METAPATH, CHECK>(g, sp, W, next, p, coop);
       case DW_ITS:
       case DW_REJ:
