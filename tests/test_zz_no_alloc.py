@@ -9,9 +9,10 @@ library's fixed scratch array, its paths and lengths against the oracle and
 against trw_walk_batch, bit for bit (the tolerance of every walk test here);
 that a call leaves the device's free memory unchanged and still succeeds when
 every allocation the library makes is forced to fail; and the NULL stream.
-Collected last but one (the full-size file is slower) so that a failure here
-leaves every other test already run."""
+Collected last, so that a run that stops at a failure here has already run
+every other test."""
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -72,6 +73,7 @@ def _call_noalloc(G, reqs, stream="torch"):
         seeds[i] = r["seed"]
         outs[i], outl[i] = op.data_ptr(), ol.data_ptr()
         results.append((op, ol))
+    gc.collect()  # graphs left by earlier tests are freed now, not between the two readings
     torch.cuda.synchronize()
     st_arg = (torch.cuda.current_stream().cuda_stream or 1) if stream == "torch" else None
     free0 = torch.cuda.mem_get_info()[0]
