@@ -226,6 +226,7 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
   for (;;) {
     int go = 1;
     unsigned long long P = 0;
+    int fresh = 0;
     if (lane == 0) {
       // the larger of the two counts; the device count is raised to the host's
       // (atomically: a copy-engine store may land at the same time) before any
@@ -236,8 +237,11 @@ __device__ void dispatcher(const ServeDev& sv, ActiveSet* act) {
         atomicMax(&st->published, H);
         P = H;
       }
-      if (P > disp_next) fence_acquire_sys();  // the new requests' records (host memory) after their count
+      fresh = P > disp_next ? 1 : 0;
     }
+    // every lane that reads the new requests' records (host memory) does so
+    // after their count
+    if (__shfl_sync(0xffffffffu, fresh, 0)) fence_acquire_sys();
     // Admission, one request at a time.  A small request with device sources
     // has its sources range-checked here by the whole warp; one out of range
     // completes the request with the invalid-argument status, and no walk runs.
